@@ -1,0 +1,227 @@
+/*
+ * egfem.h -- C ABI of the GB300 (sm_103a) EGFEM Newton hot path.
+ *
+ * The library implements the online phase of the extended group finite element
+ * method (Tolle & Marheineke, arXiv 2005.06193) for the model problem
+ *
+ *     -div((kappa + w) grad u) + gamma c = d   in Omega,      u = u_D on Gamma,
+ *     w = a_scale * g_a(Pi_a u)  in W_a (P1, P2 or P3),   c = c_scale * g_c(Pi_c u) in W_c,
+ *
+ * which is Sec. 2.1 eq. (1) with b(u) = u, the coefficient a = kappa + w and the
+ * reaction gamma c, on a conforming triangle (2D) or tetrahedron (3D) mesh with P1
+ * trial functions (Sec. 5: "linear finite elements in all of the examples").
+ *
+ * Every Newton step runs, on the GPU:
+ *   - the pointwise nonlinearity w = g(Pi u) at the W nodes (Sec. 3.1 eq. (5), Sec. 3.2);
+ *   - the trilinear tensor action r_i = sum_{m,k} T_imk (kappa + w)_m u_k + gamma (M^c c)_i - d_i
+ *     with T_imk = int eta_m grad phi_k . grad phi_i (Sec. 3.3 eq. (7), Example 4.1);
+ *   - the Jacobian of Sec. 4 with its identity blocks eliminated,
+ *     J = (T ._2 a) + (T ._3 u) diag(g_a') Pi_a + gamma M^c diag(g_c') Pi_c,
+ *     written into a fixed CSR pattern (the P1 adjacency of the mesh);
+ *   - a Jacobi-preconditioned BiCGStab solve of J delta = r and the update u <- u - delta.
+ *
+ * Conventions shared by all calls
+ *   - Device pointers (prefix d_) are caller-owned CUDA device memory on the device that
+ *     was current at egfem_build; host pointers are only read during the call.
+ *   - Vectors are contiguous float64 in node order of the mesh (P1) or of the W space.
+ *   - Dirichlet rows: r_i = u_i - d_i, J row i = e_i, and the Dirichlet columns of free
+ *     rows are zero (Sec. 2.1: the first N_D basis functions carry the boundary data).
+ *     The load vector d therefore carries the Dirichlet values u_D on Dirichlet rows.
+ *   - Every call is asynchronous on the given stream unless stated otherwise; calls that
+ *     return convergence information synchronise that stream.
+ *   - Errors are returned, never raised: no call aborts the process.  A status of
+ *     EGFEM_ERR_CUDA means a CUDA runtime call failed; egfem_last_error() describes it.
+ */
+#ifndef EGFEM_H
+#define EGFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct egfem_t *egfem_handle;
+typedef struct CUstream_st *egfem_stream;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    EGFEM_OK = 0,
+    EGFEM_ERR_INVALID_ARG = 1,   /* a pointer, size or option is out of range            */
+    EGFEM_ERR_MESH = 2,          /* malformed mesh: bad index, degenerate cell, ...      */
+    EGFEM_ERR_CUDA = 3,          /* a CUDA runtime call failed                            */
+    EGFEM_ERR_OOM = 4,           /* device or host allocation failed                      */
+    EGFEM_ERR_NOT_CONVERGED = 5, /* Newton or Krylov iteration cap reached                */
+    EGFEM_ERR_BREAKDOWN = 6,     /* BiCGStab breakdown (rho = 0 or omega = 0)             */
+    EGFEM_ERR_SINGULAR = 7,      /* zero Jacobi diagonal                                   */
+    EGFEM_ERR_NONFINITE = 8,     /* NaN or Inf in a residual norm                          */
+    EGFEM_ERR_TIMEOUT = 9,       /* a bounded device-side wait ran out                    */
+    EGFEM_ERR_UNSUPPORTED = 10   /* a valid request this build does not implement         */
+} egfem_status;
+
+/* Nonlinearities are a closed set: a host function pointer cannot run on the device. */
+typedef enum {
+    EGFEM_G_NONE = 0,  /* no nonlinear term                        */
+    EGFEM_G_POW = 1,   /* g(s) = s^p  (p a positive integer <= 8)  */
+    EGFEM_G_EXP = 2    /* g(s) = e^s                               */
+} egfem_g_kind;
+
+typedef enum {
+    EGFEM_PREC_FP64 = 0,   /* every operator value, vector and reduction in FP64          */
+    EGFEM_PREC_MIXED = 1   /* FP32 Jacobian values and Krylov vectors (FP64 dot sums);
+                              FP64 residual, norm, Newton update (iterative refinement) */
+} egfem_precision;
+
+typedef enum {
+    EGFEM_OP_CSF = 0,          /* T stored as row-segmented compressed sparse fibres        */
+    EGFEM_OP_MATRIX_FREE = 1   /* element-local evaluation: T_imk = sum_K iota^K_m S^K_ik   */
+} egfem_operator;
+
+/* Mesh (host arrays, copied by egfem_build). Sec. 2.1: conforming simplicial partition. */
+typedef struct {
+    int32_t dim;                /* 2: triangles, 3: tetrahedra                            */
+    int64_t n_nodes;            /* number of P1 nodes (vertices)                          */
+    int64_t n_cells;            /* number of cells                                        */
+    const double *coords;       /* [n_nodes * dim], node coordinates                      */
+    const int32_t *cells;       /* [n_cells * (dim + 1)], vertex indices of each cell    */
+    const uint8_t *dirichlet;   /* [n_nodes], nonzero marks a Dirichlet node             */
+} egfem_mesh;
+
+/* Problem: -div((kappa + a_scale g_a(Pi_a u)) grad u) + gamma c_scale g_c(Pi_c u) = d.   */
+typedef struct {
+    int32_t a_kind;      /* egfem_g_kind of the coefficient nonlinearity            */
+    double a_p;          /* exponent for EGFEM_G_POW                                 */
+    double a_scale;
+    int32_t a_degree;    /* Lagrange degree of W_a: 1 (GFEM), 2 or 3                 */
+    int32_t c_kind;      /* egfem_g_kind of the reaction nonlinearity               */
+    double c_p;
+    double c_scale;
+    int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM), 2 or 3                 */
+    double gamma;        /* reaction coefficient                                     */
+    double kappa;        /* constant part of the coefficient                         */
+} egfem_problem;
+
+typedef struct {
+    double newton_rtol;      /* stop when ||r||_2 <= newton_rtol * ||r(u0)||_2 (default 1e-10) */
+    double newton_atol;      /* ... or ||r||_2 <= newton_atol (default 0)                     */
+    int32_t newton_maxit;    /* Newton step cap (default 50)                                  */
+    double eta_max;          /* largest Krylov forcing term (default 1e-2)                    */
+    double eta_min;          /* smallest Krylov forcing term (default 1e-12; mixed: 1e-6)     */
+    int32_t krylov_maxit;    /* BiCGStab iteration cap per Newton step (default 100000)       */
+    int32_t precision;       /* egfem_precision (default EGFEM_PREC_FP64)                    */
+    int32_t op;              /* egfem_operator  (default EGFEM_OP_CSF)                       */
+    int32_t graph_chunk;     /* BiCGStab iterations per captured CUDA graph (default 32)     */
+    int32_t fixed_eta;       /* nonzero: use eta_max for every step (no Eisenstat-Walker)    */
+} egfem_options;
+
+#define EGFEM_HIST 64
+typedef struct {
+    int32_t status;                    /* egfem_status of the solve                      */
+    int32_t newton_iters;              /* Newton steps taken                             */
+    int64_t krylov_iters;              /* BiCGStab iterations summed over all steps      */
+    double res0;                       /* ||r(u0)||_2 over free rows (FP64)              */
+    double res_final;                  /* final ||r||_2 (FP64)                           */
+    double res_hist[EGFEM_HIST];       /* ||r||_2 after each Newton step (FP64)          */
+    int32_t krylov_hist[EGFEM_HIST];   /* BiCGStab iterations of each Newton step        */
+    double solve_ms;                   /* wall time of the solve (host clock)            */
+} egfem_stats;
+
+/* Fill *opts with the defaults listed above. */
+void egfem_default_options(egfem_options *opts);
+
+/* Offline phase (Sec. 5: "computed ... in an offline phase"): number the W spaces,
+ * integrate the element quantities, assemble T (and M^c) in the layout selected by
+ * opts->op, build the Jacobian pattern, and upload everything to the current device.
+ * mesh, prob and opts are host structs read during the call; *out receives a handle
+ * that owns all device memory it allocates (free with egfem_destroy).
+ * Errors: INVALID_ARG (null pointer, unsupported degree/dim), MESH (index out of
+ * range, zero-volume cell), OOM, CUDA. */
+egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts,
+                         egfem_handle *out);
+
+/* Release every device and host allocation of h (NULL is accepted). */
+void egfem_destroy(egfem_handle h);
+
+/* Replace the solver options of h (precision and op must equal those given at build). */
+egfem_status egfem_set_options(egfem_handle h, const egfem_options *opts);
+
+/* Sizes: P1 nodes, W_a nodes, W_c nodes, rows and nonzeros of the Jacobian pattern. */
+egfem_status egfem_sizes(egfem_handle h, int64_t *n_nodes, int64_t *n_wa, int64_t *n_wc,
+                         int64_t *jac_rows, int64_t *jac_nnz);
+
+/* Host copy of the W-space node coordinates ([n * dim]); which = 0: W_a, 1: W_c. */
+egfem_status egfem_w_coords(egfem_handle h, int32_t which, double *coords_host);
+
+/* Device pointers to the fixed Jacobian CSR pattern (owned by h; int32, sorted columns
+ * per row, Dirichlet rows hold only their diagonal). */
+egfem_status egfem_jacobian_pattern(egfem_handle h, const int32_t **d_rowptr, const int32_t **d_cols);
+
+/* Optional spatially varying kappa on W_a (Sec. 3.3 coefficient field): d_kappa holds
+ * n_wa values (copied); NULL restores the constant prob->kappa. */
+egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream stream);
+
+/* Pointwise nonlinearity (Sec. 3.2, f = g(Pi u)): d_w[m] = a_scale g_a((Pi_a u)_m) and
+ * d_wprime[m] = its derivative, for all n_wa nodes. Either output may be NULL. */
+egfem_status egfem_pointwise(egfem_handle h, const double *d_u, double *d_w, double *d_wprime,
+                             egfem_stream stream);
+
+/* Residual (Sec. 4 EGFEM root, u-block): d_r[n_nodes] from d_u[n_nodes] and load d_d[n_nodes].
+ * Always FP64, evaluated as sum_{m,k} T_imk a_m (u_k - u_i) (equal to the plain form
+ * because sum_k T_imk = 0). */
+egfem_status egfem_residual(egfem_handle h, const double *d_u, const double *d_d, double *d_r,
+                            egfem_stream stream);
+
+/* Jacobian values (Sec. 4, identity blocks eliminated) into the CSR pattern: d_vals[jac_nnz], FP64. */
+egfem_status egfem_jacobian(egfem_handle h, const double *d_u, double *d_vals, egfem_stream stream);
+
+/* y = J x with J given by CSR values d_vals in the handle's pattern (FP64). */
+egfem_status egfem_spmv(egfem_handle h, const double *d_vals, const double *d_x, double *d_y, egfem_stream stream);
+
+/* Jacobi-preconditioned BiCGStab (van der Vorst 1992) on J x = rhs, J from CSR values
+ * d_vals; x in: initial guess, out: solution.  Stops at ||rhs - J x|| <= rtol ||rhs||.
+ * Synchronises the stream.  *iters receives the iteration count. */
+egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *d_rhs, double *d_x,
+                            double rtol, int32_t maxit, int32_t *iters, egfem_stream stream);
+
+/* Newton's method (Sec. 4): d_u in: u0 (must satisfy the Dirichlet data), out: solution.
+ * Synchronises the stream.  stats may be NULL. */
+egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats,
+                                egfem_stream stream);
+
+/* Adjoint of a functional j(u*) of the converged solution (implicit function theorem;
+ * motivated by the repeated forward/backward solves of optimal control, Sec. 6):
+ *   J(u*)^T lambda = dj/du  on free rows, lambda = 0 on Dirichlet rows;
+ *   dj/dd_i = lambda_i (free rows);  dj/dkappa_m = -sum_{i,k} lambda_i T_imk u_k.
+ * d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa] out (may be NULL).
+ * Synchronises the stream. */
+egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda,
+                           double *d_grad_kappa, egfem_stats *stats, egfem_stream stream);
+
+/* Load vector of a cellwise constant source: d_i = sum_{K owns i} f_K |K| / (dim + 1)
+ * (exact integral of f phi_i), Dirichlet rows set to 0.  d_f[n_cells] in, d_d[n_nodes] out. */
+egfem_status egfem_load_cellwise(egfem_handle h, const double *d_f, double *d_d, egfem_stream stream);
+
+/* Transpose of egfem_load_cellwise: d_g[K] = |K|/(dim+1) sum_{i in K, i free} d_lam[i]. */
+egfem_status egfem_load_cellwise_transpose(egfem_handle h, const double *d_lam, double *d_g, egfem_stream stream);
+
+/* Host-only inspection of the offline assembly (no device work, no CUDA call): runs the
+ * same W-space numbering and tensor assembly as egfem_build and returns the stored
+ * trilinear form as COO triplets (i, m, k, T_imk), including the per-fibre diagonal
+ * T_imi.  Call with I == NULL to get the count in *count; then with arrays of that size.
+ * m indexes the W_a space (or is -1 for the constant-coefficient stiffness when
+ * prob->a_kind == EGFEM_G_NONE).  Used to check the assembly against an independent
+ * quadrature on machines without a GPU.  *n_wa (optional) receives the W_a size and
+ * wa_coords (optional, [n_wa * dim]) the W_a node coordinates. */
+egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem_problem *prob, int64_t *count,
+                                  int64_t *I, int64_t *M, int64_t *K, double *V, int64_t *n_wa, double *wa_coords);
+
+/* Human-readable name of a status code (static storage). */
+const char *egfem_status_string(egfem_status s);
+
+/* Description of the last CUDA or validation error seen by this thread (static storage). */
+const char *egfem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EGFEM_H */

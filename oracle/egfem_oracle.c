@@ -11,12 +11,12 @@
  *   model problem  -div((kappa + a_nl(u)) grad u) + gamma c_nl(u) = d,  u = u_D on the boundary
  *   (Sec. 2.1 eq. (1) with b(u) = u, a = kappa + w, c = gamma * c_nl; Dirichlet only).
  *
- *   SGA   (Sec. 2.1 eq. (4)/(5), Sec. 4 SGA root and Newton):
+ *   SGA   (Sec. 2.1 eqs. (3), (4); Sec. 4 SGA root (8) and Newton):
  *         r_i  = sum_K int_K (kappa + g_a(u_h)) grad u_h . grad phi_i + gamma g_c(u_h) phi_i  - d_i
  *         J_il = sum_K int_K (kappa + g_a(u_h)) grad phi_l . grad phi_i
  *                          + g_a'(u_h) phi_l grad u_h . grad phi_i + gamma g_c'(u_h) phi_l phi_i
  *         re-integrated by quadrature at every call.
- *   EGFEM (Sec. 3.1 eq. (6), Sec. 3.2 interpolation operators, Sec. 3.3 eq. (7),
+ *   EGFEM (Sec. 3.1 eq. (5), Sec. 3.2 interpolation operators, Sec. 3.3 eq. (7),
  *          Sec. 4 EGFEM root (9) and its Newton Jacobian):
  *         a = kappa + g_a(Pi_a u),  c = g_c(Pi_c u)   (pointwise, at the W-space nodes)
  *         r_i  = sum_{m,k} T_imk a_m u_k + gamma sum_m M_im c_m - d_i

@@ -1,0 +1,8 @@
+"""GB300-native (sm_103a) EGFEM Newton hot path.
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in include/egfem.h);
+``egfem`` is its thin ctypes binding and ``autograd`` wraps the adjoint in a
+``torch.autograd.Function``.
+"""
+from .egfem import (G_EXP, G_NONE, G_POW, OP_CSF, OP_MATRIX_FREE, PREC_FP64, PREC_MIXED, EgfemError, Handle,  # noqa: F401
+                    default_options, inspect_tensor, lib, make_problem)

@@ -1,0 +1,759 @@
+// egfem_api.cu -- the C ABI of include/egfem.h: build/upload, the hot-path entry
+// points, the Newton driver with captured BiCGStab chunks, and the adjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "egfem_internal.h"
+#include "egfem_kernels.cuh"
+#include "egfem_krylov.cuh"
+
+using namespace egfem;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+#define EG_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+            return e_ == cudaErrorMemoryAllocation ? EGFEM_ERR_OOM : EGFEM_ERR_CUDA;                   \
+        }                                                                                              \
+    } while (0)
+
+#define EG_TRY(expr)                                   \
+    do {                                               \
+        egfem_status s_ = (expr);                      \
+        if (s_ != EGFEM_OK) return s_;                 \
+    } while (0)
+
+template <typename T>
+egfem_status dalloc(T *&p, size_t n) {
+    p = nullptr;
+    if (n == 0) return EGFEM_OK;
+    EG_CUDA(cudaMalloc((void **)&p, n * sizeof(T)));
+    return EGFEM_OK;
+}
+
+template <typename T>
+egfem_status upload(T *&p, const std::vector<T> &v) {
+    EG_TRY(dalloc(p, v.size()));
+    if (!v.empty()) EG_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return EGFEM_OK;
+}
+
+template <typename V>
+struct KWork {
+    V *A = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    bool ready = false;
+};
+
+}  // namespace
+
+struct egfem_t {
+    int device = 0;
+    int sms = 148;
+    egfem_problem prob{};
+    egfem_options opts{};
+    egfem_mesh mesh_sizes{};
+    int32_t dim = 2;
+    int64_t n = 0, nwa = 0, nwc = 0, ncells = 0;
+    DeviceCSF csf;
+    std::vector<double> wa_coords, wc_coords;
+    uint8_t *wa_kind = nullptr;
+    int32_t *wa_sup = nullptr;
+    int32_t *cell_verts = nullptr;
+    double *cell_vol = nullptr;
+    int64_t *v2c_ptr = nullptr;
+    int32_t *v2c = nullptr;
+    int64_t *tmap = nullptr;            // SELL position of the transposed entry
+    Nonlin nl{};
+    double *kappa_field = nullptr;
+    // Newton workspace
+    double *r = nullptr, *jsell = nullptr, *dinv = nullptr;
+    double *part = nullptr;
+    KState *st = nullptr;
+    KState *h_st = nullptr;             // pinned
+    double *scal = nullptr;             // device scalars (norms)
+    double *h_scal = nullptr;           // pinned
+    uint32_t *ticket = nullptr;
+    int32_t *status = nullptr;
+    KWork<double> k64;
+    KWork<float> k32;
+    int kgrid = 1;
+    cudaStream_t hs = nullptr;          // internal stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int maxc_tpl = 8;
+};
+
+namespace {
+
+int pick_maxc(int maxc) {
+    if (maxc <= 8) return 8;
+    if (maxc <= 16) return 16;
+    if (maxc <= 32) return 32;
+    return 64;
+}
+
+void launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
+    const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
+    switch (h->maxc_tpl) {
+        case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(A); break;
+        case 16: csf_fused_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(A); break;
+        case 32: csf_fused_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(A); break;
+        default: csf_fused_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(A); break;
+    }
+}
+
+CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
+    CsfArgs A{};
+    A.n_rows = h->n;
+    A.meta = h->csf.meta;
+    A.col_idx = h->csf.col_idx; A.col_slot = h->csf.col_slot;
+    A.leaf_val = h->csf.leaf_val; A.leaf_col = h->csf.leaf_col;
+    A.fib_info = h->csf.fib_info; A.fib_tdiag = h->csf.fib_tdiag; A.fib_m = h->csf.fib_m;
+    A.rx_val = h->csf.rx_val; A.rx_info = h->csf.rx_info;
+    A.dir = h->csf.dir;
+    A.nl = h->nl;
+    A.u = u; A.d = d;
+    A.status = h->status;
+    return A;
+}
+
+template <typename V>
+KVecs<V> kvecs(egfem_t *h, KWork<V> &W) {
+    KVecs<V> K{};
+    K.n = h->n; K.meta = h->csf.meta; K.col_idx = h->csf.col_idx; K.A = W.A;
+    K.x = W.x; K.r = W.r; K.rh = W.rh; K.p = W.p; K.v = W.v; K.s = W.s; K.t = W.t; K.b = W.b;
+    K.st = h->st; K.part = h->part;
+    return K;
+}
+
+template <typename V>
+egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
+    if (W.ready) return EGFEM_OK;
+    EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
+    EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V)));
+    V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t};
+    for (V **q : vec) { EG_TRY(dalloc(*q, size_t(h->n))); EG_CUDA(cudaMemset(*q, 0, size_t(h->n) * sizeof(V))); }
+    W.ready = true;
+    return EGFEM_OK;
+}
+
+template <typename V>
+void enqueue_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
+    KVecs<V> K = kvecs(h, W);
+    for (int it = 0; it < count; ++it) {
+        kry_v<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+        kry_s<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+        kry_t<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+        kry_x<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+        kry_p<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+    }
+}
+
+template <typename V>
+egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
+    const int chunk = std::max(1, h->opts.graph_chunk);
+    if (W.graph && W.graph_chunk == chunk) return EGFEM_OK;
+    if (W.graph) { cudaGraphExecDestroy(W.graph); W.graph = nullptr; }
+    cudaGraph_t g;
+    EG_CUDA(cudaStreamBeginCapture(h->hs, cudaStreamCaptureModeThreadLocal));
+    enqueue_iterations(h, W, chunk, h->hs);
+    EG_CUDA(cudaStreamEndCapture(h->hs, &g));
+    cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { g_last_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e); return EGFEM_ERR_CUDA; }
+    W.graph_chunk = chunk;
+    return EGFEM_OK;
+}
+
+// Run BiCGStab on W.A x = W.b (already filled) on the internal stream; returns the
+// device-state outcome in *done and the iteration count in *iters.
+template <typename V>
+egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t *done, int32_t *iters) {
+    EG_TRY(ensure_graph(h, W));
+    KVecs<V> K = kvecs(h, W);
+    kry_setup<V><<<h->kgrid, KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit);
+    EG_CUDA(cudaGetLastError());
+    for (;;) {
+        EG_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        EG_CUDA(cudaStreamSynchronize(h->hs));
+        if (h->h_st->done != K_RUNNING) break;
+        EG_CUDA(cudaGraphLaunch(W.graph, h->hs));
+    }
+    *done = h->h_st->done;
+    *iters = h->h_st->iter;
+    return EGFEM_OK;
+}
+
+egfem_status join_in(egfem_t *h, cudaStream_t user) {
+    EG_CUDA(cudaEventRecord(h->ev_in, user));
+    EG_CUDA(cudaStreamWaitEvent(h->hs, h->ev_in, 0));
+    return EGFEM_OK;
+}
+
+egfem_status join_out(egfem_t *h, cudaStream_t user) {
+    EG_CUDA(cudaEventRecord(h->ev_out, h->hs));
+    EG_CUDA(cudaStreamWaitEvent(user, h->ev_out, 0));
+    return EGFEM_OK;
+}
+
+egfem_status norm2_free(egfem_t *h, const double *r, double *out_host) {
+    norm2_free_kernel<<<h->kgrid, KRY_BLOCK, 0, h->hs>>>(h->n, r, h->csf.dir, h->part, h->ticket, h->scal);
+    EG_CUDA(cudaGetLastError());
+    EG_CUDA(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->hs));
+    EG_CUDA(cudaStreamSynchronize(h->hs));
+    *out_host = h->h_scal[0];
+    return EGFEM_OK;
+}
+
+egfem_status check_status_word(egfem_t *h) {
+    int32_t s = 0;
+    EG_CUDA(cudaMemcpyAsync(&s, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs));
+    EG_CUDA(cudaStreamSynchronize(h->hs));
+    if (s & 1) { g_last_error = "zero diagonal in the Jacobian"; return EGFEM_ERR_SINGULAR; }
+    return EGFEM_OK;
+}
+
+template <typename T>
+void dfree(T *&p) { if (p) cudaFree((void *)p); p = nullptr; }
+
+egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
+    if (!mesh || !prob || !out) { g_last_error = "null argument"; return EGFEM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    std::string err;
+    egfem_status st = validate_mesh(*mesh, err);
+    if (st != EGFEM_OK) { g_last_error = err; return st; }
+    auto check_g = [&](int32_t kind, double p, int32_t deg, const char *what) -> egfem_status {
+        if (kind < EGFEM_G_NONE || kind > EGFEM_G_EXP) { g_last_error = std::string(what) + ": unknown kind"; return EGFEM_ERR_INVALID_ARG; }
+        if (kind == EGFEM_G_POW && (p < 1 || p > 8 || p != std::floor(p))) { g_last_error = std::string(what) + ": exponent must be an integer in 1..8"; return EGFEM_ERR_INVALID_ARG; }
+        if (kind != EGFEM_G_NONE && (deg < 1 || deg > 3)) { g_last_error = std::string(what) + ": degree must be 1, 2 or 3"; return EGFEM_ERR_INVALID_ARG; }
+        return EGFEM_OK;
+    };
+    EG_TRY(check_g(prob->a_kind, prob->a_p, prob->a_degree, "a"));
+    EG_TRY(check_g(prob->c_kind, prob->c_p, prob->c_degree, "c"));
+    if (prob->c_kind != EGFEM_G_NONE && prob->c_degree != 1) { g_last_error = "reaction space W_c must be P1"; return EGFEM_ERR_UNSUPPORTED; }
+    std::unique_ptr<egfem_t> h(new egfem_t());
+    egfem_default_options(&h->opts);
+    if (opts) h->opts = *opts;
+    if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
+    if (h->opts.op != EGFEM_OP_CSF) { g_last_error = "operator variant not available in this entry point"; return EGFEM_ERR_UNSUPPORTED; }
+    h->prob = *prob;
+    h->dim = mesh->dim; h->n = mesh->n_nodes; h->ncells = mesh->n_cells;
+    EG_CUDA(cudaGetDevice(&h->device));
+    EG_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+    // W spaces
+    HostWSpace Wa, Wc;
+    std::vector<int32_t> c2wa, c2wc;
+    int nla = 0, nlc = 0;
+    st = build_wspace(*mesh, prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1, Wa, c2wa, nla, err);
+    if (st != EGFEM_OK) { g_last_error = err; return st; }
+    st = build_wspace(*mesh, prob->c_kind != EGFEM_G_NONE ? prob->c_degree : 1, Wc, c2wc, nlc, err);
+    if (st != EGFEM_OK) { g_last_error = err; return st; }
+    h->nwa = Wa.n; h->nwc = Wc.n;
+    h->wa_coords = Wa.coords; h->wc_coords = Wc.coords;
+    HostCSF H;
+    st = build_csf(*mesh, *prob, Wa, c2wa, nla, Wc, c2wc, nlc, H, err);
+    if (st != EGFEM_OK) { g_last_error = err; return st; }
+    h->maxc_tpl = pick_maxc(H.max_cols);
+    // transpose map: SELL position of (k, i) for every (i, local column c -> k)
+    std::vector<int64_t> tmap(H.col_idx.size(), -1);
+    {
+        const int64_t n = H.n_rows;
+        for (int32_t s = 0; s < H.n_slices; ++s) {
+            const SliceMeta &M = H.meta[s];
+            for (int c = 0; c < M.ncol; ++c)
+                for (int r = 0; r < SLICE; ++r) {
+                    const int64_t i = int64_t(s) * SLICE + r;
+                    if (i >= n) continue;
+                    const int64_t q = M.col_base + int64_t(c) * SLICE + r;
+                    const int32_t k = H.col_idx[q];
+                    if (H.col_slot[q] < 0 && c != 0) continue;
+                    const SliceMeta &Mk = H.meta[k / SLICE];
+                    const int rk = k % SLICE;
+                    for (int ck = 0; ck < Mk.ncol; ++ck) {
+                        const int64_t qk = Mk.col_base + int64_t(ck) * SLICE + rk;
+                        if (H.col_idx[qk] == i) { tmap[q] = qk; break; }
+                    }
+                }
+        }
+    }
+    DeviceCSF &D = h->csf;
+    D.n_rows = H.n_rows; D.n_slices = H.n_slices; D.max_cols = H.max_cols;
+    D.n_colentries = int64_t(H.col_idx.size()); D.n_leaves = int64_t(H.leaf_val.size());
+    D.n_fibres = int64_t(H.fib_info.size()); D.n_rx = int64_t(H.rx_val.size()); D.nnz = H.rowptr.back();
+    EG_TRY(upload(D.meta, H.meta));
+    EG_TRY(upload(D.col_idx, H.col_idx)); EG_TRY(upload(D.col_slot, H.col_slot));
+    EG_TRY(upload(D.leaf_val, H.leaf_val)); EG_TRY(upload(D.leaf_col, H.leaf_col));
+    EG_TRY(upload(D.fib_info, H.fib_info)); EG_TRY(upload(D.fib_tdiag, H.fib_tdiag)); EG_TRY(upload(D.fib_m, H.fib_m));
+    EG_TRY(upload(D.rx_val, H.rx_val)); EG_TRY(upload(D.rx_info, H.rx_info)); EG_TRY(upload(D.rx_m, H.rx_m));
+    EG_TRY(upload(D.dir, H.dir)); EG_TRY(upload(D.rowptr, H.rowptr)); EG_TRY(upload(D.cols, H.cols));
+    EG_TRY(upload(h->tmap, tmap));
+    EG_TRY(upload(h->wa_kind, Wa.kind)); EG_TRY(upload(h->wa_sup, Wa.sup));
+    // cells and vertex -> cell incidence for the load vector
+    {
+        const int nv = mesh->dim + 1;
+        std::vector<int32_t> cv(mesh->cells, mesh->cells + mesh->n_cells * nv);
+        std::vector<double> vol(mesh->n_cells);
+        for (int64_t c = 0; c < mesh->n_cells; ++c) {
+            double B[9];
+            for (int k = 0; k < mesh->dim; ++k)
+                for (int r = 0; r < mesh->dim; ++r)
+                    B[r * mesh->dim + k] = mesh->coords[int64_t(cv[c * nv + k + 1]) * mesh->dim + r] - mesh->coords[int64_t(cv[c * nv]) * mesh->dim + r];
+            const double det = mesh->dim == 2 ? B[0] * B[3] - B[1] * B[2]
+                : B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) + B[2] * (B[3] * B[7] - B[4] * B[6]);
+            vol[c] = std::fabs(det) / (mesh->dim == 2 ? 2.0 : 6.0);
+        }
+        std::vector<int64_t> ptr(mesh->n_nodes + 1, 0);
+        for (int64_t c = 0; c < mesh->n_cells; ++c) for (int a = 0; a < nv; ++a) ptr[cv[c * nv + a] + 1]++;
+        for (int64_t v = 0; v < mesh->n_nodes; ++v) ptr[v + 1] += ptr[v];
+        std::vector<int32_t> lst(ptr.back());
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t c = 0; c < mesh->n_cells; ++c) for (int a = 0; a < nv; ++a) lst[fill[cv[c * nv + a]]++] = int32_t(c);
+        EG_TRY(upload(h->cell_verts, cv)); EG_TRY(upload(h->cell_vol, vol));
+        EG_TRY(upload(h->v2c_ptr, ptr)); EG_TRY(upload(h->v2c, lst));
+    }
+    h->nl.a_kind = prob->a_kind; h->nl.a_pi = int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
+    h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
+    h->nl.gamma = prob->gamma; h->nl.kappa = prob->kappa; h->nl.kappa_field = nullptr;
+    // workspace
+    h->kgrid = int(std::max<int64_t>(1, std::min<int64_t>((h->n + KRY_BLOCK - 1) / KRY_BLOCK, int64_t(h->sms) * 8)));
+    EG_TRY(dalloc(h->r, size_t(h->n)));
+    EG_TRY(dalloc(h->part, size_t(4 * h->kgrid)));
+    EG_TRY(dalloc(h->scal, 8));
+    EG_TRY(dalloc(h->ticket, 1)); EG_CUDA(cudaMemset(h->ticket, 0, sizeof(uint32_t)));
+    EG_TRY(dalloc(h->status, 1)); EG_CUDA(cudaMemset(h->status, 0, sizeof(int32_t)));
+    EG_TRY(dalloc(h->st, 1)); EG_CUDA(cudaMemset(h->st, 0, sizeof(KState)));
+    EG_CUDA(cudaMallocHost((void **)&h->h_st, sizeof(KState)));
+    EG_CUDA(cudaMallocHost((void **)&h->h_scal, 8 * sizeof(double)));
+    EG_CUDA(cudaStreamCreateWithFlags(&h->hs, cudaStreamNonBlocking));
+    EG_CUDA(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    EG_CUDA(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    if (h->opts.precision == EGFEM_PREC_MIXED) EG_TRY(kwork_alloc(h.get(), h->k32));
+    else EG_TRY(kwork_alloc(h.get(), h->k64));
+    EG_CUDA(cudaDeviceSynchronize());
+    *out = h.release();
+    return EGFEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void egfem_default_options(egfem_options *o) {
+    if (!o) return;
+    o->newton_rtol = 1e-10;
+    o->newton_atol = 0.0;
+    o->newton_maxit = 50;
+    o->eta_max = 1e-2;
+    o->eta_min = 1e-12;
+    o->krylov_maxit = 100000;
+    o->precision = EGFEM_PREC_FP64;
+    o->op = EGFEM_OP_CSF;
+    o->graph_chunk = 32;
+    o->fixed_eta = 0;
+}
+
+egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
+    try {
+        return build_impl(mesh, prob, opts, out);
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return EGFEM_ERR_OOM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return EGFEM_ERR_INVALID_ARG;
+    }
+}
+
+void egfem_destroy(egfem_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->hs) cudaStreamSynchronize(h->hs);
+    DeviceCSF &D = h->csf;
+    dfree(D.meta); dfree(D.col_idx); dfree(D.col_slot); dfree(D.leaf_val); dfree(D.leaf_col);
+    dfree(D.fib_info); dfree(D.fib_tdiag); dfree(D.fib_m); dfree(D.rx_val); dfree(D.rx_info); dfree(D.rx_m);
+    dfree(D.dir); dfree(D.rowptr); dfree(D.cols);
+    dfree(h->tmap); dfree(h->wa_kind); dfree(h->wa_sup); dfree(h->cell_verts); dfree(h->cell_vol);
+    dfree(h->v2c_ptr); dfree(h->v2c); dfree(h->kappa_field);
+    dfree(h->r); dfree(h->jsell); dfree(h->dinv); dfree(h->part); dfree(h->scal); dfree(h->ticket); dfree(h->status); dfree(h->st);
+    for (KWork<double> *W : {&h->k64}) {
+        if (W->graph) cudaGraphExecDestroy(W->graph);
+        dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
+    }
+    for (KWork<float> *W : {&h->k32}) {
+        if (W->graph) cudaGraphExecDestroy(W->graph);
+        dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
+    }
+    if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->hs) cudaStreamDestroy(h->hs);
+    delete h;
+}
+
+egfem_status egfem_set_options(egfem_handle h, const egfem_options *opts) {
+    if (!h || !opts) return EGFEM_ERR_INVALID_ARG;
+    if (opts->precision != h->opts.precision || opts->op != h->opts.op) {
+        g_last_error = "precision and operator are fixed at build";
+        return EGFEM_ERR_INVALID_ARG;
+    }
+    h->opts = *opts;
+    return EGFEM_OK;
+}
+
+egfem_status egfem_sizes(egfem_handle h, int64_t *n_nodes, int64_t *n_wa, int64_t *n_wc, int64_t *jac_rows, int64_t *jac_nnz) {
+    if (!h) return EGFEM_ERR_INVALID_ARG;
+    if (n_nodes) *n_nodes = h->n;
+    if (n_wa) *n_wa = h->nwa;
+    if (n_wc) *n_wc = h->nwc;
+    if (jac_rows) *jac_rows = h->n;
+    if (jac_nnz) *jac_nnz = h->csf.nnz;
+    return EGFEM_OK;
+}
+
+egfem_status egfem_w_coords(egfem_handle h, int32_t which, double *coords_host) {
+    if (!h || !coords_host || (which != 0 && which != 1)) return EGFEM_ERR_INVALID_ARG;
+    const std::vector<double> &c = which == 0 ? h->wa_coords : h->wc_coords;
+    std::memcpy(coords_host, c.data(), c.size() * sizeof(double));
+    return EGFEM_OK;
+}
+
+egfem_status egfem_jacobian_pattern(egfem_handle h, const int32_t **d_rowptr, const int32_t **d_cols) {
+    if (!h) return EGFEM_ERR_INVALID_ARG;
+    if (d_rowptr) *d_rowptr = h->csf.rowptr;
+    if (d_cols) *d_cols = h->csf.cols;
+    return EGFEM_OK;
+}
+
+egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream stream) {
+    if (!h) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    if (!d_kappa) { h->nl.kappa_field = nullptr; return EGFEM_OK; }
+    if (!h->kappa_field) EG_TRY(dalloc(h->kappa_field, size_t(h->nwa)));
+    EG_CUDA(cudaMemcpyAsync(h->kappa_field, d_kappa, size_t(h->nwa) * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    h->nl.kappa_field = h->kappa_field;
+    return EGFEM_OK;
+}
+
+egfem_status egfem_pointwise(egfem_handle h, const double *d_u, double *d_w, double *d_wprime, egfem_stream stream) {
+    if (!h || !d_u) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    const unsigned grid = unsigned((h->nwa + 255) / 256);
+    pointwise_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(h->nwa, h->wa_kind, h->wa_sup, d_u, h->nl, d_w, d_wprime);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_residual(egfem_handle h, const double *d_u, const double *d_d, double *d_r, egfem_stream stream) {
+    if (!h || !d_u || !d_d || !d_r) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    CsfArgs A = csf_args(h, d_u, d_d);
+    A.r = d_r;
+    launch_csf(h, A, (cudaStream_t)stream);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_jacobian(egfem_handle h, const double *d_u, double *d_vals, egfem_stream stream) {
+    if (!h || !d_u || !d_vals) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    CsfArgs A = csf_args(h, d_u, nullptr);
+    A.jcsr = d_vals;
+    launch_csf(h, A, (cudaStream_t)stream);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_spmv(egfem_handle h, const double *d_vals, const double *d_x, double *d_y, egfem_stream stream) {
+    if (!h || !d_vals || !d_x || !d_y) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    csr_spmv_kernel<<<unsigned((h->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(h->n, h->csf.rowptr, h->csf.cols, d_vals, d_x, d_y);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *d_rhs, double *d_x, double rtol,
+                            int32_t maxit, int32_t *iters, egfem_stream stream) {
+    if (!h || !d_vals || !d_rhs || !d_x || rtol < 0 || maxit < 0) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    EG_TRY(kwork_alloc(h, h->k64));
+    EG_TRY(join_in(h, (cudaStream_t)stream));
+    EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
+    csr_to_sell_kernel<double><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs,
+                                                                               h->k64.A, h->k64.b, h->status);
+    EG_CUDA(cudaGetLastError());
+    EG_TRY(check_status_word(h));
+    int32_t done = 0, it = 0;
+    EG_TRY(run_bicgstab(h, h->k64, rtol, maxit, &done, &it));
+    EG_CUDA(cudaMemcpyAsync(d_x, h->k64.x, size_t(h->n) * sizeof(double), cudaMemcpyDeviceToDevice, h->hs));
+    EG_TRY(join_out(h, (cudaStream_t)stream));
+    if (iters) *iters = it;
+    if (done == K_CONVERGED) return EGFEM_OK;
+    if (done == K_MAXIT) return EGFEM_ERR_NOT_CONVERGED;
+    if (done == K_BREAKDOWN) return EGFEM_ERR_BREAKDOWN;
+    return EGFEM_ERR_NONFINITE;
+}
+
+egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats, egfem_stream stream) {
+    if (!h || !d_u || !d_d) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    egfem_stats S;
+    std::memset(&S, 0, sizeof(S));
+    const bool mixed = h->opts.precision == EGFEM_PREC_MIXED;
+    EG_TRY(join_in(h, (cudaStream_t)stream));
+    EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
+    auto eval = [&](double *rn) -> egfem_status {
+        CsfArgs A = csf_args(h, d_u, d_d);
+        A.r = h->r;
+        if (mixed) { A.a32 = h->k32.A; A.q32 = h->k32.b; }
+        else { A.a64 = h->k64.A; A.q64 = h->k64.b; }
+        launch_csf(h, A, h->hs);
+        EG_CUDA(cudaGetLastError());
+        double n2;
+        EG_TRY(norm2_free(h, h->r, &n2));
+        *rn = std::sqrt(n2);
+        return EGFEM_OK;
+    };
+    double rn;
+    egfem_status status = eval(&rn);
+    if (status != EGFEM_OK) return status;
+    const double r0 = rn;
+    S.res0 = r0;
+    const double target = std::max(h->opts.newton_rtol * r0, h->opts.newton_atol);
+    double eta = h->opts.eta_max, rprev = rn;
+    int k = 0;
+    status = EGFEM_OK;
+    while (true) {
+        if (!std::isfinite(rn)) { status = EGFEM_ERR_NONFINITE; break; }
+        if (rn <= target) break;
+        if (k >= h->opts.newton_maxit) { status = EGFEM_ERR_NOT_CONVERGED; break; }
+        egfem_status ws = check_status_word(h);
+        if (ws != EGFEM_OK) { status = ws; break; }
+        // Eisenstat-Walker forcing term (choice 2, gamma = 0.9, alpha = 2), safeguarded
+        if (k > 0 && !h->opts.fixed_eta) {
+            double e = 0.9 * (rn / rprev) * (rn / rprev);
+            const double sg = 0.9 * eta * eta;
+            if (sg > 0.1) e = std::max(e, sg);
+            eta = std::min(h->opts.eta_max, e);
+            eta = std::max(eta, 0.5 * target / rn);
+        }
+        eta = std::max(eta, h->opts.eta_min);
+        if (mixed) eta = std::max(eta, 1e-6);   // FP32 Krylov floor
+        int32_t done = 0, it = 0;
+        if (mixed) status = run_bicgstab(h, h->k32, eta, h->opts.krylov_maxit, &done, &it);
+        else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, &done, &it);
+        if (status != EGFEM_OK) break;
+        if (done == K_NONFINITE) { status = EGFEM_ERR_NONFINITE; break; }
+        if (done == K_BREAKDOWN && it == 0) { status = EGFEM_ERR_BREAKDOWN; break; }
+        S.krylov_iters += it;
+        if (k < EGFEM_HIST) S.krylov_hist[k] = it;
+        const unsigned g = unsigned((h->n + 255) / 256);
+        if (mixed) newton_update_kernel<float><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k32.x);
+        else newton_update_kernel<double><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k64.x);
+        EG_CUDA(cudaGetLastError());
+        ++k;
+        rprev = rn;
+        status = eval(&rn);
+        if (status != EGFEM_OK) break;
+        if (k - 1 < EGFEM_HIST) S.res_hist[k - 1] = rn;
+    }
+    S.newton_iters = k;
+    S.res_final = rn;
+    S.status = status;
+    S.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    egfem_status js = join_out(h, (cudaStream_t)stream);
+    if (stats) *stats = S;
+    return status != EGFEM_OK ? status : js;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Adjoint and load vectors
+// ---------------------------------------------------------------------------------
+
+namespace {
+
+// AT[tmap[q]] = J[q] * dinv[col(q)]  (the transpose, Jacobi-scaled by its own diagonal)
+template <typename V>
+__global__ void transpose_scaled_kernel(int64_t n, const SliceMeta *meta, const int32_t *col_idx, const int64_t *tmap,
+                                        const double *jsell, const double *dinv, V *AT) {
+    const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const SliceMeta M = meta[row / SLICE];
+    const int lane = int(row % SLICE);
+    for (int c = 0; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        const int64_t t = tmap[q];
+        if (t < 0) continue;
+        AT[t] = V(jsell[q] * dinv[col_idx[q]]);
+    }
+}
+
+template <typename V>
+__global__ void adjoint_rhs_kernel(int64_t n, const double *g, const uint8_t *dir, const double *dinv, V *b) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = V(dir[i] ? 0.0 : g[i] * dinv[i]);
+}
+
+// grad_kappa_m -= lambda_i sum_k T_imk (u_k - u_i)   (sum_k T_imk = 0)
+__global__ void grad_kappa_kernel(int64_t n_rows, const SliceMeta *meta, const int32_t *col_idx, const double *leaf_val,
+                                  const uint8_t *leaf_col, const uint32_t *fib_info, const int32_t *fib_m, const uint8_t *dir,
+                                  const double *u, const double *lam, double *grad) {
+    const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (row >= n_rows || dir[row]) return;
+    const double li = lam[row];
+    if (li == 0.0) return;
+    const SliceMeta M = meta[row / SLICE];
+    const int lane = int(row % SLICE);
+    const double ui = u[row];
+    double D = 0.0;
+    int f = -1;
+    for (int j = 0; j < M.nleaf; ++j) {
+        const int64_t q = M.leaf_base + int64_t(j) * SLICE + lane;
+        const uint8_t lc = leaf_col[q];
+        if (lc & LEAF_FIBRE_START) {
+            if (f >= 0) {
+                const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
+                if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq]], -li * D);
+            }
+            ++f;
+            D = 0.0;
+        }
+        const int c = lc & LEAF_PAD;
+        if (c != LEAF_PAD) D += leaf_val[q] * (u[col_idx[M.col_base + int64_t(c) * SLICE + lane]] - ui);
+    }
+    if (f >= 0) {
+        const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
+        if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq]], -li * D);
+    }
+}
+
+__global__ void load_cellwise_kernel(int64_t n, int dim, const int64_t *v2c_ptr, const int32_t *v2c, const double *vol,
+                                     const uint8_t *dir, const double *f, double *d) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (dir[i]) { d[i] = 0.0; return; }
+    double s = 0.0;
+    for (int64_t t = v2c_ptr[i]; t < v2c_ptr[i + 1]; ++t) { const int32_t c = v2c[t]; s += f[c] * vol[c]; }
+    d[i] = s / double(dim + 1);
+}
+
+__global__ void load_cellwise_t_kernel(int64_t nc, int dim, const int32_t *cv, const double *vol, const uint8_t *dir,
+                                       const double *lam, double *g) {
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double s = 0.0;
+    for (int a = 0; a <= dim; ++a) { const int32_t v = cv[c * (dim + 1) + a]; if (!dir[v]) s += lam[v]; }
+    g[c] = s * vol[c] / double(dim + 1);
+}
+
+template <typename V>
+egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const double *d_g, double *d_lambda, egfem_stats *S) {
+    if (!h->jsell) EG_TRY(dalloc(h->jsell, size_t(h->csf.n_colentries)));
+    if (!h->dinv) EG_TRY(dalloc(h->dinv, size_t(h->n)));
+    EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
+    CsfArgs A = csf_args(h, d_u, nullptr);
+    A.jsell = h->jsell; A.dinv = h->dinv;
+    launch_csf(h, A, h->hs);
+    EG_CUDA(cudaGetLastError());
+    EG_TRY(check_status_word(h));
+    const unsigned g = unsigned((h->n + 255) / 256);
+    EG_CUDA(cudaMemsetAsync(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V), h->hs));
+    transpose_scaled_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->tmap, h->jsell, h->dinv, W.A);
+    adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_g, h->csf.dir, h->dinv, W.b);
+    EG_CUDA(cudaGetLastError());
+    // FP64: solve to a tight tolerance; mixed: FP32 solve followed by FP64-residual refinement
+    const bool mixed = std::is_same<V, float>::value;
+    const double rtol = mixed ? std::max(1e-6, h->opts.eta_min) : 1e-13;
+    int32_t done = 0, it = 0;
+    EG_TRY(run_bicgstab(h, W, rtol, h->opts.krylov_maxit, &done, &it));
+    S->krylov_iters += it;
+    if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
+    cast_kernel<V, double><<<g, 256, 0, h->hs>>>(h->n, W.x, d_lambda);
+    EG_CUDA(cudaGetLastError());
+    if (done == K_MAXIT) return EGFEM_ERR_NOT_CONVERGED;
+    if (done == K_BREAKDOWN) return EGFEM_ERR_BREAKDOWN;
+    return EGFEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda, double *d_grad_kappa,
+                           egfem_stats *stats, egfem_stream stream) {
+    if (!h || !d_u || !d_dJdu || !d_lambda) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    egfem_stats S;
+    std::memset(&S, 0, sizeof(S));
+    EG_TRY(join_in(h, (cudaStream_t)stream));
+    egfem_status st = (h->opts.precision == EGFEM_PREC_MIXED) ? adjoint_solve(h, h->k32, d_u, d_dJdu, d_lambda, &S)
+                                                              : adjoint_solve(h, h->k64, d_u, d_dJdu, d_lambda, &S);
+    if (st == EGFEM_OK && d_grad_kappa) {
+        EG_CUDA(cudaMemsetAsync(d_grad_kappa, 0, size_t(h->nwa) * sizeof(double), h->hs));
+        grad_kappa_kernel<<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->csf.leaf_val,
+                                                                          h->csf.leaf_col, h->csf.fib_info, h->csf.fib_m, h->csf.dir, d_u, d_lambda,
+                                                                          d_grad_kappa);
+        EG_CUDA(cudaGetLastError());
+    }
+    S.status = st;
+    if (stats) *stats = S;
+    egfem_status js = join_out(h, (cudaStream_t)stream);
+    return st != EGFEM_OK ? st : js;
+}
+
+egfem_status egfem_load_cellwise(egfem_handle h, const double *d_f, double *d_d, egfem_stream stream) {
+    if (!h || !d_f || !d_d) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    load_cellwise_kernel<<<unsigned((h->n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(h->n, h->dim, h->v2c_ptr, h->v2c,
+                                                                                           h->cell_vol, h->csf.dir, d_f, d_d);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_load_cellwise_transpose(egfem_handle h, const double *d_lam, double *d_g, egfem_stream stream) {
+    if (!h || !d_lam || !d_g) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    load_cellwise_t_kernel<<<unsigned((h->ncells + 255) / 256), 256, 0, (cudaStream_t)stream>>>(h->ncells, h->dim, h->cell_verts,
+                                                                                                  h->cell_vol, h->csf.dir, d_lam, d_g);
+    EG_CUDA(cudaGetLastError());
+    return EGFEM_OK;
+}
+
+const char *egfem_status_string(egfem_status s) {
+    switch (s) {
+        case EGFEM_OK: return "EGFEM_OK";
+        case EGFEM_ERR_INVALID_ARG: return "EGFEM_ERR_INVALID_ARG";
+        case EGFEM_ERR_MESH: return "EGFEM_ERR_MESH";
+        case EGFEM_ERR_CUDA: return "EGFEM_ERR_CUDA";
+        case EGFEM_ERR_OOM: return "EGFEM_ERR_OOM";
+        case EGFEM_ERR_NOT_CONVERGED: return "EGFEM_ERR_NOT_CONVERGED";
+        case EGFEM_ERR_BREAKDOWN: return "EGFEM_ERR_BREAKDOWN";
+        case EGFEM_ERR_SINGULAR: return "EGFEM_ERR_SINGULAR";
+        case EGFEM_ERR_NONFINITE: return "EGFEM_ERR_NONFINITE";
+        case EGFEM_ERR_TIMEOUT: return "EGFEM_ERR_TIMEOUT";
+        case EGFEM_ERR_UNSUPPORTED: return "EGFEM_ERR_UNSUPPORTED";
+    }
+    return "EGFEM_ERR_UNKNOWN";
+}
+
+const char *egfem_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

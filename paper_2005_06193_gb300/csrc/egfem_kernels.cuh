@@ -1,0 +1,209 @@
+// egfem_kernels.cuh -- device code of the EGFEM Newton hot path (sm_103a).
+//
+// Layout (built by egfem_build.cpp): rows are grouped in slices of 32 consecutive rows;
+// every per-row list (local columns, leaves, fibres, reaction entries) is stored
+// column-interleaved within its slice (entry j of row r at base + 32 j + r), so one
+// thread per row reads coalesced 32-wide words.  The tensor is row-segmented CSF:
+//     row i -> fibres (one per W node m with a nonzero T_imk) -> leaves (k != i, T_imk)
+// with the diagonal T_imi = -sum_{k != i} T_imk kept once per fibre.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "egfem_internal.h"
+
+namespace egfem {
+
+constexpr int CSF_BLOCK = 128;
+
+struct CsfArgs {
+    int64_t n_rows;
+    const SliceMeta *meta;
+    const int32_t *col_idx, *col_slot;
+    const double *leaf_val;
+    const uint8_t *leaf_col;
+    const uint32_t *fib_info;
+    const double *fib_tdiag;
+    const int32_t *fib_m;
+    const double *rx_val;
+    const uint32_t *rx_info;
+    const uint8_t *dir;
+    Nonlin nl;
+    const double *u;       // [n_rows] input
+    const double *d;       // [n_rows] load (Dirichlet rows: boundary values); may be null for J only
+    double *r;             // residual out (nullable)
+    double *jcsr;          // Jacobian values in CSR order (nullable)
+    double *a64;           // D J in SELL order, FP64 (nullable)
+    float *a32;            // D J in SELL order, FP32 (nullable)
+    double *q64;           // D r (nullable)
+    float *q32;            // D r (nullable)
+    double *jsell;         // unscaled J in SELL order (nullable)
+    double *dinv;          // 1 / J_ii (nullable)
+    int32_t *status;       // error word (singular diagonal)
+};
+
+__device__ __forceinline__ void g_eval(int32_t kind, int32_t p, double scale, double s, double &g, double &gp) {
+    if (kind == EGFEM_G_POW) {
+        double sp = 1.0;                      // s^(p-1)
+        for (int32_t k = 1; k < p; ++k) sp *= s;
+        g = scale * sp * s;
+        gp = scale * double(p) * sp;
+    } else if (kind == EGFEM_G_EXP) {
+        g = scale * exp(s);
+        gp = g;
+    } else {
+        g = 0.0;
+        gp = 0.0;
+    }
+}
+
+// (Pi u)_m = u_i + sum_t w_t (u_{c_t} - u_i), the weights w_t summing to one (Sec. 3.2).
+__device__ __forceinline__ double interp_du(uint32_t info, const double *du, int stride) {
+    const uint32_t kind = (info >> 24) & 0xF;
+    const double d0 = du[(info & 0xFF) * stride];
+    if (kind == W_VERTEX) return d0;
+    const double d1 = du[((info >> 8) & 0xFF) * stride];
+    if (kind == W_MID) return 0.5 * (d0 + d1);
+    if (kind == W_THIRD) return (2.0 * d0 + d1) * (1.0 / 3.0);
+    const double d2 = du[((info >> 16) & 0xFF) * stride];
+    return (d0 + d1 + d2) * (1.0 / 3.0);
+}
+
+// J_{i, c_t} += e * w_t  (the Pi_ml factor of the eliminated Jacobian, Sec. 4)
+__device__ __forceinline__ void scatter_pi(uint32_t info, double e, double *J, int stride) {
+    const uint32_t kind = (info >> 24) & 0xF;
+    const uint32_t c0 = info & 0xFF, c1 = (info >> 8) & 0xFF, c2 = (info >> 16) & 0xFF;
+    if (kind == W_VERTEX) { J[c0 * stride] += e; return; }
+    if (kind == W_MID) { const double h = 0.5 * e; J[c0 * stride] += h; J[c1 * stride] += h; return; }
+    if (kind == W_THIRD) { const double h = e * (1.0 / 3.0); J[c0 * stride] += 2.0 * h; J[c1 * stride] += h; return; }
+    if (kind == W_FACE) { const double h = e * (1.0 / 3.0); J[c0 * stride] += h; J[c1 * stride] += h; J[c2 * stride] += h; }
+}
+
+// Fused pointwise nonlinearity + residual + Jacobian fill (one thread per row).
+// MAXC bounds the local columns of a row; du and J live in shared memory, one column
+// of CSF_BLOCK entries per local column.
+template <int MAXC>
+__global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
+    __shared__ double s_du[MAXC * CSF_BLOCK];
+    __shared__ double s_J[MAXC * CSF_BLOCK];
+    const int tid = threadIdx.x;
+    const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
+    if (row >= A.n_rows) return;
+    const int64_t sl = row / SLICE;
+    const int lane = int(row % SLICE);
+    const SliceMeta M = A.meta[sl];
+    const double ui = A.u[row];
+    const double di = A.d ? A.d[row] : 0.0;
+    double *du = s_du + tid, *J = s_J + tid;
+    if (A.dir[row]) {
+        if (A.r) A.r[row] = ui - di;
+        if (A.q64) A.q64[row] = ui - di;
+        if (A.q32) A.q32[row] = float(ui - di);
+        if (A.dinv) A.dinv[row] = 1.0;
+        for (int c = 0; c < M.ncol; ++c) {
+            const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+            const double v = (c == 0) ? 1.0 : 0.0;
+            if (A.a64) A.a64[q] = v;
+            if (A.a32) A.a32[q] = float(v);
+            if (A.jcsr && c == 0) A.jcsr[A.col_slot[q]] = 1.0;
+            if (A.jsell) A.jsell[q] = v;
+        }
+        return;
+    }
+    for (int c = 0; c < M.ncol; ++c) {
+        const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
+        du[c * CSF_BLOCK] = A.u[g] - ui;
+        J[c * CSF_BLOCK] = 0.0;
+    }
+    const Nonlin nl = A.nl;
+    double r = 0.0, j1d = 0.0, D = 0.0, a = 0.0, gp = 0.0;
+    uint32_t info = 0;
+    int f = -1;
+    for (int j = 0; j < M.nleaf; ++j) {
+        const int64_t q = M.leaf_base + int64_t(j) * SLICE + lane;
+        const uint8_t lc = A.leaf_col[q];
+        const double T = A.leaf_val[q];
+        if (lc & LEAF_FIBRE_START) {
+            if (f >= 0) {
+                r += a * D;
+                if (gp != 0.0) scatter_pi(info, D * gp, J, CSF_BLOCK);
+            }
+            ++f;
+            const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
+            info = A.fib_info[fq];
+            const double td = A.fib_tdiag[fq];
+            if (((info >> 24) & 0xF) == W_CONST) {
+                a = nl.kappa;
+                gp = 0.0;
+            } else {
+                const double pu = ui + interp_du(info, du, CSF_BLOCK);
+                double w;
+                g_eval(nl.a_kind, nl.a_pi, nl.a_scale, pu, w, gp);
+                a = (nl.kappa_field ? nl.kappa_field[A.fib_m[fq]] : nl.kappa) + w;
+            }
+            j1d += td * a;
+            D = 0.0;
+        }
+        const int c = lc & LEAF_PAD;
+        if (c != LEAF_PAD) {
+            D += T * du[c * CSF_BLOCK];
+            J[c * CSF_BLOCK] += T * a;
+        }
+    }
+    if (f >= 0) {
+        r += a * D;
+        if (gp != 0.0) scatter_pi(info, D * gp, J, CSF_BLOCK);
+    }
+    // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
+    for (int j = 0; j < M.nrx; ++j) {
+        const int64_t q = M.rx_base + int64_t(j) * SLICE + lane;
+        const double mv = A.rx_val[q];
+        if (mv == 0.0) continue;
+        const uint32_t xi = A.rx_info[q];
+        const double pc = ui + interp_du(xi, du, CSF_BLOCK);
+        double cv, cp;
+        g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
+        r += nl.gamma * mv * cv;
+        scatter_pi(xi, nl.gamma * mv * cp, J, CSF_BLOCK);
+    }
+    const double diag = j1d + J[0];
+    const double res = r - di;
+    if (A.r) A.r[row] = res;
+    double dinv = 0.0;
+    if (diag != 0.0) dinv = 1.0 / diag;
+    else if (A.status) atomicOr(A.status, 1);
+    if (A.dinv) A.dinv[row] = dinv;
+    if (A.q64) A.q64[row] = dinv * res;
+    if (A.q32) A.q32[row] = float(dinv * res);
+    for (int c = 0; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        const int32_t slot = A.col_slot[q];
+        const double v = (c == 0) ? diag : J[c * CSF_BLOCK];
+        if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
+        if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
+        const double sv = slot >= 0 ? dinv * v : 0.0;
+        if (A.a64) A.a64[q] = sv;
+        if (A.a32) A.a32[q] = float(sv);
+    }
+}
+
+// Pointwise nonlinearity alone (Sec. 3.2), one thread per W node.
+__global__ void pointwise_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u, Nonlin nl,
+                                 double *w, double *wp) {
+    const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (m >= n_w) return;
+    const uint32_t k = kind[m];
+    double pu;
+    const double u0 = u[sup[3 * m]];
+    if (k == W_VERTEX) pu = u0;
+    else if (k == W_MID) pu = 0.5 * (u0 + u[sup[3 * m + 1]]);
+    else if (k == W_THIRD) pu = (2.0 * u0 + u[sup[3 * m + 1]]) * (1.0 / 3.0);
+    else pu = (u0 + u[sup[3 * m + 1]] + u[sup[3 * m + 2]]) * (1.0 / 3.0);
+    double g, gp;
+    g_eval(nl.a_kind, nl.a_pi, nl.a_scale, pu, g, gp);
+    if (w) w[m] = g;
+    if (wp) wp[m] = gp;
+}
+
+}  // namespace egfem

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (FP64 path): kernel outputs on identical inputs agree to 1e-12 relative
+(2-norm over the vector, or max-norm over the Jacobian values); converged Newton
+solutions agree to 1e-11 relative on grids whose condition number keeps the FP64
+solution error far below that.  Mixed precision (FP32 operator and Krylov, FP64
+residual and update): the solution agrees with the FP64 oracle to 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2005_06193_gb300 as P
+    return P
+
+
+def cuda(x, dtype=torch.float64):
+    return torch.tensor(np.asarray(x), device="cuda", dtype=dtype)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def gpu_jacobian(h, u):
+    rp, cl = h.pattern()
+    vals = torch.empty(h.sizes.jac_nnz, device="cuda", dtype=torch.float64)
+    h.jacobian(u, vals)
+    torch.cuda.synchronize()
+    n = h.sizes.jac_rows
+    return sp.csr_matrix((vals.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=(n, n))
+
+
+def match_w(oc, lc):
+    key = lambda c: [tuple(np.round(x, 12)) for x in c]
+    lk = {k: i for i, k in enumerate(key(lc))}
+    return np.array([lk[k] for k in key(oc)])
+
+
+CASES = {
+    # name: (mesh factory, oracle kwargs, library problem kwargs)
+    "u2_p2_2d": (lambda: wl.unit_square_mesh(32), dict(a=("pow", 2.0), a_deg=2), dict(a=("pow", 2), a_degree=2)),
+    "u2_p2_ragged": (lambda: wl.unit_square_mesh(13), dict(a=("pow", 2.0), a_deg=2), dict(a=("pow", 2), a_degree=2)),
+    "u3_p3_2d": (lambda: wl.unit_square_mesh(17), dict(a=("pow", 3.0), a_deg=3), dict(a=("pow", 3), a_degree=3)),
+    "u2_p1_gfem": (lambda: wl.unit_square_mesh(9), dict(a=("pow", 2.0), a_deg=1), dict(a=("pow", 2), a_degree=1)),
+    "u2_p2_3d": (lambda: wl.unit_cube_mesh(5), dict(a=("pow", 2.0), a_deg=2), dict(a=("pow", 2), a_degree=2)),
+    "bratu_3d": (lambda: wl.unit_cube_mesh(8), dict(a=None, a_deg=1, c=("exp",), c_deg=1, gamma=-2.0),
+                 dict(a=None, a_degree=1, c=("exp",), c_degree=1, gamma=-2.0)),
+}
+
+
+def _setup(P, name, **opt):
+    mk, okw, pkw = CASES[name]
+    mesh = mk()
+    orc = oracle.Problem(mesh, **okw)
+    h = P.Handle(mesh, P.make_problem(**pkw), P.default_options(**opt))
+    return mesh, orc, h
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_parity(P, name):
+    mesh, orc, h = _setup(P, name)
+    b = orc.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    for seed, scale in ((1, 1.0), (2, 0.3)):
+        u = wl.random_vector(mesh.n_nodes, seed, scale) * (1 - mesh.dirichlet)
+        r = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+        h.residual(cuda(u), cuda(b), r)
+        torch.cuda.synchronize()
+        ref = orc.residual(u, b)
+        assert rel(r.cpu().numpy(), ref) <= 1e-12
+    # u = 0: the residual is -b on free rows
+    r0 = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    h.residual(torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64), cuda(b), r0)
+    torch.cuda.synchronize()
+    assert rel(r0.cpu().numpy(), orc.residual(np.zeros(mesh.n_nodes), b)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jacobian_parity(P, name):
+    mesh, orc, h = _setup(P, name)
+    u = wl.random_vector(mesh.n_nodes, 3, 0.8) * (1 - mesh.dirichlet)
+    J = gpu_jacobian(h, cuda(u))
+    Jo = orc.jacobian(u)
+    diff = abs(J - Jo)
+    assert diff.max() <= 1e-12 * abs(Jo).max()
+    # every stored value belongs to the P1 adjacency; no oracle value outside it is nonzero
+    extra = Jo - Jo.multiply(J != 0)
+    assert abs(extra).max() <= 1e-13 * abs(Jo).max()
+
+
+@pytest.mark.parametrize("name", ["u2_p2_2d", "u3_p3_2d", "u2_p2_3d"])
+def test_pointwise_parity(P, name):
+    mesh, orc, h = _setup(P, name)
+    u = wl.random_vector(mesh.n_nodes, 4, 1.0)
+    w = torch.empty(h.sizes.n_wa, device="cuda", dtype=torch.float64)
+    wp = torch.empty_like(w)
+    h.pointwise(cuda(u), w, wp)
+    torch.cuda.synchronize()
+    ow, owp, _, _ = orc.pointwise(u)
+    perm = match_w(orc.space_coords(0), h.w_coords(0))
+    assert rel(w.cpu().numpy()[perm], ow) <= 1e-13
+    assert rel(wp.cpu().numpy()[perm], owp) <= 1e-13
+
+
+def test_spmv_and_bicgstab_parity(P):
+    mesh, orc, h = _setup(P, "u2_p2_2d")
+    u = wl.random_vector(mesh.n_nodes, 5, 0.5) * (1 - mesh.dirichlet)
+    J = gpu_jacobian(h, cuda(u))
+    vals = cuda(J.data)
+    x = wl.random_vector(mesh.n_nodes, 6)
+    y = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    h.spmv(vals, cuda(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), J @ x) <= 1e-14
+    rhs = wl.random_vector(mesh.n_nodes, 7)
+    sol = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    its = h.bicgstab(vals, cuda(rhs), sol, rtol=1e-12)
+    ref = spla.spsolve(J.tocsc(), rhs)
+    assert its > 10
+    assert rel(sol.cpu().numpy(), ref) <= 1e-9
+    xo, st, _, _ = oracle.bicgstab(J, rhs, rtol=1e-12)
+    assert rel(sol.cpu().numpy(), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["u2_p2_2d", "u2_p2_ragged", "u3_p3_2d", "u2_p2_3d", "bratu_3d"])
+def test_newton_solution_parity_fp64(P, name):
+    mesh, orc, h = _setup(P, name, newton_rtol=1e-13)
+    src = wl.mms_source if CASES[name][1].get("c") is None else (lambda *x: 0.0 * x[0])
+    b = orc.load_vector(src) * (1 - mesh.dirichlet)
+    u_ref, hist, _, _ = orc.newton(b, rtol=1e-13, solver="lu" if mesh.n_nodes < 20000 else "bicgstab")
+    u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    st = h.newton_solve(u, cuda(b))
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.res_final <= 1e-13 * st.res0
+    if name == "bratu_3d":
+        assert u_ref.max() > 0.01
+    assert rel(u.cpu().numpy(), u_ref) <= 1e-11
+
+
+def test_newton_default_tolerance_and_egfem_equals_sga(P):
+    """32 x 32, w = u^2 in P2: the GPU EGFEM solution at the default 1e-10 target is the
+    SGA (standard Galerkin) solution of the oracle up to that tolerance (Case 1)."""
+    mesh, orc, h = _setup(P, "u2_p2_2d")
+    b = orc.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    st = h.newton_solve(u, cuda(b))
+    torch.cuda.synchronize()
+    un = u.cpu().numpy()
+    assert st.res_final <= 1e-10 * st.res0
+    r_sga = orc.residual(un, b, method="sga", form="diff")
+    assert np.linalg.norm(r_sga * (1 - mesh.dirichlet)) <= 1.5e-10 * np.linalg.norm(b)
+    u_sga, _, _, _ = orc.newton(b, method="sga", rtol=1e-13)
+    assert rel(un, u_sga) <= 1e-8
+
+
+@pytest.mark.parametrize("name", ["u2_p2_2d", "bratu_3d"])
+def test_newton_mixed_precision(P, name):
+    mesh, orc, h = _setup(P, name, precision=P.PREC_MIXED)
+    src = wl.mms_source if CASES[name][1].get("c") is None else (lambda *x: 0.0 * x[0])
+    b = orc.load_vector(src) * (1 - mesh.dirichlet)
+    u_ref, _, _, _ = orc.newton(b, rtol=1e-13)
+    u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    st = h.newton_solve(u, cuda(b))
+    torch.cuda.synchronize()
+    un = u.cpu().numpy()
+    assert st.status == 0 and st.res_final <= 1e-10 * st.res0
+    # the FP64 residual of the oracle confirms the target
+    assert np.linalg.norm(orc.residual(un, b, form="diff") * (1 - mesh.dirichlet)) <= 1.5e-10 * np.linalg.norm(b)
+    assert rel(un, u_ref) <= 1e-6
+
+
+def test_adjoint_parity(P):
+    mesh, orc, h = _setup(P, "u2_p2_ragged", newton_rtol=1e-13)
+    b = orc.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    u_ref, _, _, _ = orc.newton(b, rtol=1e-14)
+    ud = wl.adjoint_target()(mesh.coords[:, 0], mesh.coords[:, 1])
+    g = (u_ref - ud) * (1 - mesh.dirichlet)
+    orc.set_kappa_field(np.ones(orc.nw))
+    lam_ref, gk_ref = orc.adjoint(u_ref, g)
+    lam = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    gk = torch.zeros(h.sizes.n_wa, device="cuda", dtype=torch.float64)
+    h.adjoint(cuda(u_ref), cuda(g), lam, gk)
+    torch.cuda.synchronize()
+    assert rel(lam.cpu().numpy(), lam_ref) <= 1e-10
+    perm = match_w(orc.space_coords(0), h.w_coords(0))
+    assert rel(gk.cpu().numpy()[perm], gk_ref) <= 1e-10
+
+
+def test_load_cellwise_matches_oracle_quadrature(P):
+    mesh = wl.unit_square_mesh(32)
+    h = P.Handle(mesh, P.make_problem())
+    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+    f = wl.random_vector(mesh.n_cells, 11)
+    d = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    h.load_cellwise(cuda(f), d)
+    torch.cuda.synchronize()
+    ref = orc.load_vector_cellwise(f) * (1 - mesh.dirichlet)
+    assert rel(d.cpu().numpy(), ref) <= 1e-13
+    lam = wl.random_vector(mesh.n_nodes, 12)
+    g = torch.empty(mesh.n_cells, device="cuda", dtype=torch.float64)
+    h.load_cellwise_transpose(cuda(lam), g)
+    torch.cuda.synchronize()
+    # transpose identity: <d(f), lam> = <f, g(lam)>
+    assert abs(np.dot(d.cpu().numpy(), lam) - np.dot(f, g.cpu().numpy())) <= 1e-12 * abs(np.dot(f, g.cpu().numpy()))
+
+
+def test_full_size_1024_residual_on_sampled_rows(P):
+    """1024 x 1024 grid (1.05 M P1, 4.2 M P2 nodes): the GPU residual and Jacobian rows
+    equal the oracle's on sampled rows (oracle assembles only the cells around them)."""
+    n = 1024
+    mesh = wl.unit_square_mesh(n)
+    h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2))
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.integers(0, mesh.n_nodes, 300), [0, 1, n, n + 1, n + 2, mesh.n_nodes - 1]]))
+    cellmask = np.isin(mesh.cells, rows).any(axis=1)
+    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2, cells=np.where(cellmask)[0].astype(np.int32))
+    u = wl.random_vector(mesh.n_nodes, 13) * (1 - mesh.dirichlet)
+    b = wl.random_vector(mesh.n_nodes, 14, 1e-5) * (1 - mesh.dirichlet)
+    r = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    h.residual(cuda(u), cuda(b), r)
+    J = gpu_jacobian(h, cuda(u))
+    torch.cuda.synchronize()
+    ref = orc.residual(u, b)
+    assert rel(r.cpu().numpy()[rows], ref[rows]) <= 1e-12
+    Jo = orc.jacobian(u)
+    for i in rows[:60]:
+        a, o = J.getrow(i).toarray().ravel(), Jo.getrow(i).toarray().ravel()
+        assert np.abs(a - o).max() <= 1e-12 * np.abs(o).max()

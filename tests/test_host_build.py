@@ -1,0 +1,122 @@
+"""CPU-only checks of the CUDA library: the C ABI loads and exports every declared
+symbol, and its host-side offline assembly (W numbering, stored CSF tensor) matches
+the oracle's independent quadrature.  No GPU code runs here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def egf():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2005_06193_gb300 as P
+    return P
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "egfem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(egfem_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_abi_exports_every_declared_symbol(egf):
+    names = _declared_functions()
+    assert len(names) >= 19
+    L = egf.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.egfem_status_string(0) == b"EGFEM_OK"
+    assert L.egfem_status_string(6) == b"EGFEM_ERR_BREAKDOWN"
+
+
+def _match_w(oc, lc):
+    """permutation p with lc[p[j]] == oc[j] (coordinates rounded to 1e-12)"""
+    key = lambda c: [tuple(np.round(x, 12)) for x in c]
+    lk = {k: i for i, k in enumerate(key(lc))}
+    return np.array([lk[k] for k in key(oc)])
+
+
+@pytest.mark.parametrize("dim,n,deg", [(2, 5, 1), (2, 5, 2), (2, 5, 3), (3, 2, 1), (3, 2, 2), (3, 2, 3)])
+def test_stored_tensor_matches_oracle_quadrature(egf, dim, n, deg):
+    """Every stored T_imk (off-diagonal leaves plus the per-fibre diagonal) equals the
+    oracle's quadrature value, and every oracle entry not stored is zero to rounding."""
+    mesh = wl.unit_square_mesh(n) if dim == 2 else wl.unit_cube_mesh(n)
+    I, M, K, V, Wc = egf.inspect_tensor(mesh, egf.make_problem(a=("pow", 2), a_degree=deg))
+    P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=deg, qpts=5)
+    oI, oM, oK, oV = P.T_coo()
+    perm = _match_w(P.space_coords(0), Wc)          # oracle m -> library m
+    assert len(perm) == len(Wc)
+    scale = np.abs(oV).max()
+    orc = {(i, perm[m], k): v for i, m, k, v in zip(oI, oM, oK, oV) if not mesh.dirichlet[i]}
+    lib = {(i, m, k): v for i, m, k, v in zip(I, M, K, V)}
+    assert not any(mesh.dirichlet[i] for (i, _, _) in lib)
+    for key, v in lib.items():
+        assert abs(orc.get(key, 0.0) - v) <= 1e-13 * scale, (key, v, orc.get(key))
+    for key, v in orc.items():
+        if key not in lib:
+            assert abs(v) <= 1e-13 * scale, (key, v)
+
+
+def test_stored_tensor_has_exact_zero_row_sums(egf):
+    mesh = wl.unit_square_mesh(7)
+    I, M, K, V, _ = egf.inspect_tensor(mesh, egf.make_problem(a=("pow", 2), a_degree=2))
+    s = {}
+    for i, m, v in zip(I, M, V):
+        s[(i, m)] = s.get((i, m), 0.0) + v
+    assert max(abs(x) for x in s.values()) <= 1e-15
+
+
+def test_constant_coefficient_stores_the_stiffness(egf):
+    """Without a coefficient nonlinearity the stored form is kappa-free stiffness A."""
+    mesh = wl.unit_cube_mesh(3)
+    I, M, K, V, _ = egf.inspect_tensor(mesh, egf.make_problem(a=None, a_degree=1, c=("exp",), c_degree=1, gamma=-2.0))
+    assert np.all(M == -1)
+    P = oracle.Problem(mesh, a=None, a_deg=1)
+    oI, oM, oK, oV = P.T_coo()
+    A = {}
+    for i, k, v in zip(oI, oK, oV):
+        if not mesh.dirichlet[i]:
+            A[(i, k)] = A.get((i, k), 0.0) + v
+    lib = {(i, k): v for i, k, v in zip(I, K, V)}
+    for key, v in A.items():
+        assert abs(lib.get(key, 0.0) - v) <= 1e-14, key
+
+
+def test_table1_w_space_sizes_match(egf):
+    """Library W numbering reproduces the P2/P3 counts of Table 1 on the 64 x 64 grid."""
+    mesh = wl.unit_square_mesh(64)
+    for deg, size in ((2, 20866), (3, 41474)):
+        _, _, _, _, W = egf.inspect_tensor(mesh, egf.make_problem(a=("pow", 2), a_degree=deg))
+        assert mesh.n_nodes + len(W) == size
+
+
+@pytest.mark.parametrize("bad", ["index", "degenerate", "repeat"])
+def test_malformed_mesh_is_rejected(egf, bad):
+    mesh = wl.unit_square_mesh(3)
+    cells = mesh.cells.copy()
+    coords = mesh.coords.copy()
+    if bad == "index":
+        cells[4, 1] = mesh.n_nodes + 5
+    elif bad == "repeat":
+        cells[2, 2] = cells[2, 0]
+    else:
+        coords[cells[3, 1]] = coords[cells[3, 0]]
+    m2 = wl.Mesh(2, coords, cells, mesh.dirichlet)
+    with pytest.raises(egf.EgfemError) as e:
+        egf.inspect_tensor(m2, egf.make_problem())
+    assert e.value.status == 2
+
+
+def test_bad_problem_is_rejected(egf):
+    mesh = wl.unit_square_mesh(3)
+    with pytest.raises(egf.EgfemError) as e:
+        egf.inspect_tensor(mesh, egf.make_problem(a_degree=4))
+    assert e.value.status == 1
