@@ -68,8 +68,10 @@ typedef enum {
 
 typedef enum {
     EGFEM_PREC_FP64 = 0,   /* every operator value, vector and reduction in FP64          */
-    EGFEM_PREC_MIXED = 1   /* FP32 Jacobian values and Krylov vectors (FP64 dot sums);
-                              FP64 residual, norm, Newton update (iterative refinement) */
+    EGFEM_PREC_MIXED = 1   /* FP32 Jacobian values and Krylov vectors (compensated dot
+                              sums); FP64 residual, norm, Newton update (iterative
+                              refinement).  A Newton step whose FP32 solve diverges or
+                              fails to decrease the FP64 residual is redone in FP64. */
 } egfem_precision;
 
 typedef enum {
@@ -124,7 +126,22 @@ typedef struct {
     double res_hist[EGFEM_HIST];       /* ||r||_2 after each Newton step (FP64)          */
     int32_t krylov_hist[EGFEM_HIST];   /* BiCGStab iterations of each Newton step        */
     double solve_ms;                   /* wall time of the solve (host clock)            */
+    int64_t kernel_launches;           /* kernels of this library launched by the call,
+                                          graph nodes included                          */
+    int32_t fp64_rescues;              /* mixed precision: Newton steps whose FP32 Krylov
+                                          solve failed and was redone in FP64           */
 } egfem_stats;
+
+#define EGFEM_PROF_MAX 8
+/* Per-kernel timing of one Newton step's kernels (egfem_profile_kernels). */
+typedef struct {
+    int32_t count;                          /* kernels filled in                          */
+    char name[EGFEM_PROF_MAX][24];          /* kernel name                                */
+    double ms[EGFEM_PROF_MAX];              /* mean duration of one launch, CUDA events   */
+    double bytes[EGFEM_PROF_MAX];           /* algorithmic DRAM bytes of one launch       */
+    double flops[EGFEM_PROF_MAX];           /* algorithmic floating-point ops of one launch */
+    int32_t fp64[EGFEM_PROF_MAX];           /* 1 when the kernel computes in FP64         */
+} egfem_profile;
 
 /* Fill *opts with the defaults listed above. */
 void egfem_default_options(egfem_options *opts);
@@ -178,8 +195,11 @@ egfem_status egfem_jacobian(egfem_handle h, const double *d_u, double *d_vals, e
 egfem_status egfem_spmv(egfem_handle h, const double *d_vals, const double *d_x, double *d_y, egfem_stream stream);
 
 /* Jacobi-preconditioned BiCGStab (van der Vorst 1992) on J x = rhs, J from CSR values
- * d_vals; x in: initial guess, out: solution.  Stops at ||rhs - J x|| <= rtol ||rhs||.
- * Synchronises the stream.  *iters receives the iteration count. */
+ * d_vals (FP64); x out: solution (the iteration starts from x = 0).  The system is scaled
+ * by D = diag(J)^{-1} on the left and the iteration stops at ||D(rhs - J x)|| <=
+ * rtol ||D rhs||.  A handle built with EGFEM_PREC_MIXED iterates in FP32 (the operator and
+ * vectors rounded once) with FP64 dot sums.  Synchronises the stream.  *iters receives
+ * the iteration count.  Errors: NOT_CONVERGED (maxit), BREAKDOWN, NONFINITE, SINGULAR. */
 egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *d_rhs, double *d_x,
                             double rtol, int32_t maxit, int32_t *iters, egfem_stream stream);
 
@@ -187,6 +207,13 @@ egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *
  * Synchronises the stream.  stats may be NULL. */
 egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats,
                                 egfem_stream stream);
+
+/* Time each kernel of the Newton step at state d_u, load d_d: the fused tensor-action /
+ * Jacobian kernel and the five BiCGStab kernels, each launched reps times back to back on
+ * the handle's stream between two CUDA events.  Alongside, the algorithmic bytes and
+ * flops of one launch (operator and vectors counted once).  Synchronises the stream. */
+egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const double *d_d, int32_t reps,
+                                   egfem_profile *out, egfem_stream stream);
 
 /* Adjoint of a functional j(u*) of the converged solution (implicit function theorem;
  * motivated by the repeated forward/backward solves of optimal control, Sec. 6):

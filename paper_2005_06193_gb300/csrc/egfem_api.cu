@@ -92,13 +92,25 @@ struct egfem_t {
     int32_t *status = nullptr;
     KWork<double> k64;
     KWork<float> k32;
-    int kgrid = 1;
+    int64_t n_pad = 0;                  // rows rounded up to whole slices (Krylov vectors)
+    int kgrid = 1;                      // blocks of the row kernels (norms)
+    int kgrid64 = 1, kgrid32 = 1;       // blocks of the FP64 / FP32 Krylov kernels
     cudaStream_t hs = nullptr;          // internal stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int maxc_tpl = 8;
+    int64_t last_graph_launches = 0;    // graph launches of the last BiCGStab solve
 };
 
 namespace {
+
+// Smallest Krylov forcing term of the mixed path: an FP32 BiCGStab's recursive residual
+// stagnates near 1e-4 on the 1024^2 problem (the FP32 iterate is then accurate to ~1e-5),
+// so asking for less only burns iterations; the FP64 Newton residual supplies the
+// remaining digits, a factor of ~5e-4 per step (iterative refinement).
+constexpr double kMixedEtaFloor = 5e-4;
+// An FP32 solve whose residual has not fallen by 10% for this many iterations stops (its
+// iterate is still applied; the FP64 Newton residual judges it).
+constexpr int32_t kMixedStall = 150;
 
 int pick_maxc(int maxc) {
     if (maxc <= 8) return 8;
@@ -133,9 +145,12 @@ CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
 }
 
 template <typename V>
+int kgrid_of(const egfem_t *h) { return sizeof(V) == 8 ? h->kgrid64 : h->kgrid32; }
+
+template <typename V>
 KVecs<V> kvecs(egfem_t *h, KWork<V> &W) {
     KVecs<V> K{};
-    K.n = h->n; K.meta = h->csf.meta; K.col_idx = h->csf.col_idx; K.A = W.A;
+    K.n_pad = h->n_pad; K.meta = h->csf.meta; K.col_idx = h->csf.col_idx; K.A = W.A;
     K.x = W.x; K.r = W.r; K.rh = W.rh; K.p = W.p; K.v = W.v; K.s = W.s; K.t = W.t; K.b = W.b;
     K.st = h->st; K.part = h->part;
     return K;
@@ -147,7 +162,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
     EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V)));
     V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t};
-    for (V **q : vec) { EG_TRY(dalloc(*q, size_t(h->n))); EG_CUDA(cudaMemset(*q, 0, size_t(h->n) * sizeof(V))); }
+    for (V **q : vec) { EG_TRY(dalloc(*q, size_t(h->n_pad))); EG_CUDA(cudaMemset(*q, 0, size_t(h->n_pad) * sizeof(V))); }
     W.ready = true;
     return EGFEM_OK;
 }
@@ -155,12 +170,13 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
 template <typename V>
 void enqueue_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
     KVecs<V> K = kvecs(h, W);
+    const int g = kgrid_of<V>(h);
     for (int it = 0; it < count; ++it) {
-        kry_v<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
-        kry_s<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
-        kry_t<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
-        kry_x<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
-        kry_p<V><<<h->kgrid, KRY_BLOCK, 0, s>>>(K);
+        kry_v<V><<<g, KRY_BLOCK, 0, s>>>(K);
+        kry_s<V><<<g, KRY_BLOCK, 0, s>>>(K);
+        kry_t<V><<<g, KRY_BLOCK, 0, s>>>(K);
+        kry_x<V><<<g, KRY_BLOCK, 0, s>>>(K);
+        kry_p<V><<<g, KRY_BLOCK, 0, s>>>(K);
     }
 }
 
@@ -183,16 +199,19 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
 // Run BiCGStab on W.A x = W.b (already filled) on the internal stream; returns the
 // device-state outcome in *done and the iteration count in *iters.
 template <typename V>
-egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t *done, int32_t *iters) {
+egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall, int32_t *done,
+                          int32_t *iters) {
     EG_TRY(ensure_graph(h, W));
     KVecs<V> K = kvecs(h, W);
-    kry_setup<V><<<h->kgrid, KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit);
+    kry_setup<V><<<kgrid_of<V>(h), KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit, stall);
     EG_CUDA(cudaGetLastError());
+    h->last_graph_launches = 0;
     for (;;) {
         EG_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
         EG_CUDA(cudaStreamSynchronize(h->hs));
         if (h->h_st->done != K_RUNNING) break;
         EG_CUDA(cudaGraphLaunch(W.graph, h->hs));
+        ++h->last_graph_launches;
     }
     *done = h->h_st->done;
     *iters = h->h_st->iter;
@@ -330,9 +349,15 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
     h->nl.gamma = prob->gamma; h->nl.kappa = prob->kappa; h->nl.kappa_field = nullptr;
     // workspace
-    h->kgrid = int(std::max<int64_t>(1, std::min<int64_t>((h->n + KRY_BLOCK - 1) / KRY_BLOCK, int64_t(h->sms) * 8)));
+    h->n_pad = int64_t(H.n_slices) * SLICE;
+    auto grid_for = [&](int64_t per_block) {
+        return int(std::max<int64_t>(1, std::min<int64_t>((h->n_pad + per_block - 1) / per_block, int64_t(h->sms) * 8)));
+    };
+    h->kgrid = grid_for(KRY_BLOCK);
+    h->kgrid64 = grid_for(KRY_BLOCK * VecT<double>::R);
+    h->kgrid32 = grid_for(KRY_BLOCK * VecT<float>::R);
     EG_TRY(dalloc(h->r, size_t(h->n)));
-    EG_TRY(dalloc(h->part, size_t(4 * h->kgrid)));
+    EG_TRY(dalloc(h->part, size_t(4 * std::max(h->kgrid, std::max(h->kgrid64, h->kgrid32)))));
     EG_TRY(dalloc(h->scal, 8));
     EG_TRY(dalloc(h->ticket, 1)); EG_CUDA(cudaMemset(h->ticket, 0, sizeof(uint32_t)));
     EG_TRY(dalloc(h->status, 1)); EG_CUDA(cudaMemset(h->status, 0, sizeof(int32_t)));
@@ -491,20 +516,32 @@ egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *
                             int32_t maxit, int32_t *iters, egfem_stream stream) {
     if (!h || !d_vals || !d_rhs || !d_x || rtol < 0 || maxit < 0) return EGFEM_ERR_INVALID_ARG;
     EG_CUDA(cudaSetDevice(h->device));
-    EG_TRY(kwork_alloc(h, h->k64));
     EG_TRY(join_in(h, (cudaStream_t)stream));
     EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
-    csr_to_sell_kernel<double><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs,
-                                                                               h->k64.A, h->k64.b, h->status);
-    EG_CUDA(cudaGetLastError());
-    EG_TRY(check_status_word(h));
     int32_t done = 0, it = 0;
-    EG_TRY(run_bicgstab(h, h->k64, rtol, maxit, &done, &it));
-    EG_CUDA(cudaMemcpyAsync(d_x, h->k64.x, size_t(h->n) * sizeof(double), cudaMemcpyDeviceToDevice, h->hs));
+    const unsigned g = unsigned((h->n + 255) / 256);
+    if (h->opts.precision == EGFEM_PREC_MIXED) {
+        EG_TRY(kwork_alloc(h, h->k32));
+        csr_to_sell_kernel<float><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs, h->k32.A, h->k32.b,
+                                                         h->status);
+        EG_CUDA(cudaGetLastError());
+        EG_TRY(check_status_word(h));
+        EG_TRY(run_bicgstab(h, h->k32, rtol, maxit, 0, &done, &it));
+        cast_kernel<float, double><<<g, 256, 0, h->hs>>>(h->n, h->k32.x, d_x);
+    } else {
+        EG_TRY(kwork_alloc(h, h->k64));
+        csr_to_sell_kernel<double><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs, h->k64.A, h->k64.b,
+                                                          h->status);
+        EG_CUDA(cudaGetLastError());
+        EG_TRY(check_status_word(h));
+        EG_TRY(run_bicgstab(h, h->k64, rtol, maxit, 0, &done, &it));
+        EG_CUDA(cudaMemcpyAsync(d_x, h->k64.x, size_t(h->n) * sizeof(double), cudaMemcpyDeviceToDevice, h->hs));
+    }
+    EG_CUDA(cudaGetLastError());
     EG_TRY(join_out(h, (cudaStream_t)stream));
     if (iters) *iters = it;
     if (done == K_CONVERGED) return EGFEM_OK;
-    if (done == K_MAXIT) return EGFEM_ERR_NOT_CONVERGED;
+    if (done == K_MAXIT || done == K_STAGNATED) return EGFEM_ERR_NOT_CONVERGED;
     if (done == K_BREAKDOWN) return EGFEM_ERR_BREAKDOWN;
     return EGFEM_ERR_NONFINITE;
 }
@@ -516,18 +553,29 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     egfem_stats S;
     std::memset(&S, 0, sizeof(S));
     const bool mixed = h->opts.precision == EGFEM_PREC_MIXED;
+    if (mixed) EG_TRY(kwork_alloc(h, h->k64));   // FP64 rescue of failed FP32 solves
     EG_TRY(join_in(h, (cudaStream_t)stream));
     EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
+    // residual, Jacobi-scaled Jacobian and right-hand side at u (both precisions when mixed)
     auto eval = [&](double *rn) -> egfem_status {
         CsfArgs A = csf_args(h, d_u, d_d);
         A.r = h->r;
+        A.a64 = h->k64.A; A.q64 = h->k64.b;
         if (mixed) { A.a32 = h->k32.A; A.q32 = h->k32.b; }
-        else { A.a64 = h->k64.A; A.q64 = h->k64.b; }
         launch_csf(h, A, h->hs);
         EG_CUDA(cudaGetLastError());
         double n2;
         EG_TRY(norm2_free(h, h->r, &n2));
         *rn = std::sqrt(n2);
+        S.kernel_launches += 2;
+        return EGFEM_OK;
+    };
+    const unsigned g = unsigned((h->n + 255) / 256);
+    auto update = [&](bool fp32, double lam) -> egfem_status {   // u -= lam x
+        if (fp32) newton_update_kernel<float><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k32.x, lam);
+        else newton_update_kernel<double><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k64.x, lam);
+        EG_CUDA(cudaGetLastError());
+        S.kernel_launches += 1;
         return EGFEM_OK;
     };
     double rn;
@@ -542,7 +590,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     while (true) {
         if (!std::isfinite(rn)) { status = EGFEM_ERR_NONFINITE; break; }
         if (rn <= target) break;
-        if (k >= h->opts.newton_maxit) { status = EGFEM_ERR_NOT_CONVERGED; break; }
+        if (k >= h->opts.newton_maxit) { status = EGFEM_ERR_NOT_CONVERGED; g_last_error = "Newton iteration cap"; break; }
         egfem_status ws = check_status_word(h);
         if (ws != EGFEM_OK) { status = ws; break; }
         // Eisenstat-Walker forcing term (choice 2, gamma = 0.9, alpha = 2), safeguarded
@@ -554,23 +602,52 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             eta = std::max(eta, 0.5 * target / rn);
         }
         eta = std::max(eta, h->opts.eta_min);
-        if (mixed) eta = std::max(eta, 1e-6);   // FP32 Krylov floor
-        int32_t done = 0, it = 0;
-        if (mixed) status = run_bicgstab(h, h->k32, eta, h->opts.krylov_maxit, &done, &it);
-        else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, &done, &it);
-        if (status != EGFEM_OK) break;
-        if (done == K_NONFINITE) { status = EGFEM_ERR_NONFINITE; break; }
-        if (done == K_BREAKDOWN && it == 0) { status = EGFEM_ERR_BREAKDOWN; break; }
-        S.krylov_iters += it;
-        if (k < EGFEM_HIST) S.krylov_hist[k] = it;
-        const unsigned g = unsigned((h->n + 255) / 256);
-        if (mixed) newton_update_kernel<float><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k32.x);
-        else newton_update_kernel<double><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k64.x);
-        EG_CUDA(cudaGetLastError());
+        bool fp32 = mixed, stepped = false;
+        const double rbefore = rn;
+        int32_t its_step = 0;
+        while (!stepped) {
+            int32_t done = 0, it = 0;
+            if (fp32) status = run_bicgstab(h, h->k32, std::max(eta, kMixedEtaFloor), h->opts.krylov_maxit, kMixedStall, &done, &it);
+            else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, 0, &done, &it);
+            if (status != EGFEM_OK) break;
+            S.kernel_launches += 1 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+            S.krylov_iters += it;
+            its_step += it;
+            const bool failed = done == K_NONFINITE || (done == K_BREAKDOWN && it == 0) || (fp32 && done == K_BREAKDOWN);
+            if (failed) {
+                if (fp32) { fp32 = false; ++S.fp64_rescues; continue; }
+                status = done == K_NONFINITE ? EGFEM_ERR_NONFINITE : EGFEM_ERR_BREAKDOWN;
+                break;
+            }
+            status = update(fp32, 1.0);
+            if (status != EGFEM_OK) break;
+            status = eval(&rn);
+            if (status != EGFEM_OK) break;
+            // damping (the paper's remark on damped iterations, Sec. 4): halve the step while
+            // the FP64 residual norm fails to decrease sufficiently (Armijo test, <= 6 halvings)
+            double lam = 1.0;
+            for (int bt = 0; bt < 6 && !(rn <= (1.0 - 1e-4 * lam) * rbefore); ++bt) {
+                status = update(fp32, -0.5 * lam);   // step length lam -> lam / 2
+                if (status != EGFEM_OK) break;
+                lam *= 0.5;
+                status = eval(&rn);
+                if (status != EGFEM_OK) break;
+            }
+            if (status != EGFEM_OK) break;
+            if (rn < rbefore) { stepped = true; break; }
+            // no step length decreases the residual: undo the step
+            status = update(fp32, -lam);
+            if (status == EGFEM_OK) status = eval(&rn);
+            if (status != EGFEM_OK) break;
+            if (fp32) { fp32 = false; ++S.fp64_rescues; continue; }
+            status = EGFEM_ERR_NOT_CONVERGED;
+            g_last_error = "Newton step failed to decrease the residual after 6 halvings";
+            break;
+        }
+        if (k < EGFEM_HIST) S.krylov_hist[k] = its_step;
+        if (!stepped) break;
         ++k;
-        rprev = rn;
-        status = eval(&rn);
-        if (status != EGFEM_OK) break;
+        rprev = rbefore;
         if (k - 1 < EGFEM_HIST) S.res_hist[k - 1] = rn;
     }
     S.newton_iters = k;
@@ -664,6 +741,23 @@ __global__ void load_cellwise_t_kernel(int64_t nc, int dim, const int32_t *cv, c
     g[c] = s * vol[c] / double(dim + 1);
 }
 
+// rho = g - J^T lambda in FP64 (Dirichlet rows: g = 0), J^T read through the transpose map
+__global__ void adjoint_residual_kernel(int64_t n, const SliceMeta *meta, const int32_t *col_idx, const int64_t *tmap,
+                                        const double *jsell, const uint8_t *dir, const double *g, const double *lam,
+                                        double *rho) {
+    const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const SliceMeta M = meta[row / SLICE];
+    const int lane = int(row % SLICE);
+    double y = 0.0;
+    for (int c = 0; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        const int64_t t = tmap[q];
+        if (t >= 0) y += jsell[t] * lam[col_idx[q]];
+    }
+    rho[row] = (dir[row] ? 0.0 : g[row]) - y;
+}
+
 template <typename V>
 egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const double *d_g, double *d_lambda, egfem_stats *S) {
     if (!h->jsell) EG_TRY(dalloc(h->jsell, size_t(h->csf.n_colentries)));
@@ -677,20 +771,107 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
     const unsigned g = unsigned((h->n + 255) / 256);
     EG_CUDA(cudaMemsetAsync(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V), h->hs));
     transpose_scaled_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->tmap, h->jsell, h->dinv, W.A);
+    if (std::is_same<V, float>::value) rowsum_form_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, W.A);
     adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_g, h->csf.dir, h->dinv, W.b);
     EG_CUDA(cudaGetLastError());
-    // FP64: solve to a tight tolerance; mixed: FP32 solve followed by FP64-residual refinement
+    // FP64: one solve to a tight tolerance.  Mixed: iterative refinement -- FP32 solves of
+    // (D J^T) delta = D rho for the FP64 residual rho = g - J^T lambda, lambda += delta.
     const bool mixed = std::is_same<V, float>::value;
-    const double rtol = mixed ? std::max(1e-6, h->opts.eta_min) : 1e-13;
     int32_t done = 0, it = 0;
-    EG_TRY(run_bicgstab(h, W, rtol, h->opts.krylov_maxit, &done, &it));
-    S->krylov_iters += it;
-    if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
-    cast_kernel<V, double><<<g, 256, 0, h->hs>>>(h->n, W.x, d_lambda);
+    if (!mixed) {
+        EG_TRY(run_bicgstab(h, W, 1e-13, h->opts.krylov_maxit, 0, &done, &it));
+        S->krylov_iters += it;
+        S->kernel_launches += 5 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+        if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
+        cast_kernel<V, double><<<g, 256, 0, h->hs>>>(h->n, W.x, d_lambda);
+        EG_CUDA(cudaGetLastError());
+        if (done == K_MAXIT) return EGFEM_ERR_NOT_CONVERGED;
+        if (done == K_BREAKDOWN) return EGFEM_ERR_BREAKDOWN;
+        return EGFEM_OK;
+    }
+    EG_CUDA(cudaMemsetAsync(d_lambda, 0, size_t(h->n) * sizeof(double), h->hs));
+    double g0 = 0.0, rn = 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        adjoint_residual_kernel<<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->tmap, h->jsell, h->csf.dir,
+                                                         d_g, d_lambda, h->r);
+        EG_CUDA(cudaGetLastError());
+        double n2;
+        EG_TRY(norm2_free(h, h->r, &n2));
+        rn = std::sqrt(n2);
+        if (sweep == 0) g0 = rn;
+        S->kernel_launches += 2;
+        if (!std::isfinite(rn)) return EGFEM_ERR_NONFINITE;
+        if (rn <= 1e-13 * g0 || rn == 0.0) return EGFEM_OK;
+        adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->r, h->csf.dir, h->dinv, W.b);
+        EG_TRY(run_bicgstab(h, W, 1e-3, h->opts.krylov_maxit, kMixedStall, &done, &it));
+        S->krylov_iters += it;
+        S->kernel_launches += 6 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+        if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
+        newton_update_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_lambda, W.x, -1.0);
+        EG_CUDA(cudaGetLastError());
+    }
+    return rn <= 1e-10 * g0 ? EGFEM_OK : EGFEM_ERR_NOT_CONVERGED;
+}
+
+template <typename V>
+egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const double *d_d, int32_t reps, egfem_profile *out,
+                          cudaStream_t user) {
+    EG_TRY(join_in(h, user));
+    cudaEvent_t e0, e1;
+    EG_CUDA(cudaEventCreate(&e0));
+    EG_CUDA(cudaEventCreate(&e1));
+    const double vb = double(sizeof(V));
+    const double N = double(h->n), CE = double(h->csf.n_colentries), L = double(h->csf.n_leaves);
+    const double F = double(h->csf.n_fibres), RX = double(h->csf.n_rx), SM = double(h->csf.n_slices) * sizeof(SliceMeta);
+    auto timeit = [&](const char *name, double bytes, double flops, int fp64, auto launch) -> egfem_status {
+        const int k = out->count;
+        if (k >= EGFEM_PROF_MAX) return EGFEM_OK;
+        launch();  // warm
+        EG_CUDA(cudaEventRecord(e0, h->hs));
+        for (int r = 0; r < reps; ++r) launch();
+        EG_CUDA(cudaEventRecord(e1, h->hs));
+        EG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        EG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        std::snprintf(out->name[k], sizeof(out->name[k]), "%s", name);
+        out->ms[k] = double(ms) / reps;
+        out->bytes[k] = bytes;
+        out->flops[k] = flops;
+        out->fp64[k] = fp64;
+        out->count = k + 1;
+        return EGFEM_OK;
+    };
+    CsfArgs A = csf_args(h, d_u, d_d);
+    A.r = h->r;
+    if (std::is_same<V, float>::value) { A.a32 = (float *)W.A; A.q32 = (float *)W.b; }
+    else { A.a64 = (double *)W.A; A.q64 = (double *)W.b; }
+    // fused kernel: leaves (value + column byte), fibres (info + diagonal), reaction entries,
+    // local columns (index + CSR slot) and the operator written, u/d/r/q once each
+    const double csf_bytes = L * 9 + F * 12 + RX * 12 + CE * (8 + vb) + N * (8 + 8 + 8 + vb + 1) + SM;
+    const double csf_flops = L * 4 + F * 12 + RX * 10 + CE * 2;
+    EG_TRY(timeit("csf_fused", csf_bytes, csf_flops, 1, [&] { launch_csf(h, A, h->hs); }));
+    KVecs<V> K = kvecs(h, W);
+    const int kg = kgrid_of<V>(h);
+    kry_setup<V><<<kg, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
+    enqueue_iterations(h, W, 1, h->hs);
     EG_CUDA(cudaGetLastError());
-    if (done == K_MAXIT) return EGFEM_ERR_NOT_CONVERGED;
-    if (done == K_BREAKDOWN) return EGFEM_ERR_BREAKDOWN;
-    return EGFEM_OK;
+    const int fp = std::is_same<V, double>::value ? 1 : 0;
+    auto run = [&](const char *name, double bytes, double flops, auto kern) -> egfem_status {
+        EG_CUDA(cudaMemsetAsync(&h->st->done, 0, sizeof(int32_t), h->hs));
+        EG_TRY(timeit(name, bytes, flops, fp, [&] { kern<<<kg, KRY_BLOCK, 0, h->hs>>>(K); }));
+        int32_t done = 0;
+        EG_CUDA(cudaMemcpy(&done, &h->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (done != K_RUNNING) out->ms[out->count - 1] = NAN;
+        return EGFEM_OK;
+    };
+    EG_TRY(run("kry_v", CE * (vb + 4) + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>));
+    EG_TRY(run("kry_s", 3 * N * vb, 2 * N, kry_s<V>));
+    EG_TRY(run("kry_t", CE * (vb + 4) + 2 * N * vb + SM, 2 * CE + 4 * N, kry_t<V>));
+    EG_TRY(run("kry_x", 7 * N * vb, 10 * N, kry_x<V>));
+    EG_TRY(run("kry_p", 4 * N * vb, 4 * N, kry_p<V>));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return join_out(h, user);
 }
 
 }  // namespace
@@ -735,6 +916,16 @@ egfem_status egfem_load_cellwise_transpose(egfem_handle h, const double *d_lam, 
                                                                                                   h->cell_vol, h->csf.dir, d_lam, d_g);
     EG_CUDA(cudaGetLastError());
     return EGFEM_OK;
+}
+
+egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const double *d_d, int32_t reps, egfem_profile *out,
+                                   egfem_stream stream) {
+    if (!h || !d_u || !d_d || !out || reps < 1) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    std::memset(out, 0, sizeof(*out));
+    const bool mixed = h->opts.precision == EGFEM_PREC_MIXED;
+    return mixed ? profile_impl(h, h->k32, d_u, d_d, reps, out, (cudaStream_t)stream)
+                 : profile_impl(h, h->k64, d_u, d_d, reps, out, (cudaStream_t)stream);
 }
 
 const char *egfem_status_string(egfem_status s) {

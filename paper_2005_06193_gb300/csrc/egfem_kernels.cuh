@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     if (A.dinv) A.dinv[row] = dinv;
     if (A.q64) A.q64[row] = dinv * res;
     if (A.q32) A.q32[row] = float(dinv * res);
+    double rowsum = 0.0;
     for (int c = 0; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int32_t slot = A.col_slot[q];
@@ -183,9 +184,12 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
         const double sv = slot >= 0 ? dinv * v : 0.0;
+        rowsum += sv;
         if (A.a64) A.a64[q] = sv;
         if (A.a32) A.a32[q] = float(sv);
     }
+    // the FP32 operator keeps its row sum in column 0 (difference-form SpMV)
+    if (A.a32) A.a32[M.col_base + lane] = float(rowsum);
 }
 
 // Pointwise nonlinearity alone (Sec. 3.2), one thread per W node.

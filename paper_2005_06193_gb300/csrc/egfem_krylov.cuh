@@ -1,8 +1,19 @@
 // egfem_krylov.cuh -- BiCGStab (van der Vorst 1992) on the Jacobi-scaled system
 // (D J) x = D b, D = diag(J)^{-1}, with the matrix in the slice-interleaved (SELL-32)
-// layout of the tensor's local columns.  V is the vector/matrix type (double for the
-// FP64 path, float for the mixed path); dot products are summed per thread in V and
-// across threads and blocks in double, in a fixed order (deterministic results).
+// layout of the tensor's local columns.
+//
+// V is the vector/matrix type: double (FP64 path) or float (mixed path).  Every thread
+// owns R = 16 / sizeof(V) consecutive rows (2 in FP64, 4 in FP32) and moves them with
+// one 128-bit load or store per array, so a warp keeps 512 B per stream in flight.
+// Vectors are padded to whole slices (pad entries stay zero), so no kernel needs a
+// bounds check inside a slice.  Dot products are summed per thread in V and across
+// threads and blocks in double, in a fixed order (deterministic results).
+//
+// FP32 operator application uses the difference form
+//     (A p)_i = s_i p_i + sum_{c != i} A_ic (p_c - p_i),   s_i = sum_c A_ic,
+// with the row sum s_i stored in place of the diagonal.  For the smooth vectors of an
+// elliptic problem the plain FP32 sum cancels O(|A||p|) terms down to O(h^2 |p|) and
+// loses ~5 digits (BiCGStab then diverges); the difference form does not cancel.
 //
 // Every kernel of an iteration reads the device state first and returns at once when
 // the solve has finished, so a captured chunk of iterations can overshoot the last one
@@ -19,31 +30,91 @@ namespace egfem {
 
 constexpr int KRY_BLOCK = 256;
 
-enum KDone : int32_t { K_RUNNING = 0, K_CONVERGED = 1, K_MAXIT = 2, K_BREAKDOWN = 3, K_NONFINITE = 4 };
+enum KDone : int32_t { K_RUNNING = 0, K_CONVERGED = 1, K_MAXIT = 2, K_BREAKDOWN = 3, K_NONFINITE = 4, K_STAGNATED = 5 };
 
 struct KState {
     double rho, alpha, omega, beta;
     double rr;          // ||r||^2 of the current iterate
     double rr0;         // ||r_0||^2
     double tol2;        // stop when rr <= tol2
-    double scratch[4];
-    int32_t iter, maxit, done, pad;
+    double best_rr;     // smallest rr so far (stagnation guard)
+    double stall_rr;    // the stagnation guard acts only once best_rr <= stall_rr
+    double scratch[2];
+    int32_t iter, maxit, done, last_improve;
+    int32_t stall;      // iterations without a 10% improvement before K_STAGNATED (0: off)
     uint32_t ticket;
 };
 
+template <typename V> struct VecT;
+template <> struct VecT<double> { using type = double2; using idx = int2; static constexpr int R = 2; };
+template <> struct VecT<float> { using type = float4; using idx = int4; static constexpr int R = 4; };
+
+template <typename V>
+struct Pack {
+    V v[VecT<V>::R];
+};
+
+template <typename V>
+__device__ __forceinline__ Pack<V> ldv(const V *p) {
+    Pack<V> o;
+    const typename VecT<V>::type t = *reinterpret_cast<const typename VecT<V>::type *>(p);
+    if constexpr (VecT<V>::R == 2) { o.v[0] = t.x; o.v[1] = t.y; }
+    else { o.v[0] = t.x; o.v[1] = t.y; o.v[2] = t.z; o.v[3] = t.w; }
+    return o;
+}
+
+template <typename V>
+__device__ __forceinline__ void stv(V *p, const Pack<V> &o) {
+    typename VecT<V>::type t;
+    if constexpr (VecT<V>::R == 2) { t.x = o.v[0]; t.y = o.v[1]; }
+    else { t.x = o.v[0]; t.y = o.v[1]; t.z = o.v[2]; t.w = o.v[3]; }
+    *reinterpret_cast<typename VecT<V>::type *>(p) = t;
+}
+
+template <typename V>
+__device__ __forceinline__ void ldi(const int32_t *p, int32_t (&c)[VecT<V>::R]) {
+    const typename VecT<V>::idx t = *reinterpret_cast<const typename VecT<V>::idx *>(p);
+    if constexpr (VecT<V>::R == 2) { c[0] = t.x; c[1] = t.y; }
+    else { c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w; }
+}
+
 template <typename V>
 struct KVecs {
-    int64_t n;
+    int64_t n_pad;      // rows rounded up to whole slices
     const SliceMeta *meta;
     const int32_t *col_idx;
     const V *A;
     V *x, *r, *rh, *p, *v, *s, *t;
     const V *b;
     KState *st;
-    double *part;       // [3 * gridDim.x]
+    double *part;       // [2 * gridDim.x]
 };
 
-template <typename V> struct Acc { using type = V; };
+// Per-thread dot-product accumulators.  FP64: plain FMA.  FP32: compensated dot product
+// (Ogita, Rump & Oishi 2005, "Dot2"): each product is split exactly by an FMA and summed
+// with Knuth's TwoSum, so the result is as accurate as if computed in twice the working
+// precision.  BiCGStab's inner products cancel strongly once r is nearly orthogonal to
+// the shadow residual; rounded FP32 products there give wrong alpha/beta and divergence.
+// Explicit _rn intrinsics keep the compiler from contracting the error-free transforms.
+template <typename V> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(hi, p);
+        const float z = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+        hi = t;
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
 
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
@@ -96,37 +167,71 @@ __device__ bool grid_reduce(double (&val)[NV], double *part, uint32_t *ticket, d
     return true;
 }
 
-// y_row = sum_c A[q] x[col(q)] over the row's local columns (SELL-32 layout).
+// y[r0 .. r0+R) = A xin for the R rows starting at r0 (r0 a multiple of R).
 template <typename V>
-__device__ __forceinline__ V sell_row(const KVecs<V> &K, int64_t row, const V *xin) {
-    const SliceMeta M = K.meta[row / SLICE];
-    const int lane = int(row % SLICE);
-    V y = V(0);
-    for (int c = 0; c < M.ncol; ++c) {
-        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
-        y += K.A[q] * xin[K.col_idx[q]];
+__device__ __forceinline__ Pack<V> sell_rows(const KVecs<V> &K, int64_t r0, const V *xin) {
+    constexpr int R = VecT<V>::R;
+    const SliceMeta M = K.meta[r0 / SLICE];
+    const int lane = int(r0 % SLICE);
+    Pack<V> y;
+    if constexpr (sizeof(V) == 4) {
+        // difference form: column 0 holds the row sum s_i and the row's own value
+        const Pack<V> xi = ldv(xin + r0);
+        const Pack<V> a0 = ldv(K.A + M.col_base + lane);
+#pragma unroll
+        for (int j = 0; j < R; ++j) y.v[j] = a0.v[j] * xi.v[j];
+        for (int c = 1; c < M.ncol; ++c) {
+            const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+            const Pack<V> a = ldv(K.A + q);
+            int32_t col[R];
+            ldi<V>(K.col_idx + q, col);
+#pragma unroll
+            for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * (__ldg(xin + col[j]) - xi.v[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) y.v[j] = V(0);
+        for (int c = 0; c < M.ncol; ++c) {
+            const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+            const Pack<V> a = ldv(K.A + q);
+            int32_t col[R];
+            ldi<V>(K.col_idx + q, col);
+#pragma unroll
+            for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * __ldg(xin + col[j]);
+        }
     }
     return y;
 }
 
 __device__ __forceinline__ bool finished(const KState *st) { return *(volatile const int32_t *)&st->done != K_RUNNING; }
 
-// setup: x = 0, r = rh = p = b, rho = (r, r)
+#define KRY_LOOP(K) \
+    for (int64_t r0 = (int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x) * VecT<V>::R; r0 < (K).n_pad; \
+         r0 += int64_t(gridDim.x) * KRY_BLOCK * VecT<V>::R)
+
+// setup: x = 0, r = rh = p = b, v = 0, rho = (r, r)
 template <typename V>
-__global__ void __launch_bounds__(KRY_BLOCK) kry_setup(KVecs<V> K, double rtol, int32_t maxit) {
+__global__ void __launch_bounds__(KRY_BLOCK) kry_setup(KVecs<V> K, double rtol, int32_t maxit, int32_t stall) {
+    constexpr int R = VecT<V>::R;
     double acc[1] = {0.0};
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK) {
-        const V b = K.b[i];
-        K.x[i] = V(0); K.r[i] = b; K.rh[i] = b; K.p[i] = b; K.v[i] = V(0);
-        acc[0] += double(b) * double(b);
+    Pack<V> z;
+#pragma unroll
+    for (int j = 0; j < R; ++j) z.v[j] = V(0);
+    KRY_LOOP(K) {
+        const Pack<V> b = ldv(K.b + r0);
+        stv(K.x + r0, z); stv(K.v + r0, z);
+        stv(K.r + r0, b); stv(K.rh + r0, b); stv(K.p + r0, b);
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[0] += double(b.v[j]) * double(b.v[j]);
     }
     double tot[1];
     if (grid_reduce<1>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
         KState &S = *K.st;
-        S.rho = tot[0]; S.rr = tot[0]; S.rr0 = tot[0];
+        S.rho = tot[0]; S.rr = tot[0]; S.rr0 = tot[0]; S.best_rr = tot[0];
         S.tol2 = rtol * rtol * tot[0];
         S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0;
-        S.iter = 0; S.maxit = maxit;
+        S.iter = 0; S.maxit = maxit; S.last_improve = 0; S.stall = stall;
+        S.stall_rr = 4e-6 * tot[0];   // the guard waits for a 500x residual reduction
         S.done = (tot[0] == 0.0) ? K_CONVERGED : (!isfinite(tot[0]) ? K_NONFINITE : K_RUNNING);
     }
 }
@@ -134,14 +239,17 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_setup(KVecs<V> K, double rtol, 
 // v = A p;  alpha = rho / (rh, v)
 template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_v(KVecs<V> K) {
+    constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
-    typename Acc<V>::type a = 0;
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK) {
-        const V y = sell_row(K, i, K.p);
-        K.v[i] = y;
-        a += K.rh[i] * y;
+    DotAcc<V> a;
+    KRY_LOOP(K) {
+        const Pack<V> y = sell_rows(K, r0, K.p);
+        stv(K.v + r0, y);
+        const Pack<V> rh = ldv(K.rh + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) a.add(rh.v[j], y.v[j]);
     }
-    double acc[1] = {double(a)}, tot[1];
+    double acc[1] = {a.value()}, tot[1];
     if (grid_reduce<1>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
         KState &S = *K.st;
         if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
@@ -152,24 +260,32 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_v(KVecs<V> K) {
 // s = r - alpha v
 template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_s(KVecs<V> K) {
+    constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
     const V alpha = V(K.st->alpha);
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK)
-        K.s[i] = K.r[i] - alpha * K.v[i];
+    KRY_LOOP(K) {
+        const Pack<V> r = ldv(K.r + r0), v = ldv(K.v + r0);
+        Pack<V> s;
+#pragma unroll
+        for (int j = 0; j < R; ++j) s.v[j] = r.v[j] - alpha * v.v[j];
+        stv(K.s + r0, s);
+    }
 }
 
 // t = A s;  omega = (t, s) / (t, t)
 template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_t(KVecs<V> K) {
+    constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
-    typename Acc<V>::type ts = 0, tt = 0;
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK) {
-        const V y = sell_row(K, i, K.s);
-        K.t[i] = y;
-        ts += y * K.s[i];
-        tt += y * y;
+    DotAcc<V> ts, tt;
+    KRY_LOOP(K) {
+        const Pack<V> y = sell_rows(K, r0, K.s);
+        stv(K.t + r0, y);
+        const Pack<V> s = ldv(K.s + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) { ts.add(y.v[j], s.v[j]); tt.add(y.v[j], y.v[j]); }
     }
-    double acc[2] = {double(ts), double(tt)}, tot[2];
+    double acc[2] = {ts.value(), tt.value()}, tot[2];
     if (grid_reduce<2>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
         KState &S = *K.st;
         if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
@@ -180,26 +296,35 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_t(KVecs<V> K) {
 // x += alpha p + omega s;  r = s - omega t;  rho' = (rh, r);  beta; convergence test on (r, r)
 template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_x(KVecs<V> K) {
+    constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
     const V alpha = V(K.st->alpha), omega = V(K.st->omega);
-    typename Acc<V>::type rho = 0, rr = 0;
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK) {
-        const V s = K.s[i];
-        K.x[i] += alpha * K.p[i] + omega * s;
-        const V r = s - omega * K.t[i];
-        K.r[i] = r;
-        rho += K.rh[i] * r;
-        rr += r * r;
+    DotAcc<V> rho, rr;
+    KRY_LOOP(K) {
+        const Pack<V> s = ldv(K.s + r0), p = ldv(K.p + r0), t = ldv(K.t + r0), rh = ldv(K.rh + r0);
+        Pack<V> x = ldv(K.x + r0), r;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            x.v[j] += alpha * p.v[j] + omega * s.v[j];
+            r.v[j] = s.v[j] - omega * t.v[j];
+            rho.add(rh.v[j], r.v[j]);
+            rr.add(r.v[j], r.v[j]);
+        }
+        stv(K.x + r0, x);
+        stv(K.r + r0, r);
     }
-    double acc[2] = {double(rho), double(rr)}, tot[2];
+    double acc[2] = {rho.value(), rr.value()}, tot[2];
     if (grid_reduce<2>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
         KState &S = *K.st;
         S.iter += 1;
         S.rr = tot[1];
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
+        if (tot[1] < 0.81 * S.best_rr) { S.best_rr = tot[1]; S.last_improve = S.iter; }
+        // a residual 1e12 times the initial one is a diverged iteration: stop before it overflows
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || tot[1] > 1e24 * S.rr0) S.done = K_NONFINITE;
         else if (tot[1] <= S.tol2) S.done = K_CONVERGED;
         else if (tot[0] == 0.0 || S.omega == 0.0) S.done = K_BREAKDOWN;
         else if (S.iter >= S.maxit) S.done = K_MAXIT;
+        else if (S.stall > 0 && S.best_rr <= S.stall_rr && S.iter - S.last_improve >= S.stall) S.done = K_STAGNATED;
         else {
             S.beta = (tot[0] / S.rho) * (S.alpha / S.omega);
             S.rho = tot[0];
@@ -210,11 +335,19 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_x(KVecs<V> K) {
 // p = r + beta (p - omega v)
 template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_p(KVecs<V> K) {
+    constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
     const V beta = V(K.st->beta), omega = V(K.st->omega);
-    for (int64_t i = int64_t(blockIdx.x) * KRY_BLOCK + threadIdx.x; i < K.n; i += int64_t(gridDim.x) * KRY_BLOCK)
-        K.p[i] = K.r[i] + beta * (K.p[i] - omega * K.v[i]);
+    KRY_LOOP(K) {
+        const Pack<V> r = ldv(K.r + r0), v = ldv(K.v + r0);
+        Pack<V> p = ldv(K.p + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) p.v[j] = r.v[j] + beta * (p.v[j] - omega * v.v[j]);
+        stv(K.p + r0, p);
+    }
 }
+
+#undef KRY_LOOP
 
 // ---------------------------------------------------------------------------------
 // Newton-level helpers
@@ -230,14 +363,15 @@ __global__ void __launch_bounds__(KRY_BLOCK) norm2_free_kernel(int64_t n, const 
     if (grid_reduce<1>(acc, part, ticket, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-// u -= x (Newton update), x in the Krylov type
+// u -= lambda x (Newton update with step length lambda), x in the Krylov type
 template <typename V>
-__global__ void newton_update_kernel(int64_t n, double *u, const V *x) {
+__global__ void newton_update_kernel(int64_t n, double *u, const V *x, double lambda) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) u[i] -= double(x[i]);
+    if (i < n) u[i] -= lambda * double(x[i]);
 }
 
-// CSR values -> Jacobi-scaled SELL operator and scaled right-hand side (egfem_bicgstab)
+// CSR values -> Jacobi-scaled SELL operator and scaled right-hand side (egfem_bicgstab).
+// FP32 operators keep the scaled row sum in column 0 (difference form, see above).
 template <typename V>
 __global__ void csr_to_sell_kernel(int64_t n, const SliceMeta *meta, const int32_t *col_slot, const double *vals,
                                    const double *rhs, V *A, V *b, int32_t *status) {
@@ -249,12 +383,28 @@ __global__ void csr_to_sell_kernel(int64_t n, const SliceMeta *meta, const int32
     double dinv = 0.0;
     if (diag != 0.0) dinv = 1.0 / diag;
     else atomicOr(status, 1);
+    double rs = 0.0;
     for (int c = 0; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int32_t s = col_slot[q];
-        A[q] = V(s >= 0 ? vals[s] * dinv : 0.0);
+        const double a = s >= 0 ? vals[s] * dinv : 0.0;
+        rs += a;
+        A[q] = V(a);
     }
+    if (sizeof(V) == 4) A[M.col_base + lane] = V(rs);
     b[row] = V(rhs[row] * dinv);
+}
+
+// Replace column 0 of a scaled SELL operator by its row sum (FP32 difference form).
+template <typename V>
+__global__ void rowsum_form_kernel(int64_t n, const SliceMeta *meta, V *A) {
+    const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const SliceMeta M = meta[row / SLICE];
+    const int lane = int(row % SLICE);
+    double rs = 0.0;
+    for (int c = 0; c < M.ncol; ++c) rs += double(A[M.col_base + int64_t(c) * SLICE + lane]);
+    A[M.col_base + lane] = V(rs);
 }
 
 // y = J x from CSR values (egfem_spmv)

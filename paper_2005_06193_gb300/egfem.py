@@ -55,14 +55,29 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("krylov_iters", ctypes.c_int64),
                 ("res0", ctypes.c_double), ("res_final", ctypes.c_double), ("res_hist", ctypes.c_double * HIST),
-                ("krylov_hist", ctypes.c_int32 * HIST), ("solve_ms", ctypes.c_double)]
+                ("krylov_hist", ctypes.c_int32 * HIST), ("solve_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("fp64_rescues", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         k = min(self.newton_iters, HIST)
         return {"status": STATUS.get(self.status, self.status), "newton_iters": self.newton_iters,
                 "krylov_iters": int(self.krylov_iters), "res0": self.res0, "res_final": self.res_final,
                 "res_hist": list(self.res_hist[:k]), "krylov_hist": list(self.krylov_hist[:k]),
-                "solve_ms": self.solve_ms}
+                "solve_ms": self.solve_ms, "kernel_launches": int(self.kernel_launches),
+                "fp64_rescues": self.fp64_rescues}
+
+
+PROF_MAX = 8
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("name", (ctypes.c_char * 24) * PROF_MAX), ("ms", ctypes.c_double * PROF_MAX),
+                ("bytes", ctypes.c_double * PROF_MAX), ("flops", ctypes.c_double * PROF_MAX),
+                ("fp64", ctypes.c_int32 * PROF_MAX)]
+
+    def as_list(self) -> list:
+        return [{"name": self.name[k].value.decode(), "ms": self.ms[k], "bytes": self.bytes[k], "flops": self.flops[k],
+                 "fp64": bool(self.fp64[k])} for k in range(self.count)]
 
 
 _lib = None
@@ -96,6 +111,7 @@ def lib() -> ctypes.CDLL:
         "egfem_newton_solve": (S, [_P, _DP, _DP, ctypes.POINTER(Stats), _P]),
         "egfem_adjoint": (S, [_P, _DP, _DP, _DP, _DP, ctypes.POINTER(Stats), _P]),
         "egfem_load_cellwise": (S, [_P, _DP, _DP, _P]),
+        "egfem_profile_kernels": (S, [_P, _DP, _DP, ctypes.c_int32, ctypes.POINTER(Profile), _P]),
         "egfem_load_cellwise_transpose": (S, [_P, _DP, _DP, _P]),
         "egfem_inspect_tensor": (S, [ctypes.POINTER(Mesh), ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_int64),
                                      _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
@@ -276,6 +292,12 @@ class Handle:
                                    _stream(stream)), "egfem_adjoint")
         return st
 
+    def profile_kernels(self, u, d, reps=20, stream=None) -> list:
+        prof = Profile()
+        _check(lib().egfem_profile_kernels(self._h, _ptr(u), _ptr(d), int(reps), ctypes.byref(prof), _stream(stream)),
+               "egfem_profile_kernels")
+        return prof.as_list()
+
     def load_cellwise(self, f, d, stream=None):
         _check(lib().egfem_load_cellwise(self._h, _ptr(f), _ptr(d), _stream(stream)), "egfem_load_cellwise")
         return d
@@ -294,7 +316,7 @@ class _DeviceArray:
     """A raw device allocation exposed through __cuda_array_interface__ (zero copy)."""
 
     def __init__(self, ptr: int, shape: tuple, typestr: str):
-        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), True), "version": 3,
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), False), "version": 3,
                                          "strides": None}
 
 

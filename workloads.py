@@ -119,6 +119,11 @@ def mms_source_cubic(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     return 2.0 * np.pi ** 2 * u * (1.0 + u ** 3) - 3.0 * u * u * (gx * gx + gy * gy)
 
 
+def smooth_source_3d(x: np.ndarray, y: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """A smooth 3D source, 10 sin(pi x) sin(pi y) sin(pi z) (test input for 3D cases)."""
+    return 10.0 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+
+
 # ---------------------------------------------------------------------------
 # Batched workload: 256 instances of -div((1 + u^3) grad u) = f_b, u in P1, w in P3.
 # ---------------------------------------------------------------------------
