@@ -224,6 +224,27 @@ egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const doub
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda,
                            double *d_grad_kappa, egfem_stats *stats, egfem_stream stream);
 
+/* Batched offline phase: count independent instances (meshes of one dimension and any
+ * sizes, one shared problem definition) assembled as one block-diagonal operator.
+ * Instance b owns the rows [offsets[b], offsets[b+1]) of every batch vector (see
+ * egfem_batch_layout); each instance's range is padded to a multiple of 32 rows with
+ * padding rows that belong to no cell and behave as Dirichlet rows (u = d there).  The
+ * single-instance calls (residual, Jacobian, ...) act on the whole batch.  No paper
+ * passage: batching is a serving pattern layered on the method. */
+egfem_status egfem_batch_build(int32_t count, const egfem_mesh *meshes, const egfem_problem *prob,
+                               const egfem_options *opts, egfem_handle *out);
+
+/* Instance count and row offsets ([count + 1], host) of a batch handle. */
+egfem_status egfem_batch_layout(egfem_handle h, int32_t *count, int64_t *offsets);
+
+/* Newton's method for every instance of a batch at once: each BiCGStab kernel launch
+ * serves all instances still iterating (per-instance scalars, convergence and damping);
+ * tile sizes are chosen by timing on the first call.  stats: [count] per-instance
+ * results (may be NULL).  Returns the first non-OK instance status, if any.
+ * Synchronises the stream. */
+egfem_status egfem_batch_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats,
+                                      egfem_stream stream);
+
 /* Load vector of a cellwise constant source: d_i = sum_{K owns i} f_K |K| / (dim + 1)
  * (exact integral of f phi_i), Dirichlet rows set to 0.  d_f[n_cells] in, d_d[n_nodes] out. */
 egfem_status egfem_load_cellwise(egfem_handle h, const double *d_f, double *d_d, egfem_stream stream);

@@ -15,6 +15,7 @@
 #include "egfem_internal.h"
 #include "egfem_kernels.cuh"
 #include "egfem_krylov.cuh"
+#include "egfem_batch.cuh"
 
 using namespace egfem;
 
@@ -99,6 +100,22 @@ struct egfem_t {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int maxc_tpl = 8;
     int64_t last_graph_launches = 0;    // graph launches of the last BiCGStab solve
+    // batch (egfem_batch_build): instance b owns rows [inst_off[b], inst_off[b+1])
+    int32_t nb = 0;
+    std::vector<int64_t> inst_off;
+    int32_t *slice_inst = nullptr;
+    uint8_t *inst_mask = nullptr, *h_mask = nullptr;
+    double *inst_eta = nullptr, *h_eta = nullptr;
+    double *inst_lam = nullptr, *h_lam = nullptr;
+    double *inst_norm2 = nullptr, *h_norm2 = nullptr;
+    KState *bst = nullptr, *h_bst = nullptr;
+    BTile *tiles = nullptr;
+    int64_t ntiles = 0;
+    int tile_factor = 0;                // rows per tile = KRY_BLOCK * R * tile_factor (0: not tuned yet)
+    int tile_R = 0;
+    double *bpart = nullptr;
+    cudaGraphExec_t bgraph64 = nullptr, bgraph32 = nullptr;
+    int bgraph_chunk = 0, bgraph_tiles = 0;
 };
 
 namespace {
@@ -423,6 +440,12 @@ void egfem_destroy(egfem_handle h) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
     }
+    dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
+    dfree(h->bst); dfree(h->tiles); dfree(h->bpart);
+    if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
+    if (h->bgraph32) cudaGraphExecDestroy(h->bgraph32);
+    for (void *q : {(void *)h->h_mask, (void *)h->h_eta, (void *)h->h_lam, (void *)h->h_norm2, (void *)h->h_bst})
+        if (q) cudaFreeHost(q);
     if (h->h_st) cudaFreeHost(h->h_st);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -946,5 +969,379 @@ const char *egfem_status_string(egfem_status s) {
 }
 
 const char *egfem_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batched solves: many instances as one block-diagonal operator (egfem_batch_*)
+// ---------------------------------------------------------------------------------
+
+namespace {
+
+template <typename V>
+egfem_status batch_tiles(egfem_t *h, int factor) {
+    constexpr int R = VecT<V>::R;
+    const int64_t rows = int64_t(KRY_BLOCK) * R * factor;
+    std::vector<BTile> T;
+    for (int32_t b = 0; b < h->nb; ++b) {
+        const int64_t t0 = int64_t(T.size());
+        const int64_t lo = h->inst_off[b], hi = h->inst_off[b + 1];
+        for (int64_t r = lo; r < hi; r += rows) T.push_back(BTile{r, std::min(hi, r + rows), t0, b, 0});
+        for (size_t q = size_t(t0); q < T.size(); ++q) T[q].ntiles_inst = int32_t(T.size() - size_t(t0));
+    }
+    dfree(h->tiles);
+    dfree(h->bpart);
+    EG_TRY(upload(h->tiles, T));
+    h->ntiles = int64_t(T.size());
+    EG_TRY(dalloc(h->bpart, size_t(2 * h->ntiles)));
+    h->tile_factor = factor;
+    h->tile_R = R;
+    if (h->bgraph64) { cudaGraphExecDestroy(h->bgraph64); h->bgraph64 = nullptr; }
+    if (h->bgraph32) { cudaGraphExecDestroy(h->bgraph32); h->bgraph32 = nullptr; }
+    return EGFEM_OK;
+}
+
+template <typename V>
+KBatch<V> kbatch(egfem_t *h, KWork<V> &W) {
+    KBatch<V> B{};
+    B.K = kvecs(h, W);
+    B.tiles = h->tiles; B.ntiles = h->ntiles; B.st = h->bst; B.part = h->bpart;
+    return B;
+}
+
+template <typename V>
+int bgrid(const egfem_t *h) { return int(std::max<int64_t>(1, std::min<int64_t>(h->ntiles, int64_t(h->sms) * 8))); }
+
+template <typename V>
+void enqueue_batch_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
+    const KBatch<V> B = kbatch(h, W);
+    const int g = bgrid<V>(h);
+    for (int it = 0; it < count; ++it) {
+        kb_v<V><<<g, KRY_BLOCK, 0, s>>>(B);
+        kb_s<V><<<g, KRY_BLOCK, 0, s>>>(B);
+        kb_t<V><<<g, KRY_BLOCK, 0, s>>>(B);
+        kb_x<V><<<g, KRY_BLOCK, 0, s>>>(B);
+        kb_p<V><<<g, KRY_BLOCK, 0, s>>>(B);
+    }
+}
+
+template <typename V>
+egfem_status batch_graph(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G) {
+    const int chunk = std::max(1, h->opts.graph_chunk);
+    if (G && h->bgraph_chunk == chunk) return EGFEM_OK;
+    if (G) { cudaGraphExecDestroy(G); G = nullptr; }
+    cudaGraph_t g;
+    EG_CUDA(cudaStreamBeginCapture(h->hs, cudaStreamCaptureModeThreadLocal));
+    enqueue_batch_iterations(h, W, chunk, h->hs);
+    EG_CUDA(cudaStreamEndCapture(h->hs, &g));
+    cudaError_t e = cudaGraphInstantiate(&G, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { g_last_error = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e); return EGFEM_ERR_CUDA; }
+    h->bgraph_chunk = chunk;
+    return EGFEM_OK;
+}
+
+// BiCGStab for every instance with h_mask set (tolerance h_eta), all in one launch per
+// kernel; returns with h_bst holding every instance's final state.
+template <typename V>
+egfem_status run_batch_bicgstab(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G, int32_t stall, int64_t *launches) {
+    EG_TRY(batch_graph(h, W, G));
+    EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(h->nb), cudaMemcpyHostToDevice, h->hs));
+    EG_CUDA(cudaMemcpyAsync(h->inst_eta, h->h_eta, size_t(h->nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
+    kb_init_state<<<(h->nb + 127) / 128, 128, 0, h->hs>>>(h->nb, h->bst, h->inst_mask, h->inst_eta, h->opts.krylov_maxit, stall);
+    const KBatch<V> B = kbatch(h, W);
+    kb_setup<V><<<bgrid<V>(h), KRY_BLOCK, 0, h->hs>>>(B);
+    EG_CUDA(cudaGetLastError());
+    *launches += 2;
+    for (;;) {
+        EG_CUDA(cudaMemcpyAsync(h->h_bst, h->bst, size_t(h->nb) * sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        EG_CUDA(cudaStreamSynchronize(h->hs));
+        bool running = false;
+        for (int32_t b = 0; b < h->nb && !running; ++b) running = h->h_bst[b].done == K_RUNNING;
+        if (!running) break;
+        EG_CUDA(cudaGraphLaunch(G, h->hs));
+        *launches += 5 * int64_t(std::max(1, h->opts.graph_chunk));
+    }
+    return EGFEM_OK;
+}
+
+// Time a few batched BiCGStab iterations for each tile size and keep the fastest
+// (the project's autotuner; it runs once per handle, on the first batched solve).
+template <typename V>
+egfem_status autotune_tiles(egfem_t *h, KWork<V> &W) {
+    cudaEvent_t e0, e1;
+    EG_CUDA(cudaEventCreate(&e0));
+    EG_CUDA(cudaEventCreate(&e1));
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int f : {1, 2, 4, 8}) {
+        EG_TRY(batch_tiles<V>(h, f));
+        for (int32_t b = 0; b < h->nb; ++b) { h->h_mask[b] = 1; h->h_eta[b] = 0.0; }
+        int64_t dummy = 0;
+        EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(h->nb), cudaMemcpyHostToDevice, h->hs));
+        EG_CUDA(cudaMemcpyAsync(h->inst_eta, h->h_eta, size_t(h->nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
+        kb_init_state<<<(h->nb + 127) / 128, 128, 0, h->hs>>>(h->nb, h->bst, h->inst_mask, h->inst_eta, 1 << 30, 0);
+        const KBatch<V> B = kbatch(h, W);
+        kb_setup<V><<<bgrid<V>(h), KRY_BLOCK, 0, h->hs>>>(B);
+        enqueue_batch_iterations(h, W, 2, h->hs);   // warm
+        EG_CUDA(cudaEventRecord(e0, h->hs));
+        enqueue_batch_iterations(h, W, 6, h->hs);
+        EG_CUDA(cudaEventRecord(e1, h->hs));
+        EG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        EG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        (void)dummy;
+        if (ms < best_ms) { best_ms = ms; best = f; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return batch_tiles<V>(h, best);
+}
+
+egfem_status batch_norms(egfem_t *h) {
+    kb_norm2<<<int(std::max<int64_t>(1, std::min<int64_t>(h->ntiles, int64_t(h->sms) * 8))), KRY_BLOCK, 0, h->hs>>>(
+        h->ntiles, h->tiles, h->bst, h->bpart, h->r, h->csf.dir, h->n, h->inst_norm2);
+    EG_CUDA(cudaGetLastError());
+    EG_CUDA(cudaMemcpyAsync(h->h_norm2, h->inst_norm2, size_t(h->nb) * sizeof(double), cudaMemcpyDeviceToHost, h->hs));
+    EG_CUDA(cudaStreamSynchronize(h->hs));
+    return EGFEM_OK;
+}
+
+egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stats *stats) {
+    const int nb = h->nb;
+    const bool mixed = h->opts.precision == EGFEM_PREC_MIXED;
+    EG_TRY(kwork_alloc(h, h->k64));
+    if (mixed) EG_TRY(kwork_alloc(h, h->k32));
+    if (!h->tile_factor) {
+        // tune on the operator at the initial state
+        CsfArgs A0 = csf_args(h, d_u, d_d);
+        A0.r = h->r; A0.a64 = h->k64.A; A0.q64 = h->k64.b;
+        if (mixed) { A0.a32 = h->k32.A; A0.q32 = h->k32.b; }
+        launch_csf(h, A0, h->hs);
+        if (mixed) EG_TRY(autotune_tiles<float>(h, h->k32));
+        else EG_TRY(autotune_tiles<double>(h, h->k64));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<egfem_stats> S(nb);
+    for (auto &x : S) std::memset(&x, 0, sizeof(x));
+    std::vector<double> rn(nb), rprev(nb), rbefore(nb), target(nb), eta(nb, h->opts.eta_max), lam(nb, 1.0);
+    std::vector<int> active(nb, 0), fp32(nb, 0), pending(nb, 0);
+    std::vector<int32_t> st(nb, EGFEM_OK);
+    int64_t launches = 0;
+    // evaluate residual/operator for instances with mask m
+    auto eval = [&](const std::vector<int> &m) -> egfem_status {
+        for (int b = 0; b < nb; ++b) h->h_mask[b] = uint8_t(m[b]);
+        EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
+        CsfArgs A = csf_args(h, d_u, d_d);
+        A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
+        if (mixed) { A.a32 = h->k32.A; A.q32 = h->k32.b; }
+        A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
+        launch_csf(h, A, h->hs);
+        EG_CUDA(cudaGetLastError());
+        EG_TRY(batch_norms(h));
+        launches += 2;
+        for (int b = 0; b < nb; ++b) if (m[b]) rn[b] = std::sqrt(h->h_norm2[b]);
+        return EGFEM_OK;
+    };
+    // u -= lam_b x_b for instances with mask m, x from the FP32 (p32) or FP64 workspace
+    auto update = [&](const std::vector<int> &m, const std::vector<double> &l, bool p32) -> egfem_status {
+        for (int b = 0; b < nb; ++b) { h->h_mask[b] = uint8_t(m[b]); h->h_lam[b] = l[b]; }
+        EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
+        EG_CUDA(cudaMemcpyAsync(h->inst_lam, h->h_lam, size_t(nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
+        const unsigned g = unsigned((h->n + 255) / 256);
+        if (p32) kb_update<float><<<g, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, h->k32.x);
+        else kb_update<double><<<g, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, h->k64.x);
+        EG_CUDA(cudaGetLastError());
+        ++launches;
+        return EGFEM_OK;
+    };
+    std::vector<int> all(nb, 1);
+    EG_TRY(eval(all));
+    for (int b = 0; b < nb; ++b) {
+        S[b].res0 = rn[b];
+        target[b] = std::max(h->opts.newton_rtol * rn[b], h->opts.newton_atol);
+        rprev[b] = rn[b];
+    }
+    for (int step = 0; step <= h->opts.newton_maxit; ++step) {
+        bool any = false;
+        for (int b = 0; b < nb; ++b) {
+            active[b] = 0;
+            if (st[b] != EGFEM_OK) continue;
+            if (!std::isfinite(rn[b])) { st[b] = EGFEM_ERR_NONFINITE; continue; }
+            if (rn[b] <= target[b]) continue;
+            if (S[b].newton_iters >= h->opts.newton_maxit) { st[b] = EGFEM_ERR_NOT_CONVERGED; continue; }
+            active[b] = 1;
+            any = true;
+            if (S[b].newton_iters > 0 && !h->opts.fixed_eta) {
+                double e = 0.9 * (rn[b] / rprev[b]) * (rn[b] / rprev[b]);
+                const double sg = 0.9 * eta[b] * eta[b];
+                if (sg > 0.1) e = std::max(e, sg);
+                eta[b] = std::max(std::min(h->opts.eta_max, e), 0.5 * target[b] / rn[b]);
+            }
+            eta[b] = std::max(eta[b], h->opts.eta_min);
+            fp32[b] = mixed ? 1 : 0;
+            rbefore[b] = rn[b];
+        }
+        if (!any) break;
+        // up to two passes: FP32 for the mixed path, then FP64 for the instances it failed
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool p32 = mixed && pass == 0;
+            bool todo = false;
+            for (int b = 0; b < nb; ++b) {
+                pending[b] = active[b] && (fp32[b] == (p32 ? 1 : 0));
+                h->h_mask[b] = uint8_t(pending[b]);
+                h->h_eta[b] = p32 ? std::max(eta[b], kMixedEtaFloor) : eta[b];
+                todo = todo || pending[b];
+            }
+            if (!todo) continue;
+            if (p32) EG_TRY(run_batch_bicgstab(h, h->k32, h->bgraph32, kMixedStall, &launches));
+            else EG_TRY(run_batch_bicgstab(h, h->k64, h->bgraph64, 0, &launches));
+            std::vector<int> ok(nb, 0);
+            for (int b = 0; b < nb; ++b) {
+                if (!pending[b]) continue;
+                const KState &K = h->h_bst[b];
+                S[b].krylov_iters += K.iter;
+                if (S[b].newton_iters < EGFEM_HIST) S[b].krylov_hist[S[b].newton_iters] += K.iter;
+                const bool failed = K.done == K_NONFINITE || K.done == K_BREAKDOWN;
+                if (failed) {
+                    if (p32) { fp32[b] = 0; ++S[b].fp64_rescues; }
+                    else { st[b] = K.done == K_NONFINITE ? EGFEM_ERR_NONFINITE : EGFEM_ERR_BREAKDOWN; active[b] = 0; }
+                    continue;
+                }
+                ok[b] = 1;
+                lam[b] = 1.0;
+            }
+            EG_TRY(update(ok, lam, p32));
+            EG_TRY(eval(ok));
+            // damping: halve the step of every instance whose residual fails the Armijo test
+            for (int bt = 0; bt < 6; ++bt) {
+                std::vector<int> bad(nb, 0);
+                std::vector<double> dl(nb, 0.0);
+                bool anybad = false;
+                for (int b = 0; b < nb; ++b)
+                    if (ok[b] && !(rn[b] <= (1.0 - 1e-4 * lam[b]) * rbefore[b])) { bad[b] = 1; dl[b] = -0.5 * lam[b]; anybad = true; }
+                if (!anybad) break;
+                EG_TRY(update(bad, dl, p32));
+                for (int b = 0; b < nb; ++b) if (bad[b]) lam[b] *= 0.5;
+                EG_TRY(eval(bad));
+            }
+            std::vector<int> undo(nb, 0);
+            bool anyundo = false;
+            for (int b = 0; b < nb; ++b) {
+                if (!ok[b]) continue;
+                if (rn[b] < rbefore[b]) {
+                    ++S[b].newton_iters;
+                    if (S[b].newton_iters - 1 < EGFEM_HIST) S[b].res_hist[S[b].newton_iters - 1] = rn[b];
+                    rprev[b] = rbefore[b];
+                    active[b] = 0;   // stepped
+                    continue;
+                }
+                undo[b] = 1;
+                anyundo = true;
+            }
+            if (anyundo) {
+                // no step length decreased the residual: step back by the applied length
+                std::vector<double> back(nb, 0.0);
+                for (int b = 0; b < nb; ++b) back[b] = -lam[b];
+                EG_TRY(update(undo, back, p32));
+                EG_TRY(eval(undo));
+                for (int b = 0; b < nb; ++b) {
+                    if (!undo[b]) continue;
+                    if (p32) { fp32[b] = 0; ++S[b].fp64_rescues; }
+                    else { st[b] = EGFEM_ERR_NOT_CONVERGED; active[b] = 0; }
+                }
+            }
+        }
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    egfem_status worst = EGFEM_OK;
+    for (int b = 0; b < nb; ++b) {
+        if (st[b] == EGFEM_OK && !(rn[b] <= target[b])) st[b] = EGFEM_ERR_NOT_CONVERGED;
+        S[b].status = st[b];
+        S[b].res_final = rn[b];
+        S[b].solve_ms = ms;
+        S[b].kernel_launches = launches;
+        if (st[b] != EGFEM_OK && worst == EGFEM_OK) worst = egfem_status(st[b]);
+    }
+    if (stats) std::memcpy(stats, S.data(), sizeof(egfem_stats) * size_t(nb));
+    return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+egfem_status egfem_batch_build(int32_t count, const egfem_mesh *meshes, const egfem_problem *prob, const egfem_options *opts,
+                               egfem_handle *out) {
+    if (count < 1 || !meshes || !prob || !out) { g_last_error = "bad batch arguments"; return EGFEM_ERR_INVALID_ARG; }
+    try {
+        const int32_t dim = meshes[0].dim;
+        std::vector<int64_t> off(size_t(count) + 1, 0), coff(size_t(count) + 1, 0);
+        for (int32_t b = 0; b < count; ++b) {
+            const egfem_mesh &m = meshes[b];
+            if (m.dim != dim) { g_last_error = "all batch meshes must share one dimension"; return EGFEM_ERR_INVALID_ARG; }
+            std::string err;
+            egfem_status st = validate_mesh(m, err);
+            if (st != EGFEM_OK) { g_last_error = "instance " + std::to_string(b) + ": " + err; return st; }
+            off[b + 1] = off[b] + (m.n_nodes + SLICE - 1) / SLICE * SLICE;
+            coff[b + 1] = coff[b] + m.n_cells;
+        }
+        const int64_t N = off[count], C = coff[count];
+        if (N >= (int64_t(1) << 31) - 1) { g_last_error = "batch too large for int32 node indices"; return EGFEM_ERR_INVALID_ARG; }
+        // disjoint union; the padding nodes of each instance belong to no cell and are Dirichlet
+        std::vector<double> X(size_t(N) * dim, 0.0);
+        std::vector<int32_t> cells(size_t(C) * (dim + 1));
+        std::vector<uint8_t> dir(size_t(N), 1);
+        for (int32_t b = 0; b < count; ++b) {
+            const egfem_mesh &m = meshes[b];
+            std::memcpy(&X[size_t(off[b]) * dim], m.coords, sizeof(double) * size_t(m.n_nodes) * dim);
+            for (int64_t v = 0; v < m.n_nodes; ++v) dir[size_t(off[b] + v)] = m.dirichlet ? (m.dirichlet[v] ? 1 : 0) : 0;
+            for (int64_t c = 0; c < m.n_cells * (dim + 1); ++c) cells[size_t(coff[b] * (dim + 1) + c)] = int32_t(m.cells[c] + off[b]);
+        }
+        egfem_mesh U{dim, N, C, X.data(), cells.data(), dir.data()};
+        egfem_status st = build_impl(&U, prob, opts, out);
+        if (st != EGFEM_OK) return st;
+        egfem_t *h = *out;
+        h->nb = count;
+        h->inst_off = off;
+        std::vector<int32_t> si(size_t(h->csf.n_slices));
+        for (int32_t b = 0; b < count; ++b)
+            for (int64_t sl = off[b] / SLICE; sl < off[b + 1] / SLICE; ++sl) si[size_t(sl)] = b;
+        auto fail = [&](egfem_status e) { egfem_destroy(h); *out = nullptr; return e; };
+        if ((st = upload(h->slice_inst, si)) != EGFEM_OK) return fail(st);
+        if ((st = dalloc(h->inst_mask, size_t(count))) != EGFEM_OK) return fail(st);
+        if ((st = dalloc(h->inst_eta, size_t(count))) != EGFEM_OK) return fail(st);
+        if ((st = dalloc(h->inst_lam, size_t(count))) != EGFEM_OK) return fail(st);
+        if ((st = dalloc(h->inst_norm2, size_t(count))) != EGFEM_OK) return fail(st);
+        if ((st = dalloc(h->bst, size_t(count))) != EGFEM_OK) return fail(st);
+        if (cudaMemset(h->bst, 0, sizeof(KState) * size_t(count)) != cudaSuccess) return fail(EGFEM_ERR_CUDA);
+        if (cudaMallocHost((void **)&h->h_mask, size_t(count)) != cudaSuccess ||
+            cudaMallocHost((void **)&h->h_eta, sizeof(double) * size_t(count)) != cudaSuccess ||
+            cudaMallocHost((void **)&h->h_lam, sizeof(double) * size_t(count)) != cudaSuccess ||
+            cudaMallocHost((void **)&h->h_norm2, sizeof(double) * size_t(count)) != cudaSuccess ||
+            cudaMallocHost((void **)&h->h_bst, sizeof(KState) * size_t(count)) != cudaSuccess)
+            return fail(EGFEM_ERR_OOM);
+        return EGFEM_OK;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return EGFEM_ERR_OOM;
+    }
+}
+
+egfem_status egfem_batch_layout(egfem_handle h, int32_t *count, int64_t *offsets) {
+    if (!h) return EGFEM_ERR_INVALID_ARG;
+    if (count) *count = h->nb;
+    if (offsets) std::memcpy(offsets, h->inst_off.data(), sizeof(int64_t) * h->inst_off.size());
+    return EGFEM_OK;
+}
+
+egfem_status egfem_batch_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats, egfem_stream stream) {
+    if (!h || !d_u || !d_d || h->nb < 1) return EGFEM_ERR_INVALID_ARG;
+    EG_CUDA(cudaSetDevice(h->device));
+    EG_TRY(join_in(h, (cudaStream_t)stream));
+    egfem_status st = batch_newton(h, d_u, d_d, stats);
+    egfem_status js = join_out(h, (cudaStream_t)stream);
+    return st != EGFEM_OK ? st : js;
+}
 
 }  // extern "C"

@@ -40,6 +40,8 @@ struct CsfArgs {
     float *q32;            // D r (nullable)
     double *jsell;         // unscaled J in SELL order (nullable)
     double *dinv;          // 1 / J_ii (nullable)
+    const int32_t *slice_inst;   // batch: instance of each slice (nullable)
+    const uint8_t *inst_mask;    // batch: rows of instances with mask 0 are skipped (nullable)
     int32_t *status;       // error word (singular diagonal)
 };
 
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     if (row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     const int lane = int(row % SLICE);
+    if (A.inst_mask && !A.inst_mask[A.slice_inst[sl]]) return;
     const SliceMeta M = A.meta[sl];
     const double ui = A.u[row];
     const double di = A.d ? A.d[row] : 0.0;

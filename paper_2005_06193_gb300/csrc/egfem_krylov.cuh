@@ -319,8 +319,10 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_x(KVecs<V> K) {
         S.iter += 1;
         S.rr = tot[1];
         if (tot[1] < 0.81 * S.best_rr) { S.best_rr = tot[1]; S.last_improve = S.iter; }
-        // a residual 1e12 times the initial one is a diverged iteration: stop before it overflows
-        if (!isfinite(tot[0]) || !isfinite(tot[1]) || tot[1] > 1e24 * S.rr0) S.done = K_NONFINITE;
+        // a diverged iteration stops before it overflows; a guarded (FP32) solve gives up
+        // once its residual is 1000 times the initial one
+        const double blowup = S.stall > 0 ? 1e6 : 1e24;
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || tot[1] > blowup * S.rr0) S.done = K_NONFINITE;
         else if (tot[1] <= S.tol2) S.done = K_CONVERGED;
         else if (tot[0] == 0.0 || S.omega == 0.0) S.done = K_BREAKDOWN;
         else if (S.iter >= S.maxit) S.done = K_MAXIT;

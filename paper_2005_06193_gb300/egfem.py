@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
         "egfem_newton_solve": (S, [_P, _DP, _DP, ctypes.POINTER(Stats), _P]),
         "egfem_adjoint": (S, [_P, _DP, _DP, _DP, _DP, ctypes.POINTER(Stats), _P]),
         "egfem_load_cellwise": (S, [_P, _DP, _DP, _P]),
+        "egfem_batch_build": (S, [ctypes.c_int32, ctypes.POINTER(Mesh), ctypes.POINTER(Problem), ctypes.POINTER(Options),
+                                  ctypes.POINTER(_P)]),
+        "egfem_batch_layout": (S, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+        "egfem_batch_newton_solve": (S, [_P, _DP, _DP, _P, _P]),
         "egfem_profile_kernels": (S, [_P, _DP, _DP, ctypes.c_int32, ctypes.POINTER(Profile), _P]),
         "egfem_load_cellwise_transpose": (S, [_P, _DP, _DP, _P]),
         "egfem_inspect_tensor": (S, [ctypes.POINTER(Mesh), ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_int64),
@@ -323,3 +327,56 @@ class _DeviceArray:
 def _wrap_device(ptr: int, shape: tuple, typestr: str):
     import torch
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+class BatchHandle(Handle):
+    """Many instances as one block-diagonal operator (egfem_batch_build).  Instance b
+    owns rows offsets[b]:offsets[b+1] of every batch vector (padded to 32 rows)."""
+
+    def __init__(self, meshes, problem: Problem, options: Options | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("egfem: a CUDA device is required (no CPU fallback)")
+        structs, keep = [], []
+        for m in meshes:
+            st, k = _mesh_struct(m)
+            structs.append(st)
+            keep.append(k)
+        arr = (Mesh * len(structs))(*structs)
+        self._h = _P()
+        self.options = options or default_options()
+        _check(lib().egfem_batch_build(len(structs), arr, ctypes.byref(problem), ctypes.byref(self.options),
+                                       ctypes.byref(self._h)), "egfem_batch_build")
+        del keep
+        self.problem = problem
+        self.dim = meshes[0].dim
+        vals = [ctypes.c_int64() for _ in range(5)]
+        _check(lib().egfem_sizes(self._h, *[ctypes.byref(v) for v in vals]), "egfem_sizes")
+        self.sizes = Sizes(*[v.value for v in vals])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        cnt = ctypes.c_int32(0)
+        _check(lib().egfem_batch_layout(self._h, ctypes.byref(cnt), None), "egfem_batch_layout")
+        off = np.zeros(cnt.value + 1, dtype=np.int64)
+        _check(lib().egfem_batch_layout(self._h, ctypes.byref(cnt), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "egfem_batch_layout")
+        self.count = cnt.value
+        self.offsets = off
+
+    def scatter(self, parts, dtype=None):
+        """Concatenate per-instance host arrays into one padded batch tensor on the device."""
+        import torch
+        out = np.zeros(self.offsets[-1])
+        for b, p in enumerate(parts):
+            out[self.offsets[b]:self.offsets[b] + len(p)] = p
+        return torch.tensor(out, device=self.device, dtype=dtype or torch.float64)
+
+    def gather(self, t, sizes):
+        a = t.detach().cpu().numpy()
+        return [a[self.offsets[b]:self.offsets[b] + sizes[b]] for b in range(self.count)]
+
+    def batch_newton_solve(self, u, d, stream=None, check=True):
+        st = (Stats * self.count)()
+        status = lib().egfem_batch_newton_solve(self._h, _ptr(u), _ptr(d), st, _stream(stream))
+        if check:
+            _check(status, "egfem_batch_newton_solve")
+        return list(st)
