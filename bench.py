@@ -114,7 +114,7 @@ def make_workload(n):
 # CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(n, newton_steps, krylov_iters, strip_rows=None, kry_sample=40):
+def oracle_sample(n, newton_steps, krylov_iters, strip_rows=None, kry_sample=60):
     """Seconds per Newton solve of the FP64 oracle on the n x n workload, estimated from a
     strip of the grid: time the oracle's residual, Jacobian and BiCGStab iterations on the
     strip's rows and scale by (all rows / strip rows) and by the Newton and Krylov
@@ -122,7 +122,7 @@ def oracle_sample(n, newton_steps, krylov_iters, strip_rows=None, kry_sample=40)
     import oracle
     import workloads as wl
     full = wl.unit_square_mesh(n)
-    rows = strip_rows or max(4, n // 16)
+    rows = strip_rows or max(4, n // 4)
     keep = np.where(wl.cell_centroids(full)[:, 1] < rows / n)[0]
     cells = full.cells[keep]
     nodes = np.unique(cells)

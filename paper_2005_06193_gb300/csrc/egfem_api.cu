@@ -59,6 +59,9 @@ struct KWork {
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
+    // grid of each iteration kernel: one wave of resident blocks (occupancy x SMs), capped
+    // by the work, so the grid-stride loops run without a tail wave
+    int g_setup = 1, g_v = 1, g_s = 1, g_t = 1, g_x = 1, g_p = 1;
 };
 
 }  // namespace
@@ -167,15 +170,29 @@ int kgrid_of(const egfem_t *h) { return sizeof(V) == 8 ? h->kgrid64 : h->kgrid32
 template <typename V>
 KVecs<V> kvecs(egfem_t *h, KWork<V> &W) {
     KVecs<V> K{};
-    K.n_pad = h->n_pad; K.meta = h->csf.meta; K.col_idx = h->csf.col_idx; K.A = W.A;
+    K.n_pad = h->n_pad; K.meta = h->csf.meta; K.col_idx = h->csf.col_idx; K.slice_off = h->csf.slice_off; K.A = W.A;
     K.x = W.x; K.r = W.r; K.rh = W.rh; K.p = W.p; K.v = W.v; K.s = W.s; K.t = W.t; K.b = W.b;
     K.st = h->st; K.part = h->part;
     return K;
 }
 
 template <typename V>
+int one_wave(const egfem_t *h, const void *func) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, KRY_BLOCK, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int64_t work = (h->n_pad + int64_t(KRY_BLOCK) * VecT<V>::R - 1) / (int64_t(KRY_BLOCK) * VecT<V>::R);
+    return int(std::max<int64_t>(1, std::min<int64_t>(work, int64_t(nb) * h->sms)));
+}
+
+template <typename V>
 egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     if (W.ready) return EGFEM_OK;
+    W.g_setup = one_wave<V>(h, (const void *)kry_setup<V>);
+    W.g_v = one_wave<V>(h, (const void *)kry_v<V>);
+    W.g_s = one_wave<V>(h, (const void *)kry_s<V>);
+    W.g_t = one_wave<V>(h, (const void *)kry_t<V>);
+    W.g_x = one_wave<V>(h, (const void *)kry_x<V>);
+    W.g_p = one_wave<V>(h, (const void *)kry_p<V>);
     EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
     EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V)));
     V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t};
@@ -187,13 +204,12 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
 template <typename V>
 void enqueue_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
     KVecs<V> K = kvecs(h, W);
-    const int g = kgrid_of<V>(h);
     for (int it = 0; it < count; ++it) {
-        kry_v<V><<<g, KRY_BLOCK, 0, s>>>(K);
-        kry_s<V><<<g, KRY_BLOCK, 0, s>>>(K);
-        kry_t<V><<<g, KRY_BLOCK, 0, s>>>(K);
-        kry_x<V><<<g, KRY_BLOCK, 0, s>>>(K);
-        kry_p<V><<<g, KRY_BLOCK, 0, s>>>(K);
+        kry_v<V><<<W.g_v, KRY_BLOCK, 0, s>>>(K);
+        kry_s<V><<<W.g_s, KRY_BLOCK, 0, s>>>(K);
+        kry_t<V><<<W.g_t, KRY_BLOCK, 0, s>>>(K);
+        kry_x<V><<<W.g_x, KRY_BLOCK, 0, s>>>(K);
+        kry_p<V><<<W.g_p, KRY_BLOCK, 0, s>>>(K);
     }
 }
 
@@ -220,7 +236,7 @@ egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, i
                           int32_t *iters) {
     EG_TRY(ensure_graph(h, W));
     KVecs<V> K = kvecs(h, W);
-    kry_setup<V><<<kgrid_of<V>(h), KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit, stall);
+    kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit, stall);
     EG_CUDA(cudaGetLastError());
     h->last_graph_launches = 0;
     for (;;) {
@@ -333,6 +349,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     D.n_fibres = int64_t(H.fib_info.size()); D.n_rx = int64_t(H.rx_val.size()); D.nnz = H.rowptr.back();
     EG_TRY(upload(D.meta, H.meta));
     EG_TRY(upload(D.col_idx, H.col_idx)); EG_TRY(upload(D.col_slot, H.col_slot));
+    EG_TRY(upload(D.slice_off, H.slice_off.empty() ? std::vector<int32_t>(1, 0) : H.slice_off));
+    for (const SliceMeta &M : H.meta) D.n_uniform += M.off_base >= 0;
     EG_TRY(upload(D.leaf_val, H.leaf_val)); EG_TRY(upload(D.leaf_col, H.leaf_col));
     EG_TRY(upload(D.fib_info, H.fib_info)); EG_TRY(upload(D.fib_tdiag, H.fib_tdiag)); EG_TRY(upload(D.fib_m, H.fib_m));
     EG_TRY(upload(D.rx_val, H.rx_val)); EG_TRY(upload(D.rx_info, H.rx_info)); EG_TRY(upload(D.rx_m, H.rx_m));
@@ -374,7 +392,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     h->kgrid64 = grid_for(KRY_BLOCK * VecT<double>::R);
     h->kgrid32 = grid_for(KRY_BLOCK * VecT<float>::R);
     EG_TRY(dalloc(h->r, size_t(h->n)));
-    EG_TRY(dalloc(h->part, size_t(4 * std::max(h->kgrid, std::max(h->kgrid64, h->kgrid32)))));
+    EG_TRY(dalloc(h->part, size_t(2 * std::max<int64_t>(int64_t(h->sms) * 8, std::max(h->kgrid, std::max(h->kgrid64, h->kgrid32))))));
     EG_TRY(dalloc(h->scal, 8));
     EG_TRY(dalloc(h->ticket, 1)); EG_CUDA(cudaMemset(h->ticket, 0, sizeof(uint32_t)));
     EG_TRY(dalloc(h->status, 1)); EG_CUDA(cudaMemset(h->status, 0, sizeof(int32_t)));
@@ -426,7 +444,7 @@ void egfem_destroy(egfem_handle h) {
     cudaSetDevice(h->device);
     if (h->hs) cudaStreamSynchronize(h->hs);
     DeviceCSF &D = h->csf;
-    dfree(D.meta); dfree(D.col_idx); dfree(D.col_slot); dfree(D.leaf_val); dfree(D.leaf_col);
+    dfree(D.meta); dfree(D.col_idx); dfree(D.col_slot); dfree(D.slice_off); dfree(D.leaf_val); dfree(D.leaf_col);
     dfree(D.fib_info); dfree(D.fib_tdiag); dfree(D.fib_m); dfree(D.rx_val); dfree(D.rx_info); dfree(D.rx_m);
     dfree(D.dir); dfree(D.rowptr); dfree(D.cols);
     dfree(h->tmap); dfree(h->wa_kind); dfree(h->wa_sup); dfree(h->cell_verts); dfree(h->cell_vol);
@@ -874,12 +892,11 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     const double csf_flops = L * 4 + F * 12 + RX * 10 + CE * 2;
     EG_TRY(timeit("csf_fused", csf_bytes, csf_flops, 1, [&] { launch_csf(h, A, h->hs); }));
     KVecs<V> K = kvecs(h, W);
-    const int kg = kgrid_of<V>(h);
-    kry_setup<V><<<kg, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
+    kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
     enqueue_iterations(h, W, 1, h->hs);
     EG_CUDA(cudaGetLastError());
     const int fp = std::is_same<V, double>::value ? 1 : 0;
-    auto run = [&](const char *name, double bytes, double flops, auto kern) -> egfem_status {
+    auto run = [&](const char *name, double bytes, double flops, auto kern, int kg) -> egfem_status {
         EG_CUDA(cudaMemsetAsync(&h->st->done, 0, sizeof(int32_t), h->hs));
         EG_TRY(timeit(name, bytes, flops, fp, [&] { kern<<<kg, KRY_BLOCK, 0, h->hs>>>(K); }));
         int32_t done = 0;
@@ -887,11 +904,18 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         if (done != K_RUNNING) out->ms[out->count - 1] = NAN;
         return EGFEM_OK;
     };
-    EG_TRY(run("kry_v", CE * (vb + 4) + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>));
-    EG_TRY(run("kry_s", 3 * N * vb, 2 * N, kry_s<V>));
-    EG_TRY(run("kry_t", CE * (vb + 4) + 2 * N * vb + SM, 2 * CE + 4 * N, kry_t<V>));
-    EG_TRY(run("kry_x", 7 * N * vb, 10 * N, kry_x<V>));
-    EG_TRY(run("kry_p", 4 * N * vb, 4 * N, kry_p<V>));
+    // column indices are read only in non-uniform slices
+    double ce_nonuni = 0;
+    {
+        std::vector<SliceMeta> hm(size_t(h->csf.n_slices));
+        EG_CUDA(cudaMemcpy(hm.data(), h->csf.meta, hm.size() * sizeof(SliceMeta), cudaMemcpyDeviceToHost));
+        for (const SliceMeta &M : hm) if (M.off_base < 0) ce_nonuni += double(M.ncol) * SLICE;
+    }
+    EG_TRY(run("kry_v", CE * vb + ce_nonuni * 4 + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>, W.g_v));
+    EG_TRY(run("kry_s", 3 * N * vb, 2 * N, kry_s<V>, W.g_s));
+    EG_TRY(run("kry_t", CE * vb + ce_nonuni * 4 + 2 * N * vb + SM, 2 * CE + 4 * N, kry_t<V>, W.g_t));
+    EG_TRY(run("kry_x", 7 * N * vb, 10 * N, kry_x<V>, W.g_x));
+    EG_TRY(run("kry_p", 4 * N * vb, 4 * N, kry_p<V>, W.g_p));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return join_out(h, user);

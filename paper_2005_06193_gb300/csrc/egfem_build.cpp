@@ -388,6 +388,7 @@ egfem_status build_csf(const egfem_mesh &m, const egfem_problem &prob, const Hos
         RowOut rows[SLICE];
         for (int32_t s = s0; s < s1; ++s) {
             SliceMeta M{};
+            M.off_base = -1;
             M.col_base = int64_t(C.col_idx.size()); M.leaf_base = int64_t(C.leaf_val.size());
             M.fib_base = int64_t(C.fib_info.size()); M.rx_base = int64_t(C.rx_val.size());
             for (int r = 0; r < SLICE; ++r) {
@@ -463,6 +464,22 @@ egfem_status build_csf(const egfem_mesh &m, const egfem_problem &prob, const Hos
         C = Chunk();
     }
     if (int64_t(out.rowptr[n]) >= (int64_t(1) << 31) - 1) { err = "Jacobian too large for int32 indices"; return EGFEM_ERR_INVALID_ARG; }
+    // uniform slices: every row of the slice sees its local columns at the same offsets
+    // (structured meshes away from the boundary), so the solver can form the column index
+    // as row + offset and skip reading col_idx
+    for (int32_t s = 0; s < nslices; ++s) {
+        SliceMeta &M = out.meta[s];
+        if (int64_t(s + 1) * SLICE > n) continue;
+        bool uni = true;
+        for (int j = 0; j < M.ncol && uni; ++j) {
+            const int64_t q0 = M.col_base + int64_t(j) * SLICE;
+            const int64_t o = int64_t(out.col_idx[q0]) - int64_t(s) * SLICE;
+            for (int r = 1; r < SLICE && uni; ++r) uni = int64_t(out.col_idx[q0 + r]) - (int64_t(s) * SLICE + r) == o;
+        }
+        if (!uni) continue;
+        M.off_base = int64_t(out.slice_off.size());
+        for (int j = 0; j < M.ncol; ++j) out.slice_off.push_back(int32_t(out.col_idx[M.col_base + int64_t(j) * SLICE] - int64_t(s) * SLICE));
+    }
     // CSR slots and column indices
     out.cols.assign(out.rowptr[n], 0);
     for (int32_t s = 0; s < nslices; ++s) {

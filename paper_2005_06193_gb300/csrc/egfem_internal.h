@@ -41,6 +41,7 @@ struct SliceMeta {
     int64_t leaf_base;  // into leaf_val / leaf_col
     int64_t fib_base;   // into fib_info / fib_tdiag / fib_m
     int64_t rx_base;    // into rx_val / rx_info / rx_m
+    int64_t off_base;   // uniform slice: into slice_off (column c of row i is i + slice_off[off_base + c]); -1 otherwise
     int32_t ncol, nleaf, nfib, nrx;
 };
 
@@ -51,6 +52,7 @@ struct HostCSF {
     int32_t n_slices = 0;
     int32_t max_cols = 0;
     std::vector<SliceMeta> meta;
+    std::vector<int32_t> slice_off;  // column offsets (col - row) of the uniform slices
     std::vector<int32_t> col_idx;    // global P1 node of each local column (pad: the row itself)
     std::vector<int32_t> col_slot;   // CSR slot of each local column (-1: Dirichlet column or pad)
     std::vector<double> leaf_val;    // T_imk for k != i
@@ -91,6 +93,8 @@ struct DeviceCSF {
     int32_t max_cols = 0;
     SliceMeta *meta = nullptr;
     int32_t *col_idx = nullptr, *col_slot = nullptr;
+    int32_t *slice_off = nullptr;
+    int64_t n_uniform = 0;
     double *leaf_val = nullptr;
     uint8_t *leaf_col = nullptr;
     uint32_t *fib_info = nullptr;

@@ -83,6 +83,7 @@ struct KVecs {
     int64_t n_pad;      // rows rounded up to whole slices
     const SliceMeta *meta;
     const int32_t *col_idx;
+    const int32_t *slice_off;   // column offsets of uniform slices
     const V *A;
     V *x, *r, *rh, *p, *v, *s, *t;
     const V *b;
@@ -167,6 +168,20 @@ __device__ bool grid_reduce(double (&val)[NV], double *part, uint32_t *ticket, d
     return true;
 }
 
+// column indices of local column c for the R rows starting at r0: from the slice's
+// offsets when the slice is uniform (no index traffic), else from col_idx
+template <typename V>
+__device__ __forceinline__ void row_cols(const KVecs<V> &K, const SliceMeta &M, int64_t r0, int64_t q, int c,
+                                         int32_t (&col)[VecT<V>::R]) {
+    if (M.off_base >= 0) {
+        const int32_t o = __ldg(K.slice_off + M.off_base + c);
+#pragma unroll
+        for (int j = 0; j < VecT<V>::R; ++j) col[j] = int32_t(r0 + j) + o;
+    } else {
+        ldi<V>(K.col_idx + q, col);
+    }
+}
+
 // y[r0 .. r0+R) = A xin for the R rows starting at r0 (r0 a multiple of R).
 template <typename V>
 __device__ __forceinline__ Pack<V> sell_rows(const KVecs<V> &K, int64_t r0, const V *xin) {
@@ -184,7 +199,7 @@ __device__ __forceinline__ Pack<V> sell_rows(const KVecs<V> &K, int64_t r0, cons
             const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
             const Pack<V> a = ldv(K.A + q);
             int32_t col[R];
-            ldi<V>(K.col_idx + q, col);
+            row_cols(K, M, r0, q, c, col);
 #pragma unroll
             for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * (__ldg(xin + col[j]) - xi.v[j]);
         }
@@ -195,7 +210,7 @@ __device__ __forceinline__ Pack<V> sell_rows(const KVecs<V> &K, int64_t r0, cons
             const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
             const Pack<V> a = ldv(K.A + q);
             int32_t col[R];
-            ldi<V>(K.col_idx + q, col);
+            row_cols(K, M, r0, q, c, col);
 #pragma unroll
             for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * __ldg(xin + col[j]);
         }
