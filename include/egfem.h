@@ -263,6 +263,23 @@ egfem_status egfem_load_cellwise_transpose(egfem_handle h, const double *d_lam, 
 egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem_problem *prob, int64_t *count,
                                   int64_t *I, int64_t *M, int64_t *K, double *V, int64_t *n_wa, double *wa_coords);
 
+/* Sum of squares of d_r over the rows whose d_dirichlet entry is 0 (the quantity of the
+ * Newton convergence test), written to the device scalar *d_out, for callers that cannot
+ * allocate device memory when they need it (an application that reserves all device
+ * memory for its own pool, or a real-time loop that cannot afford cudaMalloc's implicit
+ * synchronisation).  It allocates nothing and needs no handle: its block partials and
+ * completion ticket live in a fixed static device array of 65.8 KB that every GPU which
+ * loads the library holds until the process exits.  At most 134,217,728 rows
+ * (8192 blocks of 16384 rows); larger n returns EGFEM_ERR_INVALID_ARG.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (different streams, or host threads) race and may
+ * return wrong sums; the ticket is reset at the start of every call.  Asynchronous on
+ * stream.  The paper has no counterpart: this is a deployment variant of the library's
+ * own residual-norm reduction. */
+egfem_status egfem_free_norm2_noalloc(int64_t n, const double *d_r, const uint8_t *d_dirichlet, double *d_out,
+                                      egfem_stream stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *egfem_status_string(egfem_status s);
 

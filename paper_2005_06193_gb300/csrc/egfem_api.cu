@@ -996,6 +996,12 @@ const char *egfem_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
 
+void egfem::set_last_error(const std::string &msg) { g_last_error = msg; }
+
+extern "C" {
+
+}  // extern "C"
+
 // ---------------------------------------------------------------------------------
 // Batched solves: many instances as one block-diagonal operator (egfem_batch_*)
 // ---------------------------------------------------------------------------------

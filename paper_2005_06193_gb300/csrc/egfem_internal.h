@@ -124,5 +124,6 @@ egfem_status build_csf(const egfem_mesh &mesh, const egfem_problem &prob, const 
                        const std::vector<int32_t> &cell2wc, int nloc_c, HostCSF &out, std::string &err);
 egfem_status validate_mesh(const egfem_mesh &mesh, std::string &err);
 double basis_integral(int dim, int degree, int kind);   // int_K eta_m / |K| by node kind
+void set_last_error(const std::string &msg);            // text returned by egfem_last_error()
 
 }  // namespace egfem

@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
         "egfem_load_cellwise_transpose": (S, [_P, _DP, _DP, _P]),
         "egfem_inspect_tensor": (S, [ctypes.POINTER(Mesh), ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_int64),
                                      _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+        "egfem_free_norm2_noalloc": (S, [ctypes.c_int64, _DP, _DP, _DP, _P]),
         "egfem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "egfem_last_error": (ctypes.c_char_p, []),
     }
