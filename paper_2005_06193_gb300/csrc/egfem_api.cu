@@ -16,6 +16,7 @@
 #include "egfem_kernels.cuh"
 #include "egfem_krylov.cuh"
 #include "egfem_batch.cuh"
+#include "egfem_mf.cuh"
 
 using namespace egfem;
 
@@ -103,6 +104,9 @@ struct egfem_t {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int maxc_tpl = 8;
     int64_t last_graph_launches = 0;    // graph launches of the last BiCGStab solve
+    // element-local operator (EGFEM_OP_MATRIX_FREE)
+    double *cell_S = nullptr, *cell_E = nullptr;
+    MfLocal mf_loc{};
     // batch (egfem_batch_build): instance b owns rows [inst_off[b], inst_off[b+1])
     int32_t nb = 0;
     std::vector<int64_t> inst_off;
@@ -139,7 +143,28 @@ int pick_maxc(int maxc) {
     return 64;
 }
 
+template <int DIM>
+void launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
+    MfArgs M{};
+    M.n_cells = h->ncells; M.n_rows = h->n; M.dim = DIM;
+    M.verts = h->cell_verts; M.S = h->cell_S; M.vol = h->cell_vol; M.v2c_ptr = h->v2c_ptr; M.v2c = h->v2c;
+    M.E = h->cell_E; M.loc = h->mf_loc; M.nl = h->nl;
+    mf_cell_kernel<DIM><<<unsigned((h->ncells + 255) / 256), 256, 0, s>>>(M, A.u);
+    const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
+    switch (h->maxc_tpl) {
+        case 8: mf_row_kernel<DIM, 8><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
+        case 16: mf_row_kernel<DIM, 16><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
+        case 32: mf_row_kernel<DIM, 32><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
+        default: mf_row_kernel<DIM, 64><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
+    }
+}
+
 void launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
+    if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
+        if (h->dim == 2) launch_mf<2>(h, A, s);
+        else launch_mf<3>(h, A, s);
+        return;
+    }
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
     switch (h->maxc_tpl) {
         case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(A); break;
@@ -302,7 +327,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     egfem_default_options(&h->opts);
     if (opts) h->opts = *opts;
     if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
-    if (h->opts.op != EGFEM_OP_CSF) { g_last_error = "operator variant not available in this entry point"; return EGFEM_ERR_UNSUPPORTED; }
+    if (h->opts.op != EGFEM_OP_CSF && h->opts.op != EGFEM_OP_MATRIX_FREE) { g_last_error = "unknown operator variant"; return EGFEM_ERR_INVALID_ARG; }
     h->prob = *prob;
     h->dim = mesh->dim; h->n = mesh->n_nodes; h->ncells = mesh->n_cells;
     EG_CUDA(cudaGetDevice(&h->device));
@@ -379,6 +404,63 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
         for (int64_t c = 0; c < mesh->n_cells; ++c) for (int a = 0; a < nv; ++a) lst[fill[cv[c * nv + a]]++] = int32_t(c);
         EG_TRY(upload(h->cell_verts, cv)); EG_TRY(upload(h->cell_vol, vol));
         EG_TRY(upload(h->v2c_ptr, ptr)); EG_TRY(upload(h->v2c, lst));
+        if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
+            // per cell: S^K = |K| grad lambda_a . grad lambda_b (packed upper triangle)
+            const int d = mesh->dim, ns = nv * (nv + 1) / 2;
+            std::vector<double> S(size_t(mesh->n_cells) * ns);
+            for (int64_t c = 0; c < mesh->n_cells; ++c) {
+                double B[9], Bi[9], g[4][3];
+                for (int k = 0; k < d; ++k)
+                    for (int r = 0; r < d; ++r) B[r * d + k] = mesh->coords[int64_t(cv[c * nv + k + 1]) * d + r] - mesh->coords[int64_t(cv[c * nv]) * d + r];
+                if (d == 2) {
+                    const double det = B[0] * B[3] - B[1] * B[2];
+                    Bi[0] = B[3] / det; Bi[1] = -B[1] / det; Bi[2] = -B[2] / det; Bi[3] = B[0] / det;
+                } else {
+                    const double det = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) + B[2] * (B[3] * B[7] - B[4] * B[6]);
+                    Bi[0] = (B[4] * B[8] - B[5] * B[7]) / det; Bi[1] = (B[2] * B[7] - B[1] * B[8]) / det; Bi[2] = (B[1] * B[5] - B[2] * B[4]) / det;
+                    Bi[3] = (B[5] * B[6] - B[3] * B[8]) / det; Bi[4] = (B[0] * B[8] - B[2] * B[6]) / det; Bi[5] = (B[2] * B[3] - B[0] * B[5]) / det;
+                    Bi[6] = (B[3] * B[7] - B[4] * B[6]) / det; Bi[7] = (B[1] * B[6] - B[0] * B[7]) / det; Bi[8] = (B[0] * B[4] - B[1] * B[3]) / det;
+                }
+                for (int j = 1; j <= d; ++j) for (int r = 0; r < d; ++r) g[j][r] = Bi[(j - 1) * d + r];
+                for (int r = 0; r < d; ++r) { double t = 0; for (int j = 1; j <= d; ++j) t += g[j][r]; g[0][r] = -t; }
+                int q = 0;
+                for (int a = 0; a < nv; ++a)
+                    for (int b = a; b < nv; ++b) {
+                        double t = 0; for (int r = 0; r < d; ++r) t += g[a][r] * g[b][r];
+                        S[size_t(c) * ns + q++] = vol[c] * t;
+                    }
+            }
+            EG_TRY(upload(h->cell_S, S));
+            EG_TRY(dalloc(h->cell_E, size_t(mesh->n_cells) * size_t(2 * d + 3)));
+            // local W nodes of the reference cell in the W numbering's local order
+            MfLocal &L = h->mf_loc;
+            L = MfLocal{};
+            const int p = prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1;
+            if (prob->a_kind != EGFEM_G_NONE) {
+                auto add = [&](const double *w, int kind) {
+                    for (int a = 0; a < 4; ++a) L.w[L.nw][a] = a < nv ? w[a] : 0.0;
+                    L.iota[L.nw] = basis_integral(d, p, kind);
+                    ++L.nw;
+                };
+                for (int a = 0; a < nv; ++a) { double w[4] = {0, 0, 0, 0}; w[a] = 1.0; add(w, W_VERTEX); }
+                for (int a = 0; a < nv && p >= 2; ++a)
+                    for (int b = a + 1; b < nv; ++b)
+                        for (int t = 1; t < p; ++t) {
+                            double w[4] = {0, 0, 0, 0};
+                            w[a] = double(p - t) / double(p); w[b] = double(t) / double(p);
+                            add(w, p == 2 ? W_MID : W_THIRD);
+                        }
+                if (p == 3) {
+                    for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b) for (int e = b + 1; e < nv; ++e) {
+                        if (L.nw >= MF_MAXW) break;
+                        double w[4] = {0, 0, 0, 0};
+                        w[a] = w[b] = w[e] = 1.0 / 3.0;
+                        add(w, W_FACE);
+                    }
+                }
+                if (L.nw > MF_MAXW) { g_last_error = "matrix-free operator supports at most 10 local W nodes"; return EGFEM_ERR_UNSUPPORTED; }
+            }
+        }
     }
     h->nl.a_kind = prob->a_kind; h->nl.a_pi = int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
     h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
@@ -447,6 +529,7 @@ void egfem_destroy(egfem_handle h) {
     dfree(D.meta); dfree(D.col_idx); dfree(D.col_slot); dfree(D.slice_off); dfree(D.leaf_val); dfree(D.leaf_col);
     dfree(D.fib_info); dfree(D.fib_tdiag); dfree(D.fib_m); dfree(D.rx_val); dfree(D.rx_info); dfree(D.rx_m);
     dfree(D.dir); dfree(D.rowptr); dfree(D.cols);
+    dfree(h->cell_S); dfree(h->cell_E);
     dfree(h->tmap); dfree(h->wa_kind); dfree(h->wa_sup); dfree(h->cell_verts); dfree(h->cell_vol);
     dfree(h->v2c_ptr); dfree(h->v2c); dfree(h->kappa_field);
     dfree(h->r); dfree(h->jsell); dfree(h->dinv); dfree(h->part); dfree(h->scal); dfree(h->ticket); dfree(h->status); dfree(h->st);
@@ -508,6 +591,10 @@ egfem_status egfem_jacobian_pattern(egfem_handle h, const int32_t **d_rowptr, co
 
 egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream stream) {
     if (!h) return EGFEM_ERR_INVALID_ARG;
+    if (d_kappa && h->opts.op == EGFEM_OP_MATRIX_FREE) {
+        g_last_error = "a kappa field needs the CSF operator";
+        return EGFEM_ERR_UNSUPPORTED;
+    }
     EG_CUDA(cudaSetDevice(h->device));
     if (!d_kappa) { h->nl.kappa_field = nullptr; return EGFEM_OK; }
     if (!h->kappa_field) EG_TRY(dalloc(h->kappa_field, size_t(h->nwa)));

@@ -77,9 +77,13 @@ def _setup(P, name, **opt):
     return mesh, orc, h
 
 
+OPS = ["csf", "mf"]
+
+
+@pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_residual_parity(P, name):
-    mesh, orc, h = _setup(P, name)
+def test_residual_parity(P, name, op):
+    mesh, orc, h = _setup(P, name, op=P.OP_MATRIX_FREE if op == "mf" else P.OP_CSF)
     b = orc.load_vector(_source(mesh, name)) * (1 - mesh.dirichlet)
     for seed, scale in ((1, 1.0), (2, 0.3)):
         u = wl.random_vector(mesh.n_nodes, seed, scale) * (1 - mesh.dirichlet)
@@ -95,9 +99,10 @@ def test_residual_parity(P, name):
     assert rel(r0.cpu().numpy(), orc.residual(np.zeros(mesh.n_nodes), b)) <= 1e-12
 
 
+@pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_jacobian_parity(P, name):
-    mesh, orc, h = _setup(P, name)
+def test_jacobian_parity(P, name, op):
+    mesh, orc, h = _setup(P, name, op=P.OP_MATRIX_FREE if op == "mf" else P.OP_CSF)
     u = wl.random_vector(mesh.n_nodes, 3, 0.8) * (1 - mesh.dirichlet)
     J = gpu_jacobian(h, cuda(u))
     Jo = orc.jacobian(u)
@@ -142,9 +147,10 @@ def test_spmv_and_bicgstab_parity(P):
     assert rel(sol.cpu().numpy(), xo) <= 1e-9
 
 
+@pytest.mark.parametrize("op", OPS)
 @pytest.mark.parametrize("name", ["u2_p2_2d", "u2_p2_ragged", "u3_p3_2d", "u2_p2_3d", "bratu_3d"])
-def test_newton_solution_parity_fp64(P, name):
-    mesh, orc, h = _setup(P, name, newton_rtol=1e-13)
+def test_newton_solution_parity_fp64(P, name, op):
+    mesh, orc, h = _setup(P, name, newton_rtol=1e-13, op=P.OP_MATRIX_FREE if op == "mf" else P.OP_CSF)
     b = orc.load_vector(_source(mesh, name)) * (1 - mesh.dirichlet)
     u_ref, hist, _, _ = orc.newton(b, rtol=1e-13, solver="lu" if mesh.n_nodes < 20000 else "bicgstab")
     u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
@@ -273,3 +279,167 @@ def test_batched_newton_matches_single_instance_oracle(P, prec):
     for b, (sol, ref) in enumerate(zip(sols, refs)):
         assert stats[b].status == 0
         assert rel(sol, ref) <= (1e-11 if prec == "fp64" else 1e-6), b
+
+
+def _adjoint_setup(P, n, grid, thetas, prec="fp64", rtol=1e-13):
+    mesh = wl.unit_square_mesh(n)
+    pc = wl.param_cell_of_cells(mesh, grid)
+    ud = wl.adjoint_target()(mesh.coords[:, 0], mesh.coords[:, 1])
+    opts = P.default_options(newton_rtol=rtol, precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64)
+    return mesh, pc, ud, opts
+
+
+def _objective(P, h, theta, pc, ud, free, kappa=None):
+    from paper_2005_06193_gb300 import autograd as ag
+    f_cell = theta.reshape(-1)[pc]
+    d = ag.load_cellwise(f_cell, h)
+    u = ag.newton_solve(d, kappa, h)
+    return 0.5 * torch.sum(((u - ud) * free) ** 2), u
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autograd_adjoint_matches_central_differences_and_oracle(P, prec):
+    """Gradient of j = 0.5 ||u - u_d||^2 with respect to a 4 x 4 piecewise-constant source
+    theta and the W-space coefficient kappa, through torch.autograd and the CUDA adjoint,
+    against central differences (h = 1e-6) of FP64 re-solves (agreement 1e-5 relative: the
+    re-solves' own 1e-14 tolerance bounds the difference quotients to ~1e-10 absolute) and
+    against the oracle's FP64 adjoint at the same solution (1e-10 relative)."""
+    mesh, pc, ud_np, opts = _adjoint_setup(P, 16, 4, None, prec)
+    h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2), opts)
+    hf = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2), P.default_options(newton_rtol=1e-14))
+    free = cuda(1.0 - mesh.dirichlet)
+    ud = cuda(ud_np)
+    pc_t = torch.tensor(pc, device="cuda", dtype=torch.int64)
+    theta = cuda(wl.adjoint_theta(7, 4)).requires_grad_(True)
+    kappa = torch.ones(h.sizes.n_wa, device="cuda", dtype=torch.float64, requires_grad=True)
+    J, u = _objective(P, h, theta, pc_t, ud, free, kappa)
+    J.backward()
+    gt, gk = theta.grad.detach().cpu().numpy().ravel(), kappa.grad.detach().cpu().numpy()
+
+    def J_at(th, ka):
+        with torch.no_grad():
+            return float(_objective(P, hf, th, pc_t, ud, free, ka)[0])
+
+    eps = 1e-6
+    for p in (0, 5, 10, 15):
+        e = torch.zeros(16, device="cuda", dtype=torch.float64)
+        e[p] = eps
+        th0 = theta.detach().reshape(-1)
+        fd = (J_at((th0 + e).reshape(4, 4), kappa.detach()) - J_at((th0 - e).reshape(4, 4), kappa.detach())) / (2 * eps)
+        assert abs(fd - gt[p]) <= 1e-5 * max(1e-3, abs(gt[p])), (p, fd, gt[p])
+    for m in (100, 400, 700):
+        e = torch.zeros_like(kappa)
+        e[m] = eps
+        fd = (J_at(theta.detach(), kappa.detach() + e) - J_at(theta.detach(), kappa.detach() - e)) / (2 * eps)
+        assert abs(fd - gk[m]) <= 1e-5 * max(1e-5, abs(gk[m])), (m, fd, gk[m])
+    # oracle adjoint at the GPU solution: dj/db = lambda, dj/df_K = sum_i lambda_i int_K phi_i
+    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+    un = u.detach().cpu().numpy()
+    g = (un - ud_np) * (1 - mesh.dirichlet)
+    orc.set_kappa_field(np.ones(orc.nw))
+    lam, gk_ref = orc.adjoint(un, g)
+    gf = np.zeros(mesh.n_cells)
+    for c in range(mesh.n_cells):
+        e = np.zeros(mesh.n_cells)
+        e[c] = 1.0
+        gf[c] = np.dot(orc.load_vector_cellwise(e) * (1 - mesh.dirichlet), lam)
+    gt_ref = np.bincount(pc, weights=gf, minlength=16)
+    assert rel(gt, gt_ref) <= (1e-10 if prec == "fp64" else 1e-7)
+    perm = match_w(orc.space_coords(0), h.w_coords(0))
+    assert rel(gk[perm], gk_ref) <= (1e-10 if prec == "fp64" else 1e-7)
+
+
+def test_batched_adjoint_gradients_equal_single_instance(P):
+    """Three instances on one mesh with different theta: the batched forward solve and the
+    block-diagonal adjoint give each instance the gradient of its own single solve."""
+    from paper_2005_06193_gb300 import autograd as ag
+    n, grid = 12, 4
+    mesh = wl.unit_square_mesh(n)
+    pc = torch.tensor(wl.param_cell_of_cells(mesh, grid), device="cuda", dtype=torch.int64)
+    ud = cuda(wl.adjoint_target()(mesh.coords[:, 0], mesh.coords[:, 1]))
+    free = cuda(1.0 - mesh.dirichlet)
+    prob = P.make_problem(a=("pow", 2), a_degree=2)
+    opts = P.default_options(newton_rtol=1e-13)
+    hb = P.BatchHandle([mesh] * 3, prob, opts)
+    thetas = [cuda(wl.adjoint_theta(b, grid)).requires_grad_(True) for b in range(3)]
+    off = hb.offsets
+    # batch: cell sources concatenated in instance order (the union keeps each mesh's cells)
+    f_all = torch.cat([t.reshape(-1)[pc] for t in thetas])
+    d = ag.load_cellwise(f_all, hb)
+    u = ag.newton_solve(d, None, hb)
+    J = sum(0.5 * torch.sum(((u[off[b]:off[b] + mesh.n_nodes] - ud) * free) ** 2) for b in range(3))
+    J.backward()
+    hs = P.Handle(mesh, prob, opts)
+    for b in range(3):
+        t = thetas[b].detach().clone().requires_grad_(True)
+        Jb, _ = _objective(P, hs, t, pc, ud, free)
+        Jb.backward()
+        assert rel(thetas[b].grad.cpu().numpy(), t.grad.cpu().numpy()) <= 1e-9, b
+
+
+def test_bratu_64_cube_mixed_precision_full_size(P):
+    """64^3 cube, 6 Kuhn tetrahedra per cube (274,625 nodes, 1,572,864 tets), Bratu
+    -lap u = 2 e^u with e^u interpolated in P1: the mixed solve (FP32 operator and Krylov,
+    FP64 residual) reaches the 1e-10 FP64 residual target, its residual rows equal the
+    oracle's on sampled rows, and it agrees with the FP64 solve to 1e-6."""
+    mesh = wl.unit_cube_mesh(64)
+    prob = P.make_problem(a=None, a_degree=1, c=("exp",), c_degree=1, gamma=-2.0)
+    d = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    sols = {}
+    for prec in ("fp64", "mixed"):
+        h = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64))
+        u = torch.zeros_like(d)
+        st = h.newton_solve(u, d)
+        torch.cuda.synchronize()
+        assert st.status == 0 and st.res_final <= 1e-10 * st.res0
+        sols[prec] = (u.cpu().numpy(), st, h)
+    um, stm, hm = sols["mixed"]
+    uf = sols["fp64"][0]
+    err = rel(um, uf)
+    assert err <= 1e-6, err
+    assert um.max() > 0.05
+    rng = np.random.default_rng(1)
+    rows = np.unique(rng.integers(0, mesh.n_nodes, 150))
+    cellmask = np.isin(mesh.cells, rows).any(axis=1)
+    orc = oracle.Problem(mesh, a=None, a_deg=1, c=("exp",), c_deg=1, gamma=-2.0, qpts=3,
+                         cells=np.where(cellmask)[0].astype(np.int32))
+    r = torch.empty_like(d)
+    hm.residual(cuda(um), d, r)
+    torch.cuda.synchronize()
+    ro = orc.residual(um, np.zeros(mesh.n_nodes), form="diff")
+    rg = r.cpu().numpy()
+    scale = stm.res0 / np.sqrt(mesh.n_nodes)
+    assert np.abs(rg[rows] - ro[rows]).max() <= 1e-12 * max(scale, np.abs(ro[rows]).max())
+
+
+def test_batch_sample_of_256_p3_instances(P):
+    """The first 12 instances of the 256-instance batch (n ~ U{64..512}, w = u^3 in P3,
+    sine sources): the batched mixed solve matches a single-instance FP64 solve of each
+    instance to 1e-6 and reaches the 1e-10 FP64 residual target for all of them."""
+    inst = wl.batch_instances(count=256, seed=0)[:12]
+    meshes = [wl.unit_square_mesh(n) for n, _ in inst]
+    prob = P.make_problem(a=("pow", 3), a_degree=3)
+    hb = P.BatchHandle(meshes, prob, P.default_options(precision=P.PREC_MIXED))
+    fs = []
+    for (n, src), mesh in zip(inst, meshes):
+        cen = wl.cell_centroids(mesh)
+        fs.append(src(cen[:, 0], cen[:, 1]))
+    f = torch.tensor(np.concatenate(fs), device="cuda", dtype=torch.float64)
+    d = torch.empty(hb.sizes.n_nodes, device="cuda", dtype=torch.float64)
+    hb.load_cellwise(f, d)
+    u = torch.zeros_like(d)
+    stats = hb.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    for b, mesh in enumerate(meshes):
+        assert stats[b].status == 0 and stats[b].res_final <= 1e-10 * stats[b].res0, b
+    ub = hb.gather(u, [m.n_nodes for m in meshes])
+    for b in (0, 5, 11):
+        mesh = meshes[b]
+        h = P.Handle(mesh, prob)
+        fb = torch.tensor(fs[b], device="cuda", dtype=torch.float64)
+        db = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+        h.load_cellwise(fb, db)
+        us = torch.zeros_like(db)
+        h.newton_solve(us, db)
+        torch.cuda.synchronize()
+        assert rel(ub[b], us.cpu().numpy()) <= 1e-6, b
