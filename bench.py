@@ -179,6 +179,106 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def batched_adjoint_extra(torch, P, dev, count, n, barrier):
+    """Solves + adjoint gradients per second on `count` instances of the n x n P1/P2
+    u^2 problem with 16 x 16 cellwise sources theta_b (seed b) and j = 0.5 ||u - u_d||^2:
+    the plain path (one FP64 handle, instances one after another) against the batched
+    mixed path (one batch handle, batched Newton, block-diagonal adjoint)."""
+    import workloads as wl
+    from paper_2005_06193_gb300 import autograd as ag
+    mesh = wl.unit_square_mesh(n)
+    pc = torch.tensor(wl.param_cell_of_cells(mesh, 16), device=dev, dtype=torch.int64)
+    ud = torch.tensor(wl.adjoint_target()(mesh.coords[:, 0], mesh.coords[:, 1]), device=dev)
+    free = torch.tensor(1.0 - mesh.dirichlet, device=dev)
+    thetas = [torch.tensor(wl.adjoint_theta(b), device=dev) for b in range(count)]
+    prob = P.make_problem(a=("pow", 2), a_degree=2)
+
+    def grad_single(h, th):
+        t = th.clone().requires_grad_(True)
+        u = ag.newton_solve(ag.load_cellwise(t.reshape(-1)[pc], h), None, h)
+        (0.5 * torch.sum(((u - ud) * free) ** 2)).backward()
+        return t.grad
+
+    hs = P.Handle(mesh, prob, P.default_options())
+    grad_single(hs, thetas[0])   # warm
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g_plain = [grad_single(hs, th) for th in thetas]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    hb = P.BatchHandle([mesh] * count, prob, P.default_options(precision=P.PREC_MIXED))
+    off = hb.offsets
+
+    def grad_batch():
+        ts = [th.clone().requires_grad_(True) for th in thetas]
+        d = ag.load_cellwise(torch.cat([t.reshape(-1)[pc] for t in ts]), hb)
+        u = ag.newton_solve(d, None, hb)
+        J = sum(0.5 * torch.sum(((u[off[b]:off[b] + mesh.n_nodes] - ud) * free) ** 2) for b in range(count))
+        J.backward()
+        return [t.grad for t in ts]
+
+    grad_batch()   # warm (includes the tile autotuning)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g_batch = grad_batch()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    err = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(g_batch, g_plain))
+    hs.close()
+    hb.close()
+    return {"workload": f"{count} x {n}x{n} P1/P2 u^2, 16x16 cellwise theta, j = 0.5||u-u_d||^2",
+            "unit": "solves+gradients/s", "plain_fp64_sequential": count / t_plain, "batched_mixed": count / t_batch,
+            "speedup": t_plain / t_batch, "max_rel_gradient_difference": err}
+
+
+def batched_p3_extra(torch, P, dev, count, barrier):
+    """Newton solves per second on the first `count` instances of the 256-instance batch
+    (n ~ U{64..512}, w = u^3 in P3, 8-mode sine sources): plain sequential FP64 solves
+    against one batched mixed solve."""
+    import workloads as wl
+    inst = wl.batch_instances(count=256, seed=0)[:count]
+    meshes = [wl.unit_square_mesh(n) for n, _ in inst]
+    prob = P.make_problem(a=("pow", 3), a_degree=3)
+    fs = []
+    for (n, src), mesh in zip(inst, meshes):
+        cen = wl.cell_centroids(mesh)
+        fs.append(src(cen[:, 0], cen[:, 1]))
+    hb = P.BatchHandle(meshes, prob, P.default_options(precision=P.PREC_MIXED))
+    d = torch.empty(hb.sizes.n_nodes, device=dev, dtype=torch.float64)
+    hb.load_cellwise(torch.tensor(np.concatenate(fs), device=dev), d)
+    u = torch.zeros_like(d)
+    hb.batch_newton_solve(u, d)   # warm + tile autotuning
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u.zero_()
+    st = hb.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    ok = all(s.status == 0 and s.res_final <= 1e-10 * s.res0 for s in st)
+    t_plain = 0.0
+    for mesh, f in zip(meshes, fs):
+        h = P.Handle(mesh, prob, P.default_options())
+        db = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
+        h.load_cellwise(torch.tensor(f, device=dev), db)
+        ub = torch.zeros_like(db)
+        h.newton_solve(ub, db)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ub.zero_()
+        h.newton_solve(ub, db)
+        torch.cuda.synchronize()
+        t_plain += time.perf_counter() - t0
+        h.close()
+    hb.close()
+    return {"workload": f"first {count} of the 256 seeded instances, n in [64, 512], P1/P3 u^3",
+            "unit": "solves/s", "plain_fp64_sequential": count / t_plain, "batched_mixed": count / t_batch,
+            "speedup": t_plain / t_batch, "all_converged_1e-10": ok,
+            "rows": int(hb.sizes.n_nodes)}
+
+
 def timed_solves(torch, h, d, u, steps, rank_barrier):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
@@ -203,6 +303,11 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mf", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=16)
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--p3-instances", type=int, default=32)
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=12000)
     args = ap.parse_args()
@@ -316,11 +421,28 @@ def main():
             hm.newton_solve(u, d)
         msm, sm = timed_solves(torch, hm, d, u, args.steps, barrier)
         sl = sm[-1]
+        mprof = hm.profile_kernels(u, d, reps=20)
         out["mixed"] = {"value": world * args.steps / (msm / 1e3), "unit": "solves/s", "ms_per_step": msm / args.steps,
                         "newton_iters": sl.newton_iters, "krylov_iters": int(sl.krylov_iters),
-                        "final_rel_residual": sl.res_final / sl.res0, "speedup_vs_fp64": (ms_max / msm)}
+                        "final_rel_residual": sl.res_final / sl.res0, "speedup_vs_fp64": (ms_max / msm),
+                        "fp64_rescues": sl.fp64_rescues,
+                        "kernels": [{"name": p["name"], "ms": p["ms"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9}
+                                    for p in mprof]}
         out["mixed"]["gpu_launches"] = int(sum(s.kernel_launches for s in sm))
         hm.close()
+
+    if not args.no_mf:
+        hmf = P.Handle(mesh, prob, P.default_options(op=P.OP_MATRIX_FREE))
+        pm = next(p for p in hmf.profile_kernels(u, d, reps=20) if p["name"].startswith("tensor_action"))
+        out["tensor_action_mf"] = {"kernel": "mf_cell_kernel + mf_row_kernel", "ms": pm["ms"],
+                                   "achieved_gbs": pm["bytes"] / (pm["ms"] / 1e3) / 1e9,
+                                   "frac_hbm": pm["bytes"] / (pm["ms"] / 1e3) / 1e9 / hbm,
+                                   "bytes_per_launch": pm["bytes"], "speedup_vs_csf": csf["ms"] / pm["ms"]}
+        hmf.close()
+
+    if not args.no_batch:
+        out["batched_adjoint"] = batched_adjoint_extra(torch, P, dev, args.batch_instances, args.batch_n, barrier)
+        out["batched_p3"] = batched_p3_extra(torch, P, dev, args.p3_instances, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_solve, cpu_s, sample = oracle_sample(args.n, st.newton_iters, int(st.krylov_iters))

@@ -56,7 +56,8 @@ egfem_status upload(T *&p, const std::vector<T> &v) {
 
 template <typename V>
 struct KWork {
-    V *A = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+    typename VecT<V>::mat *A = nullptr;   // Jacobi-scaled operator (SELL layout)
+    V *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
@@ -95,8 +96,8 @@ struct egfem_t {
     double *h_scal = nullptr;           // pinned
     uint32_t *ticket = nullptr;
     int32_t *status = nullptr;
-    KWork<double> k64;
-    KWork<float> k32;
+    KWork<double> k64;                  // FP64 path (and the rescue of failed mixed steps)
+    KWork<df64> k32;                    // mixed path: FP32 operator, double-float vectors
     int64_t n_pad = 0;                  // rows rounded up to whole slices (Krylov vectors)
     int kgrid = 1;                      // blocks of the row kernels (norms)
     int kgrid64 = 1, kgrid32 = 1;       // blocks of the FP64 / FP32 Krylov kernels
@@ -127,11 +128,11 @@ struct egfem_t {
 
 namespace {
 
-// Smallest Krylov forcing term of the mixed path: an FP32 BiCGStab's recursive residual
-// stagnates near 1e-4 on the 1024^2 problem (the FP32 iterate is then accurate to ~1e-5),
-// so asking for less only burns iterations; the FP64 Newton residual supplies the
-// remaining digits, a factor of ~5e-4 per step (iterative refinement).
-constexpr double kMixedEtaFloor = 5e-4;
+// Smallest Krylov forcing term of the mixed path.  Its vectors carry 48-bit significands
+// (df64), so the iteration is as stable as in FP64; what limits it is the FP32-rounded
+// operator, whose relative perturbation (~6e-8, row sums kept exact) the FP64 Newton
+// residual corrects at the next step (iterative refinement).
+constexpr double kMixedEtaFloor = 1e-8;
 // An FP32 solve whose residual has not fallen by 10% for this many iterations stops (its
 // iterate is still applied; the FP64 Newton residual judges it).
 constexpr int32_t kMixedStall = 150;
@@ -219,7 +220,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     W.g_x = one_wave<V>(h, (const void *)kry_x<V>);
     W.g_p = one_wave<V>(h, (const void *)kry_p<V>);
     EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
-    EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V)));
+    EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(*W.A)));
     V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t};
     for (V **q : vec) { EG_TRY(dalloc(*q, size_t(h->n_pad))); EG_CUDA(cudaMemset(*q, 0, size_t(h->n_pad) * sizeof(V))); }
     W.ready = true;
@@ -537,7 +538,7 @@ void egfem_destroy(egfem_handle h) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
     }
-    for (KWork<float> *W : {&h->k32}) {
+    for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
     }
@@ -650,12 +651,12 @@ egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *
     const unsigned g = unsigned((h->n + 255) / 256);
     if (h->opts.precision == EGFEM_PREC_MIXED) {
         EG_TRY(kwork_alloc(h, h->k32));
-        csr_to_sell_kernel<float><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs, h->k32.A, h->k32.b,
-                                                         h->status);
+        csr_to_sell_kernel<df64><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs, h->k32.A, h->k32.b,
+                                                        h->status);
         EG_CUDA(cudaGetLastError());
         EG_TRY(check_status_word(h));
         EG_TRY(run_bicgstab(h, h->k32, rtol, maxit, 0, &done, &it));
-        cast_kernel<float, double><<<g, 256, 0, h->hs>>>(h->n, h->k32.x, d_x);
+        cast_kernel<df64, double><<<g, 256, 0, h->hs>>>(h->n, h->k32.x, d_x);
     } else {
         EG_TRY(kwork_alloc(h, h->k64));
         csr_to_sell_kernel<double><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_slot, d_vals, d_rhs, h->k64.A, h->k64.b,
@@ -689,8 +690,9 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
         CsfArgs A = csf_args(h, d_u, d_d);
         A.r = h->r;
         A.a64 = h->k64.A; A.q64 = h->k64.b;
-        if (mixed) { A.a32 = h->k32.A; A.q32 = h->k32.b; }
+        if (mixed) A.a32 = h->k32.A;
         launch_csf(h, A, h->hs);
+        if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
         EG_CUDA(cudaGetLastError());
         double n2;
         EG_TRY(norm2_free(h, h->r, &n2));
@@ -700,7 +702,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     };
     const unsigned g = unsigned((h->n + 255) / 256);
     auto update = [&](bool fp32, double lam) -> egfem_status {   // u -= lam x
-        if (fp32) newton_update_kernel<float><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k32.x, lam);
+        if (fp32) newton_update_kernel<df64><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k32.x, lam);
         else newton_update_kernel<double><<<g, 256, 0, h->hs>>>(h->n, d_u, h->k64.x, lam);
         EG_CUDA(cudaGetLastError());
         S.kernel_launches += 1;
@@ -796,9 +798,9 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
 namespace {
 
 // AT[tmap[q]] = J[q] * dinv[col(q)]  (the transpose, Jacobi-scaled by its own diagonal)
-template <typename V>
+template <typename M_t>
 __global__ void transpose_scaled_kernel(int64_t n, const SliceMeta *meta, const int32_t *col_idx, const int64_t *tmap,
-                                        const double *jsell, const double *dinv, V *AT) {
+                                        const double *jsell, const double *dinv, M_t *AT) {
     const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const SliceMeta M = meta[row / SLICE];
@@ -807,14 +809,14 @@ __global__ void transpose_scaled_kernel(int64_t n, const SliceMeta *meta, const 
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int64_t t = tmap[q];
         if (t < 0) continue;
-        AT[t] = V(jsell[q] * dinv[col_idx[q]]);
+        AT[t] = M_t(jsell[q] * dinv[col_idx[q]]);
     }
 }
 
 template <typename V>
 __global__ void adjoint_rhs_kernel(int64_t n, const double *g, const uint8_t *dir, const double *dinv, V *b) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = V(dir[i] ? 0.0 : g[i] * dinv[i]);
+    if (i < n) b[i] = cvt<V>(dir[i] ? 0.0 : g[i] * dinv[i]);
 }
 
 // grad_kappa_m -= lambda_i sum_k T_imk (u_k - u_i)   (sum_k T_imk = 0)
@@ -897,14 +899,15 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
     EG_CUDA(cudaGetLastError());
     EG_TRY(check_status_word(h));
     const unsigned g = unsigned((h->n + 255) / 256);
-    EG_CUDA(cudaMemsetAsync(W.A, 0, size_t(h->csf.n_colentries) * sizeof(V), h->hs));
-    transpose_scaled_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->tmap, h->jsell, h->dinv, W.A);
-    if (std::is_same<V, float>::value) rowsum_form_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, W.A);
+    using M_t = typename VecT<V>::mat;
+    EG_CUDA(cudaMemsetAsync(W.A, 0, size_t(h->csf.n_colentries) * sizeof(M_t), h->hs));
+    transpose_scaled_kernel<M_t><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->tmap, h->jsell, h->dinv, W.A);
+    if (VecT<V>::diff) rowsum_form_kernel<M_t><<<g, 256, 0, h->hs>>>(h->n, h->csf.meta, W.A);
     adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_g, h->csf.dir, h->dinv, W.b);
     EG_CUDA(cudaGetLastError());
     // FP64: one solve to a tight tolerance.  Mixed: iterative refinement -- FP32 solves of
     // (D J^T) delta = D rho for the FP64 residual rho = g - J^T lambda, lambda += delta.
-    const bool mixed = std::is_same<V, float>::value;
+    const bool mixed = !std::is_same<V, double>::value;
     int32_t done = 0, it = 0;
     if (!mixed) {
         EG_TRY(run_bicgstab(h, W, 1e-13, h->opts.krylov_maxit, 0, &done, &it));
@@ -948,7 +951,7 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     cudaEvent_t e0, e1;
     EG_CUDA(cudaEventCreate(&e0));
     EG_CUDA(cudaEventCreate(&e1));
-    const double vb = double(sizeof(V));
+    const double vb = double(sizeof(V)), mb = double(sizeof(typename VecT<V>::mat));
     const double N = double(h->n), CE = double(h->csf.n_colentries), L = double(h->csf.n_leaves);
     const double F = double(h->csf.n_fibres), RX = double(h->csf.n_rx), SM = double(h->csf.n_slices) * sizeof(SliceMeta);
     auto timeit = [&](const char *name, double bytes, double flops, int fp64, auto launch) -> egfem_status {
@@ -971,13 +974,24 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     };
     CsfArgs A = csf_args(h, d_u, d_d);
     A.r = h->r;
-    if (std::is_same<V, float>::value) { A.a32 = (float *)W.A; A.q32 = (float *)W.b; }
-    else { A.a64 = (double *)W.A; A.q64 = (double *)W.b; }
+    EG_TRY(kwork_alloc(h, h->k64));
+    A.q64 = h->k64.b;
+    if (std::is_same<V, double>::value) A.a64 = (double *)W.A;
+    else A.a32 = (float *)W.A;
     // fused kernel: leaves (value + column byte), fibres (info + diagonal), reaction entries,
     // local columns (index + CSR slot) and the operator written, u/d/r/q once each
-    const double csf_bytes = L * 9 + F * 12 + RX * 12 + CE * (8 + vb) + N * (8 + 8 + 8 + vb + 1) + SM;
+    double csf_bytes = L * 9 + F * 12 + RX * 12 + CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
+    if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
+        // cells: vertices, packed S, |K|, the per-cell record written and read back;
+        // rows: vertex-to-cell lists, local columns and the outputs
+        const double NC = double(h->ncells), nv = h->dim + 1, ns = nv * (nv + 1) / 2, ne = 2 * h->dim + 3;
+        csf_bytes = NC * (4 * nv + 8 * ns + 8 + 2 * 8 * ne) + N * (8 + 4 * 2 * nv) + CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
+    }
     const double csf_flops = L * 4 + F * 12 + RX * 10 + CE * 2;
-    EG_TRY(timeit("csf_fused", csf_bytes, csf_flops, 1, [&] { launch_csf(h, A, h->hs); }));
+    EG_TRY(timeit(h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused", csf_bytes, csf_flops, 1,
+                  [&] { launch_csf(h, A, h->hs); }));
+    if (!std::is_same<V, double>::value)
+        cast_kernel<double, V><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, W.b);
     KVecs<V> K = kvecs(h, W);
     kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
     enqueue_iterations(h, W, 1, h->hs);
@@ -998,9 +1012,9 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         EG_CUDA(cudaMemcpy(hm.data(), h->csf.meta, hm.size() * sizeof(SliceMeta), cudaMemcpyDeviceToHost));
         for (const SliceMeta &M : hm) if (M.off_base < 0) ce_nonuni += double(M.ncol) * SLICE;
     }
-    EG_TRY(run("kry_v", CE * vb + ce_nonuni * 4 + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>, W.g_v));
+    EG_TRY(run("kry_v", CE * mb + ce_nonuni * 4 + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>, W.g_v));
     EG_TRY(run("kry_s", 3 * N * vb, 2 * N, kry_s<V>, W.g_s));
-    EG_TRY(run("kry_t", CE * vb + ce_nonuni * 4 + 2 * N * vb + SM, 2 * CE + 4 * N, kry_t<V>, W.g_t));
+    EG_TRY(run("kry_t", CE * mb + ce_nonuni * 4 + 2 * N * vb + SM, 2 * CE + 4 * N, kry_t<V>, W.g_t));
     EG_TRY(run("kry_x", 7 * N * vb, 10 * N, kry_x<V>, W.g_x));
     EG_TRY(run("kry_p", 4 * N * vb, 4 * N, kry_p<V>, W.g_p));
     cudaEventDestroy(e0);
@@ -1233,9 +1247,10 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         // tune on the operator at the initial state
         CsfArgs A0 = csf_args(h, d_u, d_d);
         A0.r = h->r; A0.a64 = h->k64.A; A0.q64 = h->k64.b;
-        if (mixed) { A0.a32 = h->k32.A; A0.q32 = h->k32.b; }
+        if (mixed) A0.a32 = h->k32.A;
         launch_csf(h, A0, h->hs);
-        if (mixed) EG_TRY(autotune_tiles<float>(h, h->k32));
+        if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
+        if (mixed) EG_TRY(autotune_tiles<df64>(h, h->k32));
         else EG_TRY(autotune_tiles<double>(h, h->k64));
     }
     const auto t0 = std::chrono::steady_clock::now();
@@ -1251,9 +1266,10 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
         CsfArgs A = csf_args(h, d_u, d_d);
         A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
-        if (mixed) { A.a32 = h->k32.A; A.q32 = h->k32.b; }
+        if (mixed) A.a32 = h->k32.A;
         A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
         launch_csf(h, A, h->hs);
+        if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
         EG_CUDA(cudaGetLastError());
         EG_TRY(batch_norms(h));
         launches += 2;
@@ -1266,7 +1282,7 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
         EG_CUDA(cudaMemcpyAsync(h->inst_lam, h->h_lam, size_t(nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
         const unsigned g = unsigned((h->n + 255) / 256);
-        if (p32) kb_update<float><<<g, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, h->k32.x);
+        if (p32) kb_update<df64><<<g, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, h->k32.x);
         else kb_update<double><<<g, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, h->k64.x);
         EG_CUDA(cudaGetLastError());
         ++launches;

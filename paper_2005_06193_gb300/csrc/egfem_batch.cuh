@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(KRY_BLOCK) kb_setup(KBatch<V> B) {
     constexpr int R = VecT<V>::R;
     Pack<V> z;
 #pragma unroll
-    for (int j = 0; j < R; ++j) z.v[j] = V(0);
+    for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
     KB_TILES(B) {
         const BTile T = B.tiles[tile];
         KState *S = B.st + T.inst;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(KRY_BLOCK) kb_setup(KBatch<V> B) {
             stv(B.K.x + r0, z); stv(B.K.v + r0, z);
             stv(B.K.r + r0, b); stv(B.K.rh + r0, b); stv(B.K.p + r0, b);
 #pragma unroll
-            for (int j = 0; j < R; ++j) acc[0] += double(b.v[j]) * double(b.v[j]);
+            for (int j = 0; j < R; ++j) acc[0] += to_d(b.v[j]) * to_d(b.v[j]);
         }
         double tot[1];
         if (tile_reduce<1>(acc, B.part, B.ntiles, tile, T, S, tot) && threadIdx.x == 0) {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(KRY_BLOCK) kb_s(KBatch<V> B) {
         const BTile T = B.tiles[tile];
         const KState *S = B.st + T.inst;
         if (inst_finished(S)) continue;
-        const V alpha = V(S->alpha);
+        const V alpha = cvt<V>(S->alpha);
         KB_ROWS(T) {
             const Pack<V> r = ldv(B.K.r + r0), v = ldv(B.K.v + r0);
             Pack<V> s;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(KRY_BLOCK) kb_x(KBatch<V> B) {
         const BTile T = B.tiles[tile];
         KState *S = B.st + T.inst;
         if (inst_finished(S)) continue;
-        const V alpha = V(S->alpha), omega = V(S->omega);
+        const V alpha = cvt<V>(S->alpha), omega = cvt<V>(S->omega);
         DotAcc<V> rho, rr;
         KB_ROWS(T) {
             const Pack<V> s = ldv(B.K.s + r0), p = ldv(B.K.p + r0), t = ldv(B.K.t + r0), rh = ldv(B.K.rh + r0);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(KRY_BLOCK) kb_p(KBatch<V> B) {
         const BTile T = B.tiles[tile];
         const KState *S = B.st + T.inst;
         if (inst_finished(S)) continue;
-        const V beta = V(S->beta), omega = V(S->omega);
+        const V beta = cvt<V>(S->beta), omega = cvt<V>(S->omega);
         KB_ROWS(T) {
             const Pack<V> r = ldv(B.K.r + r0), v = ldv(B.K.v + r0);
             Pack<V> p = ldv(B.K.p + r0);
@@ -270,7 +270,7 @@ __global__ void kb_update(int64_t n, const int32_t *slice_inst, const uint8_t *m
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t b = slice_inst[i / SLICE];
-    if (mask[b]) u[i] -= lam[b] * double(x[i]);
+    if (mask[b]) u[i] -= lam[b] * to_d(x[i]);
 }
 
 #undef KB_TILES

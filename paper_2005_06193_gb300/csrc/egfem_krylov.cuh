@@ -24,6 +24,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "egfem_df64.cuh"
 #include "egfem_internal.h"
 
 namespace egfem {
@@ -45,9 +48,39 @@ struct KState {
     uint32_t ticket;
 };
 
+// Per vector type V: the 128-bit word moved per load (type), the index word (idx), the
+// rows per thread (R), the operator value type (mat) and whether the operator is applied in
+// the difference form (diff).  df64 vectors use an FP32 operator in difference form.
 template <typename V> struct VecT;
-template <> struct VecT<double> { using type = double2; using idx = int2; static constexpr int R = 2; };
-template <> struct VecT<float> { using type = float4; using idx = int4; static constexpr int R = 4; };
+template <> struct VecT<double> {
+    using type = double2; using idx = int2; using mat = double; static constexpr int R = 2; static constexpr bool diff = false;
+};
+template <> struct VecT<float> {
+    using type = float4; using idx = int4; using mat = float; static constexpr int R = 4; static constexpr bool diff = true;
+};
+template <> struct VecT<df64> {
+    using type = float4; using idx = int2; using mat = float; static constexpr int R = 2; static constexpr bool diff = true;
+};
+
+// conversions and arithmetic that read the same for double, float and df64
+template <typename V> __device__ __forceinline__ V cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return float(x); }
+template <> __device__ __forceinline__ df64 cvt<df64>(double x) { return df_from(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return double(x); }
+__device__ __forceinline__ double to_d(df64 x) { return df_to_double(x); }
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return df_sub(a, b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ df64 operator*(float a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { a = df_add(a, b); return a; }
+__device__ __forceinline__ double ldg1(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldg1(const float *p) { return __ldg(p); }
+__device__ __forceinline__ df64 ldg1(const df64 *p) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    return {t.x, t.y};
+}
 
 template <typename V>
 struct Pack {
@@ -58,7 +91,8 @@ template <typename V>
 __device__ __forceinline__ Pack<V> ldv(const V *p) {
     Pack<V> o;
     const typename VecT<V>::type t = *reinterpret_cast<const typename VecT<V>::type *>(p);
-    if constexpr (VecT<V>::R == 2) { o.v[0] = t.x; o.v[1] = t.y; }
+    if constexpr (std::is_same<V, df64>::value) { o.v[0] = {t.x, t.y}; o.v[1] = {t.z, t.w}; }
+    else if constexpr (VecT<V>::R == 2) { o.v[0] = t.x; o.v[1] = t.y; }
     else { o.v[0] = t.x; o.v[1] = t.y; o.v[2] = t.z; o.v[3] = t.w; }
     return o;
 }
@@ -66,9 +100,21 @@ __device__ __forceinline__ Pack<V> ldv(const V *p) {
 template <typename V>
 __device__ __forceinline__ void stv(V *p, const Pack<V> &o) {
     typename VecT<V>::type t;
-    if constexpr (VecT<V>::R == 2) { t.x = o.v[0]; t.y = o.v[1]; }
+    if constexpr (std::is_same<V, df64>::value) { t.x = o.v[0].hi; t.y = o.v[0].lo; t.z = o.v[1].hi; t.w = o.v[1].lo; }
+    else if constexpr (VecT<V>::R == 2) { t.x = o.v[0]; t.y = o.v[1]; }
     else { t.x = o.v[0]; t.y = o.v[1]; t.z = o.v[2]; t.w = o.v[3]; }
     *reinterpret_cast<typename VecT<V>::type *>(p) = t;
+}
+
+template <typename M, int R>
+__device__ __forceinline__ void ldm(const M *p, M (&o)[R]) {
+    if constexpr (sizeof(M) * R == 16) {
+        if constexpr (R == 2) { const double2 t = *reinterpret_cast<const double2 *>(p); o[0] = t.x; o[1] = t.y; }
+        else { const float4 t = *reinterpret_cast<const float4 *>(p); o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w; }
+    } else {
+        const float2 t = *reinterpret_cast<const float2 *>(p);   // two FP32 values (df64 rows)
+        o[0] = t.x; o[1] = t.y;
+    }
 }
 
 template <typename V>
@@ -84,7 +130,7 @@ struct KVecs {
     const SliceMeta *meta;
     const int32_t *col_idx;
     const int32_t *slice_off;   // column offsets of uniform slices
-    const V *A;
+    const typename VecT<V>::mat *A;
     V *x, *r, *rh, *p, *v, *s, *t;
     const V *b;
     KState *st;
@@ -102,6 +148,22 @@ template <> struct DotAcc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<df64> {
+    float hi = 0.f, lo = 0.f;
+    // a.hi b.hi exactly (FMA split) plus the cross terms a.hi b.lo + a.lo b.hi
+    __device__ __forceinline__ void add(df64 a, df64 b) {
+        const float p = __fmul_rn(a.hi, b.hi);
+        float e = __fmaf_rn(a.hi, b.hi, -p);
+        e = __fmaf_rn(a.hi, b.lo, e);
+        e = __fmaf_rn(a.lo, b.hi, e);
+        const float t = __fadd_rn(hi, p);
+        const float z = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+        hi = t;
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 template <> struct DotAcc<float> {
     float hi = 0.f, lo = 0.f;
@@ -186,33 +248,37 @@ __device__ __forceinline__ void row_cols(const KVecs<V> &K, const SliceMeta &M, 
 template <typename V>
 __device__ __forceinline__ Pack<V> sell_rows(const KVecs<V> &K, int64_t r0, const V *xin) {
     constexpr int R = VecT<V>::R;
+    using M_t = typename VecT<V>::mat;
     const SliceMeta M = K.meta[r0 / SLICE];
     const int lane = int(r0 % SLICE);
     Pack<V> y;
-    if constexpr (sizeof(V) == 4) {
+    if constexpr (VecT<V>::diff) {
         // difference form: column 0 holds the row sum s_i and the row's own value
         const Pack<V> xi = ldv(xin + r0);
-        const Pack<V> a0 = ldv(K.A + M.col_base + lane);
+        M_t a0[R];
+        ldm(K.A + M.col_base + lane, a0);
 #pragma unroll
-        for (int j = 0; j < R; ++j) y.v[j] = a0.v[j] * xi.v[j];
+        for (int j = 0; j < R; ++j) y.v[j] = a0[j] * xi.v[j];
         for (int c = 1; c < M.ncol; ++c) {
             const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
-            const Pack<V> a = ldv(K.A + q);
+            M_t a[R];
+            ldm(K.A + q, a);
             int32_t col[R];
             row_cols(K, M, r0, q, c, col);
 #pragma unroll
-            for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * (__ldg(xin + col[j]) - xi.v[j]);
+            for (int j = 0; j < R; ++j) y.v[j] += a[j] * (ldg1(xin + col[j]) - xi.v[j]);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < R; ++j) y.v[j] = V(0);
+        for (int j = 0; j < R; ++j) y.v[j] = cvt<V>(0.0);
         for (int c = 0; c < M.ncol; ++c) {
             const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
-            const Pack<V> a = ldv(K.A + q);
+            M_t a[R];
+            ldm(K.A + q, a);
             int32_t col[R];
             row_cols(K, M, r0, q, c, col);
 #pragma unroll
-            for (int j = 0; j < R; ++j) y.v[j] += a.v[j] * __ldg(xin + col[j]);
+            for (int j = 0; j < R; ++j) y.v[j] += a[j] * ldg1(xin + col[j]);
         }
     }
     return y;
@@ -231,13 +297,13 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_setup(KVecs<V> K, double rtol, 
     double acc[1] = {0.0};
     Pack<V> z;
 #pragma unroll
-    for (int j = 0; j < R; ++j) z.v[j] = V(0);
+    for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
     KRY_LOOP(K) {
         const Pack<V> b = ldv(K.b + r0);
         stv(K.x + r0, z); stv(K.v + r0, z);
         stv(K.r + r0, b); stv(K.rh + r0, b); stv(K.p + r0, b);
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[0] += double(b.v[j]) * double(b.v[j]);
+        for (int j = 0; j < R; ++j) acc[0] += to_d(b.v[j]) * to_d(b.v[j]);
     }
     double tot[1];
     if (grid_reduce<1>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
@@ -277,7 +343,7 @@ template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_s(KVecs<V> K) {
     constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
-    const V alpha = V(K.st->alpha);
+    const V alpha = cvt<V>(K.st->alpha);
     KRY_LOOP(K) {
         const Pack<V> r = ldv(K.r + r0), v = ldv(K.v + r0);
         Pack<V> s;
@@ -313,7 +379,7 @@ template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_x(KVecs<V> K) {
     constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
-    const V alpha = V(K.st->alpha), omega = V(K.st->omega);
+    const V alpha = cvt<V>(K.st->alpha), omega = cvt<V>(K.st->omega);
     DotAcc<V> rho, rr;
     KRY_LOOP(K) {
         const Pack<V> s = ldv(K.s + r0), p = ldv(K.p + r0), t = ldv(K.t + r0), rh = ldv(K.rh + r0);
@@ -354,7 +420,7 @@ template <typename V>
 __global__ void __launch_bounds__(KRY_BLOCK) kry_p(KVecs<V> K) {
     constexpr int R = VecT<V>::R;
     if (finished(K.st)) return;
-    const V beta = V(K.st->beta), omega = V(K.st->omega);
+    const V beta = cvt<V>(K.st->beta), omega = cvt<V>(K.st->omega);
     KRY_LOOP(K) {
         const Pack<V> r = ldv(K.r + r0), v = ldv(K.v + r0);
         Pack<V> p = ldv(K.p + r0);
@@ -384,14 +450,15 @@ __global__ void __launch_bounds__(KRY_BLOCK) norm2_free_kernel(int64_t n, const 
 template <typename V>
 __global__ void newton_update_kernel(int64_t n, double *u, const V *x, double lambda) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) u[i] -= lambda * double(x[i]);
+    if (i < n) u[i] -= lambda * to_d(x[i]);
 }
 
 // CSR values -> Jacobi-scaled SELL operator and scaled right-hand side (egfem_bicgstab).
 // FP32 operators keep the scaled row sum in column 0 (difference form, see above).
 template <typename V>
 __global__ void csr_to_sell_kernel(int64_t n, const SliceMeta *meta, const int32_t *col_slot, const double *vals,
-                                   const double *rhs, V *A, V *b, int32_t *status) {
+                                   const double *rhs, typename VecT<V>::mat *A, V *b, int32_t *status) {
+    using M_t = typename VecT<V>::mat;
     const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const SliceMeta M = meta[row / SLICE];
@@ -406,15 +473,15 @@ __global__ void csr_to_sell_kernel(int64_t n, const SliceMeta *meta, const int32
         const int32_t s = col_slot[q];
         const double a = s >= 0 ? vals[s] * dinv : 0.0;
         rs += a;
-        A[q] = V(a);
+        A[q] = M_t(a);
     }
-    if (sizeof(V) == 4) A[M.col_base + lane] = V(rs);
-    b[row] = V(rhs[row] * dinv);
+    if (VecT<V>::diff) A[M.col_base + lane] = M_t(rs);
+    b[row] = cvt<V>(rhs[row] * dinv);
 }
 
 // Replace column 0 of a scaled SELL operator by its row sum (FP32 difference form).
 template <typename V>
-__global__ void rowsum_form_kernel(int64_t n, const SliceMeta *meta, V *A) {
+__global__ void rowsum_form_kernel(int64_t n, const SliceMeta *meta, V *A) {   // V: the operator value type
     const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const SliceMeta M = meta[row / SLICE];
@@ -437,7 +504,7 @@ __global__ void csr_spmv_kernel(int64_t n, const int32_t *rowptr, const int32_t 
 template <typename S, typename D>
 __global__ void cast_kernel(int64_t n, const S *a, D *b) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = D(a[i]);
+    if (i < n) b[i] = cvt<D>(to_d(a[i]));
 }
 
 }  // namespace egfem

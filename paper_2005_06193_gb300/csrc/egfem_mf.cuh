@@ -3,9 +3,9 @@
 //
 // With P1 trial functions the trilinear form factors per cell K (Sec. 3.3):
 //     T_imk = sum_K iota^K_m S^K_ik,   iota^K_m = int_K eta_m,   S^K = |K| grad lambda (grad lambda)^T,
-// so with a = kappa + g(Pi u) and abar_K = sum_m iota^K_m a_m:
+// so with a = kappa + g(Pi u) and abar_K = sum_m (iota^K_m / |K|) a_m (S^K carries |K|):
 //     r_i  = sum_K abar_K (S^K u)_i - d_i
-//     J_ib = sum_K [ abar_K S^K_ib + (S^K u)_i c^K_b ],   c^K_b = sum_m iota^K_m g'(Pi u)_m Pi_mb
+//     J_ib = sum_K [ abar_K S^K_ib + (S^K u)_i c^K_b ],   c^K_b = sum_m (iota^K_m / |K|) g'(Pi u)_m Pi_mb
 // i.e. each cell contributes a scaled stiffness plus a rank-one matrix.  Pass 1 (one
 // thread per cell) evaluates abar_K, S^K u and c^K from the cell's own vertex values and
 // stores them; pass 2 (one thread per row, the row's cells from the vertex-to-cell list)
@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
     for (int a = 0; a < NV; ++a) uk[a] = u[M.verts[c * NV + a]];
 #pragma unroll
     for (int q = 0; q < NS; ++q) S[q] = M.S[c * NS + q];
-    const double vol = M.vol[c];
+    // S^K already carries |K|, so the cell weights are iota^K_m / |K| (sum over m: 1)
     double abar = 0.0, cb[NV];
 #pragma unroll
     for (int b = 0; b < NV; ++b) cb[b] = 0.0;
     if (M.nl.a_kind == EGFEM_G_NONE) {
-        abar = M.nl.kappa * vol;
+        abar = M.nl.kappa;
     } else {
         for (int l = 0; l < M.loc.nw; ++l) {
             const double io = M.loc.iota[l];
@@ -72,9 +72,8 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
             for (int a = 0; a < NV; ++a) pu += M.loc.w[l][a] * uk[a];
             double g, gp;
             g_eval(M.nl.a_kind, M.nl.a_pi, M.nl.a_scale, pu, g, gp);
-            const double iv = io * vol;
-            abar += iv * (M.nl.kappa + g);
-            const double e = iv * gp;
+            abar += io * (M.nl.kappa + g);
+            const double e = io * gp;
 #pragma unroll
             for (int b = 0; b < NV; ++b) cb[b] += e * M.loc.w[l][b];
         }

@@ -301,8 +301,8 @@ def _objective(P, h, theta, pc, ud, free, kappa=None):
 def test_autograd_adjoint_matches_central_differences_and_oracle(P, prec):
     """Gradient of j = 0.5 ||u - u_d||^2 with respect to a 4 x 4 piecewise-constant source
     theta and the W-space coefficient kappa, through torch.autograd and the CUDA adjoint,
-    against central differences (h = 1e-6) of FP64 re-solves (agreement 1e-5 relative: the
-    re-solves' own 1e-14 tolerance bounds the difference quotients to ~1e-10 absolute) and
+    against central differences (h = 1e-6) of FP64 re-solves (1e-5 relative + 1e-9 absolute:
+    the re-solves' own 1e-14 tolerance bounds the difference quotients to ~2e-10 absolute) and
     against the oracle's FP64 adjoint at the same solution (1e-10 relative)."""
     mesh, pc, ud_np, opts = _adjoint_setup(P, 16, 4, None, prec)
     h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2), opts)
@@ -326,12 +326,12 @@ def test_autograd_adjoint_matches_central_differences_and_oracle(P, prec):
         e[p] = eps
         th0 = theta.detach().reshape(-1)
         fd = (J_at((th0 + e).reshape(4, 4), kappa.detach()) - J_at((th0 - e).reshape(4, 4), kappa.detach())) / (2 * eps)
-        assert abs(fd - gt[p]) <= 1e-5 * max(1e-3, abs(gt[p])), (p, fd, gt[p])
+        assert abs(fd - gt[p]) <= 1e-5 * abs(gt[p]) + 1e-9, (p, fd, gt[p])
     for m in (100, 400, 700):
         e = torch.zeros_like(kappa)
         e[m] = eps
         fd = (J_at(theta.detach(), kappa.detach() + e) - J_at(theta.detach(), kappa.detach() - e)) / (2 * eps)
-        assert abs(fd - gk[m]) <= 1e-5 * max(1e-5, abs(gk[m])), (m, fd, gk[m])
+        assert abs(fd - gk[m]) <= 1e-5 * abs(gk[m]) + 1e-9, (m, fd, gk[m])
     # oracle adjoint at the GPU solution: dj/db = lambda, dj/df_K = sum_i lambda_i int_K phi_i
     orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
     un = u.detach().cpu().numpy()
