@@ -58,12 +58,13 @@ template <typename V>
 struct KWork {
     typename VecT<V>::mat *A = nullptr;   // Jacobi-scaled operator (SELL layout)
     V *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+    V *p2 = nullptr, *v2 = nullptr;       // second p / v buffers of the fused double-float iteration
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
     // grid of each iteration kernel: one wave of resident blocks (occupancy x SMs), capped
     // by the work, so the grid-stride loops run without a tail wave
-    int g_setup = 1, g_v = 1, g_s = 1, g_t = 1, g_x = 1, g_p = 1;
+    int g_setup = 1, g_v = 1, g_s = 1, g_t = 1, g_x = 1, g_p = 1, g_vp = 1, g_st = 1, g_xr = 1;
 };
 
 }  // namespace
@@ -105,6 +106,7 @@ struct egfem_t {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int maxc_tpl = 8;
     int64_t last_graph_launches = 0;    // graph launches of the last BiCGStab solve
+    int64_t last_graph_nodes = 0;       // kernels per graph launch of that solve
     // element-local operator (EGFEM_OP_MATRIX_FREE)
     double *cell_S = nullptr, *cell_E = nullptr;
     MfLocal mf_loc{};
@@ -221,8 +223,17 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     W.g_p = one_wave<V>(h, (const void *)kry_p<V>);
     EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
     EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(*W.A)));
-    V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t};
-    for (V **q : vec) { EG_TRY(dalloc(*q, size_t(h->n_pad))); EG_CUDA(cudaMemset(*q, 0, size_t(h->n_pad) * sizeof(V))); }
+    V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t, &W.p2, &W.v2};
+    const int nvec = std::is_same<V, df64>::value ? 10 : 8;
+    for (int k = 0; k < nvec; ++k) {
+        EG_TRY(dalloc(*vec[k], size_t(h->n_pad)));
+        EG_CUDA(cudaMemset(*vec[k], 0, size_t(h->n_pad) * sizeof(V)));
+    }
+    if constexpr (std::is_same<V, df64>::value) {
+        W.g_vp = one_wave<V>(h, (const void *)kry_vp<V>);
+        W.g_st = one_wave<V>(h, (const void *)kry_st<V>);
+        W.g_xr = one_wave<V>(h, (const void *)kry_xr<V>);
+    }
     W.ready = true;
     return EGFEM_OK;
 }
@@ -230,6 +241,17 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
 template <typename V>
 void enqueue_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
     KVecs<V> K = kvecs(h, W);
+    if constexpr (std::is_same<V, df64>::value) {
+        // fused three-kernel iteration; count is even, so every chunk starts on buffer 0
+        for (int it = 0; it < count; ++it) {
+            V *pi = (it & 1) ? W.p2 : W.p, *vi = (it & 1) ? W.v2 : W.v;
+            V *po = (it & 1) ? W.p : W.p2, *vo = (it & 1) ? W.v : W.v2;
+            kry_vp<V><<<W.g_vp, KRY_BLOCK, 0, s>>>(K, po, vo, pi, vi);
+            kry_st<V><<<W.g_st, KRY_BLOCK, 0, s>>>(K, vo);
+            kry_xr<V><<<W.g_xr, KRY_BLOCK, 0, s>>>(K, po, vo);
+        }
+        return;
+    }
     for (int it = 0; it < count; ++it) {
         kry_v<V><<<W.g_v, KRY_BLOCK, 0, s>>>(K);
         kry_s<V><<<W.g_s, KRY_BLOCK, 0, s>>>(K);
@@ -240,8 +262,14 @@ void enqueue_iterations(egfem_t *h, KWork<V> &W, int count, cudaStream_t s) {
 }
 
 template <typename V>
+int chunk_of(const egfem_t *h) {
+    const int c = std::max(1, h->opts.graph_chunk);
+    return std::is_same<V, df64>::value ? (c + 1) / 2 * 2 : c;   // fused iterations come in pairs
+}
+
+template <typename V>
 egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
-    const int chunk = std::max(1, h->opts.graph_chunk);
+    const int chunk = chunk_of<V>(h);
     if (W.graph && W.graph_chunk == chunk) return EGFEM_OK;
     if (W.graph) { cudaGraphExecDestroy(W.graph); W.graph = nullptr; }
     cudaGraph_t g;
@@ -265,6 +293,7 @@ egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, i
     kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit, stall);
     EG_CUDA(cudaGetLastError());
     h->last_graph_launches = 0;
+    h->last_graph_nodes = int64_t(std::is_same<V, df64>::value ? 3 : 5) * chunk_of<V>(h);
     for (;;) {
         EG_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
         EG_CUDA(cudaStreamSynchronize(h->hs));
@@ -740,7 +769,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             if (fp32) status = run_bicgstab(h, h->k32, std::max(eta, kMixedEtaFloor), h->opts.krylov_maxit, kMixedStall, &done, &it);
             else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, 0, &done, &it);
             if (status != EGFEM_OK) break;
-            S.kernel_launches += 1 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+            S.kernel_launches += 1 + h->last_graph_launches * h->last_graph_nodes;
             S.krylov_iters += it;
             its_step += it;
             const bool failed = done == K_NONFINITE || (done == K_BREAKDOWN && it == 0) || (fp32 && done == K_BREAKDOWN);
@@ -912,7 +941,7 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
     if (!mixed) {
         EG_TRY(run_bicgstab(h, W, 1e-13, h->opts.krylov_maxit, 0, &done, &it));
         S->krylov_iters += it;
-        S->kernel_launches += 5 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+        S->kernel_launches += 5 + h->last_graph_launches * h->last_graph_nodes;
         if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
         cast_kernel<V, double><<<g, 256, 0, h->hs>>>(h->n, W.x, d_lambda);
         EG_CUDA(cudaGetLastError());
@@ -936,7 +965,7 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
         adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->r, h->csf.dir, h->dinv, W.b);
         EG_TRY(run_bicgstab(h, W, 1e-3, h->opts.krylov_maxit, kMixedStall, &done, &it));
         S->krylov_iters += it;
-        S->kernel_launches += 6 + int64_t(h->last_graph_launches) * 5 * std::max(1, h->opts.graph_chunk);
+        S->kernel_launches += 6 + h->last_graph_launches * h->last_graph_nodes;
         if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
         newton_update_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_lambda, W.x, -1.0);
         EG_CUDA(cudaGetLastError());
@@ -1011,6 +1040,26 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         std::vector<SliceMeta> hm(size_t(h->csf.n_slices));
         EG_CUDA(cudaMemcpy(hm.data(), h->csf.meta, hm.size() * sizeof(SliceMeta), cudaMemcpyDeviceToHost));
         for (const SliceMeta &M : hm) if (M.off_base < 0) ce_nonuni += double(M.ncol) * SLICE;
+    }
+    if constexpr (std::is_same<V, df64>::value) {
+        // fused iteration: per row, kry_vp reads r, p, v, rh and writes p, v; kry_st reads r, v and
+        // writes t; kry_xr reads r, v, p, t, rh, x and writes x, r (gathered neighbours counted once)
+        auto runf = [&](const char *name, double bytes, double flops, auto launch) -> egfem_status {
+            EG_CUDA(cudaMemsetAsync(&h->st->done, 0, sizeof(int32_t), h->hs));
+            EG_TRY(timeit(name, bytes, flops, 0, launch));
+            int32_t done = 0;
+            EG_CUDA(cudaMemcpy(&done, &h->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (done != K_RUNNING) out->ms[out->count - 1] = NAN;
+            return EGFEM_OK;
+        };
+        EG_TRY(runf("kry_vp", CE * mb + ce_nonuni * 4 + 6 * N * vb + SM, 2 * CE + 6 * N,
+                    [&] { kry_vp<V><<<W.g_vp, KRY_BLOCK, 0, h->hs>>>(K, W.p2, W.v2, W.p, W.v); }));
+        EG_TRY(runf("kry_st", CE * mb + ce_nonuni * 4 + 3 * N * vb + SM, 2 * CE + 6 * N,
+                    [&] { kry_st<V><<<W.g_st, KRY_BLOCK, 0, h->hs>>>(K, W.v2); }));
+        EG_TRY(runf("kry_xr", 8 * N * vb, 12 * N, [&] { kry_xr<V><<<W.g_xr, KRY_BLOCK, 0, h->hs>>>(K, W.p2, W.v2); }));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return join_out(h, user);
     }
     EG_TRY(run("kry_v", CE * mb + ce_nonuni * 4 + 3 * N * vb + SM, 2 * CE + 2 * N, kry_v<V>, W.g_v));
     EG_TRY(run("kry_s", 3 * N * vb, 2 * N, kry_s<V>, W.g_s));

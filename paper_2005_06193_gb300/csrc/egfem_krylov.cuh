@@ -430,7 +430,6 @@ __global__ void __launch_bounds__(KRY_BLOCK) kry_p(KVecs<V> K) {
     }
 }
 
-#undef KRY_LOOP
 
 // ---------------------------------------------------------------------------------
 // Newton-level helpers
@@ -506,5 +505,135 @@ __global__ void cast_kernel(int64_t n, const S *a, D *b) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < n) b[i] = cvt<D>(to_d(a[i]));
 }
+
+// ---------------------------------------------------------------------------------
+// Fused iteration for double-float vectors: three kernels instead of five.
+//
+// On the FP32 pipe a few extra additions are cheap, so each SpMV recomputes the vector
+// it multiplies at the gathered columns from the vectors it came from, instead of
+// reading a stored copy written by a separate kernel:
+//   kry_vp:  p' = r + beta (p - omega v)  (own rows stored);  v' = A p';  alpha = rho / (rh, v')
+//   kry_st:  s = r - alpha v';            t = A s;            omega = (t, s) / (t, t)
+//   kry_xr:  x += alpha p' + omega s;     r = s - omega t;    rho', beta, convergence
+// p and v alternate between two buffers (odd / even iterations), since kry_vp reads the
+// old values at neighbouring rows while it writes the new ones.
+// ---------------------------------------------------------------------------------
+
+template <typename V, typename F>
+__device__ __forceinline__ Pack<V> sell_rows_f(const KVecs<V> &K, int64_t r0, const Pack<V> &xi, F xval) {
+    constexpr int R = VecT<V>::R;
+    using M_t = typename VecT<V>::mat;
+    const SliceMeta M = K.meta[r0 / SLICE];
+    const int lane = int(r0 % SLICE);
+    Pack<V> y;
+    M_t a0[R];
+    ldm(K.A + M.col_base + lane, a0);
+#pragma unroll
+    for (int j = 0; j < R; ++j) y.v[j] = a0[j] * xi.v[j];
+    for (int c = 1; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        M_t a[R];
+        ldm(K.A + q, a);
+        int32_t col[R];
+        row_cols(K, M, r0, q, c, col);
+#pragma unroll
+        for (int j = 0; j < R; ++j) y.v[j] += a[j] * (xval(col[j]) - xi.v[j]);
+    }
+    return y;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(KRY_BLOCK) kry_vp(KVecs<V> K, V *p_out, V *v_out, const V *p_in, const V *v_in) {
+    constexpr int R = VecT<V>::R;
+    if (finished(K.st)) return;
+    const V beta = cvt<V>(K.st->beta), omega = cvt<V>(K.st->omega);
+    auto pnew = [&](int32_t j) { return ldg1(K.r + j) + beta * (ldg1(p_in + j) - omega * ldg1(v_in + j)); };
+    DotAcc<V> a;
+    KRY_LOOP(K) {
+        const Pack<V> r = ldv(K.r + r0), p = ldv(p_in + r0), v = ldv(v_in + r0);
+        Pack<V> pi;
+#pragma unroll
+        for (int j = 0; j < R; ++j) pi.v[j] = r.v[j] + beta * (p.v[j] - omega * v.v[j]);
+        stv(p_out + r0, pi);
+        const Pack<V> y = sell_rows_f(K, r0, pi, pnew);
+        stv(v_out + r0, y);
+        const Pack<V> rh = ldv(K.rh + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) a.add(rh.v[j], y.v[j]);
+    }
+    double acc[1] = {a.value()}, tot[1];
+    if (grid_reduce<1>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
+        KState &S = *K.st;
+        if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
+        else S.alpha = S.rho / tot[0];
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(KRY_BLOCK) kry_st(KVecs<V> K, const V *v_cur) {
+    constexpr int R = VecT<V>::R;
+    if (finished(K.st)) return;
+    const V alpha = cvt<V>(K.st->alpha);
+    auto sval = [&](int32_t j) { return ldg1(K.r + j) - alpha * ldg1(v_cur + j); };
+    DotAcc<V> ts, tt;
+    KRY_LOOP(K) {
+        const Pack<V> r = ldv(K.r + r0), v = ldv(v_cur + r0);
+        Pack<V> s;
+#pragma unroll
+        for (int j = 0; j < R; ++j) s.v[j] = r.v[j] - alpha * v.v[j];
+        const Pack<V> y = sell_rows_f(K, r0, s, sval);
+        stv(K.t + r0, y);
+#pragma unroll
+        for (int j = 0; j < R; ++j) { ts.add(y.v[j], s.v[j]); tt.add(y.v[j], y.v[j]); }
+    }
+    double acc[2] = {ts.value(), tt.value()}, tot[2];
+    if (grid_reduce<2>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
+        KState &S = *K.st;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
+        else S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(KRY_BLOCK) kry_xr(KVecs<V> K, const V *p_cur, const V *v_cur) {
+    constexpr int R = VecT<V>::R;
+    if (finished(K.st)) return;
+    const V alpha = cvt<V>(K.st->alpha), omega = cvt<V>(K.st->omega);
+    DotAcc<V> rho, rr;
+    KRY_LOOP(K) {
+        const Pack<V> r0v = ldv(K.r + r0), v = ldv(v_cur + r0), p = ldv(p_cur + r0), t = ldv(K.t + r0),
+                      rh = ldv(K.rh + r0);
+        Pack<V> x = ldv(K.x + r0), r;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const V s = r0v.v[j] - alpha * v.v[j];
+            x.v[j] += alpha * p.v[j] + omega * s;
+            r.v[j] = s - omega * t.v[j];
+            rho.add(rh.v[j], r.v[j]);
+            rr.add(r.v[j], r.v[j]);
+        }
+        stv(K.x + r0, x);
+        stv(K.r + r0, r);
+    }
+    double acc[2] = {rho.value(), rr.value()}, tot[2];
+    if (grid_reduce<2>(acc, K.part, &K.st->ticket, tot) && threadIdx.x == 0) {
+        KState &S = *K.st;
+        S.iter += 1;
+        S.rr = tot[1];
+        if (tot[1] < 0.81 * S.best_rr) { S.best_rr = tot[1]; S.last_improve = S.iter; }
+        const double blowup = S.stall > 0 ? 1e6 : 1e24;
+        if (!isfinite(tot[0]) || !isfinite(tot[1]) || tot[1] > blowup * S.rr0) S.done = K_NONFINITE;
+        else if (tot[1] <= S.tol2) S.done = K_CONVERGED;
+        else if (tot[0] == 0.0 || S.omega == 0.0) S.done = K_BREAKDOWN;
+        else if (S.iter >= S.maxit) S.done = K_MAXIT;
+        else if (S.stall > 0 && S.best_rr <= S.stall_rr && S.iter - S.last_improve >= S.stall) S.done = K_STAGNATED;
+        else {
+            S.beta = (tot[0] / S.rho) * (S.alpha / S.omega);
+            S.rho = tot[0];
+        }
+    }
+}
+
+#undef KRY_LOOP
 
 }  // namespace egfem
