@@ -35,8 +35,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
-FP64_TFLOPS_MEASURED = 1.20   # FP64 FMA throughput measured on this machine's GB300 (dependent-chain-free probe)
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+SMS = 152                 # GB300 streaming multiprocessors
+DFMA_PER_SM_CLK = 2       # FP64 FMAs per SM per clock on GB300 (nominal 1.25 TFLOP/s FP64)
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
+# captured for the current code); the captures and their commands are summarised in profiles/.
+NCU_TRAFFIC = {}
 
 
 def load_peaks():
@@ -45,6 +49,32 @@ def load_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return PEAKS_FALLBACK, "fallback"
+
+
+def fp64_peak_tflops(peaks):
+    """FP64 FMA peak from unit counts and the maximum SM clock: SMs x DFMA/clk x 2 flops x f."""
+    return SMS * DFMA_PER_SM_CLK * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def roofline_of(k, hbm, peak_kind, fp64_peak):
+    """Roofline of one profiled kernel: whichever of HBM bandwidth and (for FP64 kernels) the
+    FP64 pipe it uses the larger fraction of is its bound."""
+    sec = k["ms"] / 1e3
+    gbs = k["bytes"] / sec / 1e9
+    tf = k["flops"] / sec / 1e12
+    r = {"kernel": k["name"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
+         "hbm_peak_kind": f"{peak_kind} (hbm_gbs, copy)",
+         "traffic": NCU_TRAFFIC.get(k["name"]), "bytes_per_launch": k["bytes"], "flops_per_launch": k["flops"]}
+    if k["fp64"] and tf / fp64_peak > gbs / hbm:
+        r.update({"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                  "peak_kind": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock"})
+    else:
+        r.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "peak_kind": f"{peak_kind} (hbm_gbs, copy)"})
+    if k["fp64"]:
+        r["fp64_tflops"] = tf
+        r["fp64_frac"] = tf / fp64_peak
+    return r
 
 
 class ClockSampler:
@@ -381,38 +411,48 @@ def main():
     prof = h.profile_kernels(u, d, reps=20)
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
-    chunk = h.options.graph_chunk
+    fp64_peak = fp64_peak_tflops(peaks)
     counts = {"csf_fused": st.newton_iters + 1}
-    for k in ("kry_v", "kry_s", "kry_t", "kry_x", "kry_p"):
+    for k in ("kry_v", "kry_s", "kry_t", "kry_x", "kry_p", "kry_persistent"):
         counts[k] = int(st.krylov_iters)
     share = {p["name"]: p["ms"] * counts.get(p["name"], 0) for p in prof}
     total_share = sum(share.values())
     dom = max(prof, key=lambda p: share[p["name"]])
-    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": f"{peak_kind} (hbm_gbs, copy)", "traffic": None,
-                "share_of_solve": share[dom["name"]] / (ms_max / args.steps),
-                "fp64_tflops": dom["flops"] / (dom["ms"] / 1e3) / 1e12,
-                "fp64_frac_of_measured": dom["flops"] / (dom["ms"] / 1e3) / 1e12 / FP64_TFLOPS_MEASURED}
+    roofline = roofline_of(dom, hbm, peak_kind, fp64_peak)
+    roofline["share_of_solve"] = share[dom["name"]] / (ms_max / args.steps)
+    if dom["name"] == "kry_persistent":
+        roofline["units_per_launch"] = f"one launch runs a whole BiCGStab solve; ms and bytes are per iteration"
     csf = next(p for p in prof if p["name"] == "csf_fused")
     tensor_action = {"kernel": "csf_fused", "ms": csf["ms"], "achieved_gbs": csf["bytes"] / (csf["ms"] / 1e3) / 1e9,
                      "frac_hbm": csf["bytes"] / (csf["ms"] / 1e3) / 1e9 / hbm,
                      "fp64_tflops": csf["flops"] / (csf["ms"] / 1e3) / 1e12,
-                     "fp64_frac_of_measured": csf["flops"] / (csf["ms"] / 1e3) / 1e12 / FP64_TFLOPS_MEASURED,
+                     "fp64_frac_of_peak": csf["flops"] / (csf["ms"] / 1e3) / 1e12 / fp64_peak,
                      "bytes_per_launch": csf["bytes"]}
+
+    # the same FP64 solve with the graph-captured iteration kernels instead of the persistent solve
+    hg = P.Handle(mesh, prob, P.default_options(krylov_persistent=0))
+    u.zero_()
+    hg.newton_solve(u, d)
+    msg, sg = timed_solves(torch, hg, d, u, min(args.steps, 3), barrier)
+    graph_driver = {"value": world * min(args.steps, 3) / (msg / 1e3), "unit": "solves/s",
+                    "ms_per_step": msg / min(args.steps, 3), "krylov_iters": int(sg[-1].krylov_iters),
+                    "gpu_launches_per_solve": int(sg[-1].kernel_launches)}
+    hg.close()
 
     out = {"metric": "newton_solves_per_s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"egfem_newton_2d_p1p2_u2_{args.n}x{args.n}", "grid": args.n, "n_p1": mesh.n_nodes,
                       "n_p2": h.sizes.n_wa, "newton_rtol": 1e-10, "precision": "fp64", "operator": "csf",
-                      "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (no flush)"},
+                      "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (no flush)",
+                      "krylov_driver": "persistent" if h.options.krylov_persistent else "graph"},
            "newton_iters": st.newton_iters, "krylov_iters": int(st.krylov_iters),
            "final_rel_residual": st.res_final / st.res0,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * mesh.n_nodes,
                    "d2h_bytes_per_step": 8 * mesh.n_nodes},
            "gpu_launches": launches, "roofline": roofline, "tensor_action": tensor_action, "clocks": clocks,
-           "kernels": [{**p, "share": share[p["name"]] / total_share} for p in prof]}
+           "kernels": [{**p, "share": share[p["name"]] / total_share} for p in prof],
+           "fp64_graph_driver": graph_driver}
 
     if not args.no_mixed:
         hm = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED))
@@ -426,8 +466,8 @@ def main():
                         "newton_iters": sl.newton_iters, "krylov_iters": int(sl.krylov_iters),
                         "final_rel_residual": sl.res_final / sl.res0, "speedup_vs_fp64": (ms_max / msm),
                         "fp64_rescues": sl.fp64_rescues,
-                        "kernels": [{"name": p["name"], "ms": p["ms"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9}
-                                    for p in mprof]}
+                        "kernels": [{"name": p["name"], "ms": p["ms"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9,
+                                     "frac_hbm": p["bytes"] / (p["ms"] / 1e3) / 1e9 / hbm} for p in mprof]}
         out["mixed"]["gpu_launches"] = int(sum(s.kernel_launches for s in sm))
         hm.close()
 

@@ -114,6 +114,9 @@ typedef struct {
     int32_t op;              /* egfem_operator  (default EGFEM_OP_CSF)                       */
     int32_t graph_chunk;     /* BiCGStab iterations per captured CUDA graph (default 32)     */
     int32_t fixed_eta;       /* nonzero: use eta_max for every step (no Eisenstat-Walker)    */
+    int32_t krylov_persistent; /* nonzero (default): each BiCGStab solve is one cooperative
+                                  launch with grid barriers; 0: graph-captured iteration
+                                  kernels (graph_chunk iterations per graph launch)          */
 } egfem_options;
 
 #define EGFEM_HIST 64
@@ -262,6 +265,19 @@ egfem_status egfem_load_cellwise_transpose(egfem_handle h, const double *d_lam, 
  * wa_coords (optional, [n_wa * dim]) the W_a node coordinates. */
 egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem_problem *prob, int64_t *count,
                                   int64_t *I, int64_t *M, int64_t *K, double *V, int64_t *n_wa, double *wa_coords);
+
+/* Self-test of the bounded device-side wait of the persistent BiCGStab solve (no handle).
+ * Launches `blocks` blocks (1..64) of which the first `arrive` (0..blocks) enter one grid
+ * barrier.  With arrive == blocks the launch is cooperative and every block must pass; with
+ * arrive < blocks the barrier cannot complete and each waiting block gives up after wait_ms
+ * milliseconds (0 < wait_ms <= 2000) and raises the barrier's error word.  ok_host (host,
+ * [blocks]) receives 1 for a block that passed, 0 for one that gave up, -1 for one that did
+ * not arrive; *err_host (host, optional) the error word.  Synchronous; allocates and frees
+ * its own 0.3 KB of device memory.  Errors: EGFEM_ERR_INVALID_ARG for sizes out of range,
+ * EGFEM_ERR_CUDA for a failed launch.  The paper has no counterpart: this checks the
+ * library's own failure handling. */
+egfem_status egfem_selftest_grid_barrier(int32_t blocks, int32_t arrive, double wait_ms, int32_t *ok_host,
+                                         int32_t *err_host);
 
 /* Sum of squares of d_r over the rows whose d_dirichlet entry is 0 (the quantity of the
  * Newton convergence test), written to the device scalar *d_out, for callers that cannot

@@ -5,4 +5,5 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in include/egfe
 ``torch.autograd.Function``.
 """
 from .egfem import (G_EXP, G_NONE, G_POW, OP_CSF, OP_MATRIX_FREE, PREC_FP64, PREC_MIXED, BatchHandle,  # noqa: F401
-                    EgfemError, Handle, default_options, inspect_tensor, lib, make_problem)
+                    EgfemError, Handle, default_options, inspect_tensor, lib, make_problem,
+                    selftest_grid_barrier)

@@ -17,6 +17,7 @@
 #include "egfem_krylov.cuh"
 #include "egfem_batch.cuh"
 #include "egfem_mf.cuh"
+#include "egfem_persist.cuh"
 
 using namespace egfem;
 
@@ -59,6 +60,9 @@ struct KWork {
     typename VecT<V>::mat *A = nullptr;   // Jacobi-scaled operator (SELL layout)
     V *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     V *p2 = nullptr, *v2 = nullptr;       // second p / v buffers of the fused double-float iteration
+    PGrid *bar = nullptr;                 // grid barrier of the persistent solve
+    double *ppart = nullptr;              // its block partials: 3 slots x 2 values x g_pk
+    int g_pk = 0;                         // blocks of the persistent solve (0: not available)
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
@@ -107,6 +111,8 @@ struct egfem_t {
     int maxc_tpl = 8;
     int64_t last_graph_launches = 0;    // graph launches of the last BiCGStab solve
     int64_t last_graph_nodes = 0;       // kernels per graph launch of that solve
+    int64_t last_krylov_kernels = 0;    // kernels the last BiCGStab solve launched
+    bool coop = false;                  // the device supports cooperative launches
     // element-local operator (EGFEM_OP_MATRIX_FREE)
     double *cell_S = nullptr, *cell_E = nullptr;
     MfLocal mf_loc{};
@@ -229,6 +235,18 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
         EG_TRY(dalloc(*vec[k], size_t(h->n_pad)));
         EG_CUDA(cudaMemset(*vec[k], 0, size_t(h->n_pad) * sizeof(V)));
     }
+    if (h->coop) {
+        // every block of a cooperative launch must be resident: at most occupancy x SMs
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kry_persistent<V>, KRY_BLOCK, 0) == cudaSuccess &&
+            nb >= 1) {
+            const int64_t work = (h->n_pad + int64_t(KRY_BLOCK) * VecT<V>::R - 1) / (int64_t(KRY_BLOCK) * VecT<V>::R);
+            W.g_pk = int(std::max<int64_t>(1, std::min<int64_t>(work, int64_t(nb) * h->sms)));
+            EG_TRY(dalloc(W.bar, 1));
+            EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
+            EG_TRY(dalloc(W.ppart, size_t(6) * size_t(W.g_pk)));
+        }
+    }
     if constexpr (std::is_same<V, df64>::value) {
         W.g_vp = one_wave<V>(h, (const void *)kry_vp<V>);
         W.g_st = one_wave<V>(h, (const void *)kry_st<V>);
@@ -288,6 +306,27 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
 template <typename V>
 egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall, int32_t *done,
                           int32_t *iters) {
+    if (h->opts.krylov_persistent && W.g_pk > 0) {
+        // the whole solve in one cooperative launch
+        KVecs<V> K = kvecs(h, W);
+        K.part = W.ppart;
+        PGrid *bar = W.bar;
+        void *args[] = {(void *)&K, (void *)&bar, (void *)&rtol, (void *)&maxit, (void *)&stall};
+        EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
+        EG_CUDA(cudaLaunchCooperativeKernel((const void *)kry_persistent<V>, dim3(W.g_pk), dim3(KRY_BLOCK), args, 0, h->hs));
+        EG_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        EG_CUDA(cudaStreamSynchronize(h->hs));
+        h->last_graph_launches = 0;
+        h->last_graph_nodes = 0;
+        h->last_krylov_kernels = 1;
+        *done = h->h_st->done;
+        *iters = h->h_st->iter;
+        if (*done == K_TIMEOUT) {
+            g_last_error = "BiCGStab: a grid-barrier wait of the persistent solve ran out";
+            return EGFEM_ERR_TIMEOUT;
+        }
+        return EGFEM_OK;
+    }
     EG_TRY(ensure_graph(h, W));
     KVecs<V> K = kvecs(h, W);
     kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, rtol, maxit, stall);
@@ -301,6 +340,7 @@ egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, i
         EG_CUDA(cudaGraphLaunch(W.graph, h->hs));
         ++h->last_graph_launches;
     }
+    h->last_krylov_kernels = 1 + h->last_graph_launches * h->last_graph_nodes;
     *done = h->h_st->done;
     *iters = h->h_st->iter;
     return EGFEM_OK;
@@ -362,6 +402,9 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     h->dim = mesh->dim; h->n = mesh->n_nodes; h->ncells = mesh->n_cells;
     EG_CUDA(cudaGetDevice(&h->device));
     EG_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+    int coop = 0;
+    EG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    h->coop = coop != 0;
     // W spaces
     HostWSpace Wa, Wc;
     std::vector<int32_t> c2wa, c2wc;
@@ -525,6 +568,44 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
 
 extern "C" {
 
+egfem_status egfem_selftest_grid_barrier(int32_t blocks, int32_t arrive, double wait_ms, int32_t *ok_host,
+                                         int32_t *err_host) {
+    if (blocks < 1 || blocks > 64 || arrive < 0 || arrive > blocks || !(wait_ms > 0.0) || wait_ms > 2000.0 || !ok_host) {
+        g_last_error = "selftest_grid_barrier: blocks in 1..64, arrive in 0..blocks, 0 < wait_ms <= 2000, ok_host set";
+        return EGFEM_ERR_INVALID_ARG;
+    }
+    PGrid *g = nullptr;
+    int32_t *ok = nullptr;
+    EG_TRY(dalloc(g, 1));
+    egfem_status st = EGFEM_OK;
+    auto fail = [&](cudaError_t e, const char *what) {
+        g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+        st = EGFEM_ERR_CUDA;
+    };
+    cudaError_t e = cudaMalloc((void **)&ok, sizeof(int32_t) * size_t(blocks));
+    if (e != cudaSuccess) fail(e, "cudaMalloc");
+    if (st == EGFEM_OK && (e = cudaMemset(g, 0, sizeof(PGrid))) != cudaSuccess) fail(e, "cudaMemset");
+    if (st == EGFEM_OK) {
+        unsigned long long limit = (unsigned long long)(wait_ms * 1e6);
+        if (arrive == blocks) {
+            void *args[] = {(void *)&g, (void *)&arrive, (void *)&limit, (void *)&ok};
+            e = cudaLaunchCooperativeKernel((const void *)pk_barrier_selftest, dim3(blocks), dim3(64), args, 0, nullptr);
+        } else {
+            pk_barrier_selftest<<<blocks, 64>>>(g, arrive, limit, ok);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) fail(e, "launch");
+    }
+    if (st == EGFEM_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) fail(e, "cudaDeviceSynchronize");
+    if (st == EGFEM_OK && (e = cudaMemcpy(ok_host, ok, sizeof(int32_t) * size_t(blocks), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        fail(e, "cudaMemcpy");
+    if (st == EGFEM_OK && err_host && (e = cudaMemcpy(err_host, &g->err, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        fail(e, "cudaMemcpy");
+    cudaFree(ok);
+    cudaFree(g);
+    return st;
+}
+
 void egfem_default_options(egfem_options *o) {
     if (!o) return;
     o->newton_rtol = 1e-10;
@@ -537,6 +618,7 @@ void egfem_default_options(egfem_options *o) {
     o->op = EGFEM_OP_CSF;
     o->graph_chunk = 32;
     o->fixed_eta = 0;
+    o->krylov_persistent = 1;
 }
 
 egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
@@ -566,10 +648,12 @@ void egfem_destroy(egfem_handle h) {
     for (KWork<double> *W : {&h->k64}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->ppart);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->ppart);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
     dfree(h->bst); dfree(h->tiles); dfree(h->bpart);
@@ -769,7 +853,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             if (fp32) status = run_bicgstab(h, h->k32, std::max(eta, kMixedEtaFloor), h->opts.krylov_maxit, kMixedStall, &done, &it);
             else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, 0, &done, &it);
             if (status != EGFEM_OK) break;
-            S.kernel_launches += 1 + h->last_graph_launches * h->last_graph_nodes;
+            S.kernel_launches += h->last_krylov_kernels;
             S.krylov_iters += it;
             its_step += it;
             const bool failed = done == K_NONFINITE || (done == K_BREAKDOWN && it == 0) || (fp32 && done == K_BREAKDOWN);
@@ -941,7 +1025,7 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
     if (!mixed) {
         EG_TRY(run_bicgstab(h, W, 1e-13, h->opts.krylov_maxit, 0, &done, &it));
         S->krylov_iters += it;
-        S->kernel_launches += 5 + h->last_graph_launches * h->last_graph_nodes;
+        S->kernel_launches += 4 + h->last_krylov_kernels;
         if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
         cast_kernel<V, double><<<g, 256, 0, h->hs>>>(h->n, W.x, d_lambda);
         EG_CUDA(cudaGetLastError());
@@ -965,7 +1049,7 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
         adjoint_rhs_kernel<V><<<g, 256, 0, h->hs>>>(h->n, h->r, h->csf.dir, h->dinv, W.b);
         EG_TRY(run_bicgstab(h, W, 1e-3, h->opts.krylov_maxit, kMixedStall, &done, &it));
         S->krylov_iters += it;
-        S->kernel_launches += 6 + h->last_graph_launches * h->last_graph_nodes;
+        S->kernel_launches += 5 + h->last_krylov_kernels;
         if (done == K_NONFINITE) return EGFEM_ERR_NONFINITE;
         newton_update_kernel<V><<<g, 256, 0, h->hs>>>(h->n, d_lambda, W.x, -1.0);
         EG_CUDA(cudaGetLastError());
@@ -1040,6 +1124,33 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         std::vector<SliceMeta> hm(size_t(h->csf.n_slices));
         EG_CUDA(cudaMemcpy(hm.data(), h->csf.meta, hm.size() * sizeof(SliceMeta), cudaMemcpyDeviceToHost));
         for (const SliceMeta &M : hm) if (M.off_base < 0) ce_nonuni += double(M.ncol) * SLICE;
+    }
+    if (h->opts.krylov_persistent && W.g_pk > 0) {
+        // persistent solve: a fixed number of iterations (rtol 0), reported per iteration.  Per
+        // row and iteration: A reads p, rh, writes v; B1 reads r, v, writes s; B2 reads s, writes
+        // t; C reads s, p, t, rh, x, writes x, r; D reads r, v, p, writes p (19 vector passes);
+        // the operator is read twice.
+        const int32_t iters = 40;
+        KVecs<V> KP = kvecs(h, W);
+        KP.part = W.ppart;
+        PGrid *bar = W.bar;
+        double rtol0 = 0.0;
+        int32_t maxit = iters, stall = 0;
+        void *args[] = {(void *)&KP, (void *)&bar, (void *)&rtol0, (void *)&maxit, (void *)&stall};
+        cudaError_t le = cudaSuccess;
+        EG_TRY(timeit("kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
+            cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs);
+            const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kry_persistent<V>, dim3(W.g_pk), dim3(KRY_BLOCK),
+                                                              args, 0, h->hs);
+            if (e != cudaSuccess) le = e;
+        }));
+        EG_CUDA(le);
+        int32_t done = 0;
+        EG_CUDA(cudaMemcpy(&done, &h->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        out->ms[out->count - 1] = (done == K_MAXIT) ? out->ms[out->count - 1] / iters : NAN;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return join_out(h, user);
     }
     if constexpr (std::is_same<V, df64>::value) {
         // fused iteration: per row, kry_vp reads r, p, v, rh and writes p, v; kry_st reads r, v and

@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int32),
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double), ("krylov_maxit", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("op", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
-                ("fixed_eta", ctypes.c_int32)]
+                ("fixed_eta", ctypes.c_int32), ("krylov_persistent", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
         "egfem_inspect_tensor": (S, [ctypes.POINTER(Mesh), ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_int64),
                                      _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
         "egfem_free_norm2_noalloc": (S, [ctypes.c_int64, _DP, _DP, _DP, _P]),
+        "egfem_selftest_grid_barrier": (S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "egfem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "egfem_last_error": (ctypes.c_char_p, []),
     }
@@ -145,6 +147,14 @@ def default_options(**kw) -> Options:
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
         setattr(o, k, v)
     return o
+
+
+def selftest_grid_barrier(blocks: int, arrive: int, wait_ms: float):
+    """Run the bounded grid-barrier self-test; returns (per-block outcome list, error word)."""
+    ok = (ctypes.c_int32 * blocks)()
+    err = ctypes.c_int32(0)
+    _check(lib().egfem_selftest_grid_barrier(blocks, arrive, wait_ms, ok, ctypes.byref(err)), "selftest_grid_barrier")
+    return list(ok), err.value
 
 
 def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_scale=1.0, gamma=0.0, kappa=1.0) -> Problem:

@@ -120,3 +120,13 @@ def test_bad_problem_is_rejected(egf):
     with pytest.raises(egf.EgfemError) as e:
         egf.inspect_tensor(mesh, egf.make_problem(a_degree=4))
     assert e.value.status == 1
+
+
+def test_barrier_selftest_rejects_bad_sizes_without_a_gpu(egf):
+    """Argument checks of the grid-barrier self-test happen before any CUDA call."""
+    L = egf.lib()
+    import ctypes
+    ok = (ctypes.c_int32 * 4)()
+    for blocks, arrive, wait in [(0, 0, 10.0), (65, 1, 10.0), (4, 5, 10.0), (4, 2, 0.0), (4, 2, 5000.0)]:
+        assert L.egfem_selftest_grid_barrier(blocks, arrive, wait, ok, None) == 1
+    assert L.egfem_selftest_grid_barrier(4, 2, 10.0, None, None) == 1
