@@ -83,8 +83,10 @@ struct egfem_t {
     int64_t n = 0, nwa = 0, nwc = 0, ncells = 0;
     DeviceCSF csf;
     std::vector<double> wa_coords, wc_coords;
-    uint8_t *wa_kind = nullptr;
-    int32_t *wa_sup = nullptr;
+    uint8_t *wa_kind = nullptr, *wc_kind = nullptr;
+    int32_t *wa_sup = nullptr, *wc_sup = nullptr;
+    double *wa_val = nullptr, *wa_gp = nullptr;   // nodal a_m, g_a' (wnode_kernel)
+    double *wc_val = nullptr, *wc_gp = nullptr;   // nodal c_m, g_c'
     int32_t *cell_verts = nullptr;
     double *cell_vol = nullptr;
     int64_t *v2c_ptr = nullptr;
@@ -131,6 +133,7 @@ struct egfem_t {
     int tile_R = 0;
     double *bpart = nullptr;
     cudaGraphExec_t bgraph64 = nullptr, bgraph32 = nullptr;
+    PGrid *bbar = nullptr;              // grid barrier of the persistent batched solve
     int bgraph_chunk = 0, bgraph_tiles = 0;
 };
 
@@ -153,7 +156,7 @@ int pick_maxc(int maxc) {
 }
 
 template <int DIM>
-void launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
+int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     MfArgs M{};
     M.n_cells = h->ncells; M.n_rows = h->n; M.dim = DIM;
     M.verts = h->cell_verts; M.S = h->cell_S; M.vol = h->cell_vol; M.v2c_ptr = h->v2c_ptr; M.v2c = h->v2c;
@@ -166,21 +169,35 @@ void launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
         case 32: mf_row_kernel<DIM, 32><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
         default: mf_row_kernel<DIM, 64><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
     }
+    return 2;
 }
 
-void launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
-    if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
-        if (h->dim == 2) launch_mf<2>(h, A, s);
-        else launch_mf<3>(h, A, s);
-        return;
+// Pointwise nonlinearity + residual + Jacobian fill at A.u; returns the kernels launched.
+int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
+    if (h->opts.op == EGFEM_OP_MATRIX_FREE) return h->dim == 2 ? launch_mf<2>(h, A, s) : launch_mf<3>(h, A, s);
+    int launched = 1;
+    // each W node's nonlinearity once (Sec. 3.2), then the tensor action gathers it per fibre
+    CsfArgs B = A;
+    if (h->wa_val) {
+        wnode_kernel<<<unsigned((h->nwa + 255) / 256), 256, 0, s>>>(h->nwa, h->wa_kind, h->wa_sup, A.u, h->nl.a_kind, h->nl.a_pi,
+                                                                  h->nl.a_scale, h->nl.kappa, h->nl.kappa_field, h->wa_val, h->wa_gp);
+        B.wa_val = h->wa_val; B.wa_gp = h->wa_gp;
+        ++launched;
+    }
+    if (h->wc_val) {
+        wnode_kernel<<<unsigned((h->nwc + 255) / 256), 256, 0, s>>>(h->nwc, h->wc_kind, h->wc_sup, A.u, h->nl.c_kind, h->nl.c_pi,
+                                                                  h->nl.c_scale, 0.0, nullptr, h->wc_val, h->wc_gp);
+        B.wc_val = h->wc_val; B.wc_gp = h->wc_gp;
+        ++launched;
     }
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
     switch (h->maxc_tpl) {
-        case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(A); break;
-        case 16: csf_fused_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(A); break;
-        case 32: csf_fused_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(A); break;
-        default: csf_fused_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(A); break;
+        case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+        case 16: csf_fused_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+        case 32: csf_fused_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+        default: csf_fused_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(B); break;
     }
+    return launched;
 }
 
 CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
@@ -190,7 +207,7 @@ CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
     A.col_idx = h->csf.col_idx; A.col_slot = h->csf.col_slot;
     A.leaf_val = h->csf.leaf_val; A.leaf_col = h->csf.leaf_col;
     A.fib_info = h->csf.fib_info; A.fib_tdiag = h->csf.fib_tdiag; A.fib_m = h->csf.fib_m;
-    A.rx_val = h->csf.rx_val; A.rx_info = h->csf.rx_info;
+    A.rx_val = h->csf.rx_val; A.rx_info = h->csf.rx_info; A.rx_m = h->csf.rx_m;
     A.dir = h->csf.dir;
     A.nl = h->nl;
     A.u = u; A.d = d;
@@ -455,6 +472,11 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     EG_TRY(upload(D.dir, H.dir)); EG_TRY(upload(D.rowptr, H.rowptr)); EG_TRY(upload(D.cols, H.cols));
     EG_TRY(upload(h->tmap, tmap));
     EG_TRY(upload(h->wa_kind, Wa.kind)); EG_TRY(upload(h->wa_sup, Wa.sup));
+    if (prob->a_kind != EGFEM_G_NONE) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
+    if (prob->c_kind != EGFEM_G_NONE) {
+        EG_TRY(upload(h->wc_kind, Wc.kind)); EG_TRY(upload(h->wc_sup, Wc.sup));
+        EG_TRY(dalloc(h->wc_val, size_t(h->nwc))); EG_TRY(dalloc(h->wc_gp, size_t(h->nwc)));
+    }
     // cells and vertex -> cell incidence for the load vector
     {
         const int nv = mesh->dim + 1;
@@ -643,6 +665,7 @@ void egfem_destroy(egfem_handle h) {
     dfree(D.dir); dfree(D.rowptr); dfree(D.cols);
     dfree(h->cell_S); dfree(h->cell_E);
     dfree(h->tmap); dfree(h->wa_kind); dfree(h->wa_sup); dfree(h->cell_verts); dfree(h->cell_vol);
+    dfree(h->wc_kind); dfree(h->wc_sup); dfree(h->wa_val); dfree(h->wa_gp); dfree(h->wc_val); dfree(h->wc_gp);
     dfree(h->v2c_ptr); dfree(h->v2c); dfree(h->kappa_field);
     dfree(h->r); dfree(h->jsell); dfree(h->dinv); dfree(h->part); dfree(h->scal); dfree(h->ticket); dfree(h->status); dfree(h->st);
     for (KWork<double> *W : {&h->k64}) {
@@ -656,7 +679,7 @@ void egfem_destroy(egfem_handle h) {
         dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->ppart);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
-    dfree(h->bst); dfree(h->tiles); dfree(h->bpart);
+    dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar);
     if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
     if (h->bgraph32) cudaGraphExecDestroy(h->bgraph32);
     for (void *q : {(void *)h->h_mask, (void *)h->h_eta, (void *)h->h_lam, (void *)h->h_norm2, (void *)h->h_bst})
@@ -804,13 +827,12 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
         A.r = h->r;
         A.a64 = h->k64.A; A.q64 = h->k64.b;
         if (mixed) A.a32 = h->k32.A;
-        launch_csf(h, A, h->hs);
+        S.kernel_launches += launch_csf(h, A, h->hs) + 1 + (mixed ? 1 : 0);
         if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
         EG_CUDA(cudaGetLastError());
         double n2;
         EG_TRY(norm2_free(h, h->r, &n2));
         *rn = std::sqrt(n2);
-        S.kernel_launches += 2;
         return EGFEM_OK;
     };
     const unsigned g = unsigned((h->n + 255) / 256);
@@ -1091,16 +1113,25 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     A.q64 = h->k64.b;
     if (std::is_same<V, double>::value) A.a64 = (double *)W.A;
     else A.a32 = (float *)W.A;
-    // fused kernel: leaves (value + column byte), fibres (info + diagonal), reaction entries,
-    // local columns (index + CSR slot) and the operator written, u/d/r/q once each
-    double csf_bytes = L * 9 + F * 12 + RX * 12 + CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
+    // nodal pass: per W node its kind and support, the value and derivative written (u counted
+    // with the rows); fused kernel: leaves (value + column byte), fibres (info, diagonal, W index),
+    // reaction entries (value, info, W index), the nodal values read once, local columns
+    // (index + CSR slot) and the operator written, u/d/r/q once each
+    const double NWA = h->wa_val ? double(h->nwa) : 0.0, NWC = h->wc_val ? double(h->nwc) : 0.0;
+    double csf_bytes = (NWA + NWC) * (1 + 12 + 2 * 16) + L * 9 + F * (NWA > 0 ? 16 : 12) + RX * (NWC > 0 ? 16 : 12) +
+                       CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
     if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
         // cells: vertices, packed S, |K|, the per-cell record written and read back;
         // rows: vertex-to-cell lists, local columns and the outputs
         const double NC = double(h->ncells), nv = h->dim + 1, ns = nv * (nv + 1) / 2, ne = 2 * h->dim + 3;
         csf_bytes = NC * (4 * nv + 8 * ns + 8 + 2 * 8 * ne) + N * (8 + 4 * 2 * nv) + CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
     }
-    const double csf_flops = L * 4 + F * 12 + RX * 10 + CE * 2;
+    // FP64 operations: 2 per leaf (D and J1), per fibre the residual, diagonal and J2 scatter
+    // (6; 12 when g is evaluated per fibre), 4 per reaction entry, 2 per local column, and
+    // the nodal pass (interpolation and g, about 6 per node)
+    const double csf_flops = h->opts.op == EGFEM_OP_MATRIX_FREE ? L * 4 + F * 12 + RX * 10 + CE * 2
+                                                                 : L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) +
+                                                                       CE * 2 + (NWA + NWC) * 6;
     EG_TRY(timeit(h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused", csf_bytes, csf_flops, 1,
                   [&] { launch_csf(h, A, h->hs); }));
     if (!std::is_same<V, double>::value)
@@ -1284,7 +1315,8 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     dfree(h->bpart);
     EG_TRY(upload(h->tiles, T));
     h->ntiles = int64_t(T.size());
-    EG_TRY(dalloc(h->bpart, size_t(2 * h->ntiles)));
+    // 3 slots x 2 values per tile, then one running count per block of the persistent solve
+    EG_TRY(dalloc(h->bpart, size_t(6 * h->ntiles + int64_t(h->sms) * 8)));
     h->tile_factor = factor;
     h->tile_R = R;
     if (h->bgraph64) { cudaGraphExecDestroy(h->bgraph64); h->bgraph64 = nullptr; }
@@ -1332,13 +1364,54 @@ egfem_status batch_graph(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G) {
     return EGFEM_OK;
 }
 
-// BiCGStab for every instance with h_mask set (tolerance h_eta), all in one launch per
-// kernel; returns with h_bst holding every instance's final state.
+// Blocks of the persistent batched solve: resident blocks (occupancy x SMs), capped by the
+// tiles; 0 when that solve cannot run (no cooperative launch, option off, or more than
+// PKB_MAXT tiles per block at the current tile size).
+template <typename V>
+int pk_batch_grid(const egfem_t *h) {
+    if (!h->coop || !h->opts.krylov_persistent || h->ntiles < 1) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kb_persistent<V>, KRY_BLOCK, 0) != cudaSuccess || nb < 1)
+        return 0;
+    const int64_t g = std::min<int64_t>(h->ntiles, std::min<int64_t>(int64_t(nb), 8) * h->sms);
+    if ((h->ntiles + g - 1) / g > PKB_MAXT) return 0;
+    return int(g);
+}
+
+template <typename V>
+egfem_status launch_batch_persistent(egfem_t *h, KWork<V> &W, int grid, int32_t maxit, int32_t stall) {
+    if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));
+    PkBatch<V> B{};
+    B.K = kvecs(h, W);
+    B.tiles = h->tiles; B.ntiles = h->ntiles; B.st = h->bst; B.part = h->bpart;
+    B.active = h->inst_mask; B.rtol = h->inst_eta; B.bar = h->bbar; B.maxit = maxit; B.stall = stall;
+    void *args[] = {(void *)&B};
+    EG_CUDA(cudaMemsetAsync(h->bbar, 0, sizeof(PGrid), h->hs));
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)kb_persistent<V>, dim3(grid), dim3(KRY_BLOCK), args, 0, h->hs));
+    return EGFEM_OK;
+}
+
+// BiCGStab for every instance with h_mask set (tolerance h_eta): one persistent launch
+// for the whole batch when available, else graph-captured iteration kernels; returns with
+// h_bst holding every instance's final state.
 template <typename V>
 egfem_status run_batch_bicgstab(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G, int32_t stall, int64_t *launches) {
-    EG_TRY(batch_graph(h, W, G));
     EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(h->nb), cudaMemcpyHostToDevice, h->hs));
     EG_CUDA(cudaMemcpyAsync(h->inst_eta, h->h_eta, size_t(h->nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
+    const int pg = pk_batch_grid<V>(h);
+    if (pg > 0) {
+        EG_TRY(launch_batch_persistent(h, W, pg, h->opts.krylov_maxit, stall));
+        EG_CUDA(cudaMemcpyAsync(h->h_bst, h->bst, size_t(h->nb) * sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        EG_CUDA(cudaStreamSynchronize(h->hs));
+        *launches += 1;
+        for (int32_t b = 0; b < h->nb; ++b)
+            if (h->h_mask[b] && h->h_bst[b].done == K_TIMEOUT) {
+                g_last_error = "batched BiCGStab: a grid-barrier wait of the persistent solve ran out";
+                return EGFEM_ERR_TIMEOUT;
+            }
+        return EGFEM_OK;
+    }
+    EG_TRY(batch_graph(h, W, G));
     kb_init_state<<<(h->nb + 127) / 128, 128, 0, h->hs>>>(h->nb, h->bst, h->inst_mask, h->inst_eta, h->opts.krylov_maxit, stall);
     const KBatch<V> B = kbatch(h, W);
     kb_setup<V><<<bgrid<V>(h), KRY_BLOCK, 0, h->hs>>>(B);
@@ -1357,7 +1430,9 @@ egfem_status run_batch_bicgstab(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G, int
 }
 
 // Time a few batched BiCGStab iterations for each tile size and keep the fastest
-// (the project's autotuner; it runs once per handle, on the first batched solve).
+// (the project's autotuner; it runs once per handle, on the first batched solve).  With
+// the persistent solve, a tile size is a candidate only if no block owns more than
+// PKB_MAXT tiles.
 template <typename V>
 egfem_status autotune_tiles(egfem_t *h, KWork<V> &W) {
     cudaEvent_t e0, e1;
@@ -1368,20 +1443,37 @@ egfem_status autotune_tiles(egfem_t *h, KWork<V> &W) {
     for (int f : {1, 2, 4, 8}) {
         EG_TRY(batch_tiles<V>(h, f));
         for (int32_t b = 0; b < h->nb; ++b) { h->h_mask[b] = 1; h->h_eta[b] = 0.0; }
-        int64_t dummy = 0;
         EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(h->nb), cudaMemcpyHostToDevice, h->hs));
         EG_CUDA(cudaMemcpyAsync(h->inst_eta, h->h_eta, size_t(h->nb) * sizeof(double), cudaMemcpyHostToDevice, h->hs));
-        kb_init_state<<<(h->nb + 127) / 128, 128, 0, h->hs>>>(h->nb, h->bst, h->inst_mask, h->inst_eta, 1 << 30, 0);
-        const KBatch<V> B = kbatch(h, W);
-        kb_setup<V><<<bgrid<V>(h), KRY_BLOCK, 0, h->hs>>>(B);
-        enqueue_batch_iterations(h, W, 2, h->hs);   // warm
-        EG_CUDA(cudaEventRecord(e0, h->hs));
-        enqueue_batch_iterations(h, W, 6, h->hs);
-        EG_CUDA(cudaEventRecord(e1, h->hs));
-        EG_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
-        EG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        (void)dummy;
+        const int pg = pk_batch_grid<V>(h);
+        if (h->coop && h->opts.krylov_persistent) {
+            if (pg == 0) continue;   // too many tiles per block at this size
+            // setup + 2 iterations (warm), then setup + 8 iterations; the difference is 6 iterations
+            EG_TRY(launch_batch_persistent(h, W, pg, 2, 0));
+            EG_CUDA(cudaEventRecord(e0, h->hs));
+            EG_TRY(launch_batch_persistent(h, W, pg, 2, 0));
+            EG_CUDA(cudaEventRecord(e1, h->hs));
+            EG_CUDA(cudaEventSynchronize(e1));
+            float ms2 = 0;
+            EG_CUDA(cudaEventElapsedTime(&ms2, e0, e1));
+            EG_CUDA(cudaEventRecord(e0, h->hs));
+            EG_TRY(launch_batch_persistent(h, W, pg, 8, 0));
+            EG_CUDA(cudaEventRecord(e1, h->hs));
+            EG_CUDA(cudaEventSynchronize(e1));
+            EG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ms -= ms2;
+        } else {
+            kb_init_state<<<(h->nb + 127) / 128, 128, 0, h->hs>>>(h->nb, h->bst, h->inst_mask, h->inst_eta, 1 << 30, 0);
+            const KBatch<V> B = kbatch(h, W);
+            kb_setup<V><<<bgrid<V>(h), KRY_BLOCK, 0, h->hs>>>(B);
+            enqueue_batch_iterations(h, W, 2, h->hs);   // warm
+            EG_CUDA(cudaEventRecord(e0, h->hs));
+            enqueue_batch_iterations(h, W, 6, h->hs);
+            EG_CUDA(cudaEventRecord(e1, h->hs));
+            EG_CUDA(cudaEventSynchronize(e1));
+            EG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        }
         if (ms < best_ms) { best_ms = ms; best = f; }
     }
     cudaEventDestroy(e0);
@@ -1428,11 +1520,10 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
         if (mixed) A.a32 = h->k32.A;
         A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
-        launch_csf(h, A, h->hs);
+        launches += launch_csf(h, A, h->hs) + 1 + (mixed ? 1 : 0);
         if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
         EG_CUDA(cudaGetLastError());
         EG_TRY(batch_norms(h));
-        launches += 2;
         for (int b = 0; b < nb; ++b) if (m[b]) rn[b] = std::sqrt(h->h_norm2[b]);
         return EGFEM_OK;
     };

@@ -40,6 +40,11 @@ struct CsfArgs {
     float *q32;            // D r (nullable)
     double *jsell;         // unscaled J in SELL order (nullable)
     double *dinv;          // 1 / J_ii (nullable)
+    const int32_t *rx_m;         // W_c index of each reaction entry
+    // nodal values of the nonlinearities, evaluated once per W node by wnode_kernel
+    // (nullable: then every fibre / reaction entry evaluates g itself)
+    const double *wa_val, *wa_gp;   // a_m = kappa_m + g_a((Pi u)_m), g_a'((Pi u)_m)
+    const double *wc_val, *wc_gp;   // c_m = g_c((Pi_c u)_m),         g_c'((Pi_c u)_m)
     const int32_t *slice_inst;   // batch: instance of each slice (nullable)
     const uint8_t *inst_mask;    // batch: rows of instances with mask 0 are skipped (nullable)
     int32_t *status;       // error word (singular diagonal)
@@ -139,6 +144,10 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 gp = 0.0;
+            } else if (A.wa_val) {
+                const int32_t m = A.fib_m[fq];
+                a = A.wa_val[m];
+                gp = A.wa_gp[m];
             } else {
                 const double pu = ui + interp_du(info, du, CSF_BLOCK);
                 double w;
@@ -164,9 +173,15 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
         const double mv = A.rx_val[q];
         if (mv == 0.0) continue;
         const uint32_t xi = A.rx_info[q];
-        const double pc = ui + interp_du(xi, du, CSF_BLOCK);
         double cv, cp;
-        g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
+        if (A.wc_val) {
+            const int32_t m = A.rx_m[q];
+            cv = A.wc_val[m];
+            cp = A.wc_gp[m];
+        } else {
+            const double pc = ui + interp_du(xi, du, CSF_BLOCK);
+            g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
+        }
         r += nl.gamma * mv * cv;
         scatter_pi(xi, nl.gamma * mv * cp, J, CSF_BLOCK);
     }
@@ -193,6 +208,28 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     }
     // the FP32 operator keeps its row sum in column 0 (difference-form SpMV)
     if (A.a32) A.a32[M.col_base + lane] = float(rowsum);
+}
+
+// Nodal values of one nonlinearity on its W space (Sec. 3.1 eq. (5), Sec. 3.2), one thread
+// per W node, each node evaluated once: val_m = base_m + g((Pi u)_m), gp_m = g'((Pi u)_m),
+// with base = kappa (constant, or the field when base_field is set) for the coefficient
+// space and 0 for the reaction space.
+__global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u,
+                                                    int32_t g_kind, int32_t g_p, double g_scale, double base,
+                                                    const double *base_field, double *val, double *gp) {
+    const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (m >= n_w) return;
+    const uint32_t k = kind[m];
+    const double u0 = u[sup[3 * m]];
+    double pu;
+    if (k == W_VERTEX) pu = u0;
+    else if (k == W_MID) pu = 0.5 * (u0 + u[sup[3 * m + 1]]);
+    else if (k == W_THIRD) pu = (2.0 * u0 + u[sup[3 * m + 1]]) * (1.0 / 3.0);
+    else pu = (u0 + u[sup[3 * m + 1]] + u[sup[3 * m + 2]]) * (1.0 / 3.0);
+    double g, d;
+    g_eval(g_kind, g_p, g_scale, pu, g, d);
+    val[m] = (base_field ? base_field[m] : base) + g;
+    gp[m] = d;
 }
 
 // Pointwise nonlinearity alone (Sec. 3.2), one thread per W node.

@@ -46,7 +46,7 @@ def test_grid_barrier_wait_runs_out_and_reports(P):
 
 def _setup(P, n, **opt):
     mesh = wl.unit_square_mesh(n)
-    orc = oracle.Problem(mesh, a=("pow", 2), a_degree=2)
+    orc = oracle.Problem(mesh, a=("pow", 2), a_deg=2)
     h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2), P.default_options(**opt))
     return mesh, orc, h
 
