@@ -60,9 +60,14 @@ struct KWork {
     typename VecT<V>::mat *A = nullptr;   // Jacobi-scaled operator (SELL layout)
     V *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     V *p2 = nullptr, *v2 = nullptr;       // second p / v buffers of the fused double-float iteration
-    PGrid *bar = nullptr;                 // grid barrier of the persistent solve
-    double *ppart = nullptr;              // its block partials: 3 slots x 2 values x g_pk
-    int g_pk = 0;                         // blocks of the persistent solve (0: not available)
+    // persistent solve (pk_solve): one tile of rows per block
+    int g_pk = 0;                         // blocks (0: not available)
+    BTile *pk_tiles = nullptr;
+    int64_t pk_ntiles = 0;
+    int64_t *pk_sys_t0 = nullptr;         // [1] = {0}
+    PkScal<V> *pk_sc = nullptr;           // [1]
+    float2 *pk_part = nullptr;            // [2 * pk_ntiles]
+    PGrid *bar = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
@@ -134,6 +139,9 @@ struct egfem_t {
     double *bpart = nullptr;
     cudaGraphExec_t bgraph64 = nullptr, bgraph32 = nullptr;
     PGrid *bbar = nullptr;              // grid barrier of the persistent batched solve
+    int64_t *bsys_t0 = nullptr;         // first tile of each instance
+    float2 *bpart2 = nullptr;           // tile partials of the persistent batched solve
+    void *bsc = nullptr;                // PkScal<V> per instance (room for the larger V)
     int bgraph_chunk = 0, bgraph_tiles = 0;
 };
 
@@ -253,15 +261,23 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
         EG_CUDA(cudaMemset(*vec[k], 0, size_t(h->n_pad) * sizeof(V)));
     }
     if (h->coop) {
-        // every block of a cooperative launch must be resident: at most occupancy x SMs
+        // every block of a cooperative launch must be resident: at most occupancy x SMs; each
+        // block owns one contiguous, slice-aligned tile of rows
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kry_persistent<V>, KRY_BLOCK, 0) == cudaSuccess &&
-            nb >= 1) {
-            const int64_t work = (h->n_pad + int64_t(KRY_BLOCK) * VecT<V>::R - 1) / (int64_t(KRY_BLOCK) * VecT<V>::R);
-            W.g_pk = int(std::max<int64_t>(1, std::min<int64_t>(work, int64_t(nb) * h->sms)));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) == cudaSuccess && nb >= 1) {
+            const int64_t g = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::min(nb, 8)) * h->sms, h->n_pad / SLICE));
+            const int64_t rows = (h->n_pad + g * SLICE - 1) / (g * SLICE) * SLICE;
+            std::vector<BTile> T;
+            for (int64_t r = 0; r < h->n_pad; r += rows) T.push_back(BTile{r, std::min(h->n_pad, r + rows), 0, 0, 0});
+            for (BTile &t : T) t.ntiles_inst = int32_t(T.size());
+            W.g_pk = int(g);
+            W.pk_ntiles = int64_t(T.size());
+            EG_TRY(upload(W.pk_tiles, T));
+            EG_TRY(upload(W.pk_sys_t0, std::vector<int64_t>(1, 0)));
+            EG_TRY(dalloc(W.pk_sc, 1));
+            EG_TRY(dalloc(W.pk_part, size_t(2 * W.pk_ntiles)));
             EG_TRY(dalloc(W.bar, 1));
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
-            EG_TRY(dalloc(W.ppart, size_t(6) * size_t(W.g_pk)));
         }
     }
     if constexpr (std::is_same<V, df64>::value) {
@@ -318,6 +334,27 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
     return EGFEM_OK;
 }
 
+// Cooperative launch of pk_solve over the given tiles and systems.
+template <typename V>
+egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, int64_t ntiles, const int64_t *sys_t0,
+                       int32_t nsys, KState *st, PkScal<V> *sc, float2 *part, const uint8_t *active, const double *rtol,
+                       double rtol0, PGrid *bar, int32_t maxit, int32_t stall) {
+    PkArgs<V> P{};
+    P.K = kvecs(h, W);
+    P.tiles = tiles; P.ntiles = ntiles; P.sys_t0 = sys_t0; P.nsys = nsys; P.st = st; P.sc = sc; P.part = part;
+    P.active = active; P.rtol = rtol; P.rtol0 = rtol0; P.bar = bar; P.maxit = maxit; P.stall = stall;
+    void *args[] = {(void *)&P};
+    EG_CUDA(cudaMemsetAsync(bar, 0, sizeof(PGrid), h->hs));
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solve<V>, dim3(grid), dim3(PK_BLOCK), args, 0, h->hs));
+    return EGFEM_OK;
+}
+
+template <typename V>
+egfem_status launch_pk_single(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
+    return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, nullptr, nullptr, rtol,
+                     W.bar, maxit, stall);
+}
+
 // Run BiCGStab on W.A x = W.b (already filled) on the internal stream; returns the
 // device-state outcome in *done and the iteration count in *iters.
 template <typename V>
@@ -325,22 +362,20 @@ egfem_status run_bicgstab(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, i
                           int32_t *iters) {
     if (h->opts.krylov_persistent && W.g_pk > 0) {
         // the whole solve in one cooperative launch
-        KVecs<V> K = kvecs(h, W);
-        K.part = W.ppart;
-        PGrid *bar = W.bar;
-        void *args[] = {(void *)&K, (void *)&bar, (void *)&rtol, (void *)&maxit, (void *)&stall};
-        EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
-        EG_CUDA(cudaLaunchCooperativeKernel((const void *)kry_persistent<V>, dim3(W.g_pk), dim3(KRY_BLOCK), args, 0, h->hs));
+        EG_TRY(launch_pk_single(h, W, rtol, maxit, stall));
         EG_CUDA(cudaMemcpyAsync(h->h_st, h->st, sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        PGrid gb{};
+        EG_CUDA(cudaMemcpyAsync(&gb, W.bar, sizeof(PGrid), cudaMemcpyDeviceToHost, h->hs));
         EG_CUDA(cudaStreamSynchronize(h->hs));
         h->last_graph_launches = 0;
         h->last_graph_nodes = 0;
         h->last_krylov_kernels = 1;
         *done = h->h_st->done;
         *iters = h->h_st->iter;
-        if (*done == K_TIMEOUT) {
-            g_last_error = "BiCGStab: a grid-barrier wait of the persistent solve ran out";
-            return EGFEM_ERR_TIMEOUT;
+        if (gb.err) {
+            g_last_error = gb.err == 2 ? "BiCGStab: more tiles than the persistent solve holds per block"
+                                       : "BiCGStab: a grid-barrier wait of the persistent solve ran out";
+            return gb.err == 2 ? EGFEM_ERR_INVALID_ARG : EGFEM_ERR_TIMEOUT;
         }
         return EGFEM_OK;
     }
@@ -671,15 +706,16 @@ void egfem_destroy(egfem_handle h) {
     for (KWork<double> *W : {&h->k64}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->ppart);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_sc); dfree(W->pk_part);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->ppart);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_sc); dfree(W->pk_part);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
-    dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar);
+    dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bsys_t0); dfree(h->bpart2);
+    if (h->bsc) cudaFree(h->bsc);
     if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
     if (h->bgraph32) cudaGraphExecDestroy(h->bgraph32);
     for (void *q : {(void *)h->h_mask, (void *)h->h_eta, (void *)h->h_lam, (void *)h->h_norm2, (void *)h->h_bst})
@@ -1162,18 +1198,9 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         // t; C reads s, p, t, rh, x, writes x, r; D reads r, v, p, writes p (19 vector passes);
         // the operator is read twice.
         const int32_t iters = 40;
-        KVecs<V> KP = kvecs(h, W);
-        KP.part = W.ppart;
-        PGrid *bar = W.bar;
-        double rtol0 = 0.0;
-        int32_t maxit = iters, stall = 0;
-        void *args[] = {(void *)&KP, (void *)&bar, (void *)&rtol0, (void *)&maxit, (void *)&stall};
         cudaError_t le = cudaSuccess;
         EG_TRY(timeit("kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
-            cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs);
-            const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kry_persistent<V>, dim3(W.g_pk), dim3(KRY_BLOCK),
-                                                              args, 0, h->hs);
-            if (e != cudaSuccess) le = e;
+            if (launch_pk_single(h, W, 0.0, iters, 0) != EGFEM_OK) le = cudaErrorLaunchFailure;
         }));
         EG_CUDA(le);
         int32_t done = 0;
@@ -1305,15 +1332,22 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     constexpr int R = VecT<V>::R;
     const int64_t rows = int64_t(KRY_BLOCK) * R * factor;
     std::vector<BTile> T;
+    std::vector<int64_t> sys_t0(size_t(h->nb));
     for (int32_t b = 0; b < h->nb; ++b) {
         const int64_t t0 = int64_t(T.size());
+        sys_t0[size_t(b)] = t0;
         const int64_t lo = h->inst_off[b], hi = h->inst_off[b + 1];
         for (int64_t r = lo; r < hi; r += rows) T.push_back(BTile{r, std::min(hi, r + rows), t0, b, 0});
         for (size_t q = size_t(t0); q < T.size(); ++q) T[q].ntiles_inst = int32_t(T.size() - size_t(t0));
     }
     dfree(h->tiles);
     dfree(h->bpart);
+    dfree(h->bsys_t0);
+    dfree(h->bpart2);
     EG_TRY(upload(h->tiles, T));
+    EG_TRY(upload(h->bsys_t0, sys_t0));
+    EG_TRY(dalloc(h->bpart2, size_t(2 * T.size())));
+    if (!h->bsc) EG_CUDA(cudaMalloc(&h->bsc, size_t(h->nb) * std::max(sizeof(PkScal<double>), sizeof(PkScal<df64>))));
     h->ntiles = int64_t(T.size());
     // 3 slots x 2 values per tile, then one running count per block of the persistent solve
     EG_TRY(dalloc(h->bpart, size_t(6 * h->ntiles + int64_t(h->sms) * 8)));
@@ -1366,29 +1400,23 @@ egfem_status batch_graph(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G) {
 
 // Blocks of the persistent batched solve: resident blocks (occupancy x SMs), capped by the
 // tiles; 0 when that solve cannot run (no cooperative launch, option off, or more than
-// PKB_MAXT tiles per block at the current tile size).
+// PK_MAXT tiles per block at the current tile size).
 template <typename V>
 int pk_batch_grid(const egfem_t *h) {
     if (!h->coop || !h->opts.krylov_persistent || h->ntiles < 1) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kb_persistent<V>, KRY_BLOCK, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) != cudaSuccess || nb < 1)
         return 0;
     const int64_t g = std::min<int64_t>(h->ntiles, std::min<int64_t>(int64_t(nb), 8) * h->sms);
-    if ((h->ntiles + g - 1) / g > PKB_MAXT) return 0;
+    if ((h->ntiles + g - 1) / g > PK_MAXT) return 0;
     return int(g);
 }
 
 template <typename V>
 egfem_status launch_batch_persistent(egfem_t *h, KWork<V> &W, int grid, int32_t maxit, int32_t stall) {
     if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));
-    PkBatch<V> B{};
-    B.K = kvecs(h, W);
-    B.tiles = h->tiles; B.ntiles = h->ntiles; B.st = h->bst; B.part = h->bpart;
-    B.active = h->inst_mask; B.rtol = h->inst_eta; B.bar = h->bbar; B.maxit = maxit; B.stall = stall;
-    void *args[] = {(void *)&B};
-    EG_CUDA(cudaMemsetAsync(h->bbar, 0, sizeof(PGrid), h->hs));
-    EG_CUDA(cudaLaunchCooperativeKernel((const void *)kb_persistent<V>, dim3(grid), dim3(KRY_BLOCK), args, 0, h->hs));
-    return EGFEM_OK;
+    return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bsys_t0, h->nb, h->bst, static_cast<PkScal<V> *>(h->bsc), h->bpart2,
+                     h->inst_mask, h->inst_eta, 0.0, h->bbar, maxit, stall);
 }
 
 // BiCGStab for every instance with h_mask set (tolerance h_eta): one persistent launch
@@ -1402,13 +1430,15 @@ egfem_status run_batch_bicgstab(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G, int
     if (pg > 0) {
         EG_TRY(launch_batch_persistent(h, W, pg, h->opts.krylov_maxit, stall));
         EG_CUDA(cudaMemcpyAsync(h->h_bst, h->bst, size_t(h->nb) * sizeof(KState), cudaMemcpyDeviceToHost, h->hs));
+        PGrid gb{};
+        EG_CUDA(cudaMemcpyAsync(&gb, h->bbar, sizeof(PGrid), cudaMemcpyDeviceToHost, h->hs));
         EG_CUDA(cudaStreamSynchronize(h->hs));
         *launches += 1;
-        for (int32_t b = 0; b < h->nb; ++b)
-            if (h->h_mask[b] && h->h_bst[b].done == K_TIMEOUT) {
-                g_last_error = "batched BiCGStab: a grid-barrier wait of the persistent solve ran out";
-                return EGFEM_ERR_TIMEOUT;
-            }
+        if (gb.err) {
+            g_last_error = gb.err == 2 ? "batched BiCGStab: more tiles than the persistent solve holds per block"
+                                       : "batched BiCGStab: a grid-barrier wait of the persistent solve ran out";
+            return gb.err == 2 ? EGFEM_ERR_INVALID_ARG : EGFEM_ERR_TIMEOUT;
+        }
         return EGFEM_OK;
     }
     EG_TRY(batch_graph(h, W, G));
@@ -1432,7 +1462,7 @@ egfem_status run_batch_bicgstab(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G, int
 // Time a few batched BiCGStab iterations for each tile size and keep the fastest
 // (the project's autotuner; it runs once per handle, on the first batched solve).  With
 // the persistent solve, a tile size is a candidate only if no block owns more than
-// PKB_MAXT tiles.
+// PK_MAXT tiles.
 template <typename V>
 egfem_status autotune_tiles(egfem_t *h, KWork<V> &W) {
     cudaEvent_t e0, e1;
