@@ -66,7 +66,7 @@ struct KWork {
     int64_t pk_ntiles = 0;
     int64_t *pk_sys_t0 = nullptr;         // [1] = {0}
     PkScal<V> *pk_sc = nullptr;           // [1]
-    float2 *pk_part = nullptr;            // [2 * pk_ntiles]
+    double *pk_part = nullptr;            // [2 * pk_ntiles]
     PGrid *bar = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
@@ -140,7 +140,7 @@ struct egfem_t {
     cudaGraphExec_t bgraph64 = nullptr, bgraph32 = nullptr;
     PGrid *bbar = nullptr;              // grid barrier of the persistent batched solve
     int64_t *bsys_t0 = nullptr;         // first tile of each instance
-    float2 *bpart2 = nullptr;           // tile partials of the persistent batched solve
+    double *bpart2 = nullptr;           // tile partials of the persistent batched solve
     void *bsc = nullptr;                // PkScal<V> per instance (room for the larger V)
     int bgraph_chunk = 0, bgraph_tiles = 0;
 };
@@ -337,7 +337,7 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
 // Cooperative launch of pk_solve over the given tiles and systems.
 template <typename V>
 egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, int64_t ntiles, const int64_t *sys_t0,
-                       int32_t nsys, KState *st, PkScal<V> *sc, float2 *part, const uint8_t *active, const double *rtol,
+                       int32_t nsys, KState *st, PkScal<V> *sc, double *part, const uint8_t *active, const double *rtol,
                        double rtol0, PGrid *bar, int32_t maxit, int32_t stall) {
     PkArgs<V> P{};
     P.K = kvecs(h, W);

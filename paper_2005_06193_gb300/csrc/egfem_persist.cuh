@@ -15,13 +15,14 @@
 //   C : x += alpha p + omega s, r = s - omega t, (rh, r), (r, r) -> beta, tests   barrier (+ sums)
 //   D : p = r + beta (p - omega v)                                     barrier
 //
-// Each block writes one partial per owned tile and inner product.  At a summing barrier the
-// LAST block to arrive, before it releases the others, sums every system's tile partials in
-// tile order (double-float arithmetic on the FP32 pipe: GB300 executes FP64 at about 1/58 of
-// the FP32 rate, and per-block FP64 reductions measurably stalled the solve), updates the
-// systems' BiCGStab scalars and states, and publishes them with the count of systems still
-// iterating; every block then reads the scalars of its tiles' systems.  The results are
-// deterministic (fixed summation order), and the loop ends in all blocks at once.
+// Each block writes one partial (double) per owned tile and inner product; double-float
+// accumulators are summed within the block in double-float arithmetic on the FP32 pipe
+// (GB300 executes FP64 at about 1/58 of the FP32 rate).  At a summing barrier the LAST block
+// to arrive, before it releases the others, sums every system's tile partials in tile order,
+// updates the systems' BiCGStab scalars and states once, and publishes them (in the vector
+// type) with the count of systems still iterating; every block then reads the scalars of its
+// tiles' systems, so no block repeats the FP64 scalar work.  The results are deterministic
+// (fixed summation order), and the loop ends in all blocks at once.
 //
 // The barrier is an arrival counter and a generation word.  The cooperative launch guarantees
 // that all blocks are resident (the host sizes the grid from the occupancy calculator), so
@@ -254,7 +255,7 @@ struct PkArgs {
     int32_t nsys;
     KState *st;               // [nsys] BiCGStab state (final state for the host)
     PkScal<V> *sc;            // [nsys] scalars published at the summing barriers
-    float2 *part;             // [2 * ntiles] tile partials (double-float)
+    double *part;             // [2 * ntiles] tile partials
     const uint8_t *active;    // [nsys] systems to solve, or null (all)
     const double *rtol;       // [nsys] tolerances, or null (rtol0 for all)
     double rtol0;
@@ -310,12 +311,13 @@ __device__ __forceinline__ df64 shfl_xor_df(df64 a, int o) {
     return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// Block sum of NV per-thread accumulators for one tile -> part[k * ntiles + tile] (df64).
+// Block sum of NV per-thread accumulators for one tile -> part[k * ntiles + tile].
 template <typename V, int NV>
-__device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], float2 *part, int64_t ntiles, int64_t tile) {
+__device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], double *part, int64_t ntiles, int64_t tile) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();   // the previous tile's readers of the shared arrays are done
     if constexpr (std::is_same<V, df64>::value) {
+        // warp and block sums in double-float arithmetic (FP32 pipe), one conversion per tile
         __shared__ float2 shf[2][PK_BLOCK / 32];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -329,7 +331,7 @@ __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], floa
             const int k = threadIdx.x;
             df64 x = {shf[k][0].x, shf[k][0].y};
             for (int q = 1; q < PK_BLOCK / 32; ++q) x = df_add(x, df64{shf[k][q].x, shf[k][q].y});
-            part[k * ntiles + tile] = make_float2(x.hi, x.lo);
+            part[k * ntiles + tile] = df_to_double(x);
         }
     } else {
         __shared__ double shd[2][PK_BLOCK];
@@ -341,10 +343,7 @@ __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], floa
 #pragma unroll
             for (int q = 0; q < PK_BLOCK / 32; ++q) x += shd[w][lane + 32 * q];
             x = warp_sum(x);
-            if (lane == 0) {
-                const df64 d = df_from(x);
-                part[w * ntiles + tile] = make_float2(d.hi, d.lo);
-            }
+            if (lane == 0) part[w * ntiles + tile] = x;
         }
     }
 }
@@ -367,20 +366,19 @@ __device__ __forceinline__ KState pk_load_state(const KState *g) {
 template <bool SETUP, typename V, int NV, typename U>
 __device__ __forceinline__ void pk_sum_update(const PkArgs<V> &P, U &&update) {
     __shared__ int s_run;
-    __shared__ float2 s_w[2][PK_BLOCK / 32];
+    __shared__ double s_w[2][PK_BLOCK / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_run = 0;
-    // one system: all warps share its tiles, then warp 0 adds the warp sums in order
+    // one system: all warps share its tiles, then the warp sums are added in order
     const bool one = P.nsys == 1;
     if (one) {
         const int32_t nt = P.tiles[0].ntiles_inst;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            df64 x = {0.f, 0.f};
-            for (int q = threadIdx.x; q < nt; q += PK_BLOCK) x = df_add(x, ldcg_df(P.part + k * P.ntiles + q));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x = df_add(x, shfl_xor_df(x, o));
-            if (lane == 0) s_w[k][w] = make_float2(x.hi, x.lo);
+            double x = 0.0;
+            for (int q = threadIdx.x; q < nt; q += PK_BLOCK) x += __ldcg(P.part + k * P.ntiles + q);
+            x = warp_sum(x);
+            if (lane == 0) s_w[k][w] = x;
         }
     }
     __syncthreads();
@@ -403,29 +401,25 @@ __device__ __forceinline__ void pk_sum_update(const PkArgs<V> &P, U &&update) {
             if (__ldcg(&P.st[b].done) != K_RUNNING) continue;
             S = pk_load_state(P.st + b);
         }
-        df64 x[NV];
+        double x[NV];
         if (one) {
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                x[k] = df64{s_w[k][0].x, s_w[k][0].y};
-                for (int q = 1; q < PK_BLOCK / 32; ++q) x[k] = df_add(x[k], df64{s_w[k][q].x, s_w[k][q].y});
+                x[k] = s_w[k][0];
+                for (int q = 1; q < PK_BLOCK / 32; ++q) x[k] += s_w[k][q];
             }
         } else {
             const int64_t t0 = P.sys_t0[b];
             const int32_t nt = P.tiles[t0].ntiles_inst;
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                x[k] = df64{0.f, 0.f};
-                for (int q = lane; q < nt; q += 32) x[k] = df_add(x[k], ldcg_df(P.part + k * P.ntiles + t0 + q));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x[k] = df_add(x[k], shfl_xor_df(x[k], o));
+                x[k] = 0.0;
+                for (int q = lane; q < nt; q += 32) x[k] += __ldcg(P.part + k * P.ntiles + t0 + q);
+                x[k] = warp_sum(x[k]);
             }
         }
         if (lane == 0) {
-            double tot[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) tot[k] = df_to_double(x[k]);
-            update(S, b, tot);
+            update(S, b, x);
             P.st[b] = S;
             P.sc[b] = PkScal<V>{cvt<V>(S.alpha), cvt<V>(S.omega), cvt<V>(S.beta), S.done, 0};
             run += (S.done == K_RUNNING);
