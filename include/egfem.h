@@ -211,10 +211,13 @@ egfem_status egfem_bicgstab(egfem_handle h, const double *d_vals, const double *
 egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, egfem_stats *stats,
                                 egfem_stream stream);
 
-/* Time each kernel of the Newton step at state d_u, load d_d: the fused tensor-action /
- * Jacobian kernel and the five BiCGStab kernels, each launched reps times back to back on
- * the handle's stream between two CUDA events.  Alongside, the algorithmic bytes and
- * flops of one launch (operator and vectors counted once).  Synchronises the stream. */
+/* Time each kernel of the Newton step at state d_u, load d_d: the tensor-action / Jacobian
+ * kernels ("csf_fused": the nodal pass plus the fused CSF kernel, or "tensor_action_mf"), and
+ * the BiCGStab solve -- "kry_persistent" (one cooperative launch running 40 iterations, reported
+ * per iteration) when krylov_persistent is set, else the iteration kernels -- each launched reps
+ * times back to back on the handle's stream between two CUDA events.  Alongside, the
+ * algorithmic bytes and flops of one launch (or iteration): operator and vectors counted once
+ * per pass.  Synchronises the stream. */
 egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const double *d_d, int32_t reps,
                                    egfem_profile *out, egfem_stream stream);
 
@@ -222,8 +225,9 @@ egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const doub
  * motivated by the repeated forward/backward solves of optimal control, Sec. 6):
  *   J(u*)^T lambda = dj/du  on free rows, lambda = 0 on Dirichlet rows;
  *   dj/dd_i = lambda_i (free rows);  dj/dkappa_m = -sum_{i,k} lambda_i T_imk u_k.
- * d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa] out (may be NULL).
- * Synchronises the stream. */
+ * The transposed system is solved by FP64 Jacobi-BiCGStab to 1e-13 relative in either
+ * precision of the handle.  d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa]
+ * out (may be NULL).  Synchronises the stream. */
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda,
                            double *d_grad_kappa, egfem_stats *stats, egfem_stream stream);
 
