@@ -469,6 +469,13 @@ def main():
                         "kernels": [{"name": p["name"], "ms": p["ms"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9,
                                      "frac_hbm": p["bytes"] / (p["ms"] / 1e3) / 1e9 / hbm} for p in mprof]}
         out["mixed"]["gpu_launches"] = int(sum(s.kernel_launches for s in sm))
+        cm = next((p for p in mprof if p["name"] == "csf_mixed"), None)
+        if cm is not None:
+            out["tensor_action_mixed"] = {
+                "kernel": "wnode_kernel + csf_mixed_kernel (FP64 residual, FP32 Jacobian)", "ms": cm["ms"],
+                "achieved_gbs": cm["bytes"] / (cm["ms"] / 1e3) / 1e9, "frac_hbm": cm["bytes"] / (cm["ms"] / 1e3) / 1e9 / hbm,
+                "fp64_tflops": cm["flops"] / (cm["ms"] / 1e3) / 1e12, "bytes_per_launch": cm["bytes"],
+                "speedup_vs_fp64": csf["ms"] / cm["ms"]}
         hm.close()
 
     if not args.no_mf:

@@ -92,6 +92,9 @@ struct egfem_t {
     int32_t *wa_sup = nullptr, *wc_sup = nullptr;
     double *wa_val = nullptr, *wa_gp = nullptr;   // nodal a_m, g_a' (wnode_kernel)
     double *wc_val = nullptr, *wc_gp = nullptr;   // nodal c_m, g_c'
+    float *wa_val32 = nullptr, *wa_gp32 = nullptr;   // FP32 copies (mixed tensor action)
+    float *leaf_val32 = nullptr;                     // FP32 copy of the tensor values (mixed)
+    bool mixed_ta_ready = false;                     // the FP32 copies above exist
     int32_t *cell_verts = nullptr;
     double *cell_vol = nullptr;
     int64_t *v2c_ptr = nullptr;
@@ -180,25 +183,61 @@ int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     return 2;
 }
 
+// FP32 copies of the tensor values and nodal buffers for csf_mixed_kernel (once per handle).
+egfem_status ensure_mixed_tensor(egfem_t *h, cudaStream_t s) {
+    if (h->mixed_ta_ready) return EGFEM_OK;
+    EG_TRY(dalloc(h->leaf_val32, size_t(std::max<int64_t>(1, h->csf.n_leaves))));
+    if (h->csf.n_leaves > 0)
+        cast_kernel<double, float><<<unsigned((h->csf.n_leaves + 255) / 256), 256, 0, s>>>(h->csf.n_leaves, h->csf.leaf_val,
+                                                                                          h->leaf_val32);
+    if (h->wa_val) {
+        EG_TRY(dalloc(h->wa_val32, size_t(h->nwa)));
+        EG_TRY(dalloc(h->wa_gp32, size_t(h->nwa)));
+    }
+    EG_CUDA(cudaGetLastError());
+    h->mixed_ta_ready = true;
+    return EGFEM_OK;
+}
+
+// The Newton step of the mixed path needs only r, D r and the FP32 operator: then the
+// mixed-precision tensor action (FP32 Jacobian) serves it.
+bool mixed_tensor_action(const egfem_t *h, const CsfArgs &A) {
+    return h->opts.op == EGFEM_OP_CSF && h->mixed_ta_ready && A.a32 && A.r && A.q64 && !A.a64 && !A.jcsr && !A.jsell &&
+           !A.dinv && !A.q32 && !A.inst_mask;
+}
+
 // Pointwise nonlinearity + residual + Jacobian fill at A.u; returns the kernels launched.
 int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     if (h->opts.op == EGFEM_OP_MATRIX_FREE) return h->dim == 2 ? launch_mf<2>(h, A, s) : launch_mf<3>(h, A, s);
     int launched = 1;
+    const bool mix = mixed_tensor_action(h, A);
     // each W node's nonlinearity once (Sec. 3.2), then the tensor action gathers it per fibre
     CsfArgs B = A;
     if (h->wa_val) {
+        float *v32 = mix ? h->wa_val32 : nullptr, *g32 = mix ? h->wa_gp32 : nullptr;
         wnode_kernel<<<unsigned((h->nwa + 255) / 256), 256, 0, s>>>(h->nwa, h->wa_kind, h->wa_sup, A.u, h->nl.a_kind, h->nl.a_pi,
-                                                                  h->nl.a_scale, h->nl.kappa, h->nl.kappa_field, h->wa_val, h->wa_gp);
-        B.wa_val = h->wa_val; B.wa_gp = h->wa_gp;
+                                                                  h->nl.a_scale, h->nl.kappa, h->nl.kappa_field, h->wa_val, h->wa_gp,
+                                                                  v32, g32);
+        B.wa_val = h->wa_val; B.wa_gp = h->wa_gp; B.wa_val32 = v32; B.wa_gp32 = g32;
         ++launched;
     }
     if (h->wc_val) {
         wnode_kernel<<<unsigned((h->nwc + 255) / 256), 256, 0, s>>>(h->nwc, h->wc_kind, h->wc_sup, A.u, h->nl.c_kind, h->nl.c_pi,
-                                                                  h->nl.c_scale, 0.0, nullptr, h->wc_val, h->wc_gp);
+                                                                  h->nl.c_scale, 0.0, nullptr, h->wc_val, h->wc_gp, nullptr, nullptr);
         B.wc_val = h->wc_val; B.wc_gp = h->wc_gp;
         ++launched;
     }
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
+    if (mix) {
+        B.leaf_val32 = h->leaf_val32;
+        switch (h->maxc_tpl) {
+            case 8: csf_mixed_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+            case 16: csf_mixed_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+            case 32: csf_mixed_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+            default: csf_mixed_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+        }
+        return launched;
+    }
     switch (h->maxc_tpl) {
         case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(B); break;
         case 16: csf_fused_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(B); break;
@@ -701,6 +740,7 @@ void egfem_destroy(egfem_handle h) {
     dfree(h->cell_S); dfree(h->cell_E);
     dfree(h->tmap); dfree(h->wa_kind); dfree(h->wa_sup); dfree(h->cell_verts); dfree(h->cell_vol);
     dfree(h->wc_kind); dfree(h->wc_sup); dfree(h->wa_val); dfree(h->wa_gp); dfree(h->wc_val); dfree(h->wc_gp);
+    dfree(h->wa_val32); dfree(h->wa_gp32); dfree(h->leaf_val32);
     dfree(h->v2c_ptr); dfree(h->v2c); dfree(h->kappa_field);
     dfree(h->r); dfree(h->jsell); dfree(h->dinv); dfree(h->part); dfree(h->scal); dfree(h->ticket); dfree(h->status); dfree(h->st);
     for (KWork<double> *W : {&h->k64}) {
@@ -858,10 +898,16 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     EG_TRY(join_in(h, (cudaStream_t)stream));
     EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
     // residual, Jacobi-scaled Jacobian and right-hand side at u (both precisions when mixed)
-    auto eval = [&](double *rn) -> egfem_status {
+    // residual and solver operator at u: the FP64 operator (need64, and always in FP64 mode),
+    // else only the FP32 one from the mixed-precision tensor action
+    bool have64 = false;
+    if (mixed && h->opts.op == EGFEM_OP_CSF) EG_TRY(ensure_mixed_tensor(h, h->hs));
+    auto eval = [&](double *rn, bool need64 = false) -> egfem_status {
         CsfArgs A = csf_args(h, d_u, d_d);
         A.r = h->r;
-        A.a64 = h->k64.A; A.q64 = h->k64.b;
+        A.q64 = h->k64.b;
+        have64 = !mixed || need64;
+        if (have64) A.a64 = h->k64.A;
         if (mixed) A.a32 = h->k32.A;
         S.kernel_launches += launch_csf(h, A, h->hs) + 1 + (mixed ? 1 : 0);
         if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
@@ -908,6 +954,10 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
         int32_t its_step = 0;
         while (!stepped) {
             int32_t done = 0, it = 0;
+            if (!fp32 && !have64) {   // an FP64 rescue needs the FP64 operator at this u
+                status = eval(&rn, true);
+                if (status != EGFEM_OK) break;
+            }
             if (fp32) status = run_bicgstab(h, h->k32, std::max(eta, kMixedEtaFloor), h->opts.krylov_maxit, kMixedStall, &done, &it);
             else status = run_bicgstab(h, h->k64, eta, h->opts.krylov_maxit, 0, &done, &it);
             if (status != EGFEM_OK) break;
@@ -1122,11 +1172,24 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     // FP64 operations: 2 per leaf (D and J1), per fibre the residual, diagonal and J2 scatter
     // (6; 12 when g is evaluated per fibre), 4 per reaction entry, 2 per local column, and
     // the nodal pass (interpolation and g, about 6 per node)
-    const double csf_flops = h->opts.op == EGFEM_OP_MATRIX_FREE ? L * 4 + F * 12 + RX * 10 + CE * 2
-                                                                 : L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) +
-                                                                       CE * 2 + (NWA + NWC) * 6;
-    EG_TRY(timeit(h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused", csf_bytes, csf_flops, 1,
-                  [&] { launch_csf(h, A, h->hs); }));
+    double csf_flops = h->opts.op == EGFEM_OP_MATRIX_FREE ? L * 4 + F * 12 + RX * 10 + CE * 2
+                                                           : L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) +
+                                                                 CE * 2 + (NWA + NWC) * 6;
+    const char *ta_name = h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused";
+    if (!std::is_same<V, double>::value && h->opts.op == EGFEM_OP_CSF) {
+        // mixed path: the mixed-precision tensor action (FP64 residual, FP32 Jacobian).  Nodal
+        // pass as above plus the FP32 copies written; leaves: FP64 and FP32 value + column byte;
+        // fibres: info + W index; nodal values read once (FP64 value, FP32 value and
+        // derivative); local columns: index + slot read, FP32 operator written; u/d/r/q.
+        // FP64 operations: 2 per leaf (D), 3 per fibre (residual, row sum), 4 per reaction
+        // entry, 1 per local column (difference), 6 per node.
+        EG_TRY(ensure_mixed_tensor(h, h->hs));
+        ta_name = "csf_mixed";
+        csf_bytes = (NWA + NWC) * (1 + 12 + 2 * 16) + NWA * 8 + L * 13 + F * 8 + NWA * 16 + RX * 16 + NWC * 16 +
+                    CE * (8 + 4) + N * (8 + 8 + 8 + 8 + 1) + SM;
+        csf_flops = L * 2 + F * 3 + RX * 4 + CE * 1 + (NWA + NWC) * 6;
+    }
+    EG_TRY(timeit(ta_name, csf_bytes, csf_flops, 1, [&] { launch_csf(h, A, h->hs); }));
     if (!std::is_same<V, double>::value)
         cast_kernel<double, V><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, W.b);
     KVecs<V> K = kvecs(h, W);

@@ -45,6 +45,8 @@ struct CsfArgs {
     // (nullable: then every fibre / reaction entry evaluates g itself)
     const double *wa_val, *wa_gp;   // a_m = kappa_m + g_a((Pi u)_m), g_a'((Pi u)_m)
     const double *wc_val, *wc_gp;   // c_m = g_c((Pi_c u)_m),         g_c'((Pi_c u)_m)
+    const float *wa_val32, *wa_gp32;   // FP32 copies of a_m, g_a' (csf_mixed_kernel)
+    const float *leaf_val32;           // FP32 copy of leaf_val (csf_mixed_kernel)
     const int32_t *slice_inst;   // batch: instance of each slice (nullable)
     const uint8_t *inst_mask;    // batch: rows of instances with mask 0 are skipped (nullable)
     int32_t *status;       // error word (singular diagonal)
@@ -85,6 +87,16 @@ __device__ __forceinline__ void scatter_pi(uint32_t info, double e, double *J, i
     if (kind == W_MID) { const double h = 0.5 * e; J[c0 * stride] += h; J[c1 * stride] += h; return; }
     if (kind == W_THIRD) { const double h = e * (1.0 / 3.0); J[c0 * stride] += 2.0 * h; J[c1 * stride] += h; return; }
     if (kind == W_FACE) { const double h = e * (1.0 / 3.0); J[c0 * stride] += h; J[c1 * stride] += h; J[c2 * stride] += h; }
+}
+
+// FP32 variant of scatter_pi
+__device__ __forceinline__ void scatter_pi32(uint32_t info, float e, float *J, int stride) {
+    const uint32_t kind = (info >> 24) & 0xF;
+    const uint32_t c0 = info & 0xFF, c1 = (info >> 8) & 0xFF, c2 = (info >> 16) & 0xFF;
+    if (kind == W_VERTEX) { J[c0 * stride] += e; return; }
+    if (kind == W_MID) { const float h = 0.5f * e; J[c0 * stride] += h; J[c1 * stride] += h; return; }
+    if (kind == W_THIRD) { const float h = e * (1.0f / 3.0f); J[c0 * stride] += 2.0f * h; J[c1 * stride] += h; return; }
+    if (kind == W_FACE) { const float h = e * (1.0f / 3.0f); J[c0 * stride] += h; J[c1 * stride] += h; J[c2 * stride] += h; }
 }
 
 // Fused pointwise nonlinearity + residual + Jacobian fill (one thread per row).
@@ -210,13 +222,128 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     if (A.a32) A.a32[M.col_base + lane] = float(rowsum);
 }
 
+// Mixed-precision tensor action for the Newton step of the mixed path (one thread per row):
+// the residual r (and D r) in FP64 exactly as csf_fused_kernel computes it, the Jacobian in
+// FP32 from the FP32 copies of T and of the nodal values, written only as the Jacobi-scaled
+// FP32 solver operator.  Its diagonal uses the exact zero row sums of T (J1_ii = -sum of the
+// row's off-diagonal J1 entries), and the row sum kept in column 0 for the difference-form
+// operator comes from the same identity -- J1 rows sum to zero, the J2 and reaction rows to
+// sum_m D_im g'_m and gamma sum_m M_im g_c'_m (Pi's rows sum to one) -- accumulated in FP64,
+// less the Dirichlet columns the operator does not store.  Needs wa_val/wa_val32 (or a
+// constant coefficient), wc_val for a reaction, leaf_val32, r, q64 and a32.
+template <int MAXC>
+__global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
+    __shared__ double s_du[MAXC * CSF_BLOCK];
+    __shared__ float s_J[MAXC * CSF_BLOCK];
+    const int tid = threadIdx.x;
+    const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
+    if (row >= A.n_rows) return;
+    const int64_t sl = row / SLICE;
+    const int lane = int(row % SLICE);
+    if (A.inst_mask && !A.inst_mask[A.slice_inst[sl]]) return;
+    const SliceMeta M = A.meta[sl];
+    const double ui = A.u[row];
+    const double di = A.d ? A.d[row] : 0.0;
+    double *du = s_du + tid;
+    float *J = s_J + tid;
+    if (A.dir[row]) {
+        A.r[row] = ui - di;
+        A.q64[row] = ui - di;
+        for (int c = 0; c < M.ncol; ++c) A.a32[M.col_base + int64_t(c) * SLICE + lane] = (c == 0) ? 1.0f : 0.0f;
+        return;
+    }
+    for (int c = 0; c < M.ncol; ++c) {
+        const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
+        du[c * CSF_BLOCK] = A.u[g] - ui;
+        J[c * CSF_BLOCK] = 0.0f;
+    }
+    const Nonlin nl = A.nl;
+    double r = 0.0, D = 0.0, a = 0.0, rs = 0.0;
+    float a32 = 0.0f, gp32 = 0.0f, s1 = 0.0f;
+    uint32_t info = 0;
+    int f = -1;
+    for (int j = 0; j < M.nleaf; ++j) {
+        const int64_t q = M.leaf_base + int64_t(j) * SLICE + lane;
+        const uint8_t lc = A.leaf_col[q];
+        if (lc & LEAF_FIBRE_START) {
+            if (f >= 0) {
+                r += a * D;
+                if (gp32 != 0.0f) {
+                    const float e = float(D) * gp32;
+                    scatter_pi32(info, e, J, CSF_BLOCK);
+                    rs += double(e);
+                }
+            }
+            ++f;
+            const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
+            info = A.fib_info[fq];
+            if (((info >> 24) & 0xF) == W_CONST) {
+                a = nl.kappa;
+                a32 = float(nl.kappa);
+                gp32 = 0.0f;
+            } else {
+                const int32_t m = A.fib_m[fq];
+                a = A.wa_val[m];
+                a32 = A.wa_val32[m];
+                gp32 = A.wa_gp32[m];
+            }
+            D = 0.0;
+        }
+        const int c = lc & LEAF_PAD;
+        if (c != LEAF_PAD) {
+            D += A.leaf_val[q] * du[c * CSF_BLOCK];
+            const float t = A.leaf_val32[q] * a32;
+            J[c * CSF_BLOCK] += t;
+            s1 += t;
+        }
+    }
+    if (f >= 0) {
+        r += a * D;
+        if (gp32 != 0.0f) {
+            const float e = float(D) * gp32;
+            scatter_pi32(info, e, J, CSF_BLOCK);
+            rs += double(e);
+        }
+    }
+    // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
+    for (int j = 0; j < M.nrx; ++j) {
+        const int64_t q = M.rx_base + int64_t(j) * SLICE + lane;
+        const double mv = A.rx_val[q];
+        if (mv == 0.0) continue;
+        const int32_t m = A.rx_m[q];
+        r += nl.gamma * mv * A.wc_val[m];
+        const double e = nl.gamma * mv * A.wc_gp[m];
+        scatter_pi32(A.rx_info[q], float(e), J, CSF_BLOCK);
+        rs += e;
+    }
+    const float diag = J[0] - s1;
+    const double res = r - di;
+    A.r[row] = res;
+    float dinv = 0.0f;
+    if (diag != 0.0f) dinv = 1.0f / diag;
+    else if (A.status) atomicOr(A.status, 1);
+    A.q64[row] = double(dinv) * res;
+    for (int c = 1; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        const float v = J[c * CSF_BLOCK];
+        if (A.col_slot[q] >= 0) {
+            A.a32[q] = dinv * v;
+        } else {
+            A.a32[q] = 0.0f;
+            rs -= double(v);
+        }
+    }
+    A.a32[M.col_base + lane] = float(double(dinv) * rs);
+}
+
 // Nodal values of one nonlinearity on its W space (Sec. 3.1 eq. (5), Sec. 3.2), one thread
 // per W node, each node evaluated once: val_m = base_m + g((Pi u)_m), gp_m = g'((Pi u)_m),
 // with base = kappa (constant, or the field when base_field is set) for the coefficient
 // space and 0 for the reaction space.
 __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u,
                                                     int32_t g_kind, int32_t g_p, double g_scale, double base,
-                                                    const double *base_field, double *val, double *gp) {
+                                                    const double *base_field, double *val, double *gp, float *val32,
+                                                    float *gp32) {
     const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n_w) return;
     const uint32_t k = kind[m];
@@ -228,8 +355,13 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
     else pu = (u0 + u[sup[3 * m + 1]] + u[sup[3 * m + 2]]) * (1.0 / 3.0);
     double g, d;
     g_eval(g_kind, g_p, g_scale, pu, g, d);
-    val[m] = (base_field ? base_field[m] : base) + g;
+    const double v = (base_field ? base_field[m] : base) + g;
+    val[m] = v;
     gp[m] = d;
+    if (val32) {   // FP32 copies for the mixed-precision Jacobian
+        val32[m] = float(v);
+        gp32[m] = float(d);
+    }
 }
 
 // Pointwise nonlinearity alone (Sec. 3.2), one thread per W node.
