@@ -235,9 +235,9 @@ __device__ __forceinline__ void pk_after_c(KState &S, double rho1, double rr, in
 
 constexpr int32_t K_TIMEOUT = 6;   // a grid-barrier wait ran out (KDone extension)
 
-// Resident blocks per SM the kernel is compiled for (register budget of 64 per thread; both
-// vector types then run without spills).
-constexpr int PK_MIN_BLOCKS = 4;
+// Resident blocks per SM the kernel is compiled for: 5 (48 registers per thread) measured
+// fastest against 4 and 6 on both vector types, at 1M and 4M rows.
+constexpr int PK_MIN_BLOCKS = 5;
 
 // scalars of one system as the vector loops use them
 template <typename V>
