@@ -224,16 +224,19 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
 
 // Mixed-precision tensor action for the Newton step of the mixed path (one thread per row):
 // the residual r (and D r) in FP64 exactly as csf_fused_kernel computes it, the Jacobian in
-// FP32 from the FP32 copies of T and of the nodal values, written only as the Jacobi-scaled
-// FP32 solver operator.  Its diagonal uses the exact zero row sums of T (J1_ii = -sum of the
-// row's off-diagonal J1 entries), and the row sum kept in column 0 for the difference-form
-// operator comes from the same identity -- J1 rows sum to zero, the J2 and reaction rows to
-// sum_m D_im g'_m and gamma sum_m M_im g_c'_m (Pi's rows sum to one) -- accumulated in FP64,
-// less the Dirichlet columns the operator does not store.  Needs wa_val/wa_val32 (or a
-// constant coefficient), wc_val for a reaction, leaf_val32, r, q64 and a32.
+// FP32 from the FP32 copies of T, of u's differences and of the nodal values, written only as
+// the Jacobi-scaled FP32 solver operator.  Its diagonal uses the exact zero row sums of T
+// (J1_ii = -sum of the row's off-diagonal J1 entries), and the row sum kept in column 0 for the
+// difference-form operator comes from the same identity -- J1 rows sum to zero, the J2 and
+// reaction rows to sum_m D_im g'_m and gamma sum_m M_im g_c'_m (Pi's rows sum to one) --
+// summed (compensated) from the contributions exactly as scattered, less the Dirichlet
+// columns the operator does not store.  FP64 work per row: the differences of u, one FMA
+// per leaf and one per fibre.  Needs wa_val/wa_val32 (or a constant coefficient), wc_val for
+// a reaction, leaf_val32, r, q64 and a32.
 template <int MAXC>
 __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     __shared__ double s_du[MAXC * CSF_BLOCK];
+    __shared__ float s_du32[MAXC * CSF_BLOCK];
     __shared__ float s_J[MAXC * CSF_BLOCK];
     const int tid = threadIdx.x;
     const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     const double ui = A.u[row];
     const double di = A.d ? A.d[row] : 0.0;
     double *du = s_du + tid;
-    float *J = s_J + tid;
+    float *du32 = s_du32 + tid, *J = s_J + tid;
     if (A.dir[row]) {
         A.r[row] = ui - di;
         A.q64[row] = ui - di;
@@ -254,12 +257,22 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     }
     for (int c = 0; c < M.ncol; ++c) {
         const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
-        du[c * CSF_BLOCK] = A.u[g] - ui;
+        const double d = A.u[g] - ui;
+        du[c * CSF_BLOCK] = d;
+        du32[c * CSF_BLOCK] = float(d);
         J[c * CSF_BLOCK] = 0.0f;
     }
     const Nonlin nl = A.nl;
-    double r = 0.0, D = 0.0, a = 0.0, rs = 0.0;
-    float a32 = 0.0f, gp32 = 0.0f, s1 = 0.0f;
+    // FP64: the residual (D, r).  FP32: the Jacobian (D32, J, s1) and its row sum (rs_hi + rs_lo,
+    // a compensated sum of the J2 and reaction contributions exactly as scattered)
+    double r = 0.0, D = 0.0, a = 0.0;
+    float a32 = 0.0f, gp32 = 0.0f, s1 = 0.0f, D32 = 0.0f, rs_hi = 0.0f, rs_lo = 0.0f;
+    auto rs_add = [&](float e) {
+        const float t = __fadd_rn(rs_hi, e);
+        const float z = __fsub_rn(t, rs_hi);
+        rs_lo = __fadd_rn(rs_lo, __fadd_rn(__fsub_rn(rs_hi, __fsub_rn(t, z)), __fsub_rn(e, z)));
+        rs_hi = t;
+    };
     uint32_t info = 0;
     int f = -1;
     for (int j = 0; j < M.nleaf; ++j) {
@@ -269,9 +282,9 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
             if (f >= 0) {
                 r += a * D;
                 if (gp32 != 0.0f) {
-                    const float e = float(D) * gp32;
+                    const float e = D32 * gp32;
                     scatter_pi32(info, e, J, CSF_BLOCK);
-                    rs += double(e);
+                    rs_add(e);
                 }
             }
             ++f;
@@ -288,11 +301,14 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
                 gp32 = A.wa_gp32[m];
             }
             D = 0.0;
+            D32 = 0.0f;
         }
         const int c = lc & LEAF_PAD;
         if (c != LEAF_PAD) {
             D += A.leaf_val[q] * du[c * CSF_BLOCK];
-            const float t = A.leaf_val32[q] * a32;
+            const float T32 = A.leaf_val32[q];
+            D32 += T32 * du32[c * CSF_BLOCK];
+            const float t = T32 * a32;
             J[c * CSF_BLOCK] += t;
             s1 += t;
         }
@@ -300,9 +316,9 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     if (f >= 0) {
         r += a * D;
         if (gp32 != 0.0f) {
-            const float e = float(D) * gp32;
+            const float e = D32 * gp32;
             scatter_pi32(info, e, J, CSF_BLOCK);
-            rs += double(e);
+            rs_add(e);
         }
     }
     // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
@@ -312,9 +328,9 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         if (mv == 0.0) continue;
         const int32_t m = A.rx_m[q];
         r += nl.gamma * mv * A.wc_val[m];
-        const double e = nl.gamma * mv * A.wc_gp[m];
-        scatter_pi32(A.rx_info[q], float(e), J, CSF_BLOCK);
-        rs += e;
+        const float e = float(nl.gamma * mv * A.wc_gp[m]);
+        scatter_pi32(A.rx_info[q], e, J, CSF_BLOCK);
+        rs_add(e);
     }
     const float diag = J[0] - s1;
     const double res = r - di;
@@ -330,10 +346,10 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
             A.a32[q] = dinv * v;
         } else {
             A.a32[q] = 0.0f;
-            rs -= double(v);
+            rs_add(-v);
         }
     }
-    A.a32[M.col_base + lane] = float(double(dinv) * rs);
+    A.a32[M.col_base + lane] = dinv * (rs_hi + rs_lo);
 }
 
 // Nodal values of one nonlinearity on its W space (Sec. 3.1 eq. (5), Sec. 3.2), one thread
