@@ -340,6 +340,8 @@ def main():
     ap.add_argument("--p3-instances", type=int, default=32)
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=12000)
+    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed"],
+                    help="build the workload, run the per-kernel profile once at u = 0 and print it (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -365,6 +367,15 @@ def main():
 
     mesh, f_cell = make_workload(args.n)
     prob = P.make_problem(a=("pow", 2), a_degree=2)
+    if args.profile_only:
+        hp = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED if args.profile_only == "mixed" else P.PREC_FP64))
+        f = torch.tensor(f_cell, device="cuda", dtype=torch.float64)
+        d = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+        hp.load_cellwise(f, d)
+        u = torch.zeros_like(d)
+        print(json.dumps(hp.profile_kernels(u, d, reps=1)), flush=True)
+        hp.close()
+        return
     h = P.Handle(mesh, prob, P.default_options())
     dev = torch.device("cuda", local)
     f = torch.tensor(f_cell, device=dev, dtype=torch.float64)

@@ -1193,8 +1193,11 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     if (!std::is_same<V, double>::value)
         cast_kernel<double, V><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, W.b);
     KVecs<V> K = kvecs(h, W);
-    kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
-    enqueue_iterations(h, W, 1, h->hs);
+    const bool persistent = h->opts.krylov_persistent && W.g_pk > 0;
+    if (!persistent) {   // state for the iteration kernels: set up, one iteration
+        kry_setup<V><<<W.g_setup, KRY_BLOCK, 0, h->hs>>>(K, 0.0, 1 << 30, 0);
+        enqueue_iterations(h, W, 1, h->hs);
+    }
     EG_CUDA(cudaGetLastError());
     const int fp = std::is_same<V, double>::value ? 1 : 0;
     auto run = [&](const char *name, double bytes, double flops, auto kern, int kg) -> egfem_status {
@@ -1212,7 +1215,7 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         EG_CUDA(cudaMemcpy(hm.data(), h->csf.meta, hm.size() * sizeof(SliceMeta), cudaMemcpyDeviceToHost));
         for (const SliceMeta &M : hm) if (M.off_base < 0) ce_nonuni += double(M.ncol) * SLICE;
     }
-    if (h->opts.krylov_persistent && W.g_pk > 0) {
+    if (persistent) {
         // persistent solve: a fixed number of iterations (rtol 0), reported per iteration.  Per
         // row and iteration: A reads p, rh, writes v; B1 reads r, v, writes s; B2 reads s, writes
         // t; C reads s, p, t, rh, x, writes x, r; D reads r, v, p, writes p (19 vector passes);
