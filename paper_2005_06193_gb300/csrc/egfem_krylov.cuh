@@ -107,19 +107,21 @@ __device__ __forceinline__ void stv(V *p, const Pack<V> &o) {
 }
 
 template <typename M, int R>
+// operator values and column indices are read-only during a solve: non-coherent loads, which
+// the compiler may also schedule ahead of the solve's vector stores
 __device__ __forceinline__ void ldm(const M *p, M (&o)[R]) {
     if constexpr (sizeof(M) * R == 16) {
-        if constexpr (R == 2) { const double2 t = *reinterpret_cast<const double2 *>(p); o[0] = t.x; o[1] = t.y; }
-        else { const float4 t = *reinterpret_cast<const float4 *>(p); o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w; }
+        if constexpr (R == 2) { const double2 t = __ldg(reinterpret_cast<const double2 *>(p)); o[0] = t.x; o[1] = t.y; }
+        else { const float4 t = __ldg(reinterpret_cast<const float4 *>(p)); o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w; }
     } else {
-        const float2 t = *reinterpret_cast<const float2 *>(p);   // two FP32 values (df64 rows)
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));   // two FP32 values (df64 rows)
         o[0] = t.x; o[1] = t.y;
     }
 }
 
 template <typename V>
 __device__ __forceinline__ void ldi(const int32_t *p, int32_t (&c)[VecT<V>::R]) {
-    const typename VecT<V>::idx t = *reinterpret_cast<const typename VecT<V>::idx *>(p);
+    const typename VecT<V>::idx t = __ldg(reinterpret_cast<const typename VecT<V>::idx *>(p));
     if constexpr (VecT<V>::R == 2) { c[0] = t.x; c[1] = t.y; }
     else { c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w; }
 }
