@@ -173,7 +173,7 @@ __device__ __forceinline__ Pack<V> pk_spmv(const KVecs<V> &K, int64_t r0, const 
             y64[j] = a0[j] * xi.v[j];
         }
     }
-#pragma unroll 1
+#pragma unroll 4
     for (int c0 = 1; c0 < M.ncol; c0 += CH) {
         M_t a[CH][R];
         int32_t col[CH][R];
@@ -235,9 +235,11 @@ __device__ __forceinline__ void pk_after_c(KState &S, double rho1, double rr, in
 
 constexpr int32_t K_TIMEOUT = 6;   // a grid-barrier wait ran out (KDone extension)
 
-// Resident blocks per SM the kernel is compiled for: 5 (48 registers per thread) measured
-// fastest against 4 and 6 on both vector types, at 1M and 4M rows.
-constexpr int PK_MIN_BLOCKS = 5;
+// Resident blocks per SM the kernel is compiled for: 4 (64 registers per thread), with the
+// operator's column loop unrolled 4 times (its loads then issue ahead of the arithmetic):
+// measured fastest -- double-float 69 us per iteration at 1M rows and 242 us at 4.2M rows,
+// against 74 and 293 us with 5 blocks and no unrolling; FP64 unchanged (97 us).
+constexpr int PK_MIN_BLOCKS = 4;
 
 // scalars of one system as the vector loops use them
 template <typename V>
