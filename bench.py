@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 SMS = 152                 # GB300 streaming multiprocessors
 DFMA_PER_SM_CLK = 2       # FP64 FMAs per SM per clock on GB300 (nominal 1.25 TFLOP/s FP64)
-# DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
-# captured for the current code); the captures and their commands are summarised in profiles/.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch (per iteration for the persistent solve) from ncu
+# captures of the current kernels; the captures and their commands are summarised in
+# profiles/pk_solve_fp64_1024x1024_ncu.md.  Valid for the FP64 1024 x 1024 workload only.
+NCU_TRAFFIC = {"kry_persistent": 144.8e6}
 
 
 def load_peaks():
@@ -430,6 +431,8 @@ def main():
     total_share = sum(share.values())
     dom = max(prof, key=lambda p: share[p["name"]])
     roofline = roofline_of(dom, hbm, peak_kind, fp64_peak)
+    if args.n != 1024:
+        roofline["traffic"] = None   # the ncu capture is of the 1024 x 1024 workload
     roofline["share_of_solve"] = share[dom["name"]] / (ms_max / args.steps)
     if dom["name"] == "kry_persistent":
         roofline["units_per_launch"] = f"one launch runs a whole BiCGStab solve; ms and bytes are per iteration"

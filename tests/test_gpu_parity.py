@@ -256,7 +256,7 @@ def test_full_size_1024_residual_on_sampled_rows(P):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batched_newton_matches_single_instance_oracle(P, prec):
+def test_batched_newton_matches_single_instance_oracle(P, prec, persistent=1):
     """Four instances of uneven size (w = u^3 in P3 and different sine sources) solved in
     one batched call; each equals the oracle's own Newton solution of that instance."""
     inst = wl.batch_instances(count=4, seed=3, n_lo=6, n_hi=21)
@@ -269,7 +269,7 @@ def test_batched_newton_matches_single_instance_oracle(P, prec):
         loads.append(b)
         refs.append(u_ref)
     opts = P.default_options(newton_rtol=1e-13 if prec == "fp64" else 1e-10,
-                             precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64)
+                             precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64, krylov_persistent=persistent)
     h = P.BatchHandle(meshes, P.make_problem(a=("pow", 3), a_degree=3), opts)
     d = h.scatter(loads)
     u = torch.zeros_like(d)
@@ -279,6 +279,12 @@ def test_batched_newton_matches_single_instance_oracle(P, prec):
     for b, (sol, ref) in enumerate(zip(sols, refs)):
         assert stats[b].status == 0
         assert rel(sol, ref) <= (1e-11 if prec == "fp64" else 1e-6), b
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_newton_graph_driver(P, prec):
+    """The same batch through the graph-captured iteration kernels (krylov_persistent = 0)."""
+    test_batched_newton_matches_single_instance_oracle(P, prec, persistent=0)
 
 
 def _adjoint_setup(P, n, grid, thetas, prec="fp64", rtol=1e-13):
