@@ -339,8 +339,8 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--p3-instances", type=int, default=32)
-    ap.add_argument("--ref-newton-steps", type=int, default=7)
-    ap.add_argument("--ref-krylov-iters", type=int, default=12000)
+    ap.add_argument("--ref-newton-steps", type=int, default=5)
+    ap.add_argument("--ref-krylov-iters", type=int, default=3500)
     ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed"],
                     help="build the workload, run the per-kernel profile once at u = 0 and print it (for ncu captures)")
     args = ap.parse_args()

@@ -140,10 +140,13 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     double r = 0.0, j1d = 0.0, D = 0.0, a = 0.0, gp = 0.0;
     uint32_t info = 0;
     int f = -1;
+    // tensor data are read-only (non-coherent loads); unrolling lets the next leaves' loads
+    // issue ahead of this leaf's arithmetic
+#pragma unroll 4
     for (int j = 0; j < M.nleaf; ++j) {
         const int64_t q = M.leaf_base + int64_t(j) * SLICE + lane;
-        const uint8_t lc = A.leaf_col[q];
-        const double T = A.leaf_val[q];
+        const uint8_t lc = __ldg(A.leaf_col + q);
+        const double T = __ldg(A.leaf_val + q);
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
@@ -151,13 +154,13 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-            info = A.fib_info[fq];
-            const double td = A.fib_tdiag[fq];
+            info = __ldg(A.fib_info + fq);
+            const double td = __ldg(A.fib_tdiag + fq);
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 gp = 0.0;
             } else if (A.wa_val) {
-                const int32_t m = A.fib_m[fq];
+                const int32_t m = __ldg(A.fib_m + fq);
                 a = A.wa_val[m];
                 gp = A.wa_gp[m];
             } else {
@@ -275,9 +278,12 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     };
     uint32_t info = 0;
     int f = -1;
+    // tensor data are read-only (non-coherent loads); unrolling lets the next leaves' loads
+    // issue ahead of this leaf's arithmetic
+#pragma unroll 4
     for (int j = 0; j < M.nleaf; ++j) {
         const int64_t q = M.leaf_base + int64_t(j) * SLICE + lane;
-        const uint8_t lc = A.leaf_col[q];
+        const uint8_t lc = __ldg(A.leaf_col + q);
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
@@ -289,13 +295,13 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-            info = A.fib_info[fq];
+            info = __ldg(A.fib_info + fq);
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 a32 = float(nl.kappa);
                 gp32 = 0.0f;
             } else {
-                const int32_t m = A.fib_m[fq];
+                const int32_t m = __ldg(A.fib_m + fq);
                 a = A.wa_val[m];
                 a32 = A.wa_val32[m];
                 gp32 = A.wa_gp32[m];
@@ -305,8 +311,8 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         }
         const int c = lc & LEAF_PAD;
         if (c != LEAF_PAD) {
-            D += A.leaf_val[q] * du[c * CSF_BLOCK];
-            const float T32 = A.leaf_val32[q];
+            D += __ldg(A.leaf_val + q) * du[c * CSF_BLOCK];
+            const float T32 = __ldg(A.leaf_val32 + q);
             D32 += T32 * du32[c * CSF_BLOCK];
             const float t = T32 * a32;
             J[c * CSF_BLOCK] += t;
