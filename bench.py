@@ -335,6 +335,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-mf", action="store_true")
+    ap.add_argument("--no-picard", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=512)
@@ -491,6 +492,19 @@ def main():
                 "fp64_tflops": cm["flops"] / (cm["ms"] / 1e3) / 1e12, "bytes_per_launch": cm["bytes"],
                 "speedup_vs_fp64": csf["ms"] / cm["ms"]}
         hm.close()
+
+    if not args.no_picard:
+        # the paper's own iteration (Picard, frozen coefficient) on the same workload
+        hpi = P.Handle(mesh, prob, P.default_options(iteration=P.ITER_PICARD, newton_maxit=200))
+        u.zero_()
+        hpi.newton_solve(u, d)
+        msp, spi = timed_solves(torch, hpi, d, u, min(args.steps, 2), barrier)
+        sl = spi[-1]
+        out["picard"] = {"value": world * min(args.steps, 2) / (msp / 1e3), "unit": "solves/s",
+                         "ms_per_step": msp / min(args.steps, 2), "picard_iters": sl.newton_iters,
+                         "krylov_iters": int(sl.krylov_iters), "final_rel_residual": sl.res_final / sl.res0,
+                         "newton_over_picard_time": (msp / min(args.steps, 2)) / (ms_max / args.steps)}
+        hpi.close()
 
     if not args.no_mf:
         hmf = P.Handle(mesh, prob, P.default_options(op=P.OP_MATRIX_FREE))

@@ -75,6 +75,13 @@ typedef enum {
 } egfem_precision;
 
 typedef enum {
+    EGFEM_ITER_NEWTON = 0,     /* Newton: the full Jacobian of Sec. 4                       */
+    EGFEM_ITER_PICARD = 1      /* Picard (Sec. 4, Example 4.1): the frozen-coefficient matrix
+                                  T .2 a(u^n), the reaction on the right-hand side; linear
+                                  convergence to the same discrete solution               */
+} egfem_iteration;
+
+typedef enum {
     EGFEM_OP_CSF = 0,          /* T stored as row-segmented compressed sparse fibres        */
     EGFEM_OP_MATRIX_FREE = 1   /* element-local evaluation: T_imk = sum_K iota^K_m S^K_ik   */
 } egfem_operator;
@@ -117,6 +124,9 @@ typedef struct {
     int32_t krylov_persistent; /* nonzero (default): each BiCGStab solve is one cooperative
                                   launch with grid barriers; 0: graph-captured iteration
                                   kernels (graph_chunk iterations per graph launch)          */
+    int32_t iteration;       /* egfem_iteration of egfem_newton_solve / batch solve and the
+                                matrix egfem_jacobian returns (default EGFEM_ITER_NEWTON);
+                                egfem_adjoint always uses the Newton Jacobian               */
 } egfem_options;
 
 #define EGFEM_HIST 64

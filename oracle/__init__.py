@@ -96,7 +96,7 @@ def lib():
             L.orc_pointwise.argtypes = [ctypes.c_void_p, _c_dp, _c_dp, _c_dp, _c_dp, _c_dp]
             for f in ("orc_egfem_residual", "orc_sga_residual"):
                 getattr(L, f).argtypes = [ctypes.c_void_p, _c_dp, _c_dp, _c_dp, ctypes.c_int, _c_dp]
-            for f in ("orc_egfem_jacobian", "orc_sga_jacobian"):
+            for f in ("orc_egfem_jacobian", "orc_sga_jacobian", "orc_picard_matrix"):
                 getattr(L, f).argtypes = [ctypes.c_void_p, _c_dp, ctypes.c_int64, _c_lp, _c_lp, _c_dp]
                 getattr(L, f).restype = ctypes.c_int64
             L.orc_quad_points.argtypes = [ctypes.c_void_p, _c_dp]
@@ -247,8 +247,10 @@ class Problem:
         return r
 
     def jacobian(self, u, method="egfem"):
+        """Newton Jacobian (method "egfem" or "sga"), or the Picard iteration matrix T .2 a(u)
+        (method "picard"; Sec. 4, Example 4.1), with Dirichlet rows/columns handled."""
         u = _f64(u)
-        f = lib().orc_egfem_jacobian if method == "egfem" else lib().orc_sga_jacobian
+        f = {"egfem": lib().orc_egfem_jacobian, "sga": lib().orc_sga_jacobian, "picard": lib().orc_picard_matrix}[method]
         n = f(self._h, _dp(u), 0, None, None, None)
         I, L = np.empty(n, dtype=np.int64), np.empty(n, dtype=np.int64)
         V = np.empty(n)
@@ -256,14 +258,17 @@ class Problem:
         return sp.csr_matrix((V, (I, L)), shape=(self.n, self.n))
 
     def newton(self, b, u0=None, uD=None, method="egfem", solver="lu", rtol=1e-10, maxit=50, ktol=1e-12,
-               form="diff", keep_iterates=False):
-        """Newton's method from u0 (default 0).  Returns (u, residual_history, iterates, krylov_iters)."""
+               form="diff", keep_iterates=False, iteration="newton"):
+        """Newton's method from u0 (default 0) -- or, with iteration="picard" (EGFEM only), the
+        Picard iteration with the frozen-coefficient matrix (Sec. 4, Example 4.1).  Returns
+        (u, residual_history, iterates, krylov_iters)."""
         u = np.zeros(self.n) if u0 is None else _f64(u0).copy()
         b, uD = _f64(b), _f64(uD)
         hist = np.zeros(maxit + 1)
         its = np.zeros((maxit + 1) * self.n) if keep_iterates else None
         ktot = ctypes.c_int(0)
-        k = lib().orc_newton(self._h, 0 if method == "egfem" else 1, 0 if solver == "lu" else 1, _dp(b), _dp(uD),
+        code = 2 if iteration == "picard" else (0 if method == "egfem" else 1)
+        k = lib().orc_newton(self._h, code, 0 if solver == "lu" else 1, _dp(b), _dp(uD),
                              _dp(u), float(rtol), int(maxit), float(ktol), FORM_DIFF if form == "diff" else FORM_PLAIN,
                              _dp(hist), _dp(its), ctypes.byref(ktot))
         if k < 0:

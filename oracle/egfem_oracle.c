@@ -630,8 +630,13 @@ void orc_egfem_residual(const orc_problem *P, const double *u, const double *b, 
     free(w); free(c);
 }
 
-/* Jacobian as sorted COO (i, l, value); returns the entry count, fills up to cap. */
-int64_t orc_egfem_jacobian(const orc_problem *P, const double *u, int64_t cap, int64_t *I, int64_t *L, double *V) {
+/* Iteration matrix as sorted COO (i, l, value); returns the entry count, fills up to cap.
+ * picard = 0: the Newton Jacobian (T .2 a) + (T .3 u) diag(g') Pi + gamma M diag(g_c') Pi_c
+ * (Sec. 4, identity blocks eliminated).  picard = 1: the frozen-coefficient matrix T .2 a of
+ * the Picard iteration (Sec. 4 and Example 4.1: the coefficient is taken at the previous
+ * iterate, the reaction term on the right-hand side). */
+static int64_t egfem_matrix(const orc_problem *P, const double *u, int picard, int64_t cap, int64_t *I, int64_t *L,
+                            double *V) {
     int nv = P->s.nv;
     double *w = malloc(sizeof(double) * P->Sa.n), *wp = malloc(sizeof(double) * P->Sa.n);
     double *c = malloc(sizeof(double) * P->Sc.n), *cp = malloc(sizeof(double) * P->Sc.n);
@@ -645,7 +650,8 @@ int64_t orc_egfem_jacobian(const orc_problem *P, const double *u, int64_t cap, i
     }
     /* (T .3 u) diag(g') Pi: D_im = sum_k T_imk u_k, then J_il += D_im g'_m Pi_ml */
     orc_coo D = {0};
-    for (size_t t = 0; t < P->T.n; ++t) coo_push(&D, P->T.t[t].i, P->T.t[t].j, 0, P->T.t[t].v * u[P->T.t[t].k]);
+    if (!picard)
+        for (size_t t = 0; t < P->T.n; ++t) coo_push(&D, P->T.t[t].i, P->T.t[t].j, 0, P->T.t[t].v * u[P->T.t[t].k]);
     coo_compress(&D);
     /* Pi rows indexed by m: Pa is sorted by (m, j) */
     size_t *pstart = calloc(P->Sa.n + 1, sizeof(size_t));
@@ -658,7 +664,7 @@ int64_t orc_egfem_jacobian(const orc_problem *P, const double *u, int64_t cap, i
     }
     free(pstart);
     /* gamma M diag(g_c') Pi_c */
-    if (P->s.c_kind != ORC_G_NONE) {
+    if (!picard && P->s.c_kind != ORC_G_NONE) {
         size_t *cs = calloc(P->Sc.n + 1, sizeof(size_t));
         for (size_t t = 0; t < P->Pc.n; ++t) cs[P->Pc.t[t].i + 1]++;
         for (int m = 0; m < P->Sc.n; ++m) cs[m + 1] += cs[m];
@@ -684,6 +690,14 @@ int64_t orc_egfem_jacobian(const orc_problem *P, const double *u, int64_t cap, i
     free(J.t); free(D.t); free(Jd.t);
     free(w); free(wp); free(c); free(cp);
     return n;
+}
+
+int64_t orc_egfem_jacobian(const orc_problem *P, const double *u, int64_t cap, int64_t *I, int64_t *L, double *V) {
+    return egfem_matrix(P, u, 0, cap, I, L, V);
+}
+
+int64_t orc_picard_matrix(const orc_problem *P, const double *u, int64_t cap, int64_t *I, int64_t *L, double *V) {
+    return egfem_matrix(P, u, 1, cap, I, L, V);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -916,12 +930,14 @@ int orc_bicgstab(int n, int64_t nnz, const int64_t *I, const int64_t *L, const d
 /* Newton iteration (Sec. 4): u <- u - J(u)^{-1} r(u)                          */
 /* ------------------------------------------------------------------------- */
 
+/* method 0 = EGFEM Newton, 1 = SGA Newton, 2 = EGFEM Picard */
 static int64_t jac(const orc_problem *P, int method, const double *u, int64_t cap, int64_t *I, int64_t *L, double *V) {
+    if (method == 2) return orc_picard_matrix(P, u, cap, I, L, V);
     return method == 0 ? orc_egfem_jacobian(P, u, cap, I, L, V) : orc_sga_jacobian(P, u, cap, I, L, V);
 }
 
 static void res(const orc_problem *P, int method, const double *u, const double *b, const double *uD, int form, double *r) {
-    if (method == 0) orc_egfem_residual(P, u, b, uD, form, r);
+    if (method != 1) orc_egfem_residual(P, u, b, uD, form, r);
     else orc_sga_residual(P, u, b, uD, form, r);
 }
 
@@ -931,7 +947,9 @@ static double norm_free(const orc_problem *P, const double *r) {
     return sqrt(s);
 }
 
-/* method 0 = EGFEM, 1 = SGA; solver 0 = banded LU, 1 = BiCGStab(ktol).
+/* method 0 = EGFEM Newton, 1 = SGA Newton, 2 = EGFEM Picard (u <- u - A(u)^{-1} r(u) with the
+ * frozen-coefficient matrix A = T .2 a(u), i.e. A(u^n) u^{n+1} = b - gamma M c(u^n));
+ * solver 0 = banded LU, 1 = BiCGStab(ktol).
  * Stops when ||r||_free <= rtol * ||r(u0)||_free.  hist (optional, maxit+1 doubles)
  * receives the residual norms; iterates (optional, (maxit+1)*nv) the iterates.
  * Returns the number of Newton steps, or a negative code. */

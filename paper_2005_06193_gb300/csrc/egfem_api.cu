@@ -257,6 +257,7 @@ CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
     A.rx_val = h->csf.rx_val; A.rx_info = h->csf.rx_info; A.rx_m = h->csf.rx_m;
     A.dir = h->csf.dir;
     A.nl = h->nl;
+    A.nl.picard = h->opts.iteration == EGFEM_ITER_PICARD;
     A.u = u; A.d = d;
     A.status = h->status;
     return A;
@@ -715,6 +716,7 @@ void egfem_default_options(egfem_options *o) {
     o->graph_chunk = 32;
     o->fixed_eta = 0;
     o->krylov_persistent = 1;
+    o->iteration = EGFEM_ITER_NEWTON;
 }
 
 egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
@@ -1098,6 +1100,7 @@ egfem_status adjoint_solve(egfem_t *h, KWork<V> &W, const double *d_u, const dou
     if (!h->dinv) EG_TRY(dalloc(h->dinv, size_t(h->n)));
     EG_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int32_t), h->hs));
     CsfArgs A = csf_args(h, d_u, nullptr);
+    A.nl.picard = 0;   // the adjoint needs the true Jacobian
     A.jsell = h->jsell; A.dinv = h->dinv;
     launch_csf(h, A, h->hs);
     EG_CUDA(cudaGetLastError());

@@ -114,6 +114,7 @@ struct Nonlin {
     int32_t c_kind; int32_t c_pi; double c_scale;
     double gamma, kappa;
     const double *kappa_field;   // W_a field or nullptr
+    int32_t picard;              // nonzero: the Picard matrix (no g' terms) instead of the Jacobian
 };
 
 // Host-side assembly entry points (egfem_build.cpp).

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
-                if (gp != 0.0) scatter_pi(info, D * gp, J, CSF_BLOCK);
+                if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, CSF_BLOCK);
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     }
     if (f >= 0) {
         r += a * D;
-        if (gp != 0.0) scatter_pi(info, D * gp, J, CSF_BLOCK);
+        if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, CSF_BLOCK);
     }
     // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
     for (int j = 0; j < M.nrx; ++j) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
             g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
         }
         r += nl.gamma * mv * cv;
-        scatter_pi(xi, nl.gamma * mv * cp, J, CSF_BLOCK);
+        if (!nl.picard) scatter_pi(xi, nl.gamma * mv * cp, J, CSF_BLOCK);
     }
     const double diag = j1d + J[0];
     const double res = r - di;
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
-                if (gp32 != 0.0f) {
+                if (gp32 != 0.0f && !nl.picard) {
                     const float e = D32 * gp32;
                     scatter_pi32(info, e, J, CSF_BLOCK);
                     rs_add(e);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     }
     if (f >= 0) {
         r += a * D;
-        if (gp32 != 0.0f) {
+        if (gp32 != 0.0f && !nl.picard) {
             const float e = D32 * gp32;
             scatter_pi32(info, e, J, CSF_BLOCK);
             rs_add(e);
@@ -334,9 +334,11 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         if (mv == 0.0) continue;
         const int32_t m = A.rx_m[q];
         r += nl.gamma * mv * A.wc_val[m];
-        const float e = float(nl.gamma * mv * A.wc_gp[m]);
-        scatter_pi32(A.rx_info[q], e, J, CSF_BLOCK);
-        rs_add(e);
+        if (!nl.picard) {
+            const float e = float(nl.gamma * mv * A.wc_gp[m]);
+            scatter_pi32(A.rx_info[q], e, J, CSF_BLOCK);
+            rs_add(e);
+        }
     }
     const float diag = J[0] - s1;
     const double res = r - di;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
         for (int b = 0; b < NV; ++b) {
             int lc = 0;
             for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lc = c; break; }
-            double v = su * E[1 + NV + b];
+            double v = nl.picard ? 0.0 : su * E[1 + NV + b];
             if (b != a) {
                 // abar S_ab off the diagonal; on it abar S_aa = -sum_{b != a} abar S_ab
                 const double t = abar * M.S[cell * NS + tri_index(a, b, NV)];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
                 r += nl.gamma * mab * g;
                 int lc = 0;
                 for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lc = c; break; }
-                J[lc * CSF_BLOCK] += nl.gamma * mab * gp;
+                if (!nl.picard) J[lc * CSF_BLOCK] += nl.gamma * mab * gp;
             }
         }
     }

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libegfem.so")
 G_NONE, G_POW, G_EXP = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 OP_CSF, OP_MATRIX_FREE = 0, 1
+ITER_NEWTON, ITER_PICARD = 0, 1
 HIST = 64
 
 STATUS = {0: "EGFEM_OK", 1: "EGFEM_ERR_INVALID_ARG", 2: "EGFEM_ERR_MESH", 3: "EGFEM_ERR_CUDA", 4: "EGFEM_ERR_OOM",
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
     _fields_ = [("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int32),
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double), ("krylov_maxit", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("op", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
-                ("fixed_eta", ctypes.c_int32), ("krylov_persistent", ctypes.c_int32)]
+                ("fixed_eta", ctypes.c_int32), ("krylov_persistent", ctypes.c_int32), ("iteration", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -459,3 +459,47 @@ def test_adjoint_gradients_match_central_differences():
         e[m] = h
         fd = (J_of(b, kappa + e)[0] - J_of(b, kappa - e)[0]) / (2 * h)
         assert abs(fd - gk[m]) <= 1e-6 * max(1e-4, abs(gk[m])), (m, fd, gk[m])
+
+
+# ---------------------------------------------------------------------------------------
+# Picard iteration (Sec. 4, Example 4.1): the frozen-coefficient matrix A(u) = T .2 a(u)
+# ---------------------------------------------------------------------------------------
+
+def test_picard_matrix_reproduces_the_residual():
+    """A(u) u - b is the plain-form residual on free rows (r = sum T_imk a_m u_k - b), and A(u)
+    is the Newton Jacobian without its g' block: for a constant coefficient they coincide."""
+    mesh = wl.unit_square_mesh(7)
+    P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+    u = wl.random_vector(mesh.n_nodes, 11, 0.7) * (1 - mesh.dirichlet)
+    b = wl.random_vector(mesh.n_nodes, 12) * (1 - mesh.dirichlet)
+    A = P.jacobian(u, method="picard")
+    r = P.residual(u, b, form="plain")
+    free = mesh.dirichlet == 0
+    assert np.abs((A @ u - b)[free] - r[free]).max() <= 1e-13 * np.abs(r).max()
+    J = P.jacobian(u)
+    assert abs(J - A).max() > 1e-3                      # the g' block is there in Newton
+    Pc = oracle.Problem(mesh, a=None, a_deg=1, kappa=2.5)
+    assert abs(Pc.jacobian(u) - Pc.jacobian(u, method="picard")).max() <= 1e-14
+
+
+def test_picard_and_newton_reach_the_same_solution():
+    """Both iterations converge to the one discrete solution; Picard linearly (more steps,
+    residual ratios bounded away from zero), Newton quadratically."""
+    mesh = wl.unit_square_mesh(12)
+    P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+    b = P.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    un, hn, _, _ = P.newton(b, rtol=1e-12)
+    up, hp, _, _ = P.newton(b, rtol=1e-12, iteration="picard", maxit=200)
+    assert np.linalg.norm(up - un) <= 1e-10 * np.linalg.norm(un)
+    assert len(hp) > len(hn) + 2
+    ratios = hp[2:] / hp[1:-1]
+    assert ratios.max() < 0.9 and np.median(ratios) > 1e-3
+
+
+def test_picard_solves_a_linear_problem_in_one_step():
+    """With a constant coefficient the Picard matrix is the stiffness matrix: one exact step."""
+    mesh = wl.unit_square_mesh(9)
+    P = oracle.Problem(mesh, a=None, a_deg=1, kappa=1.7)
+    b = P.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    u, h, _, _ = P.newton(b, rtol=1e-13, iteration="picard")
+    assert len(h) == 2 and h[-1] <= 1e-13 * h[0]
