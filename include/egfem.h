@@ -236,7 +236,8 @@ egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const doub
  *   J(u*)^T lambda = dj/du  on free rows, lambda = 0 on Dirichlet rows;
  *   dj/dd_i = lambda_i (free rows);  dj/dkappa_m = -sum_{i,k} lambda_i T_imk u_k.
  * The transposed system is solved by FP64 Jacobi-BiCGStab to 1e-13 relative in either
- * precision of the handle.  d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa]
+ * precision of the handle; on a batch handle every instance runs its own BiCGStab (own
+ * scalars and convergence test) within one persistent launch.  d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa]
  * out (may be NULL).  Synchronises the stream. */
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda,
                            double *d_grad_kappa, egfem_stats *stats, egfem_stream stream);
