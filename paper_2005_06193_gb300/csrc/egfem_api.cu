@@ -1383,14 +1383,23 @@ namespace {
 
 template <typename V>
 egfem_status batch_tiles(egfem_t *h, int factor) {
+    // about `factor` tiles per block of the persistent solve: the target tile size is the
+    // batch's rows over (blocks x factor), and each instance is cut into equal slice-aligned
+    // tiles near that size, so blocks get nearly equal work whatever the instance sizes
     constexpr int R = VecT<V>::R;
-    const int64_t rows = int64_t(KRY_BLOCK) * R * factor;
+    int nbk = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, (const void *)pk_solve<V>, PK_BLOCK, 0) != cudaSuccess || nbk < 1)
+        nbk = 1;
+    const int64_t blocks = int64_t(std::min(nbk, 8)) * h->sms;
+    const int64_t target = std::max<int64_t>(SLICE, (h->inst_off[h->nb] + blocks * factor - 1) / (blocks * factor));
     std::vector<BTile> T;
     std::vector<int64_t> sys_t0(size_t(h->nb));
     for (int32_t b = 0; b < h->nb; ++b) {
         const int64_t t0 = int64_t(T.size());
         sys_t0[size_t(b)] = t0;
         const int64_t lo = h->inst_off[b], hi = h->inst_off[b + 1];
+        const int64_t nt = std::max<int64_t>(1, (hi - lo + target / 2) / target);
+        const int64_t rows = ((hi - lo + nt - 1) / nt + SLICE - 1) / SLICE * SLICE;
         for (int64_t r = lo; r < hi; r += rows) T.push_back(BTile{r, std::min(hi, r + rows), t0, b, 0});
         for (size_t q = size_t(t0); q < T.size(); ++q) T[q].ntiles_inst = int32_t(T.size() - size_t(t0));
     }
