@@ -42,7 +42,7 @@ _LIBPATH = os.path.join(_HERE, "_build", "liborc.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-G_NONE, G_POW, G_EXP = 0, 1, 2
+G_NONE, G_POW, G_EXP, G_GRADPOW = 0, 1, 2, 3
 FORM_PLAIN, FORM_DIFF = 0, 1
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
@@ -65,7 +65,8 @@ class _Spec(ctypes.Structure):
                 ("X", _c_dp), ("cells", _c_ip), ("dir", ctypes.POINTER(ctypes.c_ubyte)),
                 ("a_kind", ctypes.c_int), ("a_p", ctypes.c_double), ("a_scale", ctypes.c_double), ("a_deg", ctypes.c_int),
                 ("c_kind", ctypes.c_int), ("c_p", ctypes.c_double), ("c_scale", ctypes.c_double), ("c_deg", ctypes.c_int),
-                ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("qpts", ctypes.c_int)]
+                ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("qpts", ctypes.c_int),
+                ("a_shift", ctypes.c_double)]
 
 
 def lib():
@@ -123,7 +124,7 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-_KIND = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP}
+_KIND = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP, "gradpow": G_GRADPOW}
 
 
 class Problem:
@@ -150,6 +151,7 @@ class Problem:
         s.dir = self._dir.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
         s.a_kind = _KIND[a[0] if a else None]
         s.a_p = float(a[1]) if a and len(a) > 1 else 1.0
+        s.a_shift = float(a[2]) if a and a[0] == "gradpow" and len(a) > 2 else 0.0
         s.a_scale, s.a_deg = float(a_scale), int(a_deg)
         s.c_kind = _KIND[c[0] if c else None]
         s.c_p = float(c[1]) if c and len(c) > 1 else 1.0

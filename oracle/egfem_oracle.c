@@ -53,7 +53,10 @@
 #define ORC_MAXNB 20   /* P3 in 3D has 20 local basis functions */
 #define ORC_MAXQ 512
 
-enum { ORC_G_NONE = 0, ORC_G_POW = 1, ORC_G_EXP = 2 };
+enum { ORC_G_NONE = 0, ORC_G_POW = 1, ORC_G_EXP = 2, ORC_G_GRADPOW = 3 };
+/* ORC_G_GRADPOW: a gradient nonlinearity for the coefficient (Sec. 5, p-Laplace and minimal
+ * surface examples): w = a_scale * (a_shift + ||grad u||^2)^a_p, with W_a = P0 (the gradient
+ * of a P1 function is constant on each cell, so the W node of a cell carries it exactly). */
 enum { ORC_FORM_PLAIN = 0, ORC_FORM_DIFF = 1 };
 
 /* ------------------------------------------------------------------------- */
@@ -400,6 +403,7 @@ typedef struct {
     int c_kind; double c_p, c_scale; int c_deg;   /* c = c_scale * g(Pi_c u), reaction gamma * M c          */
     double gamma, kappa;
     int qpts;                                      /* Gauss points per direction */
+    double a_shift;                                /* ORC_G_GRADPOW: the shift of ||grad u||^2 */
 } orc_spec;
 
 typedef struct {
@@ -416,6 +420,21 @@ typedef struct {
     double *kappa_field;  /* optional kappa per W_a node (NULL: constant)  */
     int *cell_mask;       /* cells included in the tensor assembly         */
 } orc_problem;
+
+/* the coefficient nonlinearity as a function of its argument s (for ORC_G_GRADPOW,
+ * s = ||grad u||^2) and its derivative in s */
+static double ga_val(const orc_spec *S, double s) {
+    if (S->a_kind == ORC_G_GRADPOW) return S->a_scale * pow(S->a_shift + s, S->a_p);
+    if (S->a_kind == ORC_G_POW) return S->a_scale * pow(s, S->a_p);
+    if (S->a_kind == ORC_G_EXP) return S->a_scale * exp(s);
+    return 0.0;
+}
+static double ga_der(const orc_spec *S, double s) {
+    if (S->a_kind == ORC_G_GRADPOW) return (S->a_p == 0.0) ? 0.0 : S->a_scale * S->a_p * pow(S->a_shift + s, S->a_p - 1.0);
+    if (S->a_kind == ORC_G_POW) return (S->a_p == 0.0) ? 0.0 : S->a_scale * S->a_p * pow(s, S->a_p - 1.0);
+    if (S->a_kind == ORC_G_EXP) return S->a_scale * exp(s);
+    return 0.0;
+}
 
 static double g_val(int kind, double p, double scale, double s) {
     if (kind == ORC_G_POW) return scale * pow(s, p);
@@ -588,13 +607,36 @@ static void interp_apply(const orc_coo *Pi, int n, const double *u, double *out)
     for (size_t t = 0; t < Pi->n; ++t) out[Pi->t[t].i] += Pi->t[t].v * u[Pi->t[t].j];
 }
 
+/* ||grad u_h||^2 on cell c (constant for P1) and the P1 basis gradients g[a] */
+static double cell_grad2(const orc_problem *P, int c, const double *u, double g[4][3], double gu[3]) {
+    int dim = P->s.dim, nv = dim + 1;
+    const int *cv = P->s.cells + (size_t)c * nv;
+    orc_geom G; cell_geom(dim, P->s.X, cv, &G);
+    for (int a = 0; a < nv; ++a) phys_grad(dim, &G, P->gref1 + a * dim, g[a]);
+    double s = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        gu[d] = 0.0;
+        for (int a = 0; a < nv; ++a) gu[d] += u[cv[a]] * g[a][d];
+        s += gu[d] * gu[d];
+    }
+    return s;
+}
+
 void orc_pointwise(const orc_problem *P, const double *u, double *w, double *wprime, double *c, double *cprime) {
     double *pa = malloc(sizeof(double) * P->Sa.n), *pc = malloc(sizeof(double) * P->Sc.n);
-    interp_apply(&P->Pa, P->Sa.n, u, pa);
+    if (P->s.a_kind == ORC_G_GRADPOW) {
+        /* W_a = P0: the node of cell c carries ||grad u_h||^2 on c */
+        for (int c = 0; c < P->s.nc; ++c) {
+            double g[4][3], gu[3];
+            pa[P->Sa.cell2dof[c]] = cell_grad2(P, c, u, g, gu);
+        }
+    } else {
+        interp_apply(&P->Pa, P->Sa.n, u, pa);
+    }
     interp_apply(&P->Pc, P->Sc.n, u, pc);
     for (int m = 0; m < P->Sa.n; ++m) {
-        if (w) w[m] = g_val(P->s.a_kind, P->s.a_p, P->s.a_scale, pa[m]);
-        if (wprime) wprime[m] = g_der(P->s.a_kind, P->s.a_p, P->s.a_scale, pa[m]);
+        if (w) w[m] = ga_val(&P->s, pa[m]);
+        if (wprime) wprime[m] = ga_der(&P->s, pa[m]);
     }
     for (int m = 0; m < P->Sc.n; ++m) {
         if (c) c[m] = g_val(P->s.c_kind, P->s.c_p, P->s.c_scale, pc[m]);
@@ -653,16 +695,35 @@ static int64_t egfem_matrix(const orc_problem *P, const double *u, int picard, i
     if (!picard)
         for (size_t t = 0; t < P->T.n; ++t) coo_push(&D, P->T.t[t].i, P->T.t[t].j, 0, P->T.t[t].v * u[P->T.t[t].k]);
     coo_compress(&D);
-    /* Pi rows indexed by m: Pa is sorted by (m, j) */
+    /* d(argument of g at node m)/du_l: the interpolation Pi_ml, or for a gradient nonlinearity
+     * (W_a = P0) d||grad u_K||^2/du_l = 2 grad u_K . grad phi_l on the cell K of node m */
+    orc_coo Pg = {0};
+    const orc_coo *Pm = &P->Pa;
+    if (P->s.a_kind == ORC_G_GRADPOW) {
+        int nvc = P->s.dim + 1;
+        for (int c = 0; c < P->s.nc; ++c) {
+            double g[4][3], gu[3];
+            cell_grad2(P, c, u, g, gu);
+            int m = P->Sa.cell2dof[c];
+            for (int l = 0; l < nvc; ++l) {
+                double t = 0.0;
+                for (int d = 0; d < P->s.dim; ++d) t += gu[d] * g[l][d];
+                coo_push(&Pg, m, P->s.cells[(size_t)c * nvc + l], 0, 2.0 * t);
+            }
+        }
+        coo_compress(&Pg);
+        Pm = &Pg;
+    }
     size_t *pstart = calloc(P->Sa.n + 1, sizeof(size_t));
-    for (size_t t = 0; t < P->Pa.n; ++t) pstart[P->Pa.t[t].i + 1]++;
+    for (size_t t = 0; t < Pm->n; ++t) pstart[Pm->t[t].i + 1]++;
     for (int m = 0; m < P->Sa.n; ++m) pstart[m + 1] += pstart[m];
     for (size_t t = 0; t < D.n; ++t) {
         int64_t i = D.t[t].i, m = D.t[t].j;
         double e = D.t[t].v * wp[m];
-        for (size_t q = pstart[m]; q < pstart[m + 1]; ++q) coo_push(&J, i, P->Pa.t[q].j, 0, e * P->Pa.t[q].v);
+        for (size_t q = pstart[m]; q < pstart[m + 1]; ++q) coo_push(&J, i, Pm->t[q].j, 0, e * Pm->t[q].v);
     }
     free(pstart);
+    free(Pg.t);
     /* gamma M diag(g_c') Pi_c */
     if (!picard && P->s.c_kind != ORC_G_NONE) {
         size_t *cs = calloc(P->Sc.n + 1, sizeof(size_t));
@@ -727,7 +788,13 @@ void orc_sga_residual(const orc_problem *P, const double *u, const double *b, co
             const double *phi = P->phi_q + q * ORC_MAXNB, *eta = P->eta_a_q + q * ORC_MAXNB;
             double uh = 0.0;
             for (int a = 0; a < nv; ++a) uh += u[cv[a]] * phi[a];
-            double coef = kappa_at(P, c, eta) + g_val(P->s.a_kind, P->s.a_p, P->s.a_scale, uh);
+            /* the coefficient's argument at the quadrature point: u_h, or ||grad u_h||^2 */
+            double arg = uh;
+            if (P->s.a_kind == ORC_G_GRADPOW) {
+                arg = 0.0;
+                for (int d = 0; d < dim; ++d) { double gd = 0.0; for (int a = 0; a < nv; ++a) gd += u[cv[a]] * g[a][d]; arg += gd * gd; }
+            }
+            double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
             double reac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_val(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;
@@ -762,8 +829,14 @@ int64_t orc_sga_jacobian(const orc_problem *P, const double *u, int64_t cap, int
             const double *phi = P->phi_q + q * ORC_MAXNB, *eta = P->eta_a_q + q * ORC_MAXNB;
             double uh = 0.0;
             for (int a = 0; a < nv; ++a) uh += u[cv[a]] * phi[a];
-            double coef = kappa_at(P, c, eta) + g_val(P->s.a_kind, P->s.a_p, P->s.a_scale, uh);
-            double dcoef = g_der(P->s.a_kind, P->s.a_p, P->s.a_scale, uh);
+            const int gradc = P->s.a_kind == ORC_G_GRADPOW;
+            double guh[3] = {0.0, 0.0, 0.0}, arg = uh;
+            if (gradc) {
+                arg = 0.0;
+                for (int d = 0; d < dim; ++d) { for (int a = 0; a < nv; ++a) guh[d] += u[cv[a]] * g[a][d]; arg += guh[d] * guh[d]; }
+            }
+            double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
+            double dcoef = ga_der(&P->s, arg);
             double dreac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_der(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;
@@ -775,7 +848,10 @@ int64_t orc_sga_jacobian(const orc_problem *P, const double *u, int64_t cap, int
                 for (int l = 0; l < nv; ++l) {
                     double gg = 0.0;
                     for (int d = 0; d < dim; ++d) gg += g[l][d] * g[a][d];
-                    Jloc[a * nv + l] += wq * (coef * gg + dcoef * phi[l] * gu + dreac * phi[l] * phi[a]);
+                    /* d coef / d u_l: g'(u_h) phi_l, or g'(s) 2 grad u_h . grad phi_l */
+                    double dl = phi[l];
+                    if (gradc) { dl = 0.0; for (int d = 0; d < dim; ++d) dl += 2.0 * guh[d] * g[l][d]; }
+                    Jloc[a * nv + l] += wq * (coef * gg + dcoef * dl * gu + dreac * phi[l] * phi[a]);
                 }
             }
         }

@@ -503,3 +503,62 @@ def test_picard_solves_a_linear_problem_in_one_step():
     b = P.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
     u, h, _, _ = P.newton(b, rtol=1e-13, iteration="picard")
     assert len(h) == 2 and h[-1] <= 1e-13 * h[0]
+
+
+# ---------------------------------------------------------------------------------------
+# Gradient nonlinearities with W = P0 (Sec. 5, p-Laplace and minimal surface examples)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q,shift", [(-0.5, 1.0), (0.25, 0.3), (-0.25, 0.05)])
+def test_gradient_nonlinearity_egfem_p0_equals_sga(q, shift):
+    """For P1 u the gradient is constant per cell, so EGFEM with a P0 W space (the tensor path:
+    T_iKk, nodal g(||grad u_K||^2)) equals the standard Galerkin approach (the quadrature path)
+    exactly -- the equivalence the paper reports for these examples."""
+    mesh = wl.unit_square_mesh(7)
+    P = oracle.Problem(mesh, a=("gradpow", q, shift), a_deg=0, kappa=0.4)
+    u = wl.random_vector(mesh.n_nodes, 31, 0.8)
+    b = wl.random_vector(mesh.n_nodes, 32)
+    re, rs = P.residual(u, b, form="plain"), P.residual(u, b, method="sga", form="plain")
+    assert np.abs(re - rs).max() <= 1e-13 * np.abs(re).max()
+    Je, Js = P.jacobian(u), P.jacobian(u, method="sga")
+    assert abs(Je - Js).max() <= 1e-13 * abs(Je).max()
+
+
+def test_gradient_nonlinearity_jacobian_matches_finite_differences():
+    mesh = wl.unit_square_mesh(6)
+    P = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
+    u = wl.random_vector(mesh.n_nodes, 41, 0.9)
+    b = wl.random_vector(mesh.n_nodes, 42)
+    J = P.jacobian(u).toarray()
+    free = np.where(mesh.dirichlet == 0)[0]
+    h = 1e-6
+    for l in free[::3]:
+        e = np.zeros(mesh.n_nodes)
+        e[l] = h
+        fd = (P.residual(u + e, b, form="plain") - P.residual(u - e, b, form="plain")) / (2 * h)
+        assert np.abs(fd[free] - J[free, l]).max() <= 1e-8 * max(1.0, np.abs(J).max())
+
+
+def test_constant_gradient_coefficient_is_the_stiffness_matrix():
+    """With exponent 0 the coefficient is the constant scale * 1: the Jacobian is that multiple
+    of the Poisson stiffness matrix (no derivative term)."""
+    mesh = wl.unit_square_mesh(5)
+    u = wl.random_vector(mesh.n_nodes, 51, 0.5)
+    A = oracle.Problem(mesh, a=("gradpow", 0.0, 2.0), a_deg=0, a_scale=1.5, kappa=0.0).jacobian(u)
+    S = oracle.Problem(mesh, a=None, a_deg=1, kappa=1.5).jacobian(u)
+    assert abs(A - S).max() <= 1e-13
+
+
+def test_minimal_surface_manufactured_solution_converges_at_second_order():
+    """Minimal surface on the unit square with u_D = x y (x + y) and the manufactured source:
+    the nodal RMS error falls by about 4 per mesh halving (P1, O(h^2))."""
+    errs = []
+    for n in (8, 16, 32):
+        mesh = wl.unit_square_mesh(n)
+        P = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
+        ue = wl.minsurf_exact(mesh.coords[:, 0], mesh.coords[:, 1])
+        b = P.load_vector(wl.minsurf_source) * (1 - mesh.dirichlet)
+        u, _, _, _ = P.newton(b, u0=ue, uD=ue * mesh.dirichlet, rtol=1e-8)
+        errs.append(np.sqrt(np.mean((u - ue) ** 2)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > 1.8, (errs, rates)

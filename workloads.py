@@ -18,8 +18,8 @@ structured generators stand in for them):
   Every cube is split into the 6 Kuhn (Freudenthal) tetrahedra that share the
   (0,0,0)->(1,1,1) diagonal, one per permutation of the three axes.
 
-The Dirichlet boundary is the whole boundary (all configurations use homogeneous
-Dirichlet data).
+The Dirichlet boundary is the whole boundary (homogeneous data, except the minimal-surface
+example, whose boundary values are those of its exact solution).
 """
 from __future__ import annotations
 
@@ -117,6 +117,23 @@ def mms_source_cubic(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     u = mms_exact(x, y)
     gx, gy = mms_exact_grad(x, y)
     return 2.0 * np.pi ** 2 * u * (1.0 + u ** 3) - 3.0 * u * u * (gx * gx + gy * gy)
+
+
+def minsurf_exact(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """The minimal-surface example's boundary data and exact solution, u = x y (x + y)
+    (Sec. 5, minimal surface equation on the unit square)."""
+    return x * y * (x + y)
+
+
+def minsurf_source(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """d = -div(grad u / sqrt(1 + |grad u|^2)) for u = minsurf_exact (manufactured source):
+    with q = grad u, H its Hessian and Q = 1 + |q|^2, div(q / sqrt(Q)) = lap(u) / sqrt(Q)
+    - q^T H q / Q^(3/2)."""
+    ux, uy = 2.0 * x * y + y * y, x * x + 2.0 * x * y
+    uxx, uxy, uyy = 2.0 * y, 2.0 * x + 2.0 * y, 2.0 * x
+    Q = 1.0 + ux * ux + uy * uy
+    qhq = ux * ux * uxx + 2.0 * ux * uy * uxy + uy * uy * uyy
+    return -((uxx + uyy) / np.sqrt(Q) - qhq / Q ** 1.5)
 
 
 def smooth_source_3d(x: np.ndarray, y: np.ndarray, z: np.ndarray) -> np.ndarray:
