@@ -63,7 +63,12 @@ typedef enum {
 typedef enum {
     EGFEM_G_NONE = 0,  /* no nonlinear term                        */
     EGFEM_G_POW = 1,   /* g(s) = s^p  (p a positive integer <= 8)  */
-    EGFEM_G_EXP = 2    /* g(s) = e^s                               */
+    EGFEM_G_EXP = 2,   /* g(s) = e^s                               */
+    EGFEM_G_GRADPOW = 3 /* coefficient only: g = (a_shift + ||grad u||^2)^a_p (any real
+                           a_p), the gradient nonlinearities of the p-Laplace and minimal-
+                           surface examples (Sec. 5); needs a_degree = 0 (W_a = P0, one node
+                           per cell, which carries the cell's constant gradient exactly) and
+                           the element-local operator (EGFEM_OP_MATRIX_FREE)              */
 } egfem_g_kind;
 
 typedef enum {
@@ -99,15 +104,16 @@ typedef struct {
 /* Problem: -div((kappa + a_scale g_a(Pi_a u)) grad u) + gamma c_scale g_c(Pi_c u) = d.   */
 typedef struct {
     int32_t a_kind;      /* egfem_g_kind of the coefficient nonlinearity            */
-    double a_p;          /* exponent for EGFEM_G_POW                                 */
+    double a_p;          /* exponent for EGFEM_G_POW (integer) and EGFEM_G_GRADPOW (real) */
     double a_scale;
-    int32_t a_degree;    /* Lagrange degree of W_a: 1 (GFEM), 2 or 3                 */
+    int32_t a_degree;    /* Lagrange degree of W_a: 1 (GFEM), 2 or 3; 0 (P0) for GRADPOW */
     int32_t c_kind;      /* egfem_g_kind of the reaction nonlinearity               */
     double c_p;
     double c_scale;
     int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM), 2 or 3                 */
     double gamma;        /* reaction coefficient                                     */
     double kappa;        /* constant part of the coefficient                         */
+    double a_shift;      /* EGFEM_G_GRADPOW: the shift added to ||grad u||^2 (else unused) */
 } egfem_problem;
 
 typedef struct {

@@ -477,19 +477,38 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     egfem_status st = validate_mesh(*mesh, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     auto check_g = [&](int32_t kind, double p, int32_t deg, const char *what) -> egfem_status {
-        if (kind < EGFEM_G_NONE || kind > EGFEM_G_EXP) { g_last_error = std::string(what) + ": unknown kind"; return EGFEM_ERR_INVALID_ARG; }
+        if (kind < EGFEM_G_NONE || kind > EGFEM_G_GRADPOW) { g_last_error = std::string(what) + ": unknown kind"; return EGFEM_ERR_INVALID_ARG; }
         if (kind == EGFEM_G_POW && (p < 1 || p > 8 || p != std::floor(p))) { g_last_error = std::string(what) + ": exponent must be an integer in 1..8"; return EGFEM_ERR_INVALID_ARG; }
+        if (kind == EGFEM_G_GRADPOW) return EGFEM_OK;
         if (kind != EGFEM_G_NONE && (deg < 1 || deg > 3)) { g_last_error = std::string(what) + ": degree must be 1, 2 or 3"; return EGFEM_ERR_INVALID_ARG; }
         return EGFEM_OK;
     };
     EG_TRY(check_g(prob->a_kind, prob->a_p, prob->a_degree, "a"));
     EG_TRY(check_g(prob->c_kind, prob->c_p, prob->c_degree, "c"));
     if (prob->c_kind != EGFEM_G_NONE && prob->c_degree != 1) { g_last_error = "reaction space W_c must be P1"; return EGFEM_ERR_UNSUPPORTED; }
+    if (prob->c_kind == EGFEM_G_GRADPOW) { g_last_error = "c: the gradient nonlinearity is a coefficient"; return EGFEM_ERR_INVALID_ARG; }
+    const bool gradc = prob->a_kind == EGFEM_G_GRADPOW;
+    if (gradc) {
+        // (shift + s)^q on s = ||grad u||^2 >= 0: finite with its derivative at s = 0 when
+        // shift > 0, or when shift = 0 and q is 0 or at least 1
+        const double q = prob->a_p, sh = prob->a_shift;
+        if (prob->a_degree != 0) { g_last_error = "a: the gradient coefficient lives in W_a = P0 (a_degree 0)"; return EGFEM_ERR_INVALID_ARG; }
+        if (!std::isfinite(q) || !std::isfinite(sh) || sh < 0.0 || (sh == 0.0 && q != 0.0 && q < 1.0)) {
+            g_last_error = "a: gradient exponent/shift must give a finite (shift + s)^q and derivative at s = 0";
+            return EGFEM_ERR_INVALID_ARG;
+        }
+    }
     std::unique_ptr<egfem_t> h(new egfem_t());
     egfem_default_options(&h->opts);
     if (opts) h->opts = *opts;
     if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
     if (h->opts.op != EGFEM_OP_CSF && h->opts.op != EGFEM_OP_MATRIX_FREE) { g_last_error = "unknown operator variant"; return EGFEM_ERR_INVALID_ARG; }
+    if (gradc && h->opts.op != EGFEM_OP_MATRIX_FREE) {
+        // the P0 tensor T_iKk is the cell stiffness S^K itself: the element-local operator
+        // evaluates it without a stored tensor
+        g_last_error = "the gradient coefficient needs the element-local operator (EGFEM_OP_MATRIX_FREE)";
+        return EGFEM_ERR_UNSUPPORTED;
+    }
     h->prob = *prob;
     h->dim = mesh->dim; h->n = mesh->n_nodes; h->ncells = mesh->n_cells;
     EG_CUDA(cudaGetDevice(&h->device));
@@ -501,14 +520,20 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     HostWSpace Wa, Wc;
     std::vector<int32_t> c2wa, c2wc;
     int nla = 0, nlc = 0;
-    st = build_wspace(*mesh, prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1, Wa, c2wa, nla, err);
+    // With the gradient coefficient the stored CSF is that of the constant coefficient: it
+    // fixes the Jacobian's pattern and the Krylov layout (both the P1 graph), while the
+    // element-local kernels evaluate the P0 coefficient.
+    egfem_problem layout_prob = *prob;
+    if (gradc) { layout_prob.a_kind = EGFEM_G_NONE; layout_prob.a_degree = 1; }
+    st = build_wspace(*mesh, layout_prob.a_kind != EGFEM_G_NONE ? layout_prob.a_degree : 1, Wa, c2wa, nla, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     st = build_wspace(*mesh, prob->c_kind != EGFEM_G_NONE ? prob->c_degree : 1, Wc, c2wc, nlc, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     h->nwa = Wa.n; h->nwc = Wc.n;
     h->wa_coords = Wa.coords; h->wc_coords = Wc.coords;
+    if (gradc) { h->nwa = mesh->n_cells; h->wa_coords = cell_centroids(*mesh); }   // W_a = P0
     HostCSF H;
-    st = build_csf(*mesh, *prob, Wa, c2wa, nla, Wc, c2wc, nlc, H, err);
+    st = build_csf(*mesh, layout_prob, Wa, c2wa, nla, Wc, c2wc, nlc, H, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     h->maxc_tpl = pick_maxc(H.max_cols);
     // transpose map: SELL position of (k, i) for every (i, local column c -> k)
@@ -547,7 +572,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     EG_TRY(upload(D.dir, H.dir)); EG_TRY(upload(D.rowptr, H.rowptr)); EG_TRY(upload(D.cols, H.cols));
     EG_TRY(upload(h->tmap, tmap));
     EG_TRY(upload(h->wa_kind, Wa.kind)); EG_TRY(upload(h->wa_sup, Wa.sup));
-    if (prob->a_kind != EGFEM_G_NONE) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
+    if (prob->a_kind != EGFEM_G_NONE && !gradc) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
     if (prob->c_kind != EGFEM_G_NONE) {
         EG_TRY(upload(h->wc_kind, Wc.kind)); EG_TRY(upload(h->wc_sup, Wc.sup));
         EG_TRY(dalloc(h->wc_val, size_t(h->nwc))); EG_TRY(dalloc(h->wc_gp, size_t(h->nwc)));
@@ -556,16 +581,9 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     {
         const int nv = mesh->dim + 1;
         std::vector<int32_t> cv(mesh->cells, mesh->cells + mesh->n_cells * nv);
-        std::vector<double> vol(mesh->n_cells);
-        for (int64_t c = 0; c < mesh->n_cells; ++c) {
-            double B[9];
-            for (int k = 0; k < mesh->dim; ++k)
-                for (int r = 0; r < mesh->dim; ++r)
-                    B[r * mesh->dim + k] = mesh->coords[int64_t(cv[c * nv + k + 1]) * mesh->dim + r] - mesh->coords[int64_t(cv[c * nv]) * mesh->dim + r];
-            const double det = mesh->dim == 2 ? B[0] * B[3] - B[1] * B[2]
-                : B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) + B[2] * (B[3] * B[7] - B[4] * B[6]);
-            vol[c] = std::fabs(det) / (mesh->dim == 2 ? 2.0 : 6.0);
-        }
+        std::vector<double> vol, S;
+        const bool mf = h->opts.op == EGFEM_OP_MATRIX_FREE;
+        cell_stiffness(*mesh, vol, mf ? &S : nullptr);
         std::vector<int64_t> ptr(mesh->n_nodes + 1, 0);
         for (int64_t c = 0; c < mesh->n_cells; ++c) for (int a = 0; a < nv; ++a) ptr[cv[c * nv + a] + 1]++;
         for (int64_t v = 0; v < mesh->n_nodes; ++v) ptr[v + 1] += ptr[v];
@@ -574,39 +592,16 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
         for (int64_t c = 0; c < mesh->n_cells; ++c) for (int a = 0; a < nv; ++a) lst[fill[cv[c * nv + a]]++] = int32_t(c);
         EG_TRY(upload(h->cell_verts, cv)); EG_TRY(upload(h->cell_vol, vol));
         EG_TRY(upload(h->v2c_ptr, ptr)); EG_TRY(upload(h->v2c, lst));
-        if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
+        if (mf) {
             // per cell: S^K = |K| grad lambda_a . grad lambda_b (packed upper triangle)
-            const int d = mesh->dim, ns = nv * (nv + 1) / 2;
-            std::vector<double> S(size_t(mesh->n_cells) * ns);
-            for (int64_t c = 0; c < mesh->n_cells; ++c) {
-                double B[9], Bi[9], g[4][3];
-                for (int k = 0; k < d; ++k)
-                    for (int r = 0; r < d; ++r) B[r * d + k] = mesh->coords[int64_t(cv[c * nv + k + 1]) * d + r] - mesh->coords[int64_t(cv[c * nv]) * d + r];
-                if (d == 2) {
-                    const double det = B[0] * B[3] - B[1] * B[2];
-                    Bi[0] = B[3] / det; Bi[1] = -B[1] / det; Bi[2] = -B[2] / det; Bi[3] = B[0] / det;
-                } else {
-                    const double det = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) + B[2] * (B[3] * B[7] - B[4] * B[6]);
-                    Bi[0] = (B[4] * B[8] - B[5] * B[7]) / det; Bi[1] = (B[2] * B[7] - B[1] * B[8]) / det; Bi[2] = (B[1] * B[5] - B[2] * B[4]) / det;
-                    Bi[3] = (B[5] * B[6] - B[3] * B[8]) / det; Bi[4] = (B[0] * B[8] - B[2] * B[6]) / det; Bi[5] = (B[2] * B[3] - B[0] * B[5]) / det;
-                    Bi[6] = (B[3] * B[7] - B[4] * B[6]) / det; Bi[7] = (B[1] * B[6] - B[0] * B[7]) / det; Bi[8] = (B[0] * B[4] - B[1] * B[3]) / det;
-                }
-                for (int j = 1; j <= d; ++j) for (int r = 0; r < d; ++r) g[j][r] = Bi[(j - 1) * d + r];
-                for (int r = 0; r < d; ++r) { double t = 0; for (int j = 1; j <= d; ++j) t += g[j][r]; g[0][r] = -t; }
-                int q = 0;
-                for (int a = 0; a < nv; ++a)
-                    for (int b = a; b < nv; ++b) {
-                        double t = 0; for (int r = 0; r < d; ++r) t += g[a][r] * g[b][r];
-                        S[size_t(c) * ns + q++] = vol[c] * t;
-                    }
-            }
+            const int d = mesh->dim;
             EG_TRY(upload(h->cell_S, S));
             EG_TRY(dalloc(h->cell_E, size_t(mesh->n_cells) * size_t(2 * d + 3)));
             // local W nodes of the reference cell in the W numbering's local order
             MfLocal &L = h->mf_loc;
             L = MfLocal{};
             const int p = prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1;
-            if (prob->a_kind != EGFEM_G_NONE) {
+            if (prob->a_kind != EGFEM_G_NONE && !gradc) {
                 auto add = [&](const double *w, int kind) {
                     for (int a = 0; a < 4; ++a) L.w[L.nw][a] = a < nv ? w[a] : 0.0;
                     L.iota[L.nw] = basis_integral(d, p, kind);
@@ -632,7 +627,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
             }
         }
     }
-    h->nl.a_kind = prob->a_kind; h->nl.a_pi = int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
+    h->nl.a_kind = prob->a_kind; h->nl.a_pi = gradc ? 0 : int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
+    h->nl.a_preal = prob->a_p; h->nl.a_shift = gradc ? prob->a_shift : 0.0;
     h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
     h->nl.gamma = prob->gamma; h->nl.kappa = prob->kappa; h->nl.kappa_field = nullptr;
     // workspace
@@ -810,6 +806,10 @@ egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream
         g_last_error = "a kappa field needs the CSF operator";
         return EGFEM_ERR_UNSUPPORTED;
     }
+    if (d_kappa && h->nl.a_kind == EGFEM_G_GRADPOW) {
+        g_last_error = "a kappa field is not available with the gradient coefficient";
+        return EGFEM_ERR_UNSUPPORTED;
+    }
     EG_CUDA(cudaSetDevice(h->device));
     if (!d_kappa) { h->nl.kappa_field = nullptr; return EGFEM_OK; }
     if (!h->kappa_field) EG_TRY(dalloc(h->kappa_field, size_t(h->nwa)));
@@ -820,6 +820,10 @@ egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream
 
 egfem_status egfem_pointwise(egfem_handle h, const double *d_u, double *d_w, double *d_wprime, egfem_stream stream) {
     if (!h || !d_u) return EGFEM_ERR_INVALID_ARG;
+    if (h->nl.a_kind == EGFEM_G_GRADPOW) {
+        g_last_error = "the gradient coefficient is evaluated per cell inside the element-local operator";
+        return EGFEM_ERR_UNSUPPORTED;
+    }
     EG_CUDA(cudaSetDevice(h->device));
     const unsigned grid = unsigned((h->nwa + 255) / 256);
     pointwise_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(h->nwa, h->wa_kind, h->wa_sup, d_u, h->nl, d_w, d_wprime);
@@ -1298,6 +1302,10 @@ extern "C" {
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda, double *d_grad_kappa,
                            egfem_stats *stats, egfem_stream stream) {
     if (!h || !d_u || !d_dJdu || !d_lambda) return EGFEM_ERR_INVALID_ARG;
+    if (d_grad_kappa && h->nl.a_kind == EGFEM_G_GRADPOW) {
+        g_last_error = "dJ/dkappa is not available with the gradient coefficient";
+        return EGFEM_ERR_UNSUPPORTED;
+    }
     EG_CUDA(cudaSetDevice(h->device));
     egfem_stats S;
     std::memset(&S, 0, sizeof(S));

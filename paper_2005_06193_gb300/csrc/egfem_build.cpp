@@ -87,6 +87,37 @@ static void cell_grads(const egfem_mesh &m, int64_t c, double &vol, double g[4][
     for (int r = 0; r < d; ++r) { double s = 0; for (int j = 1; j <= d; ++j) s += g[j][r]; g[0][r] = -s; }
 }
 
+// Per cell |K| and, when S is given, S^K_ab = |K| grad lambda_a . grad lambda_b packed as
+// the upper triangle row by row ((d+1)(d+2)/2 values): the P1 stiffness of the cell, which
+// is also the trilinear form of a P0 W space, T_iKk = int_K grad phi_k . grad phi_i.
+void cell_stiffness(const egfem_mesh &m, std::vector<double> &vol, std::vector<double> *S) {
+    const int d = m.dim, nv = d + 1, ns = nv * (nv + 1) / 2;
+    vol.assign(size_t(m.n_cells), 0.0);
+    if (S) S->assign(size_t(m.n_cells) * ns, 0.0);
+    for (int64_t c = 0; c < m.n_cells; ++c) {
+        double g[4][3];
+        cell_grads(m, c, vol[c], g);
+        if (!S) continue;
+        int q = 0;
+        for (int a = 0; a < nv; ++a)
+            for (int b = a; b < nv; ++b) {
+                double t = 0;
+                for (int r = 0; r < d; ++r) t += g[a][r] * g[b][r];
+                (*S)[size_t(c) * ns + q++] = vol[c] * t;
+            }
+    }
+}
+
+// The nodes of a P0 space: one per cell, at its centroid ([n_cells * dim]).
+std::vector<double> cell_centroids(const egfem_mesh &m) {
+    const int d = m.dim, nv = d + 1;
+    std::vector<double> x(size_t(m.n_cells) * d, 0.0);
+    for (int64_t c = 0; c < m.n_cells; ++c)
+        for (int a = 0; a < nv; ++a)
+            for (int r = 0; r < d; ++r) x[size_t(c) * d + r] += m.coords[int64_t(m.cells[c * nv + a]) * d + r] / double(nv);
+    return x;
+}
+
 // ---------------------------------------------------------------------------------
 // W space: vertices keep their P1 index; edge nodes follow (degree-1 per edge, ordered
 // from the lower to the higher global vertex); for degree 3, face centroids last.
@@ -507,6 +538,35 @@ extern "C" egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem
     std::string err;
     egfem_status st = validate_mesh(*mesh, err);
     if (st != EGFEM_OK) return st;
+    if (prob->a_kind == EGFEM_G_GRADPOW) {
+        // W_a = P0: the form is T_iKk = S^K_ik, which the element-local operator reads per
+        // cell (no CSF is stored for it); free rows i only, as for the stored tensor
+        if (prob->a_degree != 0) return EGFEM_ERR_INVALID_ARG;
+        const int nv = mesh->dim + 1, ns = nv * (nv + 1) / 2;
+        std::vector<double> vol, S;
+        cell_stiffness(*mesh, vol, &S);
+        int64_t cnt = 0;
+        for (int64_t c = 0; c < mesh->n_cells; ++c)
+            for (int a = 0; a < nv; ++a) {
+                const int32_t i = mesh->cells[c * nv + a];
+                if (mesh->dirichlet && mesh->dirichlet[i]) continue;
+                for (int b = 0; b < nv; ++b) {
+                    const int lo = std::min(a, b), hi = std::max(a, b);
+                    if (I) {
+                        I[cnt] = i; M[cnt] = c; K[cnt] = mesh->cells[c * nv + b];
+                        V[cnt] = S[size_t(c) * ns + lo * nv - (lo * (lo - 1)) / 2 + (hi - lo)];
+                    }
+                    ++cnt;
+                }
+            }
+        *count = cnt;
+        if (n_wa) *n_wa = mesh->n_cells;
+        if (wa_coords) {
+            const std::vector<double> x = cell_centroids(*mesh);
+            std::memcpy(wa_coords, x.data(), x.size() * sizeof(double));
+        }
+        return EGFEM_OK;
+    }
     HostWSpace Wa, Wc;
     std::vector<int32_t> c2wa, c2wc;
     int nla = 0, nlc = 0;

@@ -115,6 +115,7 @@ struct Nonlin {
     double gamma, kappa;
     const double *kappa_field;   // W_a field or nullptr
     int32_t picard;              // nonzero: the Picard matrix (no g' terms) instead of the Jacobian
+    double a_preal, a_shift;     // EGFEM_G_GRADPOW: g = a_scale (a_shift + |grad u|^2)^a_preal
 };
 
 // Host-side assembly entry points (egfem_build.cpp).
@@ -125,6 +126,8 @@ egfem_status build_csf(const egfem_mesh &mesh, const egfem_problem &prob, const 
                        const std::vector<int32_t> &cell2wc, int nloc_c, HostCSF &out, std::string &err);
 egfem_status validate_mesh(const egfem_mesh &mesh, std::string &err);
 double basis_integral(int dim, int degree, int kind);   // int_K eta_m / |K| by node kind
+void cell_stiffness(const egfem_mesh &mesh, std::vector<double> &vol, std::vector<double> *S);
+std::vector<double> cell_centroids(const egfem_mesh &mesh);
 void set_last_error(const std::string &msg);            // text returned by egfem_last_error()
 
 }  // namespace egfem

@@ -6,7 +6,9 @@
 // so with a = kappa + g(Pi u) and abar_K = sum_m (iota^K_m / |K|) a_m (S^K carries |K|):
 //     r_i  = sum_K abar_K (S^K u)_i - d_i
 //     J_ib = sum_K [ abar_K S^K_ib + (S^K u)_i c^K_b ],   c^K_b = sum_m (iota^K_m / |K|) g'(Pi u)_m Pi_mb
-// i.e. each cell contributes a scaled stiffness plus a rank-one matrix.  Pass 1 (one
+// i.e. each cell contributes a scaled stiffness plus a rank-one matrix.  A gradient
+// coefficient with W_a = P0 (Sec. 5) has the same form, its one cell node carrying
+// g(||grad u_K||^2) and c^K = 2 g' S^K u / |K|.  Pass 1 (one
 // thread per cell) evaluates abar_K, S^K u and c^K from the cell's own vertex values and
 // stores them; pass 2 (one thread per row, the row's cells from the vertex-to-cell list)
 // gathers them into r_i and the row's Jacobian entries in a fixed order (deterministic).
@@ -57,12 +59,38 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
     for (int a = 0; a < NV; ++a) uk[a] = u[M.verts[c * NV + a]];
 #pragma unroll
     for (int q = 0; q < NS; ++q) S[q] = M.S[c * NS + q];
+    // (S^K u)_a in difference form (the rows of S^K sum to zero)
+    double su[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < NV; ++b)
+            if (b != a) t += S[tri_index(a, b, NV)] * (uk[b] - uk[a]);
+        su[a] = t;
+    }
     // S^K already carries |K|, so the cell weights are iota^K_m / |K| (sum over m: 1)
     double abar = 0.0, cb[NV];
 #pragma unroll
     for (int b = 0; b < NV; ++b) cb[b] = 0.0;
     if (M.nl.a_kind == EGFEM_G_NONE) {
         abar = M.nl.kappa;
+    } else if (M.nl.a_kind == EGFEM_G_GRADPOW) {
+        // W_a = P0 (Sec. 5, gradient nonlinearities): the cell's one W node carries
+        // s = ||grad u_K||^2 = u^T S^K u / |K| = sum_a (u_a - u_0) (S^K u)_a / |K|, and
+        // ds/du_b = 2 (S^K u)_b / |K|, so c^K = 2 g'(s) S^K u / |K| (a symmetric rank one)
+        const double ivol = 1.0 / M.vol[c];
+        double sg = 0.0;
+#pragma unroll
+        for (int a = 1; a < NV; ++a) sg += (uk[a] - uk[0]) * su[a];
+        sg = fmax(sg * ivol, 0.0);
+        const double base = M.nl.a_shift + sg;
+        const double g = M.nl.a_scale * pow(base, M.nl.a_preal);
+        const double gp = M.nl.a_preal == 0.0 ? 0.0 : M.nl.a_scale * M.nl.a_preal * pow(base, M.nl.a_preal - 1.0);
+        abar = M.nl.kappa + g;
+        const double e = 2.0 * gp * ivol;
+#pragma unroll
+        for (int b = 0; b < NV; ++b) cb[b] = e * su[b];
     } else {
         for (int l = 0; l < M.loc.nw; ++l) {
             const double io = M.loc.iota[l];
@@ -82,11 +110,7 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
     E[0] = abar;
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-        double su = 0.0;
-#pragma unroll
-        for (int b = 0; b < NV; ++b)
-            if (b != a) su += S[tri_index(a, b, NV)] * (uk[b] - uk[a]);
-        E[1 + a] = su;
+        E[1 + a] = su[a];
         E[1 + NV + a] = cb[a];
     }
 }

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libegfem.so")
 
-G_NONE, G_POW, G_EXP = 0, 1, 2
+G_NONE, G_POW, G_EXP, G_GRADPOW = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 OP_CSF, OP_MATRIX_FREE = 0, 1
 ITER_NEWTON, ITER_PICARD = 0, 1
@@ -43,7 +43,7 @@ class Problem(ctypes.Structure):
     _fields_ = [("a_kind", ctypes.c_int32), ("a_p", ctypes.c_double), ("a_scale", ctypes.c_double),
                 ("a_degree", ctypes.c_int32), ("c_kind", ctypes.c_int32), ("c_p", ctypes.c_double),
                 ("c_scale", ctypes.c_double), ("c_degree", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("kappa", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("a_shift", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -159,10 +159,13 @@ def selftest_grid_barrier(blocks: int, arrive: int, wait_ms: float):
 
 
 def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_scale=1.0, gamma=0.0, kappa=1.0) -> Problem:
-    kinds = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP}
+    """a = (kind, exponent[, shift]): ("pow", p), ("exp",), ("gradpow", q, shift) for the gradient
+    coefficient (shift + |grad u|^2)^q (with a_degree=0); c likewise for the reaction."""
+    kinds = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP, "gradpow": G_GRADPOW}
     p = Problem()
     p.a_kind = kinds[a[0] if a else None]
     p.a_p = float(a[1]) if a and len(a) > 1 else 1.0
+    p.a_shift = float(a[2]) if a and a[0] == "gradpow" and len(a) > 2 else 0.0
     p.a_scale, p.a_degree = float(a_scale), int(a_degree)
     p.c_kind = kinds[c[0] if c else None]
     p.c_p = float(c[1]) if c and len(c) > 1 else 1.0

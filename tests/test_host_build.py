@@ -130,3 +130,44 @@ def test_barrier_selftest_rejects_bad_sizes_without_a_gpu(egf):
     for blocks, arrive, wait in [(0, 0, 10.0), (65, 1, 10.0), (4, 5, 10.0), (4, 2, 0.0), (4, 2, 5000.0)]:
         assert L.egfem_selftest_grid_barrier(blocks, arrive, wait, ok, None) == 1
     assert L.egfem_selftest_grid_barrier(4, 2, 10.0, None, None) == 1
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2)])
+def test_p0_form_of_the_gradient_coefficient_matches_oracle_quadrature(egf, dim, n):
+    """With W_a = P0 (gradient coefficient) the form the element-local operator reads per cell,
+    T_iKk = S^K_ik, equals the oracle's quadrature of int eta_K grad phi_k . grad phi_i."""
+    mesh = wl.unit_square_mesh(n) if dim == 2 else wl.unit_cube_mesh(n)
+    I, M, K, V, Wc = egf.inspect_tensor(mesh, egf.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0))
+    assert len(Wc) == mesh.n_cells
+    P = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0)
+    oI, oM, oK, oV = P.T_coo()
+    perm = _match_w(P.space_coords(0), Wc)
+    scale = np.abs(oV).max()
+    orc = {(i, perm[m], k): v for i, m, k, v in zip(oI, oM, oK, oV) if not mesh.dirichlet[i]}
+    lib = {}
+    for i, m, k, v in zip(I, M, K, V):
+        lib[(i, m, k)] = lib.get((i, m, k), 0.0) + v
+    assert not any(mesh.dirichlet[i] for (i, _, _) in lib)
+    assert set(lib) == set(orc)
+    for key, v in lib.items():
+        assert abs(orc[key] - v) <= 1e-13 * scale, (key, v, orc[key])
+
+
+def test_bad_gradient_coefficient_is_rejected_before_any_cuda_call(egf):
+    """Build-time checks of the gradient coefficient return before the library touches a
+    device: W_a must be P0, the operator element-local, (shift + s)^q finite at s = 0, and
+    the reaction may not take the gradient kind."""
+    import ctypes
+    mesh = wl.unit_square_mesh(3)
+    m, keep = egf.egfem._mesh_struct(mesh)
+    mf = egf.default_options(op=egf.OP_MATRIX_FREE)
+    cases = [(egf.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0), egf.default_options(op=egf.OP_CSF), 10),
+             (egf.make_problem(a=("gradpow", -0.5, 1.0), a_degree=1), mf, 1),
+             (egf.make_problem(a=("gradpow", 0.5, 0.0), a_degree=0), mf, 1),
+             (egf.make_problem(a=("gradpow", -0.5, -1.0), a_degree=0), mf, 1),
+             (egf.make_problem(a=None, c=("gradpow", 1.0, 1.0), c_degree=1), mf, 1)]
+    for prob, opts, want in cases:
+        h = ctypes.c_void_p()
+        assert egf.lib().egfem_build(ctypes.byref(m), ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(h)) == want
+        assert not h.value
+    del keep
