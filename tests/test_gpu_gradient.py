@@ -77,7 +77,7 @@ def test_gradient_jacobian_parity(P, name, iteration):
     h.jacobian(cuda(u), vals)
     torch.cuda.synchronize()
     A = sp.csr_matrix((vals.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=(mesh.n_nodes, mesh.n_nodes))
-    Ao = orc.jacobian(u, method=iteration)
+    Ao = orc.jacobian(u, method="picard" if iteration == "picard" else "egfem")
     assert abs(A - Ao).max() <= 1e-12 * abs(Ao).max()
     if iteration == "newton":
         # the gradient coefficient's Jacobian is symmetric on the free block
