@@ -135,3 +135,34 @@ def test_p_laplace_3d_newton_matches_oracle(P):
     torch.cuda.synchronize()
     assert st.status == 0
     assert rel(u.cpu().numpy(), u_orc) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_p_laplace_disk_picard_matches_oracle_and_closed_form(P, prec):
+    """p = 3/2 on the unit disk (Sec. 5): the library's Picard iteration from u = 0 reaches
+    the oracle's Picard solution, and Newton from the interpolated closed form the same one."""
+    p, n = 1.5, 16
+    mesh = wl.unit_disk_mesh(n)
+    ue = wl.plaplace_disk_exact(mesh.coords[:, 0], mesh.coords[:, 1], p)
+    q = (p - 2) / 2
+    orc = oracle.Problem(mesh, a=("gradpow", q, 1e-12), a_deg=0, kappa=0.0)
+    b = orc.load_vector(lambda x, y: np.ones_like(x)) * (1 - mesh.dirichlet)
+    u_orc, _, _, _ = orc.newton(b, rtol=1e-12, iteration="picard", maxit=300)
+    mixed = prec == "mixed"
+    prob = P.make_problem(a=("gradpow", q, 1e-12), a_degree=0, kappa=0.0)
+    base = dict(op=P.OP_MATRIX_FREE, precision=P.PREC_MIXED if mixed else P.PREC_FP64)
+    h = P.Handle(mesh, prob, P.default_options(iteration=P.ITER_PICARD, newton_maxit=300,
+                                               newton_rtol=1e-10 if mixed else 1e-12, **base))
+    u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    st = h.newton_solve(u, cuda(b))
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.newton_iters > 10
+    tol = 1e-8 if mixed else 1e-10
+    assert rel(u.cpu().numpy(), u_orc) <= tol
+    assert np.sqrt(np.mean((u.cpu().numpy() - ue) ** 2)) <= 5e-5
+    hn = P.Handle(mesh, prob, P.default_options(newton_rtol=1e-10, **base))
+    un = cuda(ue * (1 - mesh.dirichlet))
+    st = hn.newton_solve(un, cuda(b))
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.newton_iters <= 8
+    assert rel(un.cpu().numpy(), u_orc) <= tol

@@ -562,3 +562,44 @@ def test_minimal_surface_manufactured_solution_converges_at_second_order():
         errs.append(np.sqrt(np.mean((u - ue) ** 2)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates.min() > 1.8, (errs, rates)
+
+
+def test_p_laplace_disk_closed_form_second_order():
+    """p-Laplace, p = 3/2, d = 1 on the unit disk with u = 0 on its boundary (Sec. 5): the
+    Picard iteration with W = P0 reaches the closed-form solution at O(h^2) in the nodal RMS
+    error (a = ||grad u||^(p-2), regularised by a 1e-12 shift of ||grad u||^2), and Newton
+    from the interpolated exact solution reaches the same discrete solution."""
+    p = 1.5
+    errs = []
+    for n in (4, 8, 16):
+        mesh = wl.unit_disk_mesh(n)
+        ue = wl.plaplace_disk_exact(mesh.coords[:, 0], mesh.coords[:, 1], p)
+        P = oracle.Problem(mesh, a=("gradpow", (p - 2) / 2, 1e-12), a_deg=0, kappa=0.0)
+        b = P.load_vector(lambda x, y: np.ones_like(x)) * (1 - mesh.dirichlet)
+        u, h, _, _ = P.newton(b, rtol=1e-10, iteration="picard", maxit=200)
+        assert h[-1] <= 1e-10 * h[0]
+        errs.append(np.sqrt(np.mean((u - ue) ** 2)))
+        if n == 8:
+            un, hn, _, _ = P.newton(b, u0=ue * (1 - mesh.dirichlet), rtol=1e-10)
+            assert len(hn) <= 6 and np.abs(un - u).max() <= 1e-9
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > 1.8 and errs[-1] < 5e-5, (errs, rates)
+
+
+def test_unit_disk_mesh_is_a_conforming_triangulation():
+    """The disk generator: 6 n^2 positively oriented cells, every interior edge shared by two
+    cells, the boundary ring on the circle, and the area tending to pi at O(h^2)."""
+    from collections import Counter
+    for n in (1, 3, 8):
+        m = wl.unit_disk_mesh(n)
+        assert m.n_cells == 6 * n * n and m.n_nodes == 1 + 3 * n * (n + 1)
+        c = m.coords[m.cells]
+        det = (c[:, 1, 0] - c[:, 0, 0]) * (c[:, 2, 1] - c[:, 0, 1]) - (c[:, 1, 1] - c[:, 0, 1]) * (c[:, 2, 0] - c[:, 0, 0])
+        assert det.min() > 0
+        edges = Counter(tuple(sorted((t[a], t[b]))) for t in m.cells for a, b in ((0, 1), (1, 2), (2, 0)))
+        bnd = {e for e, k in edges.items() if k == 1}
+        assert set(edges.values()) <= {1, 2} and len(bnd) == 6 * n
+        assert all(m.dirichlet[v] for e in bnd for v in e)
+        assert np.allclose(np.hypot(*m.coords[m.dirichlet == 1].T), 1.0)
+        # inscribed 6n-gon: area (6n/2) sin(2 pi / 6n)
+        assert abs(det.sum() / 2 - 3 * n * np.sin(2 * np.pi / (6 * n))) <= 1e-12

@@ -90,6 +90,56 @@ def unit_cube_mesh(n: int) -> Mesh:
     return Mesh(3, coords, cells, dirichlet)
 
 
+def unit_disk_mesh(n: int) -> Mesh:
+    """Unit disk (the p-Laplace example's domain, Sec. 5) as n concentric rings: ring k
+    (k = 1..n) holds 6k vertices at radius k/n and angles 2 pi j / (6k), j = 0..6k-1;
+    vertex 0 is the centre and ring k starts at index 1 + 3k(k-1).  The band between rings
+    k-1 and k is zipped by angle into 6(2k-1) triangles, 6 n^2 in all.  The Dirichlet
+    boundary is the outer ring (its vertices lie on the circle)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    pts = [np.zeros((1, 2))]
+    starts = [0]
+    for k in range(1, n + 1):
+        t = 2.0 * np.pi * np.arange(6 * k) / (6 * k)
+        starts.append(1 + 3 * k * (k - 1))
+        pts.append(np.stack([k / n * np.cos(t), k / n * np.sin(t)], axis=1))
+    coords = np.concatenate(pts).astype(np.float64)
+    cells = []
+    for k in range(1, n + 1):
+        nin, nout = max(1, 6 * (k - 1)), 6 * k
+        inner = [starts[k - 1] + j for j in range(nin)] if k > 1 else [0]
+        outer = [starts[k] + j for j in range(nout)]
+        if k == 1:
+            cells += [[0, outer[j], outer[(j + 1) % nout]] for j in range(nout)]
+            continue
+        # zipper: advance along whichever ring's next vertex comes first in angle (exact
+        # rational comparison (j+1)/nin vs (l+1)/nout of the fractions of a turn)
+        i = l = 0
+        while i < nin or l < nout:
+            if l < nout and (i == nin or (l + 1) * nin <= (i + 1) * nout):
+                cells.append([inner[i % nin], outer[l], outer[(l + 1) % nout]])
+                l += 1
+            else:
+                cells.append([inner[i], outer[l % nout], inner[(i + 1) % nin]])
+                i += 1
+    cells = np.array(cells, dtype=np.int32)
+    # counter-clockwise orientation (the library and the oracle take |det|; kept tidy)
+    a, b, c = coords[cells[:, 0]], coords[cells[:, 1]], coords[cells[:, 2]]
+    det = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    cells[det < 0] = cells[det < 0][:, [0, 2, 1]]
+    dirichlet = np.zeros(coords.shape[0], dtype=np.uint8)
+    dirichlet[starts[n]:] = 1
+    return Mesh(2, coords, cells, dirichlet)
+
+
+def plaplace_disk_exact(x: np.ndarray, y: np.ndarray, p: float) -> np.ndarray:
+    """The closed-form solution of -div(|grad u|^(p-2) grad u) = 1 on the unit disk with u = 0
+    on its boundary (Sec. 5, p-Laplace example): 2^(-1/(p-1)) (p-1)/p (1 - |x|^(p/(p-1)))."""
+    r = np.sqrt(x * x + y * y)
+    return 2.0 ** (-1.0 / (p - 1.0)) * (p - 1.0) / p * (1.0 - r ** (p / (p - 1.0)))
+
+
 # ---------------------------------------------------------------------------
 # Manufactured solution for -div((1 + u^2) grad u) = f on the unit square.
 # With u = sin(pi x) sin(pi y):  -div((1+u^2) grad u) = -(1+u^2) lap u - 2 u |grad u|^2,
