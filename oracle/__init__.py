@@ -66,7 +66,8 @@ class _Spec(ctypes.Structure):
                 ("a_kind", ctypes.c_int), ("a_p", ctypes.c_double), ("a_scale", ctypes.c_double), ("a_deg", ctypes.c_int),
                 ("c_kind", ctypes.c_int), ("c_p", ctypes.c_double), ("c_scale", ctypes.c_double), ("c_deg", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("qpts", ctypes.c_int),
-                ("a_shift", ctypes.c_double)]
+                ("a_shift", ctypes.c_double), ("a_quad", ctypes.c_int), ("c_quad", ctypes.c_int),
+                ("rule", ctypes.c_int)]
 
 
 def lib():
@@ -94,6 +95,8 @@ def lib():
             L.orc_ref_nodes.argtypes = [ctypes.c_int, ctypes.c_int, _c_ip]
             L.orc_simplex_rule.argtypes = [ctypes.c_int, ctypes.c_int, _c_dp, _c_dp]
             L.orc_simplex_rule.restype = ctypes.c_int
+            L.orc_sym_rule.argtypes = [ctypes.c_int, ctypes.c_int, _c_dp, _c_dp]
+            L.orc_sym_rule.restype = ctypes.c_int
             L.orc_pointwise.argtypes = [ctypes.c_void_p, _c_dp, _c_dp, _c_dp, _c_dp, _c_dp]
             for f in ("orc_egfem_residual", "orc_sga_residual"):
                 getattr(L, f).argtypes = [ctypes.c_void_p, _c_dp, _c_dp, _c_dp, ctypes.c_int, _c_dp]
@@ -132,14 +135,18 @@ class Problem:
 
     w = a_scale * g_a(Pi_a u) lives in the Lagrange space of degree ``a_deg``;
     c = c_scale * g_c(Pi_c u) in the space of degree ``c_deg``.  ``g`` is
-    ``("pow", p)`` -> s^p or ``("exp",)`` -> e^s.  ``cells`` restricts the tensor
+    ``("pow", p)`` -> s^p or ``("exp",)`` -> e^s.  ``a_space="quad"`` (``c_space``) makes
+    W the quadrature space I_k of Sec. 3.2 Case 3 with k = ``a_deg`` (``c_deg``): one node
+    per point of the symmetric degree-k rule on every cell.  ``rule=k`` makes every integral
+    (the standard Galerkin approach, the load vector and the Lagrange-space tensors) use that
+    same rule instead of the collapsed Gauss rule of ``qpts`` points.  ``cells`` restricts the tensor
     assembly (and the SGA integrals) to a subset of cells, so that single rows of a
     large problem can be evaluated exactly: a row is complete when every cell that
     contains its vertex is in the subset.
     """
 
     def __init__(self, mesh, *, a=("pow", 2.0), a_scale=1.0, a_deg=2, c=None, c_scale=1.0, c_deg=1,
-                 gamma=0.0, kappa=1.0, qpts=4, cells=None):
+                 gamma=0.0, kappa=1.0, qpts=4, cells=None, a_space="lagrange", c_space="lagrange", rule=0):
         self.mesh = mesh
         self._X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
         self._cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
@@ -157,11 +164,14 @@ class Problem:
         s.c_p = float(c[1]) if c and len(c) > 1 else 1.0
         s.c_scale, s.c_deg = float(c_scale), int(c_deg)
         s.gamma, s.kappa, s.qpts = float(gamma), float(kappa), int(qpts)
+        s.a_quad, s.c_quad, s.rule = int(a_space == "quad"), int(c_space == "quad"), int(rule)
         self._spec = s
         self._sel = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
         L = lib()
         self._h = L.orc_create(ctypes.byref(s), None if self._sel is None else self._sel.ctypes.data_as(_c_ip),
                                0 if self._sel is None else len(self._sel))
+        if not self._h:
+            raise ValueError("oracle: no symmetric rule of that degree (triangle 1..4, tetrahedron 1..3)")
         self.n = mesh.n_nodes
         self.nw = L.orc_space_size(self._h, 0)
         self.nc_space = L.orc_space_size(self._h, 1)
@@ -310,6 +320,15 @@ def ref_nodes(dim, p):
 def simplex_rule(dim, q):
     pts, wts = np.empty(q ** dim * dim), np.empty(q ** dim)
     n = lib().orc_simplex_rule(dim, q, _dp(pts), _dp(wts))
+    return pts[: n * dim].reshape(n, dim), wts[:n]
+
+
+def sym_rule(dim, k):
+    """The symmetric degree-k rule behind I_k: reference points [n, dim] and weights (sum 1/d!)."""
+    pts, wts = np.empty(16 * dim), np.empty(16)
+    n = lib().orc_sym_rule(dim, k, _dp(pts), _dp(wts))
+    if n < 0:
+        raise ValueError(f"no symmetric rule of degree {k} in {dim}D")
     return pts[: n * dim].reshape(n, dim), wts[:n]
 
 

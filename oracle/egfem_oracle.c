@@ -252,6 +252,83 @@ static int simplex_rule(int dim, int q, double *pts, double *wts) {
     return n;
 }
 
+/* Symmetric rules of degree k on the reference simplex, the rules behind the quadrature
+ * spaces I_k (Sec. 3.2, Case 3; the paper cites Dunavant's symmetric Gaussian rules for the
+ * triangle).  Each rule is a union of orbits of barycentric points under vertex permutation,
+ * with the orbit parameters and weights in closed form:
+ *   triangle    k = 1: centroid;  k = 2: (2/3, 1/6, 1/6);  k = 3: centroid (weight -27/48) and
+ *               (3/5, 1/5, 1/5) (25/48);  k = 4: (1-2a, a, a) for the two roots
+ *               a = (8 - sqrt 10 +- sqrt(38 - 44 sqrt(2/5))) / 18, weights
+ *               (620 +- sqrt(213125 - 53320 sqrt 10)) / 3720;
+ *   tetrahedron k = 1: centroid;  k = 2: (1-3a, a, a, a), a = (5 - sqrt 5) / 20, weights 1/4;
+ *               k = 3: centroid (-4/5) and (1/2, 1/6, 1/6, 1/6) (9/20).
+ * Weights are given relative to the simplex volume and scaled here to sum to 1/d!.
+ * Points are returned in reference coordinates xi_j = lambda_j (j = 1..d).  Returns the
+ * number of points, or -1 for a degree this table does not hold. */
+static int orbit_push(int dim, const double *lam, double w, double *pts, double *wts, int n) {
+    /* every distinct permutation of lam[0..dim] */
+    int nv = dim + 1, perm[4];
+    double seen[24][4];
+    int ns = 0;
+    for (int i = 0; i < nv; ++i) perm[i] = i;
+    for (;;) {
+        double b[4];
+        for (int i = 0; i < nv; ++i) b[i] = lam[perm[i]];
+        int dup = 0;
+        for (int t = 0; t < ns && !dup; ++t) {
+            int same = 1;
+            for (int i = 0; i < nv; ++i) same &= seen[t][i] == b[i];
+            dup = same;
+        }
+        if (!dup) {
+            for (int i = 0; i < nv; ++i) seen[ns][i] = b[i];
+            ++ns;
+            for (int j = 1; j <= dim; ++j) pts[(size_t)n * dim + j - 1] = b[j];
+            wts[n++] = w;
+        }
+        /* next permutation (lexicographic) */
+        int i = nv - 2;
+        while (i >= 0 && perm[i] > perm[i + 1]) --i;
+        if (i < 0) break;
+        int j = nv - 1;
+        while (perm[j] < perm[i]) --j;
+        int t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+        for (int l = i + 1, r = nv - 1; l < r; ++l, --r) { t = perm[l]; perm[l] = perm[r]; perm[r] = t; }
+    }
+    return n;
+}
+
+static int sym_rule(int dim, int k, double *pts, double *wts) {
+    int n = 0;
+    if (dim == 2) {
+        if (k == 1) { double l[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3}; n = orbit_push(2, l, 1.0, pts, wts, n); }
+        else if (k == 2) { double l[3] = {2.0 / 3, 1.0 / 6, 1.0 / 6}; n = orbit_push(2, l, 1.0 / 3, pts, wts, n); }
+        else if (k == 3) {
+            double c[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3}, l[3] = {0.6, 0.2, 0.2};
+            n = orbit_push(2, c, -27.0 / 48.0, pts, wts, n);
+            n = orbit_push(2, l, 25.0 / 48.0, pts, wts, n);
+        } else if (k == 4) {
+            double r = sqrt(38.0 - 44.0 * sqrt(0.4)), q = sqrt(213125.0 - 53320.0 * sqrt(10.0));
+            double a1 = (8.0 - sqrt(10.0) + r) / 18.0, a2 = (8.0 - sqrt(10.0) - r) / 18.0;
+            double l1[3] = {1.0 - 2.0 * a1, a1, a1}, l2[3] = {1.0 - 2.0 * a2, a2, a2};
+            n = orbit_push(2, l1, (620.0 + q) / 3720.0, pts, wts, n);
+            n = orbit_push(2, l2, (620.0 - q) / 3720.0, pts, wts, n);
+        } else return -1;
+    } else {
+        if (k == 1) { double l[4] = {0.25, 0.25, 0.25, 0.25}; n = orbit_push(3, l, 1.0, pts, wts, n); }
+        else if (k == 2) {
+            double a = (5.0 - sqrt(5.0)) / 20.0, l[4] = {1.0 - 3.0 * a, a, a, a};
+            n = orbit_push(3, l, 0.25, pts, wts, n);
+        } else if (k == 3) {
+            double c[4] = {0.25, 0.25, 0.25, 0.25}, l[4] = {0.5, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+            n = orbit_push(3, c, -0.8, pts, wts, n);
+            n = orbit_push(3, l, 0.45, pts, wts, n);
+        } else return -1;
+    }
+    for (int i = 0; i < n; ++i) wts[i] /= (dim == 2 ? 2.0 : 6.0);
+    return n;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Geometry                                                                   */
 /* ------------------------------------------------------------------------- */
@@ -360,6 +437,27 @@ static int space_build(int dim, int nc, const double *X, const int *cells, int p
     return 0;
 }
 
+/* The quadrature space I_k: one node per rule point per cell, never shared between cells
+ * (the basis functions w_l delta_{x_l} are discontinuous, Sec. 3.2 Case 3); node c nq + l is
+ * the physical image of reference point l on cell c. */
+static void space_build_quad(int dim, int nc, const double *X, const int *cells, int nq, const double *qp, orc_space *S) {
+    S->p = -1; S->nloc = nq; S->n = nc * nq;
+    S->cell2dof = malloc(sizeof(int) * (size_t)nc * nq);
+    S->coords = malloc(sizeof(double) * (size_t)S->n * dim);
+    for (int c = 0; c < nc; ++c) {
+        orc_geom G; cell_geom(dim, X, cells + (size_t)c * (dim + 1), &G);
+        for (int l = 0; l < nq; ++l) {
+            int g = c * nq + l;
+            S->cell2dof[(size_t)c * nq + l] = g;
+            for (int r = 0; r < dim; ++r) {
+                double x = G.x0[r];
+                for (int k = 0; k < dim; ++k) x += G.B[r * dim + k] * qp[l * dim + k];
+                S->coords[(size_t)g * dim + r] = x;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Sparse triplet accumulation (COO, sorted and summed)                        */
 /* ------------------------------------------------------------------------- */
@@ -404,6 +502,9 @@ typedef struct {
     double gamma, kappa;
     int qpts;                                      /* Gauss points per direction */
     double a_shift;                                /* ORC_G_GRADPOW: the shift of ||grad u||^2 */
+    int a_quad, c_quad;  /* nonzero: W_a / W_c is the quadrature space I_k, k = a_deg / c_deg (Sec. 3.2 Case 3) */
+    int rule;            /* > 0: the symmetric degree-`rule` rule for every integral (SGA, load vector,
+                            Lagrange-space tensors) instead of the collapsed Gauss rule */
 } orc_spec;
 
 typedef struct {
@@ -411,6 +512,8 @@ typedef struct {
     orc_elem P1, Ea, Ec;
     orc_space Sa, Sc;
     int nq; double qp[ORC_MAXQ * 3], qw[ORC_MAXQ];
+    /* the rules of quadrature spaces (I_k): reference points and weights (sum 1/d!) */
+    int aq_n, cq_n; double aq_p[16 * 3], aq_w[16], cq_p[16 * 3], cq_w[16];
     /* basis values tabulated once at the quadrature points (phi: P1, eta_a / eta_c: W spaces)
      * and the constant reference gradients of the P1 basis */
     double *phi_q, *eta_a_q, *eta_c_q, gref1[4 * 3];
@@ -496,6 +599,29 @@ static void local_tensors(const orc_problem *P, int c, const orc_elem *EW, const
     }
 }
 
+/* Local tensors of cell c for a quadrature space (Sec. 3.2 Case 3): with eta_l = w_l delta_{x_l},
+ * Tloc[a][l][b] = w_l grad phi_b(x_l) . grad phi_a(x_l) and Mloc[a][l] = w_l phi_a(x_l), w_l the
+ * physical weight (reference weight d! |K|). */
+static void local_tensors_quad(const orc_problem *P, int c, int nq, const double *qp, const double *qw, double *Tloc, double *Mloc) {
+    int dim = P->s.dim, nv = dim + 1;
+    orc_geom G; cell_geom(dim, P->s.X, P->s.cells + (size_t)c * nv, &G);
+    double g[4][3];
+    for (int a = 0; a < nv; ++a) phys_grad(dim, &G, P->gref1 + a * dim, g[a]);
+    for (int l = 0; l < nq; ++l) {
+        double wl = qw[l] * factorial(dim) * G.vol, phi[ORC_MAXNB];
+        elem_eval(&P->P1, qp + l * dim, phi, NULL);
+        for (int a = 0; a < nv; ++a) {
+            if (Mloc) Mloc[a * nq + l] = wl * phi[a];
+            if (Tloc)
+                for (int b = 0; b < nv; ++b) {
+                    double gg = 0.0;
+                    for (int d = 0; d < dim; ++d) gg += g[b][d] * g[a][d];
+                    Tloc[(a * nq + l) * nv + b] = wl * gg;
+                }
+        }
+    }
+}
+
 orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_list) {
     orc_problem *P = calloc(1, sizeof(orc_problem));
     P->s = *spec;
@@ -503,9 +629,13 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
     elem_init(&P->P1, dim, 1);
     if (P->s.a_deg < 0) P->s.a_deg = 1;
     if (P->s.c_deg < 0) P->s.c_deg = 1;
-    elem_init(&P->Ea, dim, P->s.a_deg);
-    elem_init(&P->Ec, dim, P->s.c_deg);
-    P->nq = simplex_rule(dim, spec->qpts, P->qp, P->qw);
+    /* a quadrature space has no polynomial basis: its element slot holds P0 (unused) */
+    elem_init(&P->Ea, dim, P->s.a_quad ? 0 : P->s.a_deg);
+    elem_init(&P->Ec, dim, P->s.c_quad ? 0 : P->s.c_deg);
+    P->nq = spec->rule > 0 ? sym_rule(dim, spec->rule, P->qp, P->qw) : simplex_rule(dim, spec->qpts, P->qp, P->qw);
+    if (P->nq <= 0) { free(P); return NULL; }
+    if (P->s.a_quad && (P->aq_n = sym_rule(dim, P->s.a_deg, P->aq_p, P->aq_w)) <= 0) { free(P); return NULL; }
+    if (P->s.c_quad && (P->cq_n = sym_rule(dim, P->s.c_deg, P->cq_p, P->cq_w)) <= 0) { free(P); return NULL; }
     P->phi_q = malloc(sizeof(double) * P->nq * ORC_MAXNB);
     P->eta_a_q = malloc(sizeof(double) * P->nq * ORC_MAXNB);
     P->eta_c_q = malloc(sizeof(double) * P->nq * ORC_MAXNB);
@@ -515,8 +645,10 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
         elem_eval(&P->Ec, P->qp + q * dim, P->eta_c_q + q * ORC_MAXNB, NULL);
     }
     { double xi0[3] = {0.25, 0.25, 0.25}; elem_eval(&P->P1, xi0, NULL, P->gref1); }
-    space_build(dim, spec->nc, spec->X, spec->cells, P->s.a_deg, &P->Sa);
-    space_build(dim, spec->nc, spec->X, spec->cells, P->s.c_deg, &P->Sc);
+    if (P->s.a_quad) space_build_quad(dim, spec->nc, spec->X, spec->cells, P->aq_n, P->aq_p, &P->Sa);
+    else space_build(dim, spec->nc, spec->X, spec->cells, P->s.a_deg, &P->Sa);
+    if (P->s.c_quad) space_build_quad(dim, spec->nc, spec->X, spec->cells, P->cq_n, P->cq_p, &P->Sc);
+    else space_build(dim, spec->nc, spec->X, spec->cells, P->s.c_deg, &P->Sc);
     build_interp(P, &P->Sa, &P->Pa);
     build_interp(P, &P->Sc, &P->Pc);
     P->cell_mask = calloc(spec->nc, sizeof(int));
@@ -524,21 +656,24 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
     else for (int c = 0; c < spec->nc; ++c) P->cell_mask[c] = 1;
     /* assemble T (always) and M (when a reaction term is present) over the selected cells */
     double Tloc[4 * ORC_MAXNB * 4], Mloc[4 * ORC_MAXNB];
+    const int nwa = P->Sa.nloc, nwc = P->Sc.nloc;
     for (int c = 0; c < spec->nc; ++c) {
         if (!P->cell_mask[c]) continue;
         const int *cv = spec->cells + (size_t)c * nv;
-        local_tensors(P, c, &P->Ea, P->eta_a_q, Tloc, NULL);
-        const int *wa = P->Sa.cell2dof + (size_t)c * P->Sa.nloc;
+        if (P->s.a_quad) local_tensors_quad(P, c, P->aq_n, P->aq_p, P->aq_w, Tloc, NULL);
+        else local_tensors(P, c, &P->Ea, P->eta_a_q, Tloc, NULL);
+        const int *wa = P->Sa.cell2dof + (size_t)c * nwa;
         for (int a = 0; a < nv; ++a)
-            for (int m = 0; m < P->Ea.nb; ++m)
+            for (int m = 0; m < nwa; ++m)
                 for (int b = 0; b < nv; ++b)
-                    coo_push(&P->T, cv[a], wa[m], cv[b], Tloc[(a * P->Ea.nb + m) * nv + b]);
+                    coo_push(&P->T, cv[a], wa[m], cv[b], Tloc[(a * nwa + m) * nv + b]);
         if (spec->c_kind != ORC_G_NONE) {
-            local_tensors(P, c, &P->Ec, P->eta_c_q, NULL, Mloc);
-            const int *wc = P->Sc.cell2dof + (size_t)c * P->Sc.nloc;
+            if (P->s.c_quad) local_tensors_quad(P, c, P->cq_n, P->cq_p, P->cq_w, NULL, Mloc);
+            else local_tensors(P, c, &P->Ec, P->eta_c_q, NULL, Mloc);
+            const int *wc = P->Sc.cell2dof + (size_t)c * nwc;
             for (int a = 0; a < nv; ++a)
-                for (int m = 0; m < P->Ec.nb; ++m)
-                    coo_push(&P->M, cv[a], wc[m], 0, Mloc[a * P->Ec.nb + m]);
+                for (int m = 0; m < nwc; ++m)
+                    coo_push(&P->M, cv[a], wc[m], 0, Mloc[a * nwc + m]);
         }
     }
     coo_compress(&P->T);
@@ -597,6 +732,7 @@ void orc_ref_nodes(int dim, int p, int *alpha) {
     for (int i = 0; i < E.nb; ++i) for (int j = 0; j <= dim; ++j) alpha[i * (dim + 1) + j] = E.alpha[i][j];
 }
 int orc_simplex_rule(int dim, int q, double *pts, double *wts) { return simplex_rule(dim, q, pts, wts); }
+int orc_sym_rule(int dim, int k, double *pts, double *wts) { return sym_rule(dim, k, pts, wts); }
 
 /* ------------------------------------------------------------------------- */
 /* Pointwise nonlinearity (Sec. 3.2): f = g(Pi u) at every W node               */
@@ -625,10 +761,11 @@ static double cell_grad2(const orc_problem *P, int c, const double *u, double g[
 void orc_pointwise(const orc_problem *P, const double *u, double *w, double *wprime, double *c, double *cprime) {
     double *pa = malloc(sizeof(double) * P->Sa.n), *pc = malloc(sizeof(double) * P->Sc.n);
     if (P->s.a_kind == ORC_G_GRADPOW) {
-        /* W_a = P0: the node of cell c carries ||grad u_h||^2 on c */
+        /* W_a = P0 (or I_k): every node of cell c carries ||grad u_h||^2 on c */
         for (int c = 0; c < P->s.nc; ++c) {
             double g[4][3], gu[3];
-            pa[P->Sa.cell2dof[c]] = cell_grad2(P, c, u, g, gu);
+            double s2 = cell_grad2(P, c, u, g, gu);
+            for (int l = 0; l < P->Sa.nloc; ++l) pa[P->Sa.cell2dof[(size_t)c * P->Sa.nloc + l]] = s2;
         }
     } else {
         interp_apply(&P->Pa, P->Sa.n, u, pa);
@@ -704,11 +841,13 @@ static int64_t egfem_matrix(const orc_problem *P, const double *u, int picard, i
         for (int c = 0; c < P->s.nc; ++c) {
             double g[4][3], gu[3];
             cell_grad2(P, c, u, g, gu);
-            int m = P->Sa.cell2dof[c];
-            for (int l = 0; l < nvc; ++l) {
-                double t = 0.0;
-                for (int d = 0; d < P->s.dim; ++d) t += gu[d] * g[l][d];
-                coo_push(&Pg, m, P->s.cells[(size_t)c * nvc + l], 0, 2.0 * t);
+            for (int q = 0; q < P->Sa.nloc; ++q) {
+                int m = P->Sa.cell2dof[(size_t)c * P->Sa.nloc + q];
+                for (int l = 0; l < nvc; ++l) {
+                    double t = 0.0;
+                    for (int d = 0; d < P->s.dim; ++d) t += gu[d] * g[l][d];
+                    coo_push(&Pg, m, P->s.cells[(size_t)c * nvc + l], 0, 2.0 * t);
+                }
             }
         }
         coo_compress(&Pg);
@@ -767,6 +906,7 @@ int64_t orc_picard_matrix(const orc_problem *P, const double *u, int64_t cap, in
 
 static double kappa_at(const orc_problem *P, int c, const double *eta) {
     if (!P->kappa_field) return P->s.kappa;
+    if (P->s.a_quad) return NAN;   /* a kappa field on I_k has no values between its nodes */
     const int *wa = P->Sa.cell2dof + (size_t)c * P->Sa.nloc;
     double k = 0.0;
     for (int m = 0; m < P->Ea.nb; ++m) k += P->kappa_field[wa[m]] * eta[m];

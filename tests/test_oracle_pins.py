@@ -603,3 +603,81 @@ def test_unit_disk_mesh_is_a_conforming_triangulation():
         assert np.allclose(np.hypot(*m.coords[m.dirichlet == 1].T), 1.0)
         # inscribed 6n-gon: area (6n/2) sin(2 pi / 6n)
         assert abs(det.sum() / 2 - 3 * n * np.sin(2 * np.pi / (6 * n))) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# Quadrature spaces I_k (Sec. 3.2, Case 3)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)])
+def test_symmetric_rule_is_exact_to_its_degree_and_no_further(dim, k):
+    """The rule behind I_k integrates every monomial of degree <= k over the reference simplex
+    exactly (int xi^alpha = alpha! / (|alpha| + d)!) and misses one of degree k + 1."""
+    import itertools
+    import math
+    p, w = oracle.sym_rule(dim, k)
+    assert np.all(p >= 0) and np.all(p.sum(axis=1) <= 1)
+    worst = {}
+    for deg in range(k + 2):
+        for al in itertools.product(range(deg + 1), repeat=dim):
+            if sum(al) != deg:
+                continue
+            exact = np.prod([math.factorial(a) for a in al]) / math.factorial(deg + dim)
+            err = abs(np.sum(w * np.prod(p ** np.array(al), axis=1)) - exact)
+            worst[deg] = max(worst.get(deg, 0.0), err)
+    assert max(worst[d] for d in range(k + 1)) <= 1e-15
+    assert worst[k + 1] > 1e-6
+
+
+def test_table1_quadrature_space_size():
+    """Table 1: on the 64 x 64 grid the EGFEM with I_4 has 53377 unknowns (4225 P1 nodes plus
+    six rule points on each of the 8192 triangles)."""
+    mesh = wl.unit_square_mesh(64)
+    P = oracle.Problem(mesh, a=None, a_deg=1, c=("pow", 3.0), c_deg=4, c_space="quad", gamma=1.0)
+    assert mesh.n_nodes + P.nc_space == 53377
+
+
+@pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)])
+def test_quadrature_space_reproduces_sga_with_the_same_rule(dim, k):
+    """Case 3's claim: with W = I_k for both the coefficient and the reaction, the EGFEM
+    residual and Jacobian equal those of the standard Galerkin approach integrated by the same
+    rule (to rounding), for any nonlinearity."""
+    mesh = wl.unit_square_mesh(5) if dim == 2 else wl.unit_cube_mesh(2)
+    kw = dict(a=("pow", 3.0), a_deg=k, a_space="quad", c=("exp",), c_deg=k, c_space="quad", gamma=0.7,
+              kappa=0.5, rule=k)
+    P = oracle.Problem(mesh, **kw)
+    assert P.nw == P.nc_space == mesh.n_cells * len(oracle.sym_rule(dim, k)[1])
+    u = wl.random_vector(mesh.n_nodes, 61, 0.8)
+    b = wl.random_vector(mesh.n_nodes, 62)
+    re, rs = P.residual(u, b, form="plain"), P.residual(u, b, method="sga", form="plain")
+    assert np.abs(re - rs).max() <= 1e-13 * np.abs(rs).max()
+    Je, Js = P.jacobian(u), P.jacobian(u, method="sga")
+    assert abs(Je - Js).max() <= 1e-13 * abs(Js).max()
+
+
+def test_quadrature_and_lagrange_spaces_agree_where_both_are_exact():
+    """c = u^2 with u in P1: W_c = P2 holds it exactly, and I_3 integrates u^2 phi_i exactly,
+    so both EGFEM residuals equal the exactly integrated one; likewise a = 1 + u^2 with
+    W_a = P2 and W_a = I_2 (the integrand a(u) grad phi_k . grad phi_i is quadratic)."""
+    mesh = wl.unit_square_mesh(6)
+    u = wl.random_vector(mesh.n_nodes, 71, 0.9)
+    b = wl.random_vector(mesh.n_nodes, 72)
+    base = dict(a=("pow", 2.0), kappa=1.0, c=("pow", 2.0), gamma=1.3)
+    r_lag = oracle.Problem(mesh, a_deg=2, c_deg=2, **base).residual(u, b)
+    r_quad = oracle.Problem(mesh, a_deg=2, a_space="quad", c_deg=3, c_space="quad", **base).residual(u, b)
+    r_sga = oracle.Problem(mesh, a_deg=2, c_deg=2, qpts=4, **base).residual(u, b, method="sga")
+    scale = np.abs(r_sga).max()
+    assert np.abs(r_lag - r_sga).max() <= 1e-13 * scale
+    assert np.abs(r_quad - r_sga).max() <= 1e-13 * scale
+
+
+def test_i1_equals_p0_for_the_gradient_coefficient():
+    """For P1 u the gradient is constant per cell, so I_1 (one point, weight |K|) and P0 give
+    the same residual and Jacobian (Sec. 5 uses both for the p-Laplace and minimal surface)."""
+    mesh = wl.unit_square_mesh(6)
+    u = wl.random_vector(mesh.n_nodes, 81, 0.7)
+    b = wl.random_vector(mesh.n_nodes, 82)
+    P0 = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
+    I1 = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=1, a_space="quad", kappa=0.0)
+    assert np.abs(P0.residual(u, b) - I1.residual(u, b)).max() <= 1e-14
+    assert abs(P0.jacobian(u) - I1.jacobian(u)).max() <= 1e-14
