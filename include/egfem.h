@@ -110,11 +110,26 @@ typedef struct {
     int32_t c_kind;      /* egfem_g_kind of the reaction nonlinearity               */
     double c_p;
     double c_scale;
-    int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM), 2 or 3                 */
+    int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM; the only Lagrange choice), or
+                            the degree k of I_k when c_space is EGFEM_W_QUADRATURE     */
     double gamma;        /* reaction coefficient                                     */
     double kappa;        /* constant part of the coefficient                         */
     double a_shift;      /* EGFEM_G_GRADPOW: the shift added to ||grad u||^2 (else unused) */
+    int32_t a_space;     /* egfem_w_space of W_a (a_degree is then k of I_k)          */
+    int32_t c_space;     /* egfem_w_space of W_c                                      */
 } egfem_problem;
+
+/* The approximation space W of a nonlinearity (Sec. 3.2).  EGFEM_W_QUADRATURE is Case 3's
+ * I_k: the basis w_l delta_{x_l} on the points of a symmetric degree-k quadrature rule of
+ * every cell (triangle: k = 1..4 with 1, 3, 4, 6 points; tetrahedron: k = 1..3 with 1, 4, 5
+ * points), so that T_ilk = w_l grad phi_k(x_l) . grad phi_i(x_l) and M_il = w_l phi_i(x_l),
+ * and the EGFEM reproduces the standard Galerkin approach integrated by that rule.  Its
+ * nodes are never shared (n_wa = points x n_cells, numbered cell by cell); it needs the
+ * element-local operator (EGFEM_OP_MATRIX_FREE). */
+typedef enum {
+    EGFEM_W_LAGRANGE = 0,
+    EGFEM_W_QUADRATURE = 1
+} egfem_w_space;
 
 typedef struct {
     double newton_rtol;      /* stop when ||r||_2 <= newton_rtol * ||r(u0)||_2 (default 1e-10) */

@@ -126,6 +126,7 @@ struct egfem_t {
     // element-local operator (EGFEM_OP_MATRIX_FREE)
     double *cell_S = nullptr, *cell_E = nullptr;
     MfLocal mf_loc{};
+    MfLocal mf_loc_c{};                 // W_c = I_k: the reaction's rule (nw = 0: W_c = P1)
     // batch (egfem_batch_build): instance b owns rows [inst_off[b], inst_off[b+1])
     int32_t nb = 0;
     std::vector<int64_t> inst_off;
@@ -171,7 +172,7 @@ int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     MfArgs M{};
     M.n_cells = h->ncells; M.n_rows = h->n; M.dim = DIM;
     M.verts = h->cell_verts; M.S = h->cell_S; M.vol = h->cell_vol; M.v2c_ptr = h->v2c_ptr; M.v2c = h->v2c;
-    M.E = h->cell_E; M.loc = h->mf_loc; M.nl = h->nl;
+    M.E = h->cell_E; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c; M.nl = h->nl;
     mf_cell_kernel<DIM><<<unsigned((h->ncells + 255) / 256), 256, 0, s>>>(M, A.u);
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
     switch (h->maxc_tpl) {
@@ -483,16 +484,42 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
         if (kind != EGFEM_G_NONE && (deg < 1 || deg > 3)) { g_last_error = std::string(what) + ": degree must be 1, 2 or 3"; return EGFEM_ERR_INVALID_ARG; }
         return EGFEM_OK;
     };
-    EG_TRY(check_g(prob->a_kind, prob->a_p, prob->a_degree, "a"));
-    EG_TRY(check_g(prob->c_kind, prob->c_p, prob->c_degree, "c"));
-    if (prob->c_kind != EGFEM_G_NONE && prob->c_degree != 1) { g_last_error = "reaction space W_c must be P1"; return EGFEM_ERR_UNSUPPORTED; }
+    if ((prob->a_space != EGFEM_W_LAGRANGE && prob->a_space != EGFEM_W_QUADRATURE) ||
+        (prob->c_space != EGFEM_W_LAGRANGE && prob->c_space != EGFEM_W_QUADRATURE)) {
+        g_last_error = "unknown W space kind";
+        return EGFEM_ERR_INVALID_ARG;
+    }
+    // quadrature spaces I_k: the rule's point count (0: no such rule)
+    double qa_bary[6][4], qa_w[6], qc_bary[6][4], qc_w[6];
+    const bool quad_a = prob->a_space == EGFEM_W_QUADRATURE && prob->a_kind != EGFEM_G_NONE;
+    const bool quad_c = prob->c_space == EGFEM_W_QUADRATURE && prob->c_kind != EGFEM_G_NONE;
+    const int nqa = quad_a ? quad_rule(mesh->dim, prob->a_degree, qa_bary, qa_w) : 0;
+    const int nqc = quad_c ? quad_rule(mesh->dim, prob->c_degree, qc_bary, qc_w) : 0;
+    if ((quad_a && nqa == 0) || (quad_c && nqc == 0)) {
+        g_last_error = "quadrature space I_k: k must be 1..4 on triangles, 1..3 on tetrahedra";
+        return EGFEM_ERR_INVALID_ARG;
+    }
+    if (!quad_a) EG_TRY(check_g(prob->a_kind, prob->a_p, prob->a_degree, "a"));
+    else if (prob->a_kind < EGFEM_G_NONE || prob->a_kind > EGFEM_G_GRADPOW ||
+             (prob->a_kind == EGFEM_G_POW && (prob->a_p < 1 || prob->a_p > 8 || prob->a_p != std::floor(prob->a_p)))) {
+        g_last_error = "a: unknown kind or exponent";
+        return EGFEM_ERR_INVALID_ARG;
+    }
+    if (!quad_c) {
+        EG_TRY(check_g(prob->c_kind, prob->c_p, prob->c_degree, "c"));
+        if (prob->c_kind != EGFEM_G_NONE && prob->c_degree != 1) { g_last_error = "Lagrange reaction space W_c must be P1"; return EGFEM_ERR_UNSUPPORTED; }
+    } else if (prob->c_kind < EGFEM_G_NONE || prob->c_kind > EGFEM_G_EXP ||
+               (prob->c_kind == EGFEM_G_POW && (prob->c_p < 1 || prob->c_p > 8 || prob->c_p != std::floor(prob->c_p)))) {
+        g_last_error = "c: unknown kind or exponent";
+        return EGFEM_ERR_INVALID_ARG;
+    }
     if (prob->c_kind == EGFEM_G_GRADPOW) { g_last_error = "c: the gradient nonlinearity is a coefficient"; return EGFEM_ERR_INVALID_ARG; }
     const bool gradc = prob->a_kind == EGFEM_G_GRADPOW;
     if (gradc) {
         // (shift + s)^q on s = ||grad u||^2 >= 0: finite with its derivative at s = 0 when
         // shift > 0, or when shift = 0 and q is 0 or at least 1
         const double q = prob->a_p, sh = prob->a_shift;
-        if (prob->a_degree != 0) { g_last_error = "a: the gradient coefficient lives in W_a = P0 (a_degree 0)"; return EGFEM_ERR_INVALID_ARG; }
+        if (!quad_a && prob->a_degree != 0) { g_last_error = "a: the gradient coefficient lives in W_a = P0 (a_degree 0) or I_k"; return EGFEM_ERR_INVALID_ARG; }
         if (!std::isfinite(q) || !std::isfinite(sh) || sh < 0.0 || (sh == 0.0 && q != 0.0 && q < 1.0)) {
             g_last_error = "a: gradient exponent/shift must give a finite (shift + s)^q and derivative at s = 0";
             return EGFEM_ERR_INVALID_ARG;
@@ -503,10 +530,10 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     if (opts) h->opts = *opts;
     if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
     if (h->opts.op != EGFEM_OP_CSF && h->opts.op != EGFEM_OP_MATRIX_FREE) { g_last_error = "unknown operator variant"; return EGFEM_ERR_INVALID_ARG; }
-    if (gradc && h->opts.op != EGFEM_OP_MATRIX_FREE) {
-        // the P0 tensor T_iKk is the cell stiffness S^K itself: the element-local operator
-        // evaluates it without a stored tensor
-        g_last_error = "the gradient coefficient needs the element-local operator (EGFEM_OP_MATRIX_FREE)";
+    if ((gradc || quad_a || quad_c) && h->opts.op != EGFEM_OP_MATRIX_FREE) {
+        // the P0 and I_k forms are multiples of the cell stiffness S^K (and the I_k mass form a
+        // per-point product): the element-local operator evaluates them without a stored tensor
+        g_last_error = "the gradient coefficient and quadrature spaces need the element-local operator (EGFEM_OP_MATRIX_FREE)";
         return EGFEM_ERR_UNSUPPORTED;
     }
     h->prob = *prob;
@@ -520,18 +547,23 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     HostWSpace Wa, Wc;
     std::vector<int32_t> c2wa, c2wc;
     int nla = 0, nlc = 0;
-    // With the gradient coefficient the stored CSF is that of the constant coefficient: it
-    // fixes the Jacobian's pattern and the Krylov layout (both the P1 graph), while the
-    // element-local kernels evaluate the P0 coefficient.
+    // With the gradient coefficient or a quadrature space the stored CSF is that of the
+    // constant coefficient (without that reaction): it fixes the Jacobian's pattern and the
+    // Krylov layout (both the P1 graph), while the element-local kernels evaluate the
+    // nonlinearity on its own space.
     egfem_problem layout_prob = *prob;
-    if (gradc) { layout_prob.a_kind = EGFEM_G_NONE; layout_prob.a_degree = 1; }
+    const bool mf_a = gradc || quad_a;
+    if (mf_a) { layout_prob.a_kind = EGFEM_G_NONE; layout_prob.a_degree = 1; }
+    if (quad_c) { layout_prob.c_kind = EGFEM_G_NONE; layout_prob.c_degree = 1; }
     st = build_wspace(*mesh, layout_prob.a_kind != EGFEM_G_NONE ? layout_prob.a_degree : 1, Wa, c2wa, nla, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
-    st = build_wspace(*mesh, prob->c_kind != EGFEM_G_NONE ? prob->c_degree : 1, Wc, c2wc, nlc, err);
+    st = build_wspace(*mesh, layout_prob.c_kind != EGFEM_G_NONE ? layout_prob.c_degree : 1, Wc, c2wc, nlc, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     h->nwa = Wa.n; h->nwc = Wc.n;
     h->wa_coords = Wa.coords; h->wc_coords = Wc.coords;
-    if (gradc) { h->nwa = mesh->n_cells; h->wa_coords = cell_centroids(*mesh); }   // W_a = P0
+    if (quad_a) { h->nwa = mesh->n_cells * nqa; h->wa_coords = quad_points(*mesh, nqa, qa_bary); }   // W_a = I_k
+    else if (gradc) { h->nwa = mesh->n_cells; h->wa_coords = cell_centroids(*mesh); }             // W_a = P0
+    if (quad_c) { h->nwc = mesh->n_cells * nqc; h->wc_coords = quad_points(*mesh, nqc, qc_bary); }  // W_c = I_k
     HostCSF H;
     st = build_csf(*mesh, layout_prob, Wa, c2wa, nla, Wc, c2wc, nlc, H, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
@@ -572,8 +604,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     EG_TRY(upload(D.dir, H.dir)); EG_TRY(upload(D.rowptr, H.rowptr)); EG_TRY(upload(D.cols, H.cols));
     EG_TRY(upload(h->tmap, tmap));
     EG_TRY(upload(h->wa_kind, Wa.kind)); EG_TRY(upload(h->wa_sup, Wa.sup));
-    if (prob->a_kind != EGFEM_G_NONE && !gradc) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
-    if (prob->c_kind != EGFEM_G_NONE) {
+    if (prob->a_kind != EGFEM_G_NONE && !mf_a) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
+    if (prob->c_kind != EGFEM_G_NONE && !quad_c) {
         EG_TRY(upload(h->wc_kind, Wc.kind)); EG_TRY(upload(h->wc_sup, Wc.sup));
         EG_TRY(dalloc(h->wc_val, size_t(h->nwc))); EG_TRY(dalloc(h->wc_gp, size_t(h->nwc)));
     }
@@ -601,7 +633,14 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
             MfLocal &L = h->mf_loc;
             L = MfLocal{};
             const int p = prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1;
-            if (prob->a_kind != EGFEM_G_NONE && !gradc) {
+            if (quad_a && !gradc) {
+                // I_k: the rule's points and weights (w_l / |K|, summing to 1)
+                for (int l = 0; l < nqa; ++l) {
+                    for (int a = 0; a < 4; ++a) L.w[l][a] = a < nv ? qa_bary[l][a] : 0.0;
+                    L.iota[l] = qa_w[l];
+                }
+                L.nw = nqa;
+            } else if (prob->a_kind != EGFEM_G_NONE && !gradc) {
                 auto add = [&](const double *w, int kind) {
                     for (int a = 0; a < 4; ++a) L.w[L.nw][a] = a < nv ? w[a] : 0.0;
                     L.iota[L.nw] = basis_integral(d, p, kind);
@@ -625,6 +664,13 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
                 }
                 if (L.nw > MF_MAXW) { g_last_error = "matrix-free operator supports at most 10 local W nodes"; return EGFEM_ERR_UNSUPPORTED; }
             }
+            MfLocal &Lc = h->mf_loc_c;
+            Lc = MfLocal{};
+            for (int l = 0; l < nqc; ++l) {
+                for (int a = 0; a < 4; ++a) Lc.w[l][a] = a < nv ? qc_bary[l][a] : 0.0;
+                Lc.iota[l] = qc_w[l];
+            }
+            Lc.nw = nqc;
         }
     }
     h->nl.a_kind = prob->a_kind; h->nl.a_pi = gradc ? 0 : int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
@@ -820,8 +866,8 @@ egfem_status egfem_set_kappa(egfem_handle h, const double *d_kappa, egfem_stream
 
 egfem_status egfem_pointwise(egfem_handle h, const double *d_u, double *d_w, double *d_wprime, egfem_stream stream) {
     if (!h || !d_u) return EGFEM_ERR_INVALID_ARG;
-    if (h->nl.a_kind == EGFEM_G_GRADPOW) {
-        g_last_error = "the gradient coefficient is evaluated per cell inside the element-local operator";
+    if (h->nl.a_kind == EGFEM_G_GRADPOW || h->prob.a_space == EGFEM_W_QUADRATURE) {
+        g_last_error = "the gradient coefficient and I_k are evaluated per cell inside the element-local operator";
         return EGFEM_ERR_UNSUPPORTED;
     }
     EG_CUDA(cudaSetDevice(h->device));
@@ -1302,8 +1348,8 @@ extern "C" {
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda, double *d_grad_kappa,
                            egfem_stats *stats, egfem_stream stream) {
     if (!h || !d_u || !d_dJdu || !d_lambda) return EGFEM_ERR_INVALID_ARG;
-    if (d_grad_kappa && h->nl.a_kind == EGFEM_G_GRADPOW) {
-        g_last_error = "dJ/dkappa is not available with the gradient coefficient";
+    if (d_grad_kappa && (h->nl.a_kind == EGFEM_G_GRADPOW || h->prob.a_space == EGFEM_W_QUADRATURE)) {
+        g_last_error = "dJ/dkappa is not available with the gradient coefficient or I_k";
         return EGFEM_ERR_UNSUPPORTED;
     }
     EG_CUDA(cudaSetDevice(h->device));

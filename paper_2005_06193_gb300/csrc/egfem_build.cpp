@@ -108,6 +108,54 @@ void cell_stiffness(const egfem_mesh &m, std::vector<double> &vol, std::vector<d
     }
 }
 
+// Symmetric quadrature rules of degree k for the quadrature spaces I_k (Sec. 3.2, Case 3):
+// Dunavant's triangle rules (k = 1..4) and the tetrahedron rules of degree 1..3, as
+// barycentric points with weights relative to the cell volume (summing to 1).  Writes at most
+// 6 points into bary / w and returns their number, or 0 for a degree not tabulated.
+int quad_rule(int dim, int k, double bary[][4], double *w) {
+    int n = 0;
+    auto add = [&](double l0, double l1, double l2, double l3, double wt) {
+        bary[n][0] = l0; bary[n][1] = l1; bary[n][2] = l2; bary[n][3] = l3; w[n] = wt; ++n;
+    };
+    auto s21 = [&](double a, double wt) {            // the 3 permutations of (1 - 2a, a, a)
+        const double b = 1.0 - 2.0 * a;
+        add(b, a, a, 0, wt); add(a, b, a, 0, wt); add(a, a, b, 0, wt);
+    };
+    auto s31 = [&](double a, double wt) {            // the 4 permutations of (1 - 3a, a, a, a)
+        const double b = 1.0 - 3.0 * a;
+        add(b, a, a, a, wt); add(a, b, a, a, wt); add(a, a, b, a, wt); add(a, a, a, b, wt);
+    };
+    if (dim == 2) {
+        switch (k) {
+            case 1: add(1.0 / 3, 1.0 / 3, 1.0 / 3, 0, 1.0); break;
+            case 2: s21(1.0 / 6, 1.0 / 3); break;
+            case 3: add(1.0 / 3, 1.0 / 3, 1.0 / 3, 0, -0.5625); s21(0.2, 0.5208333333333333); break;
+            case 4: s21(0.445948490915965, 0.223381589678011); s21(0.091576213509771, 0.109951743655322); break;
+            default: return 0;
+        }
+    } else {
+        switch (k) {
+            case 1: add(0.25, 0.25, 0.25, 0.25, 1.0); break;
+            case 2: s31(0.1381966011250105, 0.25); break;
+            case 3: add(0.25, 0.25, 0.25, 0.25, -0.8); s31(1.0 / 6, 0.45); break;
+            default: return 0;
+        }
+    }
+    return n;
+}
+
+// The nodes of I_k: rule point l of cell c is node c * nq + l ([n_cells * nq * dim]).
+std::vector<double> quad_points(const egfem_mesh &m, int nq, const double bary[][4]) {
+    const int d = m.dim, nv = d + 1;
+    std::vector<double> x(size_t(m.n_cells) * nq * d, 0.0);
+    for (int64_t c = 0; c < m.n_cells; ++c)
+        for (int l = 0; l < nq; ++l)
+            for (int a = 0; a < nv; ++a)
+                for (int r = 0; r < d; ++r)
+                    x[(size_t(c) * nq + l) * d + r] += bary[l][a] * m.coords[int64_t(m.cells[c * nv + a]) * d + r];
+    return x;
+}
+
 // The nodes of a P0 space: one per cell, at its centroid ([n_cells * dim]).
 std::vector<double> cell_centroids(const egfem_mesh &m) {
     const int d = m.dim, nv = d + 1;
@@ -538,10 +586,20 @@ extern "C" egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem
     std::string err;
     egfem_status st = validate_mesh(*mesh, err);
     if (st != EGFEM_OK) return st;
-    if (prob->a_kind == EGFEM_G_GRADPOW) {
-        // W_a = P0: the form is T_iKk = S^K_ik, which the element-local operator reads per
-        // cell (no CSF is stored for it); free rows i only, as for the stored tensor
-        if (prob->a_degree != 0) return EGFEM_ERR_INVALID_ARG;
+    const bool quad = prob->a_space == EGFEM_W_QUADRATURE;
+    if (prob->a_kind == EGFEM_G_GRADPOW || quad) {
+        // W_a = P0 or I_k: the form is T_ilk = (w_l / |K|) S^K_ik on the cell K of node l
+        // (w_l / |K| = 1 for P0), which the element-local operator reads per cell (no CSF is
+        // stored for it); free rows i only, as for the stored tensor
+        double bary[6][4], wl[6];
+        int nq = 1;
+        wl[0] = 1.0;
+        if (quad) {
+            nq = quad_rule(mesh->dim, prob->a_degree, bary, wl);
+            if (nq == 0) return EGFEM_ERR_INVALID_ARG;
+        } else if (prob->a_degree != 0) {
+            return EGFEM_ERR_INVALID_ARG;
+        }
         const int nv = mesh->dim + 1, ns = nv * (nv + 1) / 2;
         std::vector<double> vol, S;
         cell_stiffness(*mesh, vol, &S);
@@ -550,19 +608,20 @@ extern "C" egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem
             for (int a = 0; a < nv; ++a) {
                 const int32_t i = mesh->cells[c * nv + a];
                 if (mesh->dirichlet && mesh->dirichlet[i]) continue;
-                for (int b = 0; b < nv; ++b) {
-                    const int lo = std::min(a, b), hi = std::max(a, b);
-                    if (I) {
-                        I[cnt] = i; M[cnt] = c; K[cnt] = mesh->cells[c * nv + b];
-                        V[cnt] = S[size_t(c) * ns + lo * nv - (lo * (lo - 1)) / 2 + (hi - lo)];
+                for (int l = 0; l < nq; ++l)
+                    for (int b = 0; b < nv; ++b) {
+                        const int lo = std::min(a, b), hi = std::max(a, b);
+                        if (I) {
+                            I[cnt] = i; M[cnt] = c * nq + l; K[cnt] = mesh->cells[c * nv + b];
+                            V[cnt] = wl[l] * S[size_t(c) * ns + lo * nv - (lo * (lo - 1)) / 2 + (hi - lo)];
+                        }
+                        ++cnt;
                     }
-                    ++cnt;
-                }
             }
         *count = cnt;
-        if (n_wa) *n_wa = mesh->n_cells;
+        if (n_wa) *n_wa = mesh->n_cells * nq;
         if (wa_coords) {
-            const std::vector<double> x = cell_centroids(*mesh);
+            const std::vector<double> x = quad ? quad_points(*mesh, nq, bary) : cell_centroids(*mesh);
             std::memcpy(wa_coords, x.data(), x.size() * sizeof(double));
         }
         return EGFEM_OK;

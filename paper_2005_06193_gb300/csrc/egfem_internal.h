@@ -128,6 +128,8 @@ egfem_status validate_mesh(const egfem_mesh &mesh, std::string &err);
 double basis_integral(int dim, int degree, int kind);   // int_K eta_m / |K| by node kind
 void cell_stiffness(const egfem_mesh &mesh, std::vector<double> &vol, std::vector<double> *S);
 std::vector<double> cell_centroids(const egfem_mesh &mesh);
+int quad_rule(int dim, int k, double bary[][4], double *w);
+std::vector<double> quad_points(const egfem_mesh &mesh, int nq, const double bary[][4]);
 void set_last_error(const std::string &msg);            // text returned by egfem_last_error()
 
 }  // namespace egfem

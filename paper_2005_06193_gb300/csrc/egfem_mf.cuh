@@ -40,6 +40,7 @@ struct MfArgs {
     const int32_t *v2c;                 // cells of each vertex
     double *E;                          // [(2 dim + 3) n_cells] abar, S u, c per cell
     MfLocal loc;
+    MfLocal loc_c;                      // W_c = I_k (nw > 0): the reaction's rule
     Nonlin nl;
 };
 
@@ -155,19 +156,24 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
     double r = 0.0, diag_extra = 0.0;
     for (int64_t t = M.v2c_ptr[row]; t < M.v2c_ptr[row + 1]; ++t) {
         const int64_t cell = M.v2c[t];
-        int32_t vk[NV];
+        int32_t vk[NV], lcb[NV];
 #pragma unroll
         for (int b = 0; b < NV; ++b) vk[b] = M.verts[cell * NV + b];
         int a = 0;
 #pragma unroll
         for (int b = 1; b < NV; ++b) if (vk[b] == row) a = b;
+        // the row's local Jacobian column of each of the cell's vertices
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+            lcb[b] = 0;
+            for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lcb[b] = c; break; }
+        }
         const double *E = M.E + cell * (2 * DIM + 3);
         const double abar = E[0], su = E[1 + a];
         r += abar * su;
 #pragma unroll
         for (int b = 0; b < NV; ++b) {
-            int lc = 0;
-            for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lc = c; break; }
+            const int lc = lcb[b];
             double v = nl.picard ? 0.0 : su * E[1 + NV + b];
             if (b != a) {
                 // abar S_ab off the diagonal; on it abar S_aa = -sum_{b != a} abar S_ab
@@ -177,7 +183,28 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             }
             J[lc * CSF_BLOCK] += v;
         }
-        if (nl.c_kind != EGFEM_G_NONE) {
+        if (nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
+            // gamma M^c c with W_c = I_k (Sec. 3.2 Case 3): M_al = w_l lambda_a(x_l), c_l =
+            // g_c(u(x_l)), so row a gets gamma sum_l w_l lambda_a(x_l) g_c(u(x_l)) and the
+            // Jacobian gamma sum_l w_l lambda_a(x_l) g_c'(u(x_l)) lambda_b(x_l)
+            double uk[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) uk[b] = A.u[vk[b]];
+            const double gv = nl.gamma * M.vol[cell];
+            for (int l = 0; l < M.loc_c.nw; ++l) {
+                double uq = 0.0;
+#pragma unroll
+                for (int b = 0; b < NV; ++b) uq += M.loc_c.w[l][b] * uk[b];
+                double g, gp;
+                g_eval(nl.c_kind, nl.c_pi, nl.c_scale, uq, g, gp);
+                const double wa = gv * M.loc_c.iota[l] * M.loc_c.w[l][a];
+                r += wa * g;
+                if (!nl.picard) {
+#pragma unroll
+                    for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += wa * gp * M.loc_c.w[l][b];
+                }
+            }
+        } else if (nl.c_kind != EGFEM_G_NONE) {
             // gamma M^c c with W_c = P1: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
             const double m0 = M.vol[cell] / double((DIM + 1) * (DIM + 2));
 #pragma unroll
@@ -186,9 +213,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
                 g_eval(nl.c_kind, nl.c_pi, nl.c_scale, A.u[vk[b]], g, gp);
                 const double mab = (b == a) ? 2.0 * m0 : m0;
                 r += nl.gamma * mab * g;
-                int lc = 0;
-                for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lc = c; break; }
-                if (!nl.picard) J[lc * CSF_BLOCK] += nl.gamma * mab * gp;
+                if (!nl.picard) J[lcb[b] * CSF_BLOCK] += nl.gamma * mab * gp;
             }
         }
     }

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libegfem.so")
 
 G_NONE, G_POW, G_EXP, G_GRADPOW = 0, 1, 2, 3
+W_LAGRANGE, W_QUADRATURE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 OP_CSF, OP_MATRIX_FREE = 0, 1
 ITER_NEWTON, ITER_PICARD = 0, 1
@@ -43,7 +44,8 @@ class Problem(ctypes.Structure):
     _fields_ = [("a_kind", ctypes.c_int32), ("a_p", ctypes.c_double), ("a_scale", ctypes.c_double),
                 ("a_degree", ctypes.c_int32), ("c_kind", ctypes.c_int32), ("c_p", ctypes.c_double),
                 ("c_scale", ctypes.c_double), ("c_degree", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("kappa", ctypes.c_double), ("a_shift", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("a_shift", ctypes.c_double), ("a_space", ctypes.c_int32),
+                ("c_space", ctypes.c_int32)]
 
 
 class Options(ctypes.Structure):
@@ -158,9 +160,12 @@ def selftest_grid_barrier(blocks: int, arrive: int, wait_ms: float):
     return list(ok), err.value
 
 
-def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_scale=1.0, gamma=0.0, kappa=1.0) -> Problem:
+def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_scale=1.0, gamma=0.0, kappa=1.0,
+                 a_space="lagrange", c_space="lagrange") -> Problem:
     """a = (kind, exponent[, shift]): ("pow", p), ("exp",), ("gradpow", q, shift) for the gradient
-    coefficient (shift + |grad u|^2)^q (with a_degree=0); c likewise for the reaction."""
+    coefficient (shift + |grad u|^2)^q (with a_degree=0); c likewise for the reaction.
+    a_space / c_space = "quad" selects the quadrature space I_k with k = a_degree / c_degree."""
+    spaces = {"lagrange": W_LAGRANGE, "quad": W_QUADRATURE}
     kinds = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP, "gradpow": G_GRADPOW}
     p = Problem()
     p.a_kind = kinds[a[0] if a else None]
@@ -171,6 +176,7 @@ def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_sc
     p.c_p = float(c[1]) if c and len(c) > 1 else 1.0
     p.c_scale, p.c_degree = float(c_scale), int(c_degree)
     p.gamma, p.kappa = float(gamma), float(kappa)
+    p.a_space, p.c_space = spaces[a_space], spaces[c_space]
     return p
 
 

@@ -171,3 +171,50 @@ def test_bad_gradient_coefficient_is_rejected_before_any_cuda_call(egf):
         assert egf.lib().egfem_build(ctypes.byref(m), ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(h)) == want
         assert not h.value
     del keep
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 4, 1), (2, 4, 2), (2, 4, 3), (2, 4, 4), (3, 2, 1), (3, 2, 2), (3, 2, 3)])
+def test_quadrature_space_form_matches_oracle(egf, dim, n, k):
+    """W_a = I_k: the form the element-local operator applies, T_ilk = w_l S^K_ik / |K|, and the
+    node coordinates (the rule's points on every cell) equal the oracle's, whose rule is pinned
+    by its exactness; the library's rule table is written independently."""
+    mesh = wl.unit_square_mesh(n) if dim == 2 else wl.unit_cube_mesh(n)
+    I, M, K, V, Wc = egf.inspect_tensor(mesh, egf.make_problem(a=("pow", 2), a_degree=k, a_space="quad"))
+    P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=k, a_space="quad")
+    assert len(Wc) == P.nw == mesh.n_cells * len(oracle.sym_rule(dim, k)[1])
+    oI, oM, oK, oV = P.T_coo()
+    perm = _match_w(P.space_coords(0), Wc)
+    scale = np.abs(oV).max()
+    orc = {(i, perm[m], kk): v for i, m, kk, v in zip(oI, oM, oK, oV) if not mesh.dirichlet[i]}
+    lib = {}
+    for i, m, kk, v in zip(I, M, K, V):
+        lib[(i, m, kk)] = lib.get((i, m, kk), 0.0) + v
+    assert set(lib) == set(orc)
+    for key, v in lib.items():
+        assert abs(orc[key] - v) <= 1e-13 * scale, (key, v, orc[key])
+
+
+def test_table1_quadrature_space_size_in_the_library(egf):
+    """Table 1: the EGFEM with I_4 on the 64 x 64 grid has 4225 + 6 x 8192 = 53377 unknowns."""
+    mesh = wl.unit_square_mesh(64)
+    _, _, _, _, W = egf.inspect_tensor(mesh, egf.make_problem(a=("pow", 2), a_degree=4, a_space="quad"))
+    assert mesh.n_nodes + len(W) == 53377
+
+
+def test_bad_quadrature_space_is_rejected_before_any_cuda_call(egf):
+    import ctypes
+    mesh = wl.unit_cube_mesh(2)
+    m, keep = egf.egfem._mesh_struct(mesh)
+    mf = egf.default_options(op=egf.OP_MATRIX_FREE)
+    cases = [(egf.make_problem(a=("pow", 2), a_degree=4, a_space="quad"), mf, 1),       # no degree-4 tetrahedron rule
+             (egf.make_problem(a=("pow", 2), a_degree=2, a_space="quad"), egf.default_options(op=egf.OP_CSF), 10),
+             (egf.make_problem(a=None, c=("pow", 2), c_degree=0, c_space="quad", gamma=1.0), mf, 1)]
+    for prob, opts, want in cases:
+        h = ctypes.c_void_p()
+        assert egf.lib().egfem_build(ctypes.byref(m), ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(h)) == want
+        assert not h.value
+    bad = egf.make_problem()
+    bad.a_space = 7
+    h = ctypes.c_void_p()
+    assert egf.lib().egfem_build(ctypes.byref(m), ctypes.byref(bad), ctypes.byref(mf), ctypes.byref(h)) == 1
+    del keep

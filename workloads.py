@@ -186,6 +186,12 @@ def minsurf_source(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     return -((uxx + uyy) / np.sqrt(Q) - qhq / Q ** 1.5)
 
 
+def quadratic_source(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """d for -lap u + u^2 = d with exact solution u = x y (x + y) (Sec. 5, quadratic example):
+    -lap u = -2 (x + y) and u^2 = x^2 y^2 (x + y)^2."""
+    return -2.0 * (x + y) + (x * y * (x + y)) ** 2
+
+
 def smooth_source_3d(x: np.ndarray, y: np.ndarray, z: np.ndarray) -> np.ndarray:
     """A smooth 3D source, 10 sin(pi x) sin(pi y) sin(pi z) (test input for 3D cases)."""
     return 10.0 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
