@@ -310,6 +310,79 @@ def batched_p3_extra(torch, P, dev, count, barrier):
             "rows": int(hb.sizes.n_nodes)}
 
 
+def _mf_kernel_line(prof, hbm, fp64_peak):
+    pm = next(p for p in prof if p["name"].startswith("tensor_action"))
+    return {"kernel": "mf_cell_kernel + mf_row_kernel", "ms": pm["ms"], "bytes_per_launch": pm["bytes"],
+            "achieved_gbs": pm["bytes"] / (pm["ms"] / 1e3) / 1e9, "frac_hbm": pm["bytes"] / (pm["ms"] / 1e3) / 1e9 / hbm,
+            "fp64_tflops": pm["flops"] / (pm["ms"] / 1e3) / 1e12,
+            "fp64_frac_of_peak": pm["flops"] / (pm["ms"] / 1e3) / 1e12 / fp64_peak}
+
+
+def gradient_setup(torch, P, dev, n):
+    """Minimal surface on the n x n square (Sec. 5): a = (1 + |grad u|^2)^(-1/2) on W = P0,
+    u_D = x y (x + y), manufactured source sampled at cell centroids, Newton from the boundary
+    data with a smooth interior bump.  Returns (handle, d, u0)."""
+    import workloads as wl
+    mesh = wl.unit_square_mesh(n)
+    h = P.Handle(mesh, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
+                 P.default_options(op=P.OP_MATRIX_FREE))
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    ue = wl.minsurf_exact(x, y)
+    xc = wl.cell_centroids(mesh)
+    f = torch.tensor(wl.minsurf_source(xc[:, 0], xc[:, 1]), device=dev, dtype=torch.float64)
+    d = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
+    h.load_cellwise(f, d)
+    d += torch.tensor(ue * mesh.dirichlet, device=dev)
+    u0 = torch.tensor(ue + 0.2 * np.sin(np.pi * x) * np.sin(np.pi * y), device=dev, dtype=torch.float64)
+    return h, d, u0
+
+
+def quadrature_setup(torch, P, dev, n):
+    """The quadratic example -lap u + u^2 = d on the n x n square (Sec. 5) with W_c = I_3 (the
+    paper's Case 3 choice for it), u_D = x y (x + y), manufactured source at cell centroids,
+    Newton from the boundary data.  Returns (handle, d, u0)."""
+    import workloads as wl
+    mesh = wl.unit_square_mesh(n)
+    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, kappa=1.0, c=("pow", 2), c_degree=3, c_space="quad",
+                                      gamma=1.0), P.default_options(op=P.OP_MATRIX_FREE))
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    uD = wl.minsurf_exact(x, y) * mesh.dirichlet
+    xc = wl.cell_centroids(mesh)
+    f = torch.tensor(wl.quadratic_source(xc[:, 0], xc[:, 1]), device=dev, dtype=torch.float64)
+    d = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
+    h.load_cellwise(f, d)
+    d += torch.tensor(uD, device=dev)
+    return h, d, torch.tensor(uD, device=dev, dtype=torch.float64)
+
+
+def next_row_extra(torch, P, dev, n, steps, barrier, setup, workload, hbm, fp64_peak):
+    h, d, u0 = setup(torch, P, dev, n)
+    u = u0.clone()
+    h.newton_solve(u, d)
+    torch.cuda.synchronize()
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        u.copy_(u0)
+        stats.append(h.newton_solve(u, d))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = stats[-1]
+    prof = h.profile_kernels(u, d, reps=20)
+    out = {"workload": workload, "value": steps / (ms / 1e3), "unit": "solves/s", "ms_per_step": ms / steps,
+           "newton_iters": st.newton_iters, "krylov_iters": int(st.krylov_iters),
+           "final_rel_residual": st.res_final / st.res0, "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+           "n_wa": h.sizes.n_wa, "n_wc": h.sizes.n_wc,
+           "tensor_action": _mf_kernel_line(prof, hbm, fp64_peak),
+           "kernels": [{"name": p["name"], "ms": p["ms"]} for p in prof]}
+    h.close()
+    return out
+
+
 def timed_solves(torch, h, d, u, steps, rank_barrier):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
@@ -337,13 +410,15 @@ def main():
     ap.add_argument("--no-mf", action="store_true")
     ap.add_argument("--no-picard", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the gradient-coefficient and I_k lines")
     ap.add_argument("--batch-instances", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--p3-instances", type=int, default=32)
     ap.add_argument("--ref-newton-steps", type=int, default=5)
     ap.add_argument("--ref-krylov-iters", type=int, default=3500)
-    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed"],
-                    help="build the workload, run the per-kernel profile once at u = 0 and print it (for ncu captures)")
+    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed", "gradient", "quadrature"],
+                    help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
+                         "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -367,6 +442,12 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.profile_only in ("gradient", "quadrature"):
+        setup = gradient_setup if args.profile_only == "gradient" else quadrature_setup
+        hp, d, u0 = setup(torch, P, torch.device("cuda", local), args.n)
+        print(json.dumps(hp.profile_kernels(u0, d, reps=1)), flush=True)
+        hp.close()
+        return
     mesh, f_cell = make_workload(args.n)
     prob = P.make_problem(a=("pow", 2), a_degree=2)
     if args.profile_only:
@@ -514,6 +595,13 @@ def main():
                                    "frac_hbm": pm["bytes"] / (pm["ms"] / 1e3) / 1e9 / hbm,
                                    "bytes_per_launch": pm["bytes"], "speedup_vs_csf": csf["ms"] / pm["ms"]}
         hmf.close()
+
+    if not args.no_next:
+        # NEXT rows: the gradient coefficient (P0) and a quadrature space (I_3), same grid
+        out["gradient_minsurf"] = next_row_extra(torch, P, dev, args.n, min(args.steps, 3), barrier, gradient_setup,
+                                                 f"minimal_surface_p0_{args.n}x{args.n}", hbm, fp64_peak)
+        out["quadrature_i3"] = next_row_extra(torch, P, dev, args.n, min(args.steps, 3), barrier, quadrature_setup,
+                                              f"quadratic_reaction_i3_{args.n}x{args.n}", hbm, fp64_peak)
 
     if not args.no_batch:
         out["batched_adjoint"] = batched_adjoint_extra(torch, P, dev, args.batch_instances, args.batch_n, barrier)

@@ -1250,9 +1250,19 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     // FP64 operations: 2 per leaf (D and J1), per fibre the residual, diagonal and J2 scatter
     // (6; 12 when g is evaluated per fibre), 4 per reaction entry, 2 per local column, and
     // the nodal pass (interpolation and g, about 6 per node)
-    double csf_flops = h->opts.op == EGFEM_OP_MATRIX_FREE ? L * 4 + F * 12 + RX * 10 + CE * 2
-                                                           : L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) +
-                                                                 CE * 2 + (NWA + NWC) * 6;
+    double csf_flops = L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) + CE * 2 + (NWA + NWC) * 6;
+    if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
+        // cell pass: S u in difference form (3 per off-diagonal pair), then per local W node
+        // the interpolation, g and the c^K update (4 nv + 6; the gradient coefficient: 3 nv and
+        // pow, counted as 20); row pass, per (row, cell) pair: r and the nv Jacobian entries
+        // (6 nv + 2), plus the reaction (P1 W_c: 6 per vertex; I_k: per point 5 nv + 8)
+        const double NC = double(h->ncells), nv = h->dim + 1;
+        const double nw = h->nl.a_kind == EGFEM_G_GRADPOW ? 0.0 : double(h->mf_loc.nw);
+        const double coef = h->nl.a_kind == EGFEM_G_GRADPOW ? 3 * nv + 20 : nw * (4 * nv + 6);
+        const double react = h->nl.c_kind == EGFEM_G_NONE ? 0.0
+                             : h->mf_loc_c.nw > 0 ? double(h->mf_loc_c.nw) * (5 * nv + 8) : 6 * nv;
+        csf_flops = NC * (3 * nv * (nv - 1) + coef) + NC * nv * (6 * nv + 2 + react);
+    }
     const char *ta_name = h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused";
     if (!std::is_same<V, double>::value && h->opts.op == EGFEM_OP_CSF) {
         // mixed path: the mixed-precision tensor action (FP64 residual, FP32 Jacobian).  Nodal
