@@ -127,6 +127,7 @@ struct egfem_t {
     double *cell_S = nullptr, *cell_E = nullptr;
     MfLocal mf_loc{};
     MfLocal mf_loc_c{};                 // W_c = I_k: the reaction's rule (nw = 0: W_c = P1)
+    int32_t mf_ne = 0;                  // doubles per cell record of the element-local operator
     // batch (egfem_batch_build): instance b owns rows [inst_off[b], inst_off[b+1])
     int32_t nb = 0;
     std::vector<int64_t> inst_off;
@@ -172,7 +173,7 @@ int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     MfArgs M{};
     M.n_cells = h->ncells; M.n_rows = h->n; M.dim = DIM;
     M.verts = h->cell_verts; M.S = h->cell_S; M.vol = h->cell_vol; M.v2c_ptr = h->v2c_ptr; M.v2c = h->v2c;
-    M.E = h->cell_E; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c; M.nl = h->nl;
+    M.E = h->cell_E; M.ne = h->mf_ne; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c; M.nl = h->nl;
     mf_cell_kernel<DIM><<<unsigned((h->ncells + 255) / 256), 256, 0, s>>>(M, A.u);
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
     switch (h->maxc_tpl) {
@@ -628,7 +629,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
             // per cell: S^K = |K| grad lambda_a . grad lambda_b (packed upper triangle)
             const int d = mesh->dim;
             EG_TRY(upload(h->cell_S, S));
-            EG_TRY(dalloc(h->cell_E, size_t(mesh->n_cells) * size_t(2 * d + 3)));
+            h->mf_ne = 2 * d + 3 + (nqc > 0 ? (d + 1) + (d + 1) * (d + 2) / 2 : 0);
+            EG_TRY(dalloc(h->cell_E, size_t(mesh->n_cells) * size_t(h->mf_ne)));
             // local W nodes of the reference cell in the W numbering's local order
             MfLocal &L = h->mf_loc;
             L = MfLocal{};
@@ -1244,7 +1246,7 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
         // cells: vertices, packed S, |K|, the per-cell record written and read back;
         // rows: vertex-to-cell lists, local columns and the outputs
-        const double NC = double(h->ncells), nv = h->dim + 1, ns = nv * (nv + 1) / 2, ne = 2 * h->dim + 3;
+        const double NC = double(h->ncells), nv = h->dim + 1, ns = nv * (nv + 1) / 2, ne = double(h->mf_ne);
         csf_bytes = NC * (4 * nv + 8 * ns + 8 + 2 * 8 * ne) + N * (8 + 4 * 2 * nv) + CE * (8 + mb) + N * (8 + 8 + 8 + 8 + 1) + SM;
     }
     // FP64 operations: 2 per leaf (D and J1), per fibre the residual, diagonal and J2 scatter
@@ -1254,14 +1256,18 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
         // cell pass: S u in difference form (3 per off-diagonal pair), then per local W node
         // the interpolation, g and the c^K update (4 nv + 6; the gradient coefficient: 3 nv and
-        // pow, counted as 20); row pass, per (row, cell) pair: r and the nv Jacobian entries
-        // (6 nv + 2), plus the reaction (P1 W_c: 6 per vertex; I_k: per point 5 nv + 8)
+        // the power, counted as 12); row pass, per (row, cell) pair: r and the nv Jacobian
+        // entries (6 nv + 2)
         const double NC = double(h->ncells), nv = h->dim + 1;
         const double nw = h->nl.a_kind == EGFEM_G_GRADPOW ? 0.0 : double(h->mf_loc.nw);
-        const double coef = h->nl.a_kind == EGFEM_G_GRADPOW ? 3 * nv + 20 : nw * (4 * nv + 6);
-        const double react = h->nl.c_kind == EGFEM_G_NONE ? 0.0
-                             : h->mf_loc_c.nw > 0 ? double(h->mf_loc_c.nw) * (5 * nv + 8) : 6 * nv;
-        csf_flops = NC * (3 * nv * (nv - 1) + coef) + NC * nv * (6 * nv + 2 + react);
+        const double coef = h->nl.a_kind == EGFEM_G_GRADPOW ? 3 * nv + 12 : nw * (4 * nv + 6);
+        // reaction: P1 W_c, 6 per vertex in the row pass; I_k, per point nv + 6 + 2 nv + 3 ns in
+        // the cell pass and nv + 1 per (row, cell) pair
+        const double nsd = nv * (nv + 1) / 2;
+        const double react_row = h->nl.c_kind == EGFEM_G_NONE ? 0.0 : h->mf_loc_c.nw > 0 ? nv + 1 : 6 * nv;
+        const double react_cell = h->nl.c_kind != EGFEM_G_NONE && h->mf_loc_c.nw > 0
+                                      ? double(h->mf_loc_c.nw) * (3 * nv + 6 + 3 * nsd) : 0.0;
+        csf_flops = NC * (3 * nv * (nv - 1) + coef + react_cell) + NC * nv * (6 * nv + 2 + react_row);
     }
     const char *ta_name = h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused";
     if (!std::is_same<V, double>::value && h->opts.op == EGFEM_OP_CSF) {

@@ -38,7 +38,8 @@ struct MfArgs {
     const double *vol;                  // [n_cells]
     const int64_t *v2c_ptr;             // [n_rows + 1]
     const int32_t *v2c;                 // cells of each vertex
-    double *E;                          // [(2 dim + 3) n_cells] abar, S u, c per cell
+    double *E;                          // [ne n_cells] abar, S u, c per cell (+ rho, R with W_c = I_k)
+    int32_t ne;                         // doubles per cell record: 2 dim + 3, or + (d+1) + (d+1)(d+2)/2
     MfLocal loc;
     MfLocal loc_c;                      // W_c = I_k (nw > 0): the reaction's rule
     Nonlin nl;
@@ -47,6 +48,26 @@ struct MfArgs {
 __device__ __forceinline__ int tri_index(int a, int b, int nv) {   // packed upper triangle
     if (a > b) { const int t = a; a = b; b = t; }
     return a * nv - (a * (a - 1)) / 2 + (b - a);
+}
+
+// t = base^q for the gradient coefficient.  When 4q is an integer of magnitude <= 8 (the
+// minimal surface q = -1/2, the p-Laplacian q = (p - 2)/2 for p = 3/2, 5/2, 3, ...) it is a
+// product of square roots and powers of base, which costs far fewer FP64 operations than a
+// general power; otherwise pow.  base > 0 whenever q < 0 (the build requires a positive shift).
+__device__ __forceinline__ double gradpow_base(double base, double q) {
+    const double q4 = 4.0 * q;
+    if (q4 == rint(q4) && fabs(q4) <= 8.0) {
+        int k = int(q4);
+        double r = base;                       // k quarter powers of base
+        if (k % 4 == 0) { k /= 4; }
+        else if (k % 2 == 0) { r = sqrt(base); k /= 2; }
+        else { r = sqrt(sqrt(base)); }
+        const int e = k < 0 ? -k : k;
+        double t = 1.0;
+        for (int i = 0; i < e; ++i) t *= r;
+        return k < 0 ? 1.0 / t : t;
+    }
+    return pow(base, q);
 }
 
 // pass 1: per cell abar_K, (S^K u)_a (difference form), c^K_b
@@ -85,9 +106,12 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
 #pragma unroll
         for (int a = 1; a < NV; ++a) sg += (uk[a] - uk[0]) * su[a];
         sg = fmax(sg * ivol, 0.0);
-        const double base = M.nl.a_shift + sg;
-        const double g = M.nl.a_scale * pow(base, M.nl.a_preal);
-        const double gp = M.nl.a_preal == 0.0 ? 0.0 : M.nl.a_scale * M.nl.a_preal * pow(base, M.nl.a_preal - 1.0);
+        const double base = M.nl.a_shift + sg, q = M.nl.a_preal;
+        const double t = gradpow_base(base, q);
+        const double g = M.nl.a_scale * t;
+        // g' = scale q base^(q-1) = q g / base; at base = 0 (shift 0, so q = 0 or q >= 1) it is
+        // scale for q = 1 and 0 otherwise
+        const double gp = q == 0.0 ? 0.0 : base > 0.0 ? q * g / base : (q == 1.0 ? M.nl.a_scale : 0.0);
         abar = M.nl.kappa + g;
         const double e = 2.0 * gp * ivol;
 #pragma unroll
@@ -107,12 +131,43 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
             for (int b = 0; b < NV; ++b) cb[b] += e * M.loc.w[l][b];
         }
     }
-    double *E = M.E + c * (2 * DIM + 3);
+    double *E = M.E + c * M.ne;
     E[0] = abar;
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
         E[1 + a] = su[a];
         E[1 + NV + a] = cb[a];
+    }
+    if (M.nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
+        // W_c = I_k (Sec. 3.2 Case 3): M_al = w_l lambda_a(x_l) and c_l = g_c(u(x_l)), so the
+        // cell adds rho_a = gamma sum_l w_l lambda_a(x_l) g_c(u(x_l)) to row a's residual and
+        // R_ab = gamma sum_l w_l lambda_a(x_l) lambda_b(x_l) g_c'(u(x_l)) to its Jacobian;
+        // both are evaluated here once per cell and gathered by the row pass
+        double rho[NV], R[NS];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) rho[a] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) R[q] = 0.0;
+        const double gv = M.nl.gamma * M.vol[c];
+        for (int l = 0; l < M.loc_c.nw; ++l) {
+            double uq = 0.0;
+#pragma unroll
+            for (int b = 0; b < NV; ++b) uq += M.loc_c.w[l][b] * uk[b];
+            double g, gp;
+            g_eval(M.nl.c_kind, M.nl.c_pi, M.nl.c_scale, uq, g, gp);
+            const double wl = gv * M.loc_c.iota[l], wg = wl * g, wd = wl * gp;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                const double la = M.loc_c.w[l][a];
+                rho[a] += wg * la;
+#pragma unroll
+                for (int b = a; b < NV; ++b) R[tri_index(a, b, NV)] += wd * la * M.loc_c.w[l][b];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NV; ++a) E[1 + 2 * NV + a] = rho[a];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) E[1 + 3 * NV + q] = R[q];
     }
 }
 
@@ -168,7 +223,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             lcb[b] = 0;
             for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lcb[b] = c; break; }
         }
-        const double *E = M.E + cell * (2 * DIM + 3);
+        const double *E = M.E + cell * M.ne;
         const double abar = E[0], su = E[1 + a];
         r += abar * su;
 #pragma unroll
@@ -184,25 +239,11 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             J[lc * CSF_BLOCK] += v;
         }
         if (nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
-            // gamma M^c c with W_c = I_k (Sec. 3.2 Case 3): M_al = w_l lambda_a(x_l), c_l =
-            // g_c(u(x_l)), so row a gets gamma sum_l w_l lambda_a(x_l) g_c(u(x_l)) and the
-            // Jacobian gamma sum_l w_l lambda_a(x_l) g_c'(u(x_l)) lambda_b(x_l)
-            double uk[NV];
+            // gamma M^c c with W_c = I_k: the cell pass's rho_a and R_ab (see there)
+            r += E[1 + 2 * NV + a];
+            if (!nl.picard) {
 #pragma unroll
-            for (int b = 0; b < NV; ++b) uk[b] = A.u[vk[b]];
-            const double gv = nl.gamma * M.vol[cell];
-            for (int l = 0; l < M.loc_c.nw; ++l) {
-                double uq = 0.0;
-#pragma unroll
-                for (int b = 0; b < NV; ++b) uq += M.loc_c.w[l][b] * uk[b];
-                double g, gp;
-                g_eval(nl.c_kind, nl.c_pi, nl.c_scale, uq, g, gp);
-                const double wa = gv * M.loc_c.iota[l] * M.loc_c.w[l][a];
-                r += wa * g;
-                if (!nl.picard) {
-#pragma unroll
-                    for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += wa * gp * M.loc_c.w[l][b];
-                }
+                for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + tri_index(a, b, NV)];
             }
         } else if (nl.c_kind != EGFEM_G_NONE) {
             // gamma M^c c with W_c = P1: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))

@@ -32,11 +32,14 @@ def rel(a, b):
 
 
 # (mesh, exponent q, shift, scale, kappa): minimal surface (q = -1/2, shift 1), a regularised
-# p-Laplacian with p = 3 (q = 1/2) and a shear-thinning exponent in 3D
+# p-Laplacian with p = 3 (q = 1/2), a shear-thinning exponent in 3D (these three take the
+# square-root path of the power) and two exponents with 4q not an integer (the general power)
 CASES = {
     "minsurf_2d": (lambda: wl.unit_square_mesh(13), -0.5, 1.0, 1.0, 0.0),
     "plap3_2d": (lambda: wl.unit_square_mesh(11), 0.5, 0.05, 1.0, 0.0),
     "shear_3d": (lambda: wl.unit_cube_mesh(4), -0.25, 0.3, 2.0, 0.4),
+    "general_q_2d": (lambda: wl.unit_square_mesh(9), 0.3, 0.2, 1.5, 0.1),   # 4q not an integer: pow
+    "general_q_3d": (lambda: wl.unit_cube_mesh(3), -0.7, 0.5, 1.0, 0.2),
 }
 
 
