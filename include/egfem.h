@@ -119,7 +119,7 @@ typedef struct {
     int32_t c_space;     /* egfem_w_space of W_c                                      */
 } egfem_problem;
 
-/* The approximation space W of a nonlinearity (Sec. 3.2).  EGFEM_W_QUADRATURE is Case 3's
+/* The approximation space W of a nonlinearity (Sec. 3.1).  EGFEM_W_QUADRATURE is Case 3's
  * I_k: the basis w_l delta_{x_l} on the points of a symmetric degree-k quadrature rule of
  * every cell (triangle: k = 1..4 with 1, 3, 4, 6 points; tetrahedron: k = 1..3 with 1, 4, 5
  * points), so that T_ilk = w_l grad phi_k(x_l) . grad phi_i(x_l) and M_il = w_l phi_i(x_l),

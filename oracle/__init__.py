@@ -136,7 +136,7 @@ class Problem:
     w = a_scale * g_a(Pi_a u) lives in the Lagrange space of degree ``a_deg``;
     c = c_scale * g_c(Pi_c u) in the space of degree ``c_deg``.  ``g`` is
     ``("pow", p)`` -> s^p or ``("exp",)`` -> e^s.  ``a_space="quad"`` (``c_space``) makes
-    W the quadrature space I_k of Sec. 3.2 Case 3 with k = ``a_deg`` (``c_deg``): one node
+    W the quadrature space I_k of Sec. 3.1, Case 3 with k = ``a_deg`` (``c_deg``): one node
     per point of the symmetric degree-k rule on every cell.  ``rule=k`` makes every integral
     (the standard Galerkin approach, the load vector and the Lagrange-space tensors) use that
     same rule instead of the collapsed Gauss rule of ``qpts`` points.  ``cells`` restricts the tensor

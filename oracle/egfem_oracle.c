@@ -253,7 +253,7 @@ static int simplex_rule(int dim, int q, double *pts, double *wts) {
 }
 
 /* Symmetric rules of degree k on the reference simplex, the rules behind the quadrature
- * spaces I_k (Sec. 3.2, Case 3; the paper cites Dunavant's symmetric Gaussian rules for the
+ * spaces I_k (Sec. 3.1, Case 3; the paper cites Dunavant's symmetric Gaussian rules for the
  * triangle).  Each rule is a union of orbits of barycentric points under vertex permutation,
  * with the orbit parameters and weights in closed form:
  *   triangle    k = 1: centroid;  k = 2: (2/3, 1/6, 1/6);  k = 3: centroid (weight -27/48) and
@@ -438,7 +438,7 @@ static int space_build(int dim, int nc, const double *X, const int *cells, int p
 }
 
 /* The quadrature space I_k: one node per rule point per cell, never shared between cells
- * (the basis functions w_l delta_{x_l} are discontinuous, Sec. 3.2 Case 3); node c nq + l is
+ * (the basis functions w_l delta_{x_l} are discontinuous, Sec. 3.1, Case 3); node c nq + l is
  * the physical image of reference point l on cell c. */
 static void space_build_quad(int dim, int nc, const double *X, const int *cells, int nq, const double *qp, orc_space *S) {
     S->p = -1; S->nloc = nq; S->n = nc * nq;
@@ -502,7 +502,7 @@ typedef struct {
     double gamma, kappa;
     int qpts;                                      /* Gauss points per direction */
     double a_shift;                                /* ORC_G_GRADPOW: the shift of ||grad u||^2 */
-    int a_quad, c_quad;  /* nonzero: W_a / W_c is the quadrature space I_k, k = a_deg / c_deg (Sec. 3.2 Case 3) */
+    int a_quad, c_quad;  /* nonzero: W_a / W_c is the quadrature space I_k, k = a_deg / c_deg (Sec. 3.1, Case 3) */
     int rule;            /* > 0: the symmetric degree-`rule` rule for every integral (SGA, load vector,
                             Lagrange-space tensors) instead of the collapsed Gauss rule */
 } orc_spec;
@@ -599,7 +599,7 @@ static void local_tensors(const orc_problem *P, int c, const orc_elem *EW, const
     }
 }
 
-/* Local tensors of cell c for a quadrature space (Sec. 3.2 Case 3): with eta_l = w_l delta_{x_l},
+/* Local tensors of cell c for a quadrature space (Sec. 3.1, Case 3): with eta_l = w_l delta_{x_l},
  * Tloc[a][l][b] = w_l grad phi_b(x_l) . grad phi_a(x_l) and Mloc[a][l] = w_l phi_a(x_l), w_l the
  * physical weight (reference weight d! |K|). */
 static void local_tensors_quad(const orc_problem *P, int c, int nq, const double *qp, const double *qw, double *Tloc, double *Mloc) {

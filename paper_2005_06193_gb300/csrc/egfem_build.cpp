@@ -108,7 +108,7 @@ void cell_stiffness(const egfem_mesh &m, std::vector<double> &vol, std::vector<d
     }
 }
 
-// Symmetric quadrature rules of degree k for the quadrature spaces I_k (Sec. 3.2, Case 3):
+// Symmetric quadrature rules of degree k for the quadrature spaces I_k (Sec. 3.1, Case 3):
 // Dunavant's triangle rules (k = 1..4) and the tetrahedron rules of degree 1..3, as
 // barycentric points with weights relative to the cell volume (summing to 1).  Writes at most
 // 6 points into bary / w and returns their number, or 0 for a degree not tabulated.

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
         E[1 + NV + a] = cb[a];
     }
     if (M.nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
-        // W_c = I_k (Sec. 3.2 Case 3): M_al = w_l lambda_a(x_l) and c_l = g_c(u(x_l)), so the
+        // W_c = I_k (Sec. 3.1, Case 3): M_al = w_l lambda_a(x_l) and c_l = g_c(u(x_l)), so the
         // cell adds rho_a = gamma sum_l w_l lambda_a(x_l) g_c(u(x_l)) to row a's residual and
         // R_ab = gamma sum_l w_l lambda_a(x_l) lambda_b(x_l) g_c'(u(x_l)) to its Jacobian;
         // both are evaluated here once per cell and gathered by the row pass

@@ -1,4 +1,4 @@
-"""GPU checks of the quadrature spaces I_k (Sec. 3.2, Case 3) in the element-local operator:
+"""GPU checks of the quadrature spaces I_k (Sec. 3.1, Case 3) in the element-local operator:
 residual and Jacobian against the oracle's EGFEM with the same spaces (which equals the standard
 Galerkin approach under that rule), and the quadratic example's Newton solution (Sec. 5,
 -lap u + u^2 = d with W_c = I_3) against the oracle's I_3 and P2 solutions."""

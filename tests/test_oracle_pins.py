@@ -606,7 +606,7 @@ def test_unit_disk_mesh_is_a_conforming_triangulation():
 
 
 # ---------------------------------------------------------------------------------------
-# Quadrature spaces I_k (Sec. 3.2, Case 3)
+# Quadrature spaces I_k (Sec. 3.1, Case 3)
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dim,k", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)])
