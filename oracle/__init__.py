@@ -67,7 +67,7 @@ class _Spec(ctypes.Structure):
                 ("c_kind", ctypes.c_int), ("c_p", ctypes.c_double), ("c_scale", ctypes.c_double), ("c_deg", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("qpts", ctypes.c_int),
                 ("a_shift", ctypes.c_double), ("a_quad", ctypes.c_int), ("c_quad", ctypes.c_int),
-                ("rule", ctypes.c_int)]
+                ("rule", ctypes.c_int), ("sigma", ctypes.c_double)]
 
 
 def lib():
@@ -131,7 +131,7 @@ _KIND = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP, "gradpow": G_
 
 
 class Problem:
-    """One discretised problem  -div((kappa + w) grad u) + gamma c = d,  u = u_D on Gamma.
+    """One discretised problem  -div((kappa + w) grad u) + gamma c + sigma u = d,  u = u_D on Gamma.
 
     w = a_scale * g_a(Pi_a u) lives in the Lagrange space of degree ``a_deg``;
     c = c_scale * g_c(Pi_c u) in the space of degree ``c_deg``.  ``g`` is
@@ -139,14 +139,16 @@ class Problem:
     W the quadrature space I_k of Sec. 3.1, Case 3 with k = ``a_deg`` (``c_deg``): one node
     per point of the symmetric degree-k rule on every cell.  ``rule=k`` makes every integral
     (the standard Galerkin approach, the load vector and the Lagrange-space tensors) use that
-    same rule instead of the collapsed Gauss rule of ``qpts`` points.  ``cells`` restricts the tensor
+    same rule instead of the collapsed Gauss rule of ``qpts`` points.  ``sigma`` adds the linear
+    reaction sigma * int u phi_i (P1 mass matrix).  ``cells`` restricts the tensor
     assembly (and the SGA integrals) to a subset of cells, so that single rows of a
     large problem can be evaluated exactly: a row is complete when every cell that
     contains its vertex is in the subset.
     """
 
     def __init__(self, mesh, *, a=("pow", 2.0), a_scale=1.0, a_deg=2, c=None, c_scale=1.0, c_deg=1,
-                 gamma=0.0, kappa=1.0, qpts=4, cells=None, a_space="lagrange", c_space="lagrange", rule=0):
+                 gamma=0.0, kappa=1.0, qpts=4, cells=None, a_space="lagrange", c_space="lagrange", rule=0,
+                 sigma=0.0):
         self.mesh = mesh
         self._X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
         self._cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
@@ -165,6 +167,7 @@ class Problem:
         s.c_scale, s.c_deg = float(c_scale), int(c_deg)
         s.gamma, s.kappa, s.qpts = float(gamma), float(kappa), int(qpts)
         s.a_quad, s.c_quad, s.rule = int(a_space == "quad"), int(c_space == "quad"), int(rule)
+        s.sigma = float(sigma)
         self._spec = s
         self._sel = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
         L = lib()

@@ -505,6 +505,8 @@ typedef struct {
     int a_quad, c_quad;  /* nonzero: W_a / W_c is the quadrature space I_k, k = a_deg / c_deg (Sec. 3.1, Case 3) */
     int rule;            /* > 0: the symmetric degree-`rule` rule for every integral (SGA, load vector,
                             Lagrange-space tensors) instead of the collapsed Gauss rule */
+    double sigma;        /* linear reaction sigma * int u phi_i = sigma (M u)_i, M the P1 mass matrix
+                            (the M u term of the superconductivity decomposition (b), Sec. 5) */
 } orc_spec;
 
 typedef struct {
@@ -520,6 +522,7 @@ typedef struct {
     orc_coo T;            /* (i, m, k) -> T_imk over the assembled cells */
     orc_coo M;            /* (i, m, 0) -> M_im                            */
     orc_coo Pa, Pc;       /* (m, j, 0) -> (Pi)_mj                         */
+    orc_coo Mu;           /* (i, k, 0) -> int phi_k phi_i (when sigma != 0) */
     double *kappa_field;  /* optional kappa per W_a node (NULL: constant)  */
     int *cell_mask;       /* cells included in the tensor assembly         */
 } orc_problem;
@@ -678,13 +681,24 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
     }
     coo_compress(&P->T);
     coo_compress(&P->M);
+    if (spec->sigma != 0.0) {
+        /* the P1 mass matrix by the same quadrature (the P1 element as its own W space) */
+        for (int c = 0; c < spec->nc; ++c) {
+            if (!P->cell_mask[c]) continue;
+            const int *cv = spec->cells + (size_t)c * nv;
+            local_tensors(P, c, &P->P1, P->phi_q, NULL, Mloc);
+            for (int a = 0; a < nv; ++a)
+                for (int m = 0; m < nv; ++m) coo_push(&P->Mu, cv[a], cv[m], 0, Mloc[a * nv + m]);
+        }
+        coo_compress(&P->Mu);
+    }
     return P;
 }
 
 void orc_destroy(orc_problem *P) {
     if (!P) return;
     space_free(&P->Sa); space_free(&P->Sc);
-    free(P->T.t); free(P->M.t); free(P->Pa.t); free(P->Pc.t);
+    free(P->T.t); free(P->M.t); free(P->Pa.t); free(P->Pc.t); free(P->Mu.t);
     free(P->kappa_field); free(P->cell_mask);
     free(P->phi_q); free(P->eta_a_q); free(P->eta_c_q);
     free(P);
@@ -802,6 +816,7 @@ void orc_egfem_residual(const orc_problem *P, const double *u, const double *b, 
     }
     if (P->s.c_kind != ORC_G_NONE)
         for (size_t t = 0; t < P->M.n; ++t) r[P->M.t[t].i] += P->s.gamma * P->M.t[t].v * c[P->M.t[t].j];
+    for (size_t t = 0; t < P->Mu.n; ++t) r[P->Mu.t[t].i] += P->s.sigma * P->Mu.t[t].v * u[P->Mu.t[t].j];
     for (int i = 0; i < nv; ++i) {
         if (P->s.dir[i]) r[i] = u[i] - (uD ? uD[i] : 0.0);
         else r[i] -= b ? b[i] : 0.0;
@@ -827,6 +842,8 @@ static int64_t egfem_matrix(const orc_problem *P, const double *u, int picard, i
         double a = (P->kappa_field ? P->kappa_field[m] : P->s.kappa) + w[m];
         coo_push(&J, i, l, 0, P->T.t[t].v * a);
     }
+    /* the linear reaction sigma M (a linear term: in the Picard matrix as well) */
+    for (size_t t = 0; t < P->Mu.n; ++t) coo_push(&J, P->Mu.t[t].i, P->Mu.t[t].j, 0, P->s.sigma * P->Mu.t[t].v);
     /* (T .3 u) diag(g') Pi: D_im = sum_k T_imk u_k, then J_il += D_im g'_m Pi_ml */
     orc_coo D = {0};
     if (!picard)
@@ -936,6 +953,7 @@ void orc_sga_residual(const orc_problem *P, const double *u, const double *b, co
             }
             double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
             double reac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_val(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
+            reac += P->s.sigma * uh;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;
                 for (int b2 = 0; b2 < nv; ++b2) {
@@ -978,6 +996,7 @@ int64_t orc_sga_jacobian(const orc_problem *P, const double *u, int64_t cap, int
             double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
             double dcoef = ga_der(&P->s, arg);
             double dreac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_der(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
+            dreac += P->s.sigma;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;
                 for (int b2 = 0; b2 < nv; ++b2) {

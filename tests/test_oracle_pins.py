@@ -681,3 +681,76 @@ def test_i1_equals_p0_for_the_gradient_coefficient():
     I1 = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=1, a_space="quad", kappa=0.0)
     assert np.abs(P0.residual(u, b) - I1.residual(u, b)).max() <= 1e-14
     assert abs(P0.jacobian(u) - I1.jacobian(u)).max() <= 1e-14
+
+
+# ---------------------------------------------------------------------------------------
+# Reaction EGFEM with higher-order W_c: the superconductivity example (Sec. 5, Table 1)
+# ---------------------------------------------------------------------------------------
+
+def _supercond(mesh, nu, **w):
+    """Decomposition (b): nu K u + M u + M^c c with c = u^3 on W_c (kappa = nu, sigma = 1)."""
+    return oracle.Problem(mesh, a=None, a_deg=1, kappa=nu, c=("pow", 3.0), gamma=1.0, sigma=1.0, **w)
+
+
+def test_laplacian_of_the_superconductivity_solution():
+    """The manufactured source's closed-form Laplacian against central differences."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    x, y = rng.uniform(0.1, 0.9, 20), rng.uniform(0.1, 0.9, 20)
+    h = 1e-4
+    u = wl.supercond_exact
+    lap_fd = (u(x + h, y) + u(x - h, y) + u(x, y + h) + u(x, y - h) - 4 * u(x, y)) / h ** 2
+    lap = (u(x, y) ** 3 + u(x, y) - wl.supercond_source(x, y, 1.0))   # = lap u for nu = 1
+    assert np.abs(lap - lap_fd).max() <= 1e-5 * np.abs(lap).max()
+
+
+@pytest.mark.parametrize("space", ["p3", "p2", "i4"])
+def test_superconductivity_egfem_reproduces_sga(space):
+    """c = u^3 with u in P1 is a cubic on every cell: P3 W_c holds it exactly (Case 1) and I_4
+    integrates u^3 phi_i exactly (Case 3), so both EGFEM variants of Table 1 equal the standard
+    Galerkin approach; P2 W_c only interpolates c (Case 2) and differs from it."""
+    mesh = wl.unit_square_mesh(6)
+    u = wl.random_vector(mesh.n_nodes, 91, 0.8)
+    b = wl.random_vector(mesh.n_nodes, 92) * 1e-3
+    kw = {"p3": dict(c_deg=3), "p2": dict(c_deg=2), "i4": dict(c_deg=4, c_space="quad")}[space]
+    P = _supercond(mesh, 0.01, **kw)
+    S = _supercond(mesh, 0.01, c_deg=3)
+    r, rs = P.residual(u, b), S.residual(u, b, method="sga")
+    if space in ("p3", "i4"):
+        assert np.abs(r - rs).max() <= 1e-13 * np.abs(rs).max()
+        assert abs(P.jacobian(u) - S.jacobian(u, method="sga")).max() <= 1e-13 * abs(S.jacobian(u, method="sga")).max()
+    else:
+        assert np.abs(r - rs).max() > 1e-10 * np.abs(rs).max()
+
+
+def test_sigma_term_is_the_p1_mass_matrix():
+    """sigma M u with M_ab = |K| (1 + delta_ab) / 12 per triangle (closed form of int phi_a phi_b)."""
+    mesh = wl.unit_square_mesh(4)
+    P = oracle.Problem(mesh, a=None, a_deg=1, kappa=0.0, sigma=2.5)
+    u = wl.random_vector(mesh.n_nodes, 93)
+    M = np.zeros((mesh.n_nodes, mesh.n_nodes))
+    for cell in mesh.cells:
+        X = mesh.coords[cell]
+        e1, e2 = X[1] - X[0], X[2] - X[0]
+        area = 0.5 * abs(e1[0] * e2[1] - e1[1] * e2[0])
+        for a in range(3):
+            for b2 in range(3):
+                M[cell[a], cell[b2]] += area * (2.0 if a == b2 else 1.0) / 12.0
+    free = mesh.dirichlet == 0
+    r = P.residual(u, np.zeros(mesh.n_nodes))
+    assert np.abs(r[free] - 2.5 * (M @ u)[free]).max() <= 1e-15
+
+
+@pytest.mark.parametrize("space", ["p3", "i4"])
+def test_superconductivity_manufactured_solution_second_order(space):
+    kw = {"p3": dict(c_deg=3), "i4": dict(c_deg=4, c_space="quad")}[space]
+    errs = []
+    for n in (8, 16, 32):
+        mesh = wl.unit_square_mesh(n)
+        P = _supercond(mesh, 1.0, **kw)
+        ue = wl.supercond_exact(mesh.coords[:, 0], mesh.coords[:, 1])
+        b = P.load_vector(lambda x, y: wl.supercond_source(x, y, 1.0)) * (1 - mesh.dirichlet)
+        uD = ue * mesh.dirichlet
+        u, h, _, _ = P.newton(b, u0=uD, uD=uD, rtol=1e-11)
+        errs.append(np.sqrt(np.mean((u - ue) ** 2)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > 1.8, (errs, rates)

@@ -192,6 +192,22 @@ def quadratic_source(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     return -2.0 * (x + y) + (x * y * (x + y)) ** 2
 
 
+def supercond_exact(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """The superconductivity example's boundary data and exact solution (Sec. 5, simplified
+    Ginzburg-Landau model): u = sin(2 pi x) sin(2 pi y) exp(2 x) / 6."""
+    return np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y) * np.exp(2 * x) / 6.0
+
+
+def supercond_source(x: np.ndarray, y: np.ndarray, nu: float) -> np.ndarray:
+    """d = -nu lap u + u^3 + u for u = supercond_exact (manufactured source): with
+    f(x) = sin(2 pi x) e^(2x), f'' = (4 - 4 pi^2) sin(2 pi x) e^(2x) + 8 pi cos(2 pi x) e^(2x), so
+    lap u = e^(2x) sin(2 pi y) ((4 - 8 pi^2) sin(2 pi x) + 8 pi cos(2 pi x)) / 6."""
+    u = supercond_exact(x, y)
+    lap = np.exp(2 * x) * np.sin(2 * np.pi * y) * ((4 - 8 * np.pi ** 2) * np.sin(2 * np.pi * x)
+                                                    + 8 * np.pi * np.cos(2 * np.pi * x)) / 6.0
+    return -nu * lap + u ** 3 + u
+
+
 def smooth_source_3d(x: np.ndarray, y: np.ndarray, z: np.ndarray) -> np.ndarray:
     """A smooth 3D source, 10 sin(pi x) sin(pi y) sin(pi z) (test input for 3D cases)."""
     return 10.0 * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
