@@ -101,7 +101,7 @@ typedef struct {
     const uint8_t *dirichlet;   /* [n_nodes], nonzero marks a Dirichlet node             */
 } egfem_mesh;
 
-/* Problem: -div((kappa + a_scale g_a(Pi_a u)) grad u) + gamma c_scale g_c(Pi_c u) = d.   */
+/* Problem: -div((kappa + a_scale g_a(Pi_a u)) grad u) + gamma c_scale g_c(Pi_c u) + sigma u = d. */
 typedef struct {
     int32_t a_kind;      /* egfem_g_kind of the coefficient nonlinearity            */
     double a_p;          /* exponent for EGFEM_G_POW (integer) and EGFEM_G_GRADPOW (real) */
@@ -110,13 +110,16 @@ typedef struct {
     int32_t c_kind;      /* egfem_g_kind of the reaction nonlinearity               */
     double c_p;
     double c_scale;
-    int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM; the only Lagrange choice), or
-                            the degree k of I_k when c_space is EGFEM_W_QUADRATURE     */
+    int32_t c_degree;    /* Lagrange degree of W_c: 1 (GFEM), 2 or 3 (3D: 2; degrees > 1
+                            need EGFEM_OP_MATRIX_FREE), or k of I_k (c_space)          */
     double gamma;        /* reaction coefficient                                     */
     double kappa;        /* constant part of the coefficient                         */
     double a_shift;      /* EGFEM_G_GRADPOW: the shift added to ||grad u||^2 (else unused) */
     int32_t a_space;     /* egfem_w_space of W_a (a_degree is then k of I_k)          */
     int32_t c_space;     /* egfem_w_space of W_c                                      */
+    double sigma;        /* linear reaction sigma int u phi_i = sigma (M u)_i, M the P1 mass
+                            matrix (the M u term of the superconductivity decomposition (b),
+                            Sec. 5); nonzero needs EGFEM_OP_MATRIX_FREE                   */
 } egfem_problem;
 
 /* The approximation space W of a nonlinearity (Sec. 3.1).  EGFEM_W_QUADRATURE is Case 3's

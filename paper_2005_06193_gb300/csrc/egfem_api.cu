@@ -472,6 +472,60 @@ egfem_status check_status_word(egfem_t *h) {
 template <typename T>
 void dfree(T *&p) { if (p) cudaFree((void *)p); p = nullptr; }
 
+// Local nodes of the degree-p Lagrange W space on the reference cell, in the W numbering's
+// local order (vertices; edge nodes from the lower to the higher local vertex; face centroids),
+// with iota_l = int_K eta_l / |K| and mu_la = int_K lambda_a eta_l / |K|.  mu comes from the
+// expansion eta_alpha = prod_j prod_{i < alpha_j} (p lambda_j - i) / (i + 1) integrated
+// monomial by monomial, int_K lambda^beta / |K| = d! beta! / (|beta| + d)!.
+egfem_status lagrange_local(int d, int p, MfLocal &L) {
+    const int nv = d + 1;
+    int count = 1;                                  // C(p + d, d) nodes
+    for (int i = 1; i <= d; ++i) count = count * (p + i) / i;
+    if (count > MF_MAXW) { g_last_error = "element-local operator supports at most 10 local W nodes"; return EGFEM_ERR_UNSUPPORTED; }
+    auto fact = [](int k) { double f = 1.0; for (int i = 2; i <= k; ++i) f *= i; return f; };
+    auto add = [&](const int *alpha, int kind) {
+        // eta as a dense polynomial in (lambda_0..lambda_3), exponents 0..4 each
+        std::vector<double> poly(625, 0.0), next(625);
+        poly[0] = 1.0;
+        for (int j = 0; j < nv; ++j)
+            for (int i = 0; i < alpha[j]; ++i) {
+                std::fill(next.begin(), next.end(), 0.0);
+                const int step = (j == 0 ? 1 : j == 1 ? 5 : j == 2 ? 25 : 125);
+                for (int e = 0; e < 625; ++e) {
+                    if (poly[e] == 0.0) continue;
+                    next[e + step] += poly[e] * double(p) / double(i + 1);
+                    next[e] -= poly[e] * double(i) / double(i + 1);
+                }
+                poly.swap(next);
+            }
+        const int l = L.nw++;
+        for (int a = 0; a < 4; ++a) L.w[l][a] = a < nv ? double(alpha[a]) / double(p) : 0.0;
+        L.iota[l] = basis_integral(d, p, kind);
+        for (int a = 0; a < 4; ++a) {
+            double m = 0.0;
+            for (int e = 0; a < nv && e < 625; ++e) {
+                if (poly[e] == 0.0) continue;
+                int ex[4] = {e % 5, (e / 5) % 5, (e / 25) % 5, e / 125};
+                ex[a] += 1;
+                double num = fact(d);
+                int tot = 0;
+                for (int j = 0; j < nv; ++j) { num *= fact(ex[j]); tot += ex[j]; }
+                m += poly[e] * num / fact(tot + d);
+            }
+            L.mu[l][a] = m;
+        }
+    };
+    for (int a = 0; a < nv; ++a) { int al[4] = {0, 0, 0, 0}; al[a] = p; add(al, W_VERTEX); }
+    for (int a = 0; a < nv && p >= 2; ++a)
+        for (int b = a + 1; b < nv; ++b)
+            for (int t = 1; t < p; ++t) { int al[4] = {0, 0, 0, 0}; al[a] = p - t; al[b] = t; add(al, p == 2 ? W_MID : W_THIRD); }
+    if (p == 3)
+        for (int a = 0; a < nv; ++a)
+            for (int b = a + 1; b < nv; ++b)
+                for (int e = b + 1; e < nv; ++e) { int al[4] = {0, 0, 0, 0}; al[a] = al[b] = al[e] = 1; add(al, W_FACE); }
+    return EGFEM_OK;
+}
+
 egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
     if (!mesh || !prob || !out) { g_last_error = "null argument"; return EGFEM_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -508,7 +562,6 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     }
     if (!quad_c) {
         EG_TRY(check_g(prob->c_kind, prob->c_p, prob->c_degree, "c"));
-        if (prob->c_kind != EGFEM_G_NONE && prob->c_degree != 1) { g_last_error = "Lagrange reaction space W_c must be P1"; return EGFEM_ERR_UNSUPPORTED; }
     } else if (prob->c_kind < EGFEM_G_NONE || prob->c_kind > EGFEM_G_EXP ||
                (prob->c_kind == EGFEM_G_POW && (prob->c_p < 1 || prob->c_p > 8 || prob->c_p != std::floor(prob->c_p)))) {
         g_last_error = "c: unknown kind or exponent";
@@ -516,6 +569,9 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     }
     if (prob->c_kind == EGFEM_G_GRADPOW) { g_last_error = "c: the gradient nonlinearity is a coefficient"; return EGFEM_ERR_INVALID_ARG; }
     const bool gradc = prob->a_kind == EGFEM_G_GRADPOW;
+    // a Lagrange W_c of degree 2 or 3 (evaluated by the element-local operator)
+    const bool lag_c = !quad_c && prob->c_kind != EGFEM_G_NONE && prob->c_degree > 1;
+    if (!std::isfinite(prob->sigma)) { g_last_error = "sigma must be finite"; return EGFEM_ERR_INVALID_ARG; }
     if (gradc) {
         // (shift + s)^q on s = ||grad u||^2 >= 0: finite with its derivative at s = 0 when
         // shift > 0, or when shift = 0 and q is 0 or at least 1
@@ -531,10 +587,11 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     if (opts) h->opts = *opts;
     if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
     if (h->opts.op != EGFEM_OP_CSF && h->opts.op != EGFEM_OP_MATRIX_FREE) { g_last_error = "unknown operator variant"; return EGFEM_ERR_INVALID_ARG; }
-    if ((gradc || quad_a || quad_c) && h->opts.op != EGFEM_OP_MATRIX_FREE) {
-        // the P0 and I_k forms are multiples of the cell stiffness S^K (and the I_k mass form a
-        // per-point product): the element-local operator evaluates them without a stored tensor
-        g_last_error = "the gradient coefficient and quadrature spaces need the element-local operator (EGFEM_OP_MATRIX_FREE)";
+    if ((gradc || quad_a || quad_c || lag_c || prob->sigma != 0.0) && h->opts.op != EGFEM_OP_MATRIX_FREE) {
+        // the P0 and I_k forms are multiples of the cell stiffness S^K, and the reaction forms
+        // on I_k or P2/P3 and the linear mass term are per-cell products: the element-local
+        // operator evaluates them without a stored tensor
+        g_last_error = "the gradient coefficient, quadrature spaces, W_c of degree > 1 and sigma need the element-local operator (EGFEM_OP_MATRIX_FREE)";
         return EGFEM_ERR_UNSUPPORTED;
     }
     h->prob = *prob;
@@ -555,7 +612,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     egfem_problem layout_prob = *prob;
     const bool mf_a = gradc || quad_a;
     if (mf_a) { layout_prob.a_kind = EGFEM_G_NONE; layout_prob.a_degree = 1; }
-    if (quad_c) { layout_prob.c_kind = EGFEM_G_NONE; layout_prob.c_degree = 1; }
+    const bool mf_c = quad_c || lag_c;
+    if (mf_c) { layout_prob.c_kind = EGFEM_G_NONE; layout_prob.c_degree = 1; }
     st = build_wspace(*mesh, layout_prob.a_kind != EGFEM_G_NONE ? layout_prob.a_degree : 1, Wa, c2wa, nla, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
     st = build_wspace(*mesh, layout_prob.c_kind != EGFEM_G_NONE ? layout_prob.c_degree : 1, Wc, c2wc, nlc, err);
@@ -565,6 +623,14 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     if (quad_a) { h->nwa = mesh->n_cells * nqa; h->wa_coords = quad_points(*mesh, nqa, qa_bary); }   // W_a = I_k
     else if (gradc) { h->nwa = mesh->n_cells; h->wa_coords = cell_centroids(*mesh); }             // W_a = P0
     if (quad_c) { h->nwc = mesh->n_cells * nqc; h->wc_coords = quad_points(*mesh, nqc, qc_bary); }  // W_c = I_k
+    if (lag_c) {                                                                                 // W_c = P2, P3
+        HostWSpace Wh;
+        std::vector<int32_t> c2wh;
+        int nlh = 0;
+        st = build_wspace(*mesh, prob->c_degree, Wh, c2wh, nlh, err);
+        if (st != EGFEM_OK) { g_last_error = err; return st; }
+        h->nwc = Wh.n; h->wc_coords = Wh.coords;
+    }
     HostCSF H;
     st = build_csf(*mesh, layout_prob, Wa, c2wa, nla, Wc, c2wc, nlc, H, err);
     if (st != EGFEM_OK) { g_last_error = err; return st; }
@@ -606,7 +672,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     EG_TRY(upload(h->tmap, tmap));
     EG_TRY(upload(h->wa_kind, Wa.kind)); EG_TRY(upload(h->wa_sup, Wa.sup));
     if (prob->a_kind != EGFEM_G_NONE && !mf_a) { EG_TRY(dalloc(h->wa_val, size_t(h->nwa))); EG_TRY(dalloc(h->wa_gp, size_t(h->nwa))); }
-    if (prob->c_kind != EGFEM_G_NONE && !quad_c) {
+    if (prob->c_kind != EGFEM_G_NONE && !mf_c) {
         EG_TRY(upload(h->wc_kind, Wc.kind)); EG_TRY(upload(h->wc_sup, Wc.sup));
         EG_TRY(dalloc(h->wc_val, size_t(h->nwc))); EG_TRY(dalloc(h->wc_gp, size_t(h->nwc)));
     }
@@ -629,12 +695,11 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
             // per cell: S^K = |K| grad lambda_a . grad lambda_b (packed upper triangle)
             const int d = mesh->dim;
             EG_TRY(upload(h->cell_S, S));
-            h->mf_ne = 2 * d + 3 + (nqc > 0 ? (d + 1) + (d + 1) * (d + 2) / 2 : 0);
+            h->mf_ne = 2 * d + 3 + (mf_c ? (d + 1) + (d + 1) * (d + 1) : 0);
             EG_TRY(dalloc(h->cell_E, size_t(mesh->n_cells) * size_t(h->mf_ne)));
             // local W nodes of the reference cell in the W numbering's local order
             MfLocal &L = h->mf_loc;
             L = MfLocal{};
-            const int p = prob->a_kind != EGFEM_G_NONE ? prob->a_degree : 1;
             if (quad_a && !gradc) {
                 // I_k: the rule's points and weights (w_l / |K|, summing to 1)
                 for (int l = 0; l < nqa; ++l) {
@@ -643,42 +708,30 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
                 }
                 L.nw = nqa;
             } else if (prob->a_kind != EGFEM_G_NONE && !gradc) {
-                auto add = [&](const double *w, int kind) {
-                    for (int a = 0; a < 4; ++a) L.w[L.nw][a] = a < nv ? w[a] : 0.0;
-                    L.iota[L.nw] = basis_integral(d, p, kind);
-                    ++L.nw;
-                };
-                for (int a = 0; a < nv; ++a) { double w[4] = {0, 0, 0, 0}; w[a] = 1.0; add(w, W_VERTEX); }
-                for (int a = 0; a < nv && p >= 2; ++a)
-                    for (int b = a + 1; b < nv; ++b)
-                        for (int t = 1; t < p; ++t) {
-                            double w[4] = {0, 0, 0, 0};
-                            w[a] = double(p - t) / double(p); w[b] = double(t) / double(p);
-                            add(w, p == 2 ? W_MID : W_THIRD);
-                        }
-                if (p == 3) {
-                    for (int a = 0; a < nv; ++a) for (int b = a + 1; b < nv; ++b) for (int e = b + 1; e < nv; ++e) {
-                        if (L.nw >= MF_MAXW) break;
-                        double w[4] = {0, 0, 0, 0};
-                        w[a] = w[b] = w[e] = 1.0 / 3.0;
-                        add(w, W_FACE);
-                    }
-                }
-                if (L.nw > MF_MAXW) { g_last_error = "matrix-free operator supports at most 10 local W nodes"; return EGFEM_ERR_UNSUPPORTED; }
+                EG_TRY(lagrange_local(d, prob->a_degree, L));
             }
             MfLocal &Lc = h->mf_loc_c;
             Lc = MfLocal{};
-            for (int l = 0; l < nqc; ++l) {
-                for (int a = 0; a < 4; ++a) Lc.w[l][a] = a < nv ? qc_bary[l][a] : 0.0;
-                Lc.iota[l] = qc_w[l];
+            if (quad_c) {
+                // I_k: M_al / |K| = (w_l / |K|) lambda_a(x_l)
+                for (int l = 0; l < nqc; ++l) {
+                    for (int a = 0; a < 4; ++a) {
+                        Lc.w[l][a] = a < nv ? qc_bary[l][a] : 0.0;
+                        Lc.mu[l][a] = qc_w[l] * Lc.w[l][a];
+                    }
+                    Lc.iota[l] = qc_w[l];
+                }
+                Lc.nw = nqc;
+            } else if (lag_c) {
+                EG_TRY(lagrange_local(d, prob->c_degree, Lc));
             }
-            Lc.nw = nqc;
         }
     }
     h->nl.a_kind = prob->a_kind; h->nl.a_pi = gradc ? 0 : int32_t(prob->a_p); h->nl.a_scale = prob->a_scale;
     h->nl.a_preal = prob->a_p; h->nl.a_shift = gradc ? prob->a_shift : 0.0;
     h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
     h->nl.gamma = prob->gamma; h->nl.kappa = prob->kappa; h->nl.kappa_field = nullptr;
+    h->nl.sigma = prob->sigma;
     // workspace
     h->n_pad = int64_t(H.n_slices) * SLICE;
     auto grid_for = [&](int64_t per_block) {
@@ -1261,12 +1314,13 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         const double NC = double(h->ncells), nv = h->dim + 1;
         const double nw = h->nl.a_kind == EGFEM_G_GRADPOW ? 0.0 : double(h->mf_loc.nw);
         const double coef = h->nl.a_kind == EGFEM_G_GRADPOW ? 3 * nv + 12 : nw * (4 * nv + 6);
-        // reaction: P1 W_c, 6 per vertex in the row pass; I_k, per point nv + 6 + 2 nv + 3 ns in
-        // the cell pass and nv + 1 per (row, cell) pair
-        const double nsd = nv * (nv + 1) / 2;
-        const double react_row = h->nl.c_kind == EGFEM_G_NONE ? 0.0 : h->mf_loc_c.nw > 0 ? nv + 1 : 6 * nv;
+        // reaction: P1 W_c, 6 per vertex in the row pass; I_k, P2, P3, per local node
+        // nv + 6 + 3 nv + 2 nv^2 in the cell pass and nv + 1 per (row, cell) pair; the linear
+        // term sigma M, 3 per vertex of each (row, cell) pair
+        const double react_row = (h->nl.c_kind == EGFEM_G_NONE ? 0.0 : h->mf_loc_c.nw > 0 ? nv + 1 : 6 * nv) +
+                                 (h->nl.sigma != 0.0 ? 3 * nv : 0.0);
         const double react_cell = h->nl.c_kind != EGFEM_G_NONE && h->mf_loc_c.nw > 0
-                                      ? double(h->mf_loc_c.nw) * (3 * nv + 6 + 3 * nsd) : 0.0;
+                                      ? double(h->mf_loc_c.nw) * (4 * nv + 6 + 2 * nv * nv) : 0.0;
         csf_flops = NC * (3 * nv * (nv - 1) + coef + react_cell) + NC * nv * (6 * nv + 2 + react_row);
     }
     const char *ta_name = h->opts.op == EGFEM_OP_MATRIX_FREE ? "tensor_action_mf" : "csf_fused";

@@ -28,6 +28,7 @@ struct MfLocal {
     int32_t nw;                         // local W nodes
     double w[MF_MAXW][4];               // barycentric weights on the cell's vertices
     double iota[MF_MAXW];               // int_K eta_l / |K|
+    double mu[MF_MAXW][4];              // int_K lambda_a eta_l / |K| (reaction spaces)
 };
 
 struct MfArgs {
@@ -38,10 +39,10 @@ struct MfArgs {
     const double *vol;                  // [n_cells]
     const int64_t *v2c_ptr;             // [n_rows + 1]
     const int32_t *v2c;                 // cells of each vertex
-    double *E;                          // [ne n_cells] abar, S u, c per cell (+ rho, R with W_c = I_k)
-    int32_t ne;                         // doubles per cell record: 2 dim + 3, or + (d+1) + (d+1)(d+2)/2
+    double *E;                          // [ne n_cells] abar, S u, c per cell (+ rho, R with loc_c)
+    int32_t ne;                         // doubles per cell record: 2 dim + 3, or + (d+1) + (d+1)^2
     MfLocal loc;
-    MfLocal loc_c;                      // W_c = I_k (nw > 0): the reaction's rule
+    MfLocal loc_c;                      // W_c = I_k, P2 or P3 (nw > 0): the reaction's local nodes
     Nonlin nl;
 };
 
@@ -139,15 +140,16 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
         E[1 + NV + a] = cb[a];
     }
     if (M.nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
-        // W_c = I_k (Sec. 3.1, Case 3): M_al = w_l lambda_a(x_l) and c_l = g_c(u(x_l)), so the
-        // cell adds rho_a = gamma sum_l w_l lambda_a(x_l) g_c(u(x_l)) to row a's residual and
-        // R_ab = gamma sum_l w_l lambda_a(x_l) lambda_b(x_l) g_c'(u(x_l)) to its Jacobian;
-        // both are evaluated here once per cell and gathered by the row pass
-        double rho[NV], R[NS];
+        // W_c = I_k (Sec. 3.1, Case 3) or P2/P3: M^K_al = |K| mu_la (w_l lambda_a(x_l) for I_k,
+        // int_K lambda_a eta_l for a Lagrange space) and c_l = g_c((Pi u)_l), so the cell adds
+        // rho_a = gamma |K| sum_l mu_la g_c((Pi u)_l) to row a's residual and
+        // R_ab = gamma |K| sum_l mu_la g_c'((Pi u)_l) Pi_lb to its Jacobian; both are evaluated
+        // here once per cell and gathered by the row pass
+        double rho[NV], R[NV * NV];
 #pragma unroll
         for (int a = 0; a < NV; ++a) rho[a] = 0.0;
 #pragma unroll
-        for (int q = 0; q < NS; ++q) R[q] = 0.0;
+        for (int q = 0; q < NV * NV; ++q) R[q] = 0.0;
         const double gv = M.nl.gamma * M.vol[c];
         for (int l = 0; l < M.loc_c.nw; ++l) {
             double uq = 0.0;
@@ -155,19 +157,20 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
             for (int b = 0; b < NV; ++b) uq += M.loc_c.w[l][b] * uk[b];
             double g, gp;
             g_eval(M.nl.c_kind, M.nl.c_pi, M.nl.c_scale, uq, g, gp);
-            const double wl = gv * M.loc_c.iota[l], wg = wl * g, wd = wl * gp;
+            const double wg = gv * g, wd = gv * gp;
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
-                const double la = M.loc_c.w[l][a];
-                rho[a] += wg * la;
+                const double ma = M.loc_c.mu[l][a];
+                rho[a] += wg * ma;
+                const double md = wd * ma;
 #pragma unroll
-                for (int b = a; b < NV; ++b) R[tri_index(a, b, NV)] += wd * la * M.loc_c.w[l][b];
+                for (int b = 0; b < NV; ++b) R[a * NV + b] += md * M.loc_c.w[l][b];
             }
         }
 #pragma unroll
         for (int a = 0; a < NV; ++a) E[1 + 2 * NV + a] = rho[a];
 #pragma unroll
-        for (int q = 0; q < NS; ++q) E[1 + 3 * NV + q] = R[q];
+        for (int q = 0; q < NV * NV; ++q) E[1 + 3 * NV + q] = R[q];
     }
 }
 
@@ -238,12 +241,22 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             }
             J[lc * CSF_BLOCK] += v;
         }
+        if (nl.sigma != 0.0) {
+            // linear reaction sigma M^K: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
+            const double m0 = nl.sigma * M.vol[cell] / double((DIM + 1) * (DIM + 2));
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+                const double mab = (b == a) ? 2.0 * m0 : m0;
+                r += mab * A.u[vk[b]];
+                J[lcb[b] * CSF_BLOCK] += mab;
+            }
+        }
         if (nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
-            // gamma M^c c with W_c = I_k: the cell pass's rho_a and R_ab (see there)
+            // gamma M^c c with W_c = I_k, P2 or P3: the cell pass's rho_a and R_ab (see there)
             r += E[1 + 2 * NV + a];
             if (!nl.picard) {
 #pragma unroll
-                for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + tri_index(a, b, NV)];
+                for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + a * NV + b];
             }
         } else if (nl.c_kind != EGFEM_G_NONE) {
             // gamma M^c c with W_c = P1: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
