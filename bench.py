@@ -355,6 +355,64 @@ def quadrature_setup(torch, P, dev, n):
     return h, d, torch.tensor(uD, device=dev, dtype=torch.float64)
 
 
+# Table 1 (Sec. 5, superconductivity, decomposition (b)): the paper's own solve times in seconds
+# (Matlab R2019b on an i7-8700, Picard iteration) for context only; None where its Picard
+# iteration did not converge
+TABLE1_B_SECONDS = {("p3", 1.0): 0.076, ("i4", 1.0): 0.077, ("p3", 1e-2): 0.599, ("i4", 1e-2): 0.579,
+                    ("p3", 1e-3): None, ("i4", 1e-3): None}
+
+
+def supercond_setup(torch, P, dev, n, nu, space):
+    """Superconductivity decomposition (b) on the n x n square (Sec. 5): nu K u + M u + M^c c with
+    c = u^3 on W_c = P3 or I_4, u_D = sin(2 pi x) sin(2 pi y) e^(2x) / 6, manufactured source at
+    cell centroids, Newton from the boundary data.  Returns (handle, d, u0)."""
+    import workloads as wl
+    mesh = wl.unit_square_mesh(n)
+    deg, cs = (3, "lagrange") if space == "p3" else (4, "quad")
+    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, kappa=nu, c=("pow", 3), c_degree=deg, c_space=cs,
+                                      gamma=1.0, sigma=1.0), P.default_options(op=P.OP_MATRIX_FREE, newton_maxit=100))
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    uD = wl.supercond_exact(x, y) * mesh.dirichlet
+    xc = wl.cell_centroids(mesh)
+    f = torch.tensor(wl.supercond_source(xc[:, 0], xc[:, 1], nu), device=dev, dtype=torch.float64)
+    d = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
+    h.load_cellwise(f, d)
+    d += torch.tensor(uD, device=dev)
+    return h, d, torch.tensor(uD, device=dev, dtype=torch.float64)
+
+
+def supercond_extra(torch, P, dev, steps, barrier, hbm, fp64_peak, n_big):
+    rows = []
+    for nu in (1.0, 1e-2, 1e-3):
+        for space in ("p3", "i4"):
+            h, d, u0 = supercond_setup(torch, P, dev, 64, nu, space)
+            u = u0.clone()
+            h.newton_solve(u, d)
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(steps, 5)
+            e0.record()
+            for _ in range(reps):
+                u.copy_(u0)
+                st = h.newton_solve(u, d)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"nu": nu, "w_c": space, "unknowns": h.sizes.n_nodes + h.sizes.n_wc,
+                         "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "newton_iters": st.newton_iters,
+                         "krylov_iters": int(st.krylov_iters), "status": int(st.status),
+                         "paper_seconds_context": TABLE1_B_SECONDS[(space, nu)]})
+            h.close()
+    out = {"workload": "superconductivity decomposition (b), 64x64 grid (Table 1), Newton to 1e-10",
+           "table1": rows}
+    if n_big:
+        out["large"] = next_row_extra(torch, P, dev, n_big, min(steps, 3), barrier,
+                                      lambda t, PP, dv, n: supercond_setup(t, PP, dv, n, 1.0, "p3"),
+                                      f"superconductivity_b_p3_nu1_{n_big}x{n_big}", hbm, fp64_peak)
+    return out
+
+
 def next_row_extra(torch, P, dev, n, steps, barrier, setup, workload, hbm, fp64_peak):
     h, d, u0 = setup(torch, P, dev, n)
     u = u0.clone()
@@ -416,7 +474,7 @@ def main():
     ap.add_argument("--p3-instances", type=int, default=32)
     ap.add_argument("--ref-newton-steps", type=int, default=5)
     ap.add_argument("--ref-krylov-iters", type=int, default=3500)
-    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed", "gradient", "quadrature"],
+    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed", "gradient", "quadrature", "supercond"],
                     help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
                          "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
@@ -442,8 +500,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    if args.profile_only in ("gradient", "quadrature"):
-        setup = gradient_setup if args.profile_only == "gradient" else quadrature_setup
+    if args.profile_only in ("gradient", "quadrature", "supercond"):
+        setup = {"gradient": gradient_setup, "quadrature": quadrature_setup,
+                 "supercond": lambda t, PP, dv, n: supercond_setup(t, PP, dv, n, 1.0, "p3")}[args.profile_only]
         hp, d, u0 = setup(torch, P, torch.device("cuda", local), args.n)
         print(json.dumps(hp.profile_kernels(u0, d, reps=1)), flush=True)
         hp.close()
@@ -602,6 +661,7 @@ def main():
                                                  f"minimal_surface_p0_{args.n}x{args.n}", hbm, fp64_peak)
         out["quadrature_i3"] = next_row_extra(torch, P, dev, args.n, min(args.steps, 3), barrier, quadrature_setup,
                                               f"quadratic_reaction_i3_{args.n}x{args.n}", hbm, fp64_peak)
+        out["superconductivity"] = supercond_extra(torch, P, dev, args.steps, barrier, hbm, fp64_peak, args.n)
 
     if not args.no_batch:
         out["batched_adjoint"] = batched_adjoint_extra(torch, P, dev, args.batch_instances, args.batch_n, barrier)
