@@ -151,6 +151,15 @@ typedef struct {
     int32_t iteration;       /* egfem_iteration of egfem_newton_solve / batch solve and the
                                 matrix egfem_jacobian returns (default EGFEM_ITER_NEWTON);
                                 egfem_adjoint always uses the Newton Jacobian               */
+    int32_t krylov_block_rows; /* single-system persistent solve: fewest rows per block (rounded
+                                  up to 32); the grid is min(rows / this, resident blocks).
+                                  0 (default) picks the library's value; read at the first
+                                  solve of a handle                                          */
+    int32_t krylov_cluster;  /* FP64 single-system solve in one thread-block cluster (the Krylov
+                                vectors in distributed shared memory; systems up to about
+                                16 x 4096 rows): 0 (default) when it fits, with the cluster
+                                size chosen by the library; 1..16 that cluster size; -1
+                                never.  Read at the first solve of a handle                   */
 } egfem_options;
 
 #define EGFEM_HIST 64

@@ -18,6 +18,7 @@
 #include "egfem_batch.cuh"
 #include "egfem_mf.cuh"
 #include "egfem_persist.cuh"
+#include "egfem_cluster.cuh"
 
 using namespace egfem;
 
@@ -68,6 +69,9 @@ struct KWork {
     PkScal<V> *pk_sc = nullptr;           // [1]
     double *pk_part = nullptr;            // [2 * pk_ntiles]
     PGrid *bar = nullptr;
+    // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
+    int pkc_cluster = 0;
+    int32_t pkc_rows = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
@@ -160,6 +164,10 @@ constexpr double kMixedEtaFloor = 1e-8;
 // An FP32 solve whose residual has not fallen by 10% for this many iterations stops (its
 // iterate is still applied; the FP64 Newton residual judges it).
 constexpr int32_t kMixedStall = 150;
+
+// Fewest rows per block of the single-system persistent solve: below this a grid barrier
+// over more blocks costs more than the rows it spreads.
+constexpr int32_t kPkBlockRows = 32;
 
 int pick_maxc(int maxc) {
     if (maxc <= 8) return 8;
@@ -285,6 +293,61 @@ int one_wave(const egfem_t *h, const void *func) {
     return int(std::max<int64_t>(1, std::min<int64_t>(work, int64_t(nb) * h->sms)));
 }
 
+// Cluster solve plan for one FP64 system: the rows must fit the Krylov vectors of the cluster's
+// CTAs in shared memory (7 doubles per row); the cluster size is the smallest power of two
+// giving at most kPkcTargetRows rows per CTA (or the krylov_cluster option), and the launch
+// configuration must be schedulable (cudaOccupancyMaxActiveClusters).  Leaves W.pkc_cluster = 0
+// when any of this fails: the grid-wide persistent solve is used instead.
+constexpr int64_t kPkcTargetRows = 512;
+
+egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
+    W.pkc_cluster = 0;
+    if (h->opts.krylov_cluster < 0 || !h->opts.krylov_persistent) return EGFEM_OK;
+    int smem_optin = 0;
+    EG_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const int64_t static_smem = 4096;   // the kernel's static shared memory, rounded up
+    const int64_t rows_max = (int64_t(smem_optin) - static_smem) / (PKC_NVEC * 8) / SLICE * SLICE;
+    if (rows_max < SLICE) return EGFEM_OK;
+    auto rows_for = [&](int64_t c) { return (h->n_pad + c * SLICE - 1) / (c * SLICE) * SLICE; };
+    int64_t c = h->opts.krylov_cluster > 0 ? h->opts.krylov_cluster : 1;
+    if (h->opts.krylov_cluster == 0)
+        while (c < PKC_MAX_CLUSTER && rows_for(c) > kPkcTargetRows) c *= 2;
+    if (c > PKC_MAX_CLUSTER || rows_for(c) > rows_max) return EGFEM_OK;
+    const int64_t rows = rows_for(c);
+    const size_t smem = size_t(rows) * PKC_NVEC * sizeof(double);
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(c); attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(unsigned(c)); cfg.blockDim = dim3(PKC_BLOCK); cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->hs; cfg.attrs = attr; cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)pkc_solve, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return EGFEM_OK;
+    }
+    W.pkc_cluster = int(c);
+    W.pkc_rows = int32_t(rows);
+    return EGFEM_OK;
+}
+
+egfem_status launch_pkc(egfem_t *h, KWork<double> &W, double rtol, int32_t maxit, int32_t stall) {
+    PkcArgs P{};
+    P.K = kvecs(h, W);
+    P.st = h->st; P.n_pad = h->n_pad; P.rows_cta = W.pkc_rows; P.rtol = rtol; P.maxit = maxit; P.stall = stall;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(W.pkc_cluster); attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(unsigned(W.pkc_cluster)); cfg.blockDim = dim3(PKC_BLOCK);
+    cfg.dynamicSmemBytes = size_t(W.pkc_rows) * PKC_NVEC * sizeof(double);
+    cfg.stream = h->hs; cfg.attrs = attr; cfg.numAttrs = 1;
+    EG_CUDA(cudaLaunchKernelEx(&cfg, pkc_solve, P));
+    return EGFEM_OK;
+}
+
 template <typename V>
 egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     if (W.ready) return EGFEM_OK;
@@ -307,7 +370,9 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
         // block owns one contiguous, slice-aligned tile of rows
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) == cudaSuccess && nb >= 1) {
-            const int64_t g = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::min(nb, 8)) * h->sms, h->n_pad / SLICE));
+            const int64_t min_rows = (int64_t(h->opts.krylov_block_rows > 0 ? h->opts.krylov_block_rows : kPkBlockRows) +
+                                      SLICE - 1) / SLICE * SLICE;
+            const int64_t g = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::min(nb, 8)) * h->sms, h->n_pad / min_rows));
             const int64_t rows = (h->n_pad + g * SLICE - 1) / (g * SLICE) * SLICE;
             std::vector<BTile> T;
             for (int64_t r = 0; r < h->n_pad; r += rows) T.push_back(BTile{r, std::min(h->n_pad, r + rows), 0, 0, 0});
@@ -322,6 +387,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
         }
     }
+    if constexpr (std::is_same<V, double>::value) EG_TRY(pkc_plan(h, W));
     if constexpr (std::is_same<V, df64>::value) {
         W.g_vp = one_wave<V>(h, (const void *)kry_vp<V>);
         W.g_st = one_wave<V>(h, (const void *)kry_st<V>);
@@ -393,6 +459,8 @@ egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, in
 
 template <typename V>
 egfem_status launch_pk_single(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
+    if constexpr (std::is_same<V, double>::value)
+        if (W.pkc_cluster > 0) return launch_pkc(h, W, rtol, maxit, stall);
     return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, nullptr, nullptr, rtol,
                      W.bar, maxit, stall);
 }
@@ -814,6 +882,8 @@ void egfem_default_options(egfem_options *o) {
     o->fixed_eta = 0;
     o->krylov_persistent = 1;
     o->iteration = EGFEM_ITER_NEWTON;
+    o->krylov_block_rows = 0;
+    o->krylov_cluster = 0;
 }
 
 egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
@@ -1370,7 +1440,9 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         // the operator is read twice.
         const int32_t iters = 40;
         cudaError_t le = cudaSuccess;
-        EG_TRY(timeit("kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
+        bool cl = false;
+        if constexpr (std::is_same<V, double>::value) cl = W.pkc_cluster > 0;
+        EG_TRY(timeit(cl ? "kry_cluster" : "kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
             if (launch_pk_single(h, W, 0.0, iters, 0) != EGFEM_OK) le = cudaErrorLaunchFailure;
         }));
         EG_CUDA(le);

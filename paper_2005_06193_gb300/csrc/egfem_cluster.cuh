@@ -1,0 +1,240 @@
+// egfem_cluster.cuh -- Jacobi-BiCGStab for one system small enough to live in the distributed
+// shared memory of one thread-block cluster (up to 16 CTAs, one per SM).
+//
+// The grid-wide persistent solve (egfem_persist.cuh) pays, at every one of its five grid
+// barriers per iteration, a chain of dependent L2 round trips (arrival atomic, last-block sum,
+// fence, release, poll, scalar read): about 30 us per iteration however few rows there are.
+// Here the cluster's CTAs own contiguous slice-aligned row ranges; the seven Krylov vectors of
+// those rows stay in each CTA's shared memory for the whole solve; the SpMV gathers its
+// neighbours' entries from the owning CTA's shared memory (mapa + ld.shared::cluster); and the
+// hardware cluster barrier (barrier.cluster.arrive.release / wait.acquire) replaces the grid
+// barrier.  Each reduction is two-level: the CTA's partial goes to its own shared memory, and
+// after the barrier every thread adds the cluster's partials in rank order, so every CTA
+// computes bit-identical scalars and takes the same decisions -- every CTA executes the same
+// sequence of barriers, and no thread ever waits on a flag another CTA sets.
+//
+// The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve and
+// is read from global memory.  Arithmetic and stopping rules are those of pk_solve<double>.
+#pragma once
+
+#include "egfem_persist.cuh"
+
+namespace egfem {
+
+constexpr int PKC_BLOCK = 512;          // threads per CTA
+constexpr int PKC_NVEC = 7;             // p, v, s, t, r, rh, x in shared memory
+constexpr int PKC_MAX_CLUSTER = 16;     // non-portable cluster size (one GPC holds it)
+
+enum { PV_P = 0, PV_V, PV_S, PV_T, PV_R, PV_RH, PV_X };
+
+struct PkcArgs {
+    KVecs<double> K;        // operator, b (rhs) and x (solution out) in global memory
+    KState *st;             // final state (written by rank 0)
+    int64_t n_pad;          // rows (whole slices)
+    int32_t rows_cta;       // rows per CTA (a multiple of SLICE); the last CTA may own fewer
+    double rtol;
+    int32_t maxit, stall;
+};
+
+__device__ __forceinline__ void pkc_cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pkc_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pkc_nranks() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// a double in CTA `rank`'s shared memory at the offset of `p` in this CTA's
+__device__ __forceinline__ double pkc_ld_remote(const double *p, uint32_t rank) {
+    uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p)), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra));
+    return v;
+}
+
+// Block-level sum of NV per-thread values (fixed order); thread 0 stores them to out[].
+template <int NV>
+__device__ __forceinline__ void pkc_block_sum(const double (&x)[NV], double *out) {
+    __shared__ double s_w[NV][PKC_BLOCK / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double v = warp_sum(x[k]);
+        if (lane == 0) s_w[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = s_w[k][0];
+            for (int q = 1; q < PKC_BLOCK / 32; ++q) t += s_w[k][q];
+            out[k] = t;
+        }
+    }
+}
+
+// After a cluster barrier: the cluster-wide sums of the partials in buf (rank order).
+template <int NV>
+__device__ __forceinline__ void pkc_cluster_sum(const double *buf, uint32_t nranks, double (&tot)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
+    for (uint32_t q = 0; q < nranks; ++q)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] += pkc_ld_remote(buf + k, q);
+}
+
+// y_g = (A x)_g for the owned row g (local index l); x is vector `vec` of the cluster
+__device__ __forceinline__ double pkc_spmv_row(const PkcArgs &P, const double *sv, int vec, int64_t g, int64_t base,
+                                               int64_t rows_here) {
+    const KVecs<double> &K = P.K;
+    const SliceMeta M = K.meta[g / SLICE];
+    const int lane = int(g % SLICE);
+    const double *xv = sv + int64_t(vec) * P.rows_cta;
+    double y = __ldg(K.A + M.col_base + lane) * xv[g - base];
+#pragma unroll 4
+    for (int c = 1; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        const double a = __ldg(K.A + q);
+        const int64_t col = M.off_base >= 0 ? g + __ldg(K.slice_off + M.off_base + c) : int64_t(__ldg(K.col_idx + q));
+        double xc;
+        if (col >= base && col < base + rows_here) {
+            xc = xv[col - base];
+        } else {
+            const uint32_t o = uint32_t(col / P.rows_cta);
+            xc = pkc_ld_remote(xv + (col - int64_t(o) * P.rows_cta), o);
+        }
+        y = fma(a, xc, y);
+    }
+    return y;
+}
+
+#define PKC_ROWS for (int64_t l = threadIdx.x; l < rows_here; l += PKC_BLOCK)
+
+// The solve: x = 0 start, BiCGStab until (r, r) <= rtol^2 (b, b), a breakdown, the iteration
+// cap, divergence or (stall > 0) stagnation.  One cluster; grid = the cluster.
+__global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
+    extern __shared__ double sv[];              // [PKC_NVEC][rows_cta]
+    __shared__ double red_a[1], red_o[2], red_r[2], red_0[1];
+    const uint32_t rank = pkc_rank(), nranks = pkc_nranks();
+    const int64_t base = int64_t(rank) * P.rows_cta;
+    const int64_t rows_here = base >= P.n_pad ? 0 : (P.n_pad - base < P.rows_cta ? P.n_pad - base : P.rows_cta);
+    const int64_t RC = P.rows_cta;
+    double *p = sv + PV_P * RC, *v = sv + PV_V * RC, *s = sv + PV_S * RC, *t = sv + PV_T * RC;
+    double *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
+    const KVecs<double> &K = P.K;
+
+    // setup: x = v = 0, r = rh = p = b, (b, b)
+    double acc0 = 0.0;
+    PKC_ROWS {
+        const double b = __ldg(K.b + base + l);
+        x[l] = 0.0; v[l] = 0.0; s[l] = 0.0; t[l] = 0.0;
+        r[l] = b; rh[l] = b; p[l] = b;
+        acc0 = fma(b, b, acc0);
+    }
+    {
+        const double a1[1] = {acc0};
+        pkc_block_sum<1>(a1, red_0);
+    }
+    pkc_cluster_barrier();   // also: every CTA of the cluster has started before any remote access
+    KState S;
+    {
+        double tot[1];
+        pkc_cluster_sum<1>(red_0, nranks, tot);
+        const double bb = tot[0];
+        S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
+        S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+        S.rho = S.rr = S.rr0 = S.best_rr = bb;
+        S.tol2 = P.rtol * P.rtol * bb;
+        S.stall_rr = 4e-6 * bb;
+        S.done = (bb == 0.0) ? K_CONVERGED : (!isfinite(bb) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
+    }
+
+    while (S.done == K_RUNNING) {
+        // A: v = A p, (rh, v)
+        double acc = 0.0;
+        PKC_ROWS {
+            const double y = pkc_spmv_row(P, sv, PV_P, base + l, base, rows_here);
+            v[l] = y;
+            acc = fma(rh[l], y, acc);
+        }
+        {
+            const double a1[1] = {acc};
+            pkc_block_sum<1>(a1, red_a);
+        }
+        pkc_cluster_barrier();
+        {
+            double tot[1];
+            pkc_cluster_sum<1>(red_a, nranks, tot);
+            if (tot[0] == 0.0 || !isfinite(tot[0])) { S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE; break; }
+            S.alpha = S.rho / tot[0];
+        }
+
+        // B1: s = r - alpha v (every CTA's s is complete before the SpMV gathers it)
+        PKC_ROWS s[l] = r[l] - S.alpha * v[l];
+        pkc_cluster_barrier();
+
+        // B2: t = A s, (t, s), (t, t)
+        double ts = 0.0, tt = 0.0;
+        PKC_ROWS {
+            const double y = pkc_spmv_row(P, sv, PV_S, base + l, base, rows_here);
+            t[l] = y;
+            ts = fma(y, s[l], ts);
+            tt = fma(y, y, tt);
+        }
+        {
+            const double a2[2] = {ts, tt};
+            pkc_block_sum<2>(a2, red_o);
+        }
+        pkc_cluster_barrier();
+        {
+            double tot[2];
+            pkc_cluster_sum<2>(red_o, nranks, tot);
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) { S.done = K_NONFINITE; break; }
+            S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+        }
+
+        // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
+        double rr1 = 0.0, rr2 = 0.0;
+        PKC_ROWS {
+            x[l] = x[l] + (S.alpha * p[l] + S.omega * s[l]);
+            const double rn = s[l] - S.omega * t[l];
+            r[l] = rn;
+            rr1 = fma(rh[l], rn, rr1);
+            rr2 = fma(rn, rn, rr2);
+        }
+        {
+            const double a2[2] = {rr1, rr2};
+            pkc_block_sum<2>(a2, red_r);
+        }
+        pkc_cluster_barrier();
+        {
+            double tot[2];
+            pkc_cluster_sum<2>(red_r, nranks, tot);
+            pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
+        }
+        if (S.done != K_RUNNING) break;
+
+        // D: p = r + beta (p - omega v)
+        PKC_ROWS p[l] = r[l] + S.beta * (p[l] - S.omega * v[l]);
+        pkc_cluster_barrier();
+    }
+
+    // results: x of the owned rows, the state from rank 0; the final barrier keeps every
+    // CTA's shared memory alive until the last remote read of the partials above is done
+    PKC_ROWS K.x[base + l] = x[l];
+    if (rank == 0 && threadIdx.x == 0) *P.st = S;
+    pkc_cluster_barrier();
+}
+
+#undef PKC_ROWS
+
+}  // namespace egfem
