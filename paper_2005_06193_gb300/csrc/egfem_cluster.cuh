@@ -9,9 +9,9 @@
 // neighbours' entries from the owning CTA's shared memory (mapa + ld.shared::cluster); and the
 // hardware cluster barrier (barrier.cluster.arrive.release / wait.acquire) replaces the grid
 // barrier.  Each reduction is two-level: the CTA's partial goes to its own shared memory, and
-// after the barrier every thread adds the cluster's partials in rank order, so every CTA
-// computes bit-identical scalars and takes the same decisions -- every CTA executes the same
-// sequence of barriers, and no thread ever waits on a flag another CTA sets.
+// after the barrier one warp of every CTA adds the cluster's partials in a fixed order, so
+// every CTA computes bit-identical scalars and takes the same decisions -- every CTA executes
+// the same sequence of barriers, and no thread ever waits on a flag another CTA sets.
 //
 // The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve and
 // is read from global memory.  Arithmetic and stopping rules are those of pk_solve<double>.
@@ -82,14 +82,21 @@ __device__ __forceinline__ void pkc_block_sum(const double (&x)[NV], double *out
     }
 }
 
-// After a cluster barrier: the cluster-wide sums of the partials in buf (rank order).
-template <int NV>
-__device__ __forceinline__ void pkc_cluster_sum(const double *buf, uint32_t nranks, double (&tot)[NV]) {
+// After a cluster barrier, warp 0 of every CTA: lane q loads CTA q's partials and the warp
+// adds them in a fixed shuffle order, so every CTA gets bit-identical sums; lane 0 then applies
+// update(S, tot) to the CTA's shared state, which the closing __syncthreads publishes to the
+// CTA.  (GB300 issues about two FP64 operations per clock per SM: the scalar work is done by
+// one warp, not recomputed by every thread.)
+template <int NV, typename U>
+__device__ __forceinline__ void pkc_reduce_update(const double *buf, uint32_t nranks, KState &S, U &&update) {
+    if (threadIdx.x < 32) {
+        const uint32_t lane = threadIdx.x;
+        double tot[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-    for (uint32_t q = 0; q < nranks; ++q)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += pkc_ld_remote(buf + k, q);
+        for (int k = 0; k < NV; ++k) tot[k] = warp_sum(lane < nranks ? pkc_ld_remote(buf + k, lane) : 0.0);
+        if (lane == 0) update(S, tot);
+    }
+    __syncthreads();
 }
 
 // y_g = (A x)_g for the owned row g (local index l); x is vector `vec` of the cluster
@@ -124,6 +131,7 @@ __device__ __forceinline__ double pkc_spmv_row(const PkcArgs &P, const double *s
 __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
     extern __shared__ double sv[];              // [PKC_NVEC][rows_cta]
     __shared__ double red_a[1], red_o[2], red_r[2], red_0[1];
+    __shared__ KState S;                        // this CTA's copy of the state (warp 0 writes it)
     const uint32_t rank = pkc_rank(), nranks = pkc_nranks();
     const int64_t base = int64_t(rank) * P.rows_cta;
     const int64_t rows_here = base >= P.n_pad ? 0 : (P.n_pad - base < P.rows_cta ? P.n_pad - base : P.rows_cta);
@@ -145,18 +153,15 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         pkc_block_sum<1>(a1, red_0);
     }
     pkc_cluster_barrier();   // also: every CTA of the cluster has started before any remote access
-    KState S;
-    {
-        double tot[1];
-        pkc_cluster_sum<1>(red_0, nranks, tot);
+    pkc_reduce_update<1>(red_0, nranks, S, [&](KState &Q, const double *tot) {
         const double bb = tot[0];
-        S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
-        S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
-        S.rho = S.rr = S.rr0 = S.best_rr = bb;
-        S.tol2 = P.rtol * P.rtol * bb;
-        S.stall_rr = 4e-6 * bb;
-        S.done = (bb == 0.0) ? K_CONVERGED : (!isfinite(bb) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
-    }
+        Q.iter = 0; Q.last_improve = 0; Q.maxit = P.maxit; Q.stall = P.stall; Q.ticket = 0u;
+        Q.alpha = 1.0; Q.omega = 1.0; Q.beta = 0.0; Q.scratch[0] = Q.scratch[1] = 0.0;
+        Q.rho = Q.rr = Q.rr0 = Q.best_rr = bb;
+        Q.tol2 = P.rtol * P.rtol * bb;
+        Q.stall_rr = 4e-6 * bb;
+        Q.done = (bb == 0.0) ? K_CONVERGED : (!isfinite(bb) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
+    });
 
     while (S.done == K_RUNNING) {
         // A: v = A p, (rh, v)
@@ -171,15 +176,15 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
             pkc_block_sum<1>(a1, red_a);
         }
         pkc_cluster_barrier();
-        {
-            double tot[1];
-            pkc_cluster_sum<1>(red_a, nranks, tot);
-            if (tot[0] == 0.0 || !isfinite(tot[0])) { S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE; break; }
-            S.alpha = S.rho / tot[0];
-        }
+        pkc_reduce_update<1>(red_a, nranks, S, [&](KState &Q, const double *tot) {
+            if (tot[0] == 0.0 || !isfinite(tot[0])) Q.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
+            else Q.alpha = Q.rho / tot[0];
+        });
+        if (S.done != K_RUNNING) break;
 
         // B1: s = r - alpha v (every CTA's s is complete before the SpMV gathers it)
-        PKC_ROWS s[l] = r[l] - S.alpha * v[l];
+        const double al = S.alpha;
+        PKC_ROWS s[l] = r[l] - al * v[l];
         pkc_cluster_barrier();
 
         // B2: t = A s, (t, s), (t, t)
@@ -195,18 +200,18 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
             pkc_block_sum<2>(a2, red_o);
         }
         pkc_cluster_barrier();
-        {
-            double tot[2];
-            pkc_cluster_sum<2>(red_o, nranks, tot);
-            if (!isfinite(tot[0]) || !isfinite(tot[1])) { S.done = K_NONFINITE; break; }
-            S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
-        }
+        pkc_reduce_update<2>(red_o, nranks, S, [&](KState &Q, const double *tot) {
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) Q.done = K_NONFINITE;
+            else Q.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+        });
+        if (S.done != K_RUNNING) break;
 
         // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
+        const double om = S.omega;
         double rr1 = 0.0, rr2 = 0.0;
         PKC_ROWS {
-            x[l] = x[l] + (S.alpha * p[l] + S.omega * s[l]);
-            const double rn = s[l] - S.omega * t[l];
+            x[l] = x[l] + (al * p[l] + om * s[l]);
+            const double rn = s[l] - om * t[l];
             r[l] = rn;
             rr1 = fma(rh[l], rn, rr1);
             rr2 = fma(rn, rn, rr2);
@@ -216,15 +221,14 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
             pkc_block_sum<2>(a2, red_r);
         }
         pkc_cluster_barrier();
-        {
-            double tot[2];
-            pkc_cluster_sum<2>(red_r, nranks, tot);
-            pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
-        }
+        pkc_reduce_update<2>(red_r, nranks, S, [&](KState &Q, const double *tot) {
+            pk_after_c(Q, tot[0], tot[1], P.maxit, P.stall);
+        });
         if (S.done != K_RUNNING) break;
 
         // D: p = r + beta (p - omega v)
-        PKC_ROWS p[l] = r[l] + S.beta * (p[l] - S.omega * v[l]);
+        const double be = S.beta;
+        PKC_ROWS p[l] = r[l] + be * (p[l] - om * v[l]);
         pkc_cluster_barrier();
     }
 
