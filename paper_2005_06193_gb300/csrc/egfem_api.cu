@@ -294,7 +294,7 @@ int one_wave(const egfem_t *h, const void *func) {
 }
 
 // Cluster solve plan for one FP64 system: the rows must fit the Krylov vectors of the cluster's
-// CTAs in shared memory (7 doubles per row); the cluster size is the smallest power of two
+// CTAs in shared memory (PKC_NVEC doubles per row); the cluster size is the smallest power of two
 // giving at most kPkcTargetRows rows per CTA (or the krylov_cluster option), and the launch
 // configuration must be schedulable (cudaOccupancyMaxActiveClusters).  Leaves W.pkc_cluster = 0
 // when any of this fails: the grid-wide persistent solve is used instead.
