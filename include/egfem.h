@@ -157,7 +157,7 @@ typedef struct {
                                   solve of a handle                                          */
     int32_t krylov_cluster;  /* FP64 single-system solve in one thread-block cluster (the Krylov
                                 vectors in distributed shared memory; systems up to about
-                                16 x 3168 rows): 0 (default) when it fits, with the cluster
+                                16 x 3904 rows): 0 (default) when it fits, with the cluster
                                 size chosen by the library; 1..16 that cluster size; -1
                                 never.  Read at the first solve of a handle                   */
 } egfem_options;

@@ -305,7 +305,7 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     if (h->opts.krylov_cluster < 0 || !h->opts.krylov_persistent) return EGFEM_OK;
     int smem_optin = 0;
     EG_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    const int64_t static_smem = 4096;   // the kernel's static shared memory, rounded up
+    const int64_t static_smem = 12288;  // the kernel's static shared memory (8.4 KB), rounded up
     const int64_t rows_max = (int64_t(smem_optin) - static_smem) / (PKC_NVEC * 8) / SLICE * SLICE;
     if (rows_max < SLICE) return EGFEM_OK;
     auto rows_for = [&](int64_t c) { return (h->n_pad + c * SLICE - 1) / (c * SLICE) * SLICE; };

@@ -11,9 +11,14 @@
 // barrier.  Each reduction is two-level: the CTA's partial goes to its own shared memory, and
 // after the barrier one warp of every CTA adds the cluster's partials in a fixed order, so
 // every CTA computes bit-identical scalars and takes the same decisions -- every CTA executes
-// the same sequence of barriers, and no thread ever waits on a flag another CTA sets.  The
-// pointwise updates p = r + beta (p - omega v) and s = r - alpha v are formed inside the SpMV
-// for the gathered neighbours, which leaves three barriers per iteration instead of five.
+// the same sequence of barriers, and no thread ever waits on a flag another CTA sets.
+//
+// GB300 issues about two FP64 operations per clock per SM, so at these sizes the FP64
+// instruction count, not memory or the barriers (about 0.3 us each), sets the time: a
+// reduction stores each thread's partial to shared memory and one warp adds only the
+// partials of threads that own rows; the pointwise vector updates stay separate phases
+// (forming p and s inside the SpMV for each gathered neighbour would save two barriers but
+// triple the SpMV's FP64 work).
 //
 // The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve and
 // is read from global memory.  Arithmetic and stopping rules are those of pk_solve<double>.
@@ -24,11 +29,10 @@
 namespace egfem {
 
 constexpr int PKC_BLOCK = 512;          // threads per CTA
-constexpr int PKC_WARPS = PKC_BLOCK / 32;
-constexpr int PKC_NVEC = 9;             // p and v (two buffers each), s, t, r, rh, x in shared memory
+constexpr int PKC_NVEC = 7;             // p, v, s, t, r, rh, x in shared memory
 constexpr int PKC_MAX_CLUSTER = 16;     // non-portable cluster size (one GPC holds it)
 
-enum { PV_P0 = 0, PV_P1, PV_V0, PV_V1, PV_S, PV_T, PV_R, PV_RH, PV_X };
+enum { PV_P = 0, PV_V, PV_S, PV_T, PV_R, PV_RH, PV_X };
 
 struct PkcArgs {
     KVecs<double> K;        // operator, b (rhs) and x (solution out) in global memory
@@ -64,78 +68,61 @@ __device__ __forceinline__ double pkc_ld_remote(const double *p, uint32_t rank) 
     return v;
 }
 
-// Each warp's sums of NV per-thread values (fixed shuffle order) to buf[k * PKC_WARPS + warp].
+// Reduction, first half (before the cluster barrier): every thread stores its NV partials to
+// th[k][tid]; after a __syncthreads warp 0 adds those of the nact threads that own rows (lane j
+// takes tid = j, j + 32, ... in order, then a fixed shuffle tree) and lane 0 stores the CTA's
+// sums to cta[k].
 template <int NV>
-__device__ __forceinline__ void pkc_warp_partial(const double (&x)[NV], double *buf) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ void pkc_cta_partial(const double (&x)[NV], double (*th)[PKC_BLOCK], int nact, double *cta) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const double v = warp_sum(x[k]);
-        if (lane == 0) buf[k * PKC_WARPS + w] = v;
+    for (int k = 0; k < NV; ++k) th[k][threadIdx.x] = x[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int j = threadIdx.x; j < nact; j += 32) a += th[k][j];
+            a = warp_sum(a);
+            if (threadIdx.x == 0) cta[k] = a;
+        }
     }
 }
 
-// After a cluster barrier, warp 0 of every CTA: each lane adds its share of the cluster's warp
-// partials (entry e = rank * PKC_WARPS + warp, lanes strided, e increasing) and the warp adds
-// the lanes in a fixed shuffle order, so every CTA gets bit-identical sums; lane 0 applies
-// update(S, tot) to the CTA's shared state and the closing __syncthreads publishes it.  (GB300
-// issues about two FP64 operations per clock per SM: scalar work is done once per CTA by one
-// warp, not recomputed by every thread.)
+// Second half (after the cluster barrier): warp 0 of every CTA loads the cluster's CTA sums
+// (lane q from CTA q) and adds them in a fixed shuffle order, so every CTA gets bit-identical
+// totals; lane 0 applies update(S, tot) to the CTA's shared state and the closing
+// __syncthreads publishes it to the CTA.
 template <int NV, typename U>
-__device__ __forceinline__ void pkc_reduce_update(const double *buf, uint32_t nranks, KState &S, U &&update) {
+__device__ __forceinline__ void pkc_reduce_update(const double *cta, uint32_t nranks, KState &S, U &&update) {
     if (threadIdx.x < 32) {
-        const uint32_t lane = threadIdx.x, ne = nranks * PKC_WARPS;
+        const uint32_t lane = threadIdx.x;
         double tot[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double acc = 0.0;
-            for (uint32_t e = lane; e < ne; e += 32)
-                acc += pkc_ld_remote(buf + k * PKC_WARPS + (e % PKC_WARPS), e / PKC_WARPS);
-            tot[k] = warp_sum(acc);
-        }
+        for (int k = 0; k < NV; ++k) tot[k] = warp_sum(lane < nranks ? pkc_ld_remote(cta + k, lane) : 0.0);
         if (lane == 0) update(S, tot);
     }
     __syncthreads();
 }
 
-// The three values (r_j, a_j, b_j) of column j, from this CTA's shared memory or the owner's
-struct PkcCol {
-    double r, a, b;
-};
-
-__device__ __forceinline__ PkcCol pkc_gather(const double *r, const double *va, const double *vb, int64_t col, int64_t base,
-                                             int64_t rows_here, int64_t rc) {
-    PkcCol c;
-    if (col >= base && col < base + rows_here) {
-        const int64_t o = col - base;
-        c.r = r[o]; c.a = va[o]; c.b = vb[o];
-    } else {
-        const uint32_t q = uint32_t(col / rc);
-        const int64_t o = col - int64_t(q) * rc;
-        c.r = pkc_ld_remote(r + o, q); c.a = pkc_ld_remote(va + o, q); c.b = pkc_ld_remote(vb + o, q);
-    }
-    return c;
-}
-
-// y_g = sum_c A_gc z_c for the owned row g, where z_j = f(r_j, a_j, b_j) is formed from the
-// stored vectors as it is gathered (z_g, the row's own value, is passed in).  f(r, a, b) is
-// r + beta (a - omega b) for p (a = previous p, b = previous v) and r - alpha a for s (a = v);
-// every CTA forms a neighbour's z from the same operands in the same order as its owner, so the
-// products are those of the stored vector.
-template <typename F>
-__device__ __forceinline__ double pkc_spmv_row(const KVecs<double> &K, int64_t g, int64_t base, int64_t rows_here,
-                                               int64_t rc, double zg, const double *r, const double *va,
-                                               const double *vb, F &&f) {
+// y_g = (A x)_g for the owned row g; x is vector `vec` of the cluster, xg its value at g
+__device__ __forceinline__ double pkc_spmv_row(const KVecs<double> &K, const double *xv, int64_t g, int64_t base,
+                                               int64_t rows_here, int64_t rc, double xg) {
     const SliceMeta M = K.meta[g / SLICE];
     const int lane = int(g % SLICE);
-    double y = __ldg(K.A + M.col_base + lane) * zg;
+    double y = __ldg(K.A + M.col_base + lane) * xg;
 #pragma unroll 4
     for (int c = 1; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const double a = __ldg(K.A + q);
         const int64_t col = M.off_base >= 0 ? g + __ldg(K.slice_off + M.off_base + c) : int64_t(__ldg(K.col_idx + q));
-        const PkcCol z = pkc_gather(r, va, vb, col, base, rows_here, rc);
-        y = fma(a, f(z.r, z.a, z.b), y);
+        double xc;
+        if (col >= base && col < base + rows_here) {
+            xc = xv[col - base];
+        } else {
+            const uint32_t o = uint32_t(col / rc);
+            xc = pkc_ld_remote(xv + (col - int64_t(o) * rc), o);
+        }
+        y = fma(a, xc, y);
     }
     return y;
 }
@@ -143,42 +130,37 @@ __device__ __forceinline__ double pkc_spmv_row(const KVecs<double> &K, int64_t g
 #define PKC_ROWS for (int64_t l = threadIdx.x; l < rows_here; l += PKC_BLOCK)
 
 // The solve: x = 0 start, BiCGStab until (r, r) <= rtol^2 (b, b), a breakdown, the iteration
-// cap, divergence or (stall > 0) stagnation.  One cluster; grid = the cluster.
-//
-// Per iteration three phases, each ending with a reduction and a cluster barrier:
-//   A: p = r + beta (p' - omega v') (own rows; neighbours' formed while gathered),
-//      v = A p, (rh, v)                                     -> alpha
-//   B: s = r - alpha v (likewise), t = A s, (t, s), (t, t)   -> omega
-//   C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r) -> beta, convergence
-// p and v alternate between two buffers: phase A reads the previous iteration's (p', v') of
-// its neighbours while every CTA writes the new ones to the other buffer.  r is written only
-// in phase C, which no CTA reads remotely; s never leaves its CTA.
+// cap, divergence or (stall > 0) stagnation.  One cluster; grid = the cluster.  The phases and
+// their order are those of pk_solve<double>: A v = A p | B1 s = r - alpha v | B2 t = A s |
+// C x, r | D p, with a cluster barrier after each.
 __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
     extern __shared__ double sv[];              // [PKC_NVEC][rows_cta]
-    __shared__ double red_0[PKC_WARPS], red_a[PKC_WARPS], red_o[2 * PKC_WARPS], red_r[2 * PKC_WARPS];
+    __shared__ double th[2][PKC_BLOCK];         // per-thread partials of the reduction in progress
+    __shared__ double cta_0[1], cta_a[1], cta_o[2], cta_r[2];
     __shared__ KState S;                        // this CTA's copy of the state (warp 0 writes it)
     const uint32_t rank = pkc_rank(), nranks = pkc_nranks();
     const int64_t RC = P.rows_cta;
     const int64_t base = int64_t(rank) * RC;
     const int64_t rows_here = base >= P.n_pad ? 0 : (P.n_pad - base < RC ? P.n_pad - base : RC);
-    double *s = sv + PV_S * RC, *t = sv + PV_T * RC, *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
+    const int nact = int(rows_here < PKC_BLOCK ? rows_here : PKC_BLOCK);   // threads that own rows
+    double *p = sv + PV_P * RC, *v = sv + PV_V * RC, *s = sv + PV_S * RC, *t = sv + PV_T * RC;
+    double *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
     const KVecs<double> &K = P.K;
 
-    // setup: x = p' = v' = 0, r = rh = b, (b, b)
+    // setup: x = v = 0, r = rh = p = b, (b, b)
     double acc0 = 0.0;
     PKC_ROWS {
         const double b = __ldg(K.b + base + l);
-        x[l] = 0.0; s[l] = 0.0; t[l] = 0.0;
-        sv[PV_P0 * RC + l] = 0.0; sv[PV_P1 * RC + l] = 0.0; sv[PV_V0 * RC + l] = 0.0; sv[PV_V1 * RC + l] = 0.0;
-        r[l] = b; rh[l] = b;
+        x[l] = 0.0; v[l] = 0.0; s[l] = 0.0; t[l] = 0.0;
+        r[l] = b; rh[l] = b; p[l] = b;
         acc0 = fma(b, b, acc0);
     }
     {
         const double a1[1] = {acc0};
-        pkc_warp_partial<1>(a1, red_0);
+        pkc_cta_partial<1>(a1, th, nact, cta_0);
     }
     pkc_cluster_barrier();   // also: every CTA of the cluster has started before any remote access
-    pkc_reduce_update<1>(red_0, nranks, S, [&](KState &Q, const double *tot) {
+    pkc_reduce_update<1>(cta_0, nranks, S, [&](KState &Q, const double *tot) {
         const double bb = tot[0];
         Q.iter = 0; Q.last_improve = 0; Q.maxit = P.maxit; Q.stall = P.stall; Q.ticket = 0u;
         Q.alpha = 1.0; Q.omega = 1.0; Q.beta = 0.0; Q.scratch[0] = Q.scratch[1] = 0.0;
@@ -188,51 +170,45 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         Q.done = (bb == 0.0) ? K_CONVERGED : (!isfinite(bb) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
     });
 
-    int cur = 0;   // buffer of the p, v being formed; 1 - cur holds the previous ones
     while (S.done == K_RUNNING) {
-        double *p = sv + (PV_P0 + cur) * RC, *v = sv + (PV_V0 + cur) * RC;
-        const double *pp = sv + (PV_P0 + 1 - cur) * RC, *vp = sv + (PV_V0 + 1 - cur) * RC;
-        const double be = S.beta, om0 = S.omega;
-        auto fp = [be, om0](double rj, double pj, double vj) { return rj + be * (pj - om0 * vj); };
-
-        // A: p, v = A p, (rh, v)
+        // A: v = A p, (rh, v)
         double acc = 0.0;
         PKC_ROWS {
-            const double pg = fp(r[l], pp[l], vp[l]);
-            p[l] = pg;
-            const double y = pkc_spmv_row(K, base + l, base, rows_here, RC, pg, r, pp, vp, fp);
+            const double y = pkc_spmv_row(K, p, base + l, base, rows_here, RC, p[l]);
             v[l] = y;
             acc = fma(rh[l], y, acc);
         }
         {
             const double a1[1] = {acc};
-            pkc_warp_partial<1>(a1, red_a);
+            pkc_cta_partial<1>(a1, th, nact, cta_a);
         }
         pkc_cluster_barrier();
-        pkc_reduce_update<1>(red_a, nranks, S, [&](KState &Q, const double *tot) {
+        pkc_reduce_update<1>(cta_a, nranks, S, [&](KState &Q, const double *tot) {
             if (tot[0] == 0.0 || !isfinite(tot[0])) Q.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
             else Q.alpha = Q.rho / tot[0];
         });
         if (S.done != K_RUNNING) break;
 
-        // B: s = r - alpha v, t = A s, (t, s), (t, t)
+        // B1: s = r - alpha v (every CTA's s is complete before the SpMV gathers it)
         const double al = S.alpha;
-        auto fs = [al](double rj, double vj, double) { return rj - al * vj; };
+        PKC_ROWS s[l] = r[l] - al * v[l];
+        pkc_cluster_barrier();
+
+        // B2: t = A s, (t, s), (t, t)
         double ts = 0.0, tt = 0.0;
         PKC_ROWS {
-            const double sg = fs(r[l], v[l], 0.0);
-            s[l] = sg;
-            const double y = pkc_spmv_row(K, base + l, base, rows_here, RC, sg, r, v, v, fs);
+            const double sl = s[l];
+            const double y = pkc_spmv_row(K, s, base + l, base, rows_here, RC, sl);
             t[l] = y;
-            ts = fma(y, sg, ts);
+            ts = fma(y, sl, ts);
             tt = fma(y, y, tt);
         }
         {
             const double a2[2] = {ts, tt};
-            pkc_warp_partial<2>(a2, red_o);
+            pkc_cta_partial<2>(a2, th, nact, cta_o);
         }
         pkc_cluster_barrier();
-        pkc_reduce_update<2>(red_o, nranks, S, [&](KState &Q, const double *tot) {
+        pkc_reduce_update<2>(cta_o, nranks, S, [&](KState &Q, const double *tot) {
             if (!isfinite(tot[0]) || !isfinite(tot[1])) Q.done = K_NONFINITE;
             else Q.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
         });
@@ -250,13 +226,18 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         }
         {
             const double a2[2] = {rr1, rr2};
-            pkc_warp_partial<2>(a2, red_r);
+            pkc_cta_partial<2>(a2, th, nact, cta_r);
         }
         pkc_cluster_barrier();
-        pkc_reduce_update<2>(red_r, nranks, S, [&](KState &Q, const double *tot) {
+        pkc_reduce_update<2>(cta_r, nranks, S, [&](KState &Q, const double *tot) {
             pk_after_c(Q, tot[0], tot[1], P.maxit, P.stall);
         });
-        cur = 1 - cur;
+        if (S.done != K_RUNNING) break;
+
+        // D: p = r + beta (p - omega v)
+        const double be = S.beta;
+        PKC_ROWS p[l] = r[l] + be * (p[l] - om * v[l]);
+        pkc_cluster_barrier();
     }
 
     // results: x of the owned rows, the state from rank 0; the final barrier keeps every

@@ -59,7 +59,7 @@ def test_cluster_solve_matches_oracle_and_grid_solve(P, case, cluster):
 
 
 def test_cluster_solve_too_large_falls_back_to_the_grid_solve(P):
-    """16 x 3168 rows is the most a cluster holds: a 300 x 300 grid (90 601 rows) uses the
+    """16 x 3904 rows is the most a cluster holds: a 300 x 300 grid (90 601 rows) uses the
     grid-wide solve even when a cluster is asked for."""
     mesh = wl.unit_square_mesh(300)
     h = P.Handle(mesh, P.make_problem(a=None, a_degree=1), P.default_options(krylov_cluster=16))
