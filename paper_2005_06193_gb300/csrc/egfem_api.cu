@@ -72,6 +72,8 @@ struct KWork {
     // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
     int pkc_cluster = 0;
     int32_t pkc_rows = 0;
+    int32_t pkc_op = 0;                   // ELL columns of the shared-memory operator copy (0: none)
+    size_t pkc_smem = 0;                  // dynamic shared memory per CTA
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     bool ready = false;
@@ -306,15 +308,17 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     int smem_optin = 0;
     EG_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const int64_t static_smem = 12288;  // the kernel's static shared memory (8.4 KB), rounded up
-    const int64_t rows_max = (int64_t(smem_optin) - static_smem) / (PKC_NVEC * 8) / SLICE * SLICE;
-    if (rows_max < SLICE) return EGFEM_OK;
+    const int mc = h->csf.max_cols;     // ELL columns of the shared-memory operator copy
+    auto rows_max = [&](int op) { return (int64_t(smem_optin) - static_smem) / pkc_row_bytes(op) / SLICE * SLICE; };
     auto rows_for = [&](int64_t c) { return (h->n_pad + c * SLICE - 1) / (c * SLICE) * SLICE; };
     int64_t c = h->opts.krylov_cluster > 0 ? h->opts.krylov_cluster : 1;
     if (h->opts.krylov_cluster == 0)
         while (c < PKC_MAX_CLUSTER && rows_for(c) > kPkcTargetRows) c *= 2;
-    if (c > PKC_MAX_CLUSTER || rows_for(c) > rows_max) return EGFEM_OK;
+    if (c > PKC_MAX_CLUSTER || rows_for(c) > rows_max(0)) return EGFEM_OK;
     const int64_t rows = rows_for(c);
-    const size_t smem = size_t(rows) * PKC_NVEC * sizeof(double);
+    // the operator goes to shared memory when it fits (column codes hold 16-bit offsets)
+    const int op = (mc <= 255 && rows <= 65535 && rows <= rows_max(mc)) ? mc : 0;
+    const size_t smem = size_t((rows * pkc_row_bytes(op) + 15) / 16 * 16);
     EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg{};
@@ -330,19 +334,22 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     }
     W.pkc_cluster = int(c);
     W.pkc_rows = int32_t(rows);
+    W.pkc_op = op;
+    W.pkc_smem = smem;
     return EGFEM_OK;
 }
 
 egfem_status launch_pkc(egfem_t *h, KWork<double> &W, double rtol, int32_t maxit, int32_t stall) {
     PkcArgs P{};
     P.K = kvecs(h, W);
-    P.st = h->st; P.n_pad = h->n_pad; P.rows_cta = W.pkc_rows; P.rtol = rtol; P.maxit = maxit; P.stall = stall;
+    P.st = h->st; P.n_pad = h->n_pad; P.rows_cta = W.pkc_rows; P.op_cols = W.pkc_op;
+    P.rtol = rtol; P.maxit = maxit; P.stall = stall;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = unsigned(W.pkc_cluster); attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(unsigned(W.pkc_cluster)); cfg.blockDim = dim3(PKC_BLOCK);
-    cfg.dynamicSmemBytes = size_t(W.pkc_rows) * PKC_NVEC * sizeof(double);
+    cfg.dynamicSmemBytes = W.pkc_smem;
     cfg.stream = h->hs; cfg.attrs = attr; cfg.numAttrs = 1;
     EG_CUDA(cudaLaunchKernelEx(&cfg, pkc_solve, P));
     return EGFEM_OK;

@@ -20,8 +20,11 @@
 // (forming p and s inside the SpMV for each gathered neighbour would save two barriers but
 // triple the SpMV's FP64 work).
 //
-// The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve and
-// is read from global memory.  Arithmetic and stopping rules are those of pk_solve<double>.
+// The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve.
+// When it fits beside the vectors, each CTA copies its rows of it to shared memory at the
+// start (ELL values and column codes naming the owning CTA and offset), and the iterations
+// touch no global memory; otherwise it is read from global memory.  Arithmetic and stopping
+// rules are those of pk_solve<double>.
 #pragma once
 
 #include "egfem_persist.cuh"
@@ -39,9 +42,16 @@ struct PkcArgs {
     KState *st;             // final state (written by rank 0)
     int64_t n_pad;          // rows (whole slices)
     int32_t rows_cta;       // rows per CTA (a multiple of SLICE); the last CTA may own fewer
+    int32_t op_cols;        // > 0: the operator is copied to shared memory as op_cols ELL columns
     double rtol;
     int32_t maxit, stall;
 };
+
+// Shared-memory bytes per row: the Krylov vectors, and with the operator copy its ELL values,
+// column codes (owning rank << 16 | offset in that CTA) and the row's column count.
+__host__ __device__ constexpr int64_t pkc_row_bytes(int op_cols) {
+    return int64_t(PKC_NVEC) * 8 + (op_cols > 0 ? int64_t(op_cols) * 12 + 1 : 0);
+}
 
 __device__ __forceinline__ void pkc_cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -127,6 +137,21 @@ __device__ __forceinline__ double pkc_spmv_row(const KVecs<double> &K, const dou
     return y;
 }
 
+// the same product from the shared-memory copy of the operator (row l of this CTA)
+__device__ __forceinline__ double pkc_spmv_row_smem(const double *opv, const uint32_t *opc, const uint8_t *opn,
+                                                    const double *xv, int64_t l, int64_t rc, uint32_t rank, double xg) {
+    double y = opv[l] * xg;
+    const int nc = opn[l];
+#pragma unroll 4
+    for (int c = 1; c < nc; ++c) {
+        const uint32_t code = opc[int64_t(c) * rc + l];
+        const uint32_t o = code >> 16, off = code & 0xFFFFu;
+        const double xc = o == rank ? xv[off] : pkc_ld_remote(xv + off, o);
+        y = fma(opv[int64_t(c) * rc + l], xc, y);
+    }
+    return y;
+}
+
 #define PKC_ROWS for (int64_t l = threadIdx.x; l < rows_here; l += PKC_BLOCK)
 
 // The solve: x = 0 start, BiCGStab until (r, r) <= rtol^2 (b, b), a breakdown, the iteration
@@ -146,6 +171,32 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
     double *p = sv + PV_P * RC, *v = sv + PV_V * RC, *s = sv + PV_S * RC, *t = sv + PV_T * RC;
     double *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
     const KVecs<double> &K = P.K;
+    // the operator copy (when P.op_cols > 0): values [op_cols][RC], codes [op_cols][RC], counts [RC]
+    const int MC = P.op_cols;
+    double *opv = sv + PKC_NVEC * RC;
+    uint32_t *opc = reinterpret_cast<uint32_t *>(opv + int64_t(MC) * RC);
+    uint8_t *opn = reinterpret_cast<uint8_t *>(opc + int64_t(MC) * RC);
+    if (MC > 0) {
+        PKC_ROWS {
+            const int64_t g = base + l;
+            const SliceMeta M = K.meta[g / SLICE];
+            const int lane = int(g % SLICE);
+            opn[l] = uint8_t(M.ncol < MC ? M.ncol : MC);
+            for (int c = 0; c < MC; ++c) {
+                double a = 0.0;
+                uint32_t code = (rank << 16) | uint32_t(l);
+                if (c < M.ncol) {
+                    const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+                    a = __ldg(K.A + q);
+                    const int64_t col = M.off_base >= 0 ? g + __ldg(K.slice_off + M.off_base + c) : int64_t(__ldg(K.col_idx + q));
+                    const uint32_t o = uint32_t(col / RC);
+                    code = (o << 16) | uint32_t(col - int64_t(o) * RC);
+                }
+                opv[int64_t(c) * RC + l] = a;
+                opc[int64_t(c) * RC + l] = code;
+            }
+        }
+    }
 
     // setup: x = v = 0, r = rh = p = b, (b, b)
     double acc0 = 0.0;
@@ -174,7 +225,8 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         // A: v = A p, (rh, v)
         double acc = 0.0;
         PKC_ROWS {
-            const double y = pkc_spmv_row(K, p, base + l, base, rows_here, RC, p[l]);
+            const double y = MC > 0 ? pkc_spmv_row_smem(opv, opc, opn, p, l, RC, rank, p[l])
+                                    : pkc_spmv_row(K, p, base + l, base, rows_here, RC, p[l]);
             v[l] = y;
             acc = fma(rh[l], y, acc);
         }
@@ -198,7 +250,8 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         double ts = 0.0, tt = 0.0;
         PKC_ROWS {
             const double sl = s[l];
-            const double y = pkc_spmv_row(K, s, base + l, base, rows_here, RC, sl);
+            const double y = MC > 0 ? pkc_spmv_row_smem(opv, opc, opn, s, l, RC, rank, sl)
+                                    : pkc_spmv_row(K, s, base + l, base, rows_here, RC, sl);
             t[l] = y;
             ts = fma(y, sl, ts);
             tt = fma(y, y, tt);
