@@ -300,7 +300,7 @@ int one_wave(const egfem_t *h, const void *func) {
 // giving at most kPkcTargetRows rows per CTA (or the krylov_cluster option), and the launch
 // configuration must be schedulable (cudaOccupancyMaxActiveClusters).  Leaves W.pkc_cluster = 0
 // when any of this fails: the grid-wide persistent solve is used instead.
-constexpr int64_t kPkcTargetRows = 512;
+constexpr int64_t kPkcTargetRows = 128;
 
 egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     W.pkc_cluster = 0;
