@@ -67,7 +67,7 @@ class _Spec(ctypes.Structure):
                 ("c_kind", ctypes.c_int), ("c_p", ctypes.c_double), ("c_scale", ctypes.c_double), ("c_deg", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("qpts", ctypes.c_int),
                 ("a_shift", ctypes.c_double), ("a_quad", ctypes.c_int), ("c_quad", ctypes.c_int),
-                ("rule", ctypes.c_int), ("sigma", ctypes.c_double)]
+                ("rule", ctypes.c_int), ("sigma", ctypes.c_double), ("c_product", ctypes.c_int)]
 
 
 def lib():
@@ -140,7 +140,9 @@ class Problem:
     per point of the symmetric degree-k rule on every cell.  ``rule=k`` makes every integral
     (the standard Galerkin approach, the load vector and the Lagrange-space tensors) use that
     same rule instead of the collapsed Gauss rule of ``qpts`` points.  ``sigma`` adds the linear
-    reaction sigma * int u phi_i (P1 mass matrix).  ``cells`` restricts the tensor
+    reaction sigma * int u phi_i (P1 mass matrix).  ``c_product=True`` makes the reaction
+    gamma * int c u phi_i (the trilinear mass form M3 : (u x c), decomposition (a) of the
+    superconductivity example) instead of gamma * int c phi_i.  ``cells`` restricts the tensor
     assembly (and the SGA integrals) to a subset of cells, so that single rows of a
     large problem can be evaluated exactly: a row is complete when every cell that
     contains its vertex is in the subset.
@@ -148,7 +150,7 @@ class Problem:
 
     def __init__(self, mesh, *, a=("pow", 2.0), a_scale=1.0, a_deg=2, c=None, c_scale=1.0, c_deg=1,
                  gamma=0.0, kappa=1.0, qpts=4, cells=None, a_space="lagrange", c_space="lagrange", rule=0,
-                 sigma=0.0):
+                 sigma=0.0, c_product=False):
         self.mesh = mesh
         self._X = np.ascontiguousarray(mesh.coords, dtype=np.float64)
         self._cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
@@ -168,6 +170,7 @@ class Problem:
         s.gamma, s.kappa, s.qpts = float(gamma), float(kappa), int(qpts)
         s.a_quad, s.c_quad, s.rule = int(a_space == "quad"), int(c_space == "quad"), int(rule)
         s.sigma = float(sigma)
+        s.c_product = int(bool(c_product))
         self._spec = s
         self._sel = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
         L = lib()

@@ -507,6 +507,8 @@ typedef struct {
                             Lagrange-space tensors) instead of the collapsed Gauss rule */
     double sigma;        /* linear reaction sigma * int u phi_i = sigma (M u)_i, M the P1 mass matrix
                             (the M u term of the superconductivity decomposition (b), Sec. 5) */
+    int c_product;       /* nonzero: the reaction is gamma int c u phi_i = gamma M3 : (u x c) with the
+                            trilinear mass form M3_imk = int eta_m phi_k phi_i (decomposition (a)) */
 } orc_spec;
 
 typedef struct {
@@ -523,6 +525,7 @@ typedef struct {
     orc_coo M;            /* (i, m, 0) -> M_im                            */
     orc_coo Pa, Pc;       /* (m, j, 0) -> (Pi)_mj                         */
     orc_coo Mu;           /* (i, k, 0) -> int phi_k phi_i (when sigma != 0) */
+    orc_coo M3;           /* (i, m, k) -> int eta_m phi_k phi_i (c_product)  */
     double *kappa_field;  /* optional kappa per W_a node (NULL: constant)  */
     int *cell_mask;       /* cells included in the tensor assembly         */
 } orc_problem;
@@ -625,6 +628,33 @@ static void local_tensors_quad(const orc_problem *P, int c, int nq, const double
     }
 }
 
+/* Trilinear mass form of cell c (decomposition (a) of the superconductivity example, Sec. 5):
+ * M3loc[a][m][b] = int_K eta_m phi_b phi_a, by the oracle's quadrature for a Lagrange W and by
+ * the delta basis w_l phi_a(x_l) phi_b(x_l) for a quadrature space. */
+static void local_mass3(const orc_problem *P, int c, int quad, const orc_elem *EW, const double *eta_tab, int nq,
+                        const double *qp, const double *qw, double *M3) {
+    int dim = P->s.dim, nv = dim + 1;
+    orc_geom G; cell_geom(dim, P->s.X, P->s.cells + (size_t)c * nv, &G);
+    if (quad) {
+        for (int l = 0; l < nq; ++l) {
+            double wl = qw[l] * factorial(dim) * G.vol, phi[ORC_MAXNB];
+            elem_eval(&P->P1, qp + l * dim, phi, NULL);
+            for (int a = 0; a < nv; ++a)
+                for (int b = 0; b < nv; ++b) M3[(a * nq + l) * nv + b] = wl * phi[a] * phi[b];
+        }
+        return;
+    }
+    int nw = EW->nb;
+    memset(M3, 0, sizeof(double) * nv * nw * nv);
+    for (int q = 0; q < P->nq; ++q) {
+        double wq = P->qw[q] * factorial(dim) * G.vol;
+        const double *eta = eta_tab + q * ORC_MAXNB, *phi = P->phi_q + q * ORC_MAXNB;
+        for (int a = 0; a < nv; ++a)
+            for (int m = 0; m < nw; ++m)
+                for (int b = 0; b < nv; ++b) M3[(a * nw + m) * nv + b] += wq * eta[m] * phi[a] * phi[b];
+    }
+}
+
 orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_list) {
     orc_problem *P = calloc(1, sizeof(orc_problem));
     P->s = *spec;
@@ -670,7 +700,14 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
             for (int m = 0; m < nwa; ++m)
                 for (int b = 0; b < nv; ++b)
                     coo_push(&P->T, cv[a], wa[m], cv[b], Tloc[(a * nwa + m) * nv + b]);
-        if (spec->c_kind != ORC_G_NONE) {
+        if (spec->c_kind != ORC_G_NONE && spec->c_product) {
+            double M3loc[4 * ORC_MAXNB * 4];
+            local_mass3(P, c, P->s.c_quad, &P->Ec, P->eta_c_q, P->cq_n, P->cq_p, P->cq_w, M3loc);
+            const int *wc = P->Sc.cell2dof + (size_t)c * nwc;
+            for (int a = 0; a < nv; ++a)
+                for (int m = 0; m < nwc; ++m)
+                    for (int b = 0; b < nv; ++b) coo_push(&P->M3, cv[a], wc[m], cv[b], M3loc[(a * nwc + m) * nv + b]);
+        } else if (spec->c_kind != ORC_G_NONE) {
             if (P->s.c_quad) local_tensors_quad(P, c, P->cq_n, P->cq_p, P->cq_w, NULL, Mloc);
             else local_tensors(P, c, &P->Ec, P->eta_c_q, NULL, Mloc);
             const int *wc = P->Sc.cell2dof + (size_t)c * nwc;
@@ -681,6 +718,7 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
     }
     coo_compress(&P->T);
     coo_compress(&P->M);
+    coo_compress(&P->M3);
     if (spec->sigma != 0.0) {
         /* the P1 mass matrix by the same quadrature (the P1 element as its own W space) */
         for (int c = 0; c < spec->nc; ++c) {
@@ -698,7 +736,7 @@ orc_problem *orc_create(const orc_spec *spec, const int *cell_list, int n_cell_l
 void orc_destroy(orc_problem *P) {
     if (!P) return;
     space_free(&P->Sa); space_free(&P->Sc);
-    free(P->T.t); free(P->M.t); free(P->Pa.t); free(P->Pc.t); free(P->Mu.t);
+    free(P->T.t); free(P->M.t); free(P->Pa.t); free(P->Pc.t); free(P->Mu.t); free(P->M3.t);
     free(P->kappa_field); free(P->cell_mask);
     free(P->phi_q); free(P->eta_a_q); free(P->eta_c_q);
     free(P);
@@ -817,6 +855,9 @@ void orc_egfem_residual(const orc_problem *P, const double *u, const double *b, 
     if (P->s.c_kind != ORC_G_NONE)
         for (size_t t = 0; t < P->M.n; ++t) r[P->M.t[t].i] += P->s.gamma * P->M.t[t].v * c[P->M.t[t].j];
     for (size_t t = 0; t < P->Mu.n; ++t) r[P->Mu.t[t].i] += P->s.sigma * P->Mu.t[t].v * u[P->Mu.t[t].j];
+    /* product reaction: gamma sum_{m,k} M3_imk c_m u_k */
+    for (size_t t = 0; t < P->M3.n; ++t)
+        r[P->M3.t[t].i] += P->s.gamma * P->M3.t[t].v * c[P->M3.t[t].j] * u[P->M3.t[t].k];
     for (int i = 0; i < nv; ++i) {
         if (P->s.dir[i]) r[i] = u[i] - (uD ? uD[i] : 0.0);
         else r[i] -= b ? b[i] : 0.0;
@@ -880,8 +921,28 @@ static int64_t egfem_matrix(const orc_problem *P, const double *u, int picard, i
     }
     free(pstart);
     free(Pg.t);
+    /* product reaction: gamma (M3 .2 c) (kept by Picard), and gamma (M3 .3 u) diag(c') Pi_c */
+    if (P->s.c_product && P->s.c_kind != ORC_G_NONE) {
+        for (size_t t = 0; t < P->M3.n; ++t)
+            coo_push(&J, P->M3.t[t].i, P->M3.t[t].k, 0, P->s.gamma * P->M3.t[t].v * c[P->M3.t[t].j]);
+        if (!picard) {
+            orc_coo E = {0};   /* E_im = sum_k M3_imk u_k */
+            for (size_t t = 0; t < P->M3.n; ++t) coo_push(&E, P->M3.t[t].i, P->M3.t[t].j, 0, P->M3.t[t].v * u[P->M3.t[t].k]);
+            coo_compress(&E);
+            size_t *cs = calloc(P->Sc.n + 1, sizeof(size_t));
+            for (size_t t = 0; t < P->Pc.n; ++t) cs[P->Pc.t[t].i + 1]++;
+            for (int m = 0; m < P->Sc.n; ++m) cs[m + 1] += cs[m];
+            for (size_t t = 0; t < E.n; ++t) {
+                int64_t i = E.t[t].i, m = E.t[t].j;
+                double e = P->s.gamma * E.t[t].v * cp[m];
+                for (size_t q = cs[m]; q < cs[m + 1]; ++q) coo_push(&J, i, P->Pc.t[q].j, 0, e * P->Pc.t[q].v);
+            }
+            free(cs);
+            free(E.t);
+        }
+    }
     /* gamma M diag(g_c') Pi_c */
-    if (!picard && P->s.c_kind != ORC_G_NONE) {
+    if (!picard && P->s.c_kind != ORC_G_NONE && !P->s.c_product) {
         size_t *cs = calloc(P->Sc.n + 1, sizeof(size_t));
         for (size_t t = 0; t < P->Pc.n; ++t) cs[P->Pc.t[t].i + 1]++;
         for (int m = 0; m < P->Sc.n; ++m) cs[m + 1] += cs[m];
@@ -953,6 +1014,7 @@ void orc_sga_residual(const orc_problem *P, const double *u, const double *b, co
             }
             double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
             double reac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_val(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
+            if (P->s.c_product) reac *= uh;
             reac += P->s.sigma * uh;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;
@@ -996,6 +1058,8 @@ int64_t orc_sga_jacobian(const orc_problem *P, const double *u, int64_t cap, int
             double coef = kappa_at(P, c, eta) + ga_val(&P->s, arg);
             double dcoef = ga_der(&P->s, arg);
             double dreac = (P->s.c_kind != ORC_G_NONE) ? P->s.gamma * g_der(P->s.c_kind, P->s.c_p, P->s.c_scale, uh) : 0.0;
+            if (P->s.c_product && P->s.c_kind != ORC_G_NONE)   /* d(g(u) u)/du = g'(u) u + g(u) */
+                dreac = dreac * uh + P->s.gamma * g_val(P->s.c_kind, P->s.c_p, P->s.c_scale, uh);
             dreac += P->s.sigma;
             for (int a = 0; a < nv; ++a) {
                 double gu = 0.0;

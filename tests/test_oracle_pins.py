@@ -754,3 +754,39 @@ def test_superconductivity_manufactured_solution_second_order(space):
         errs.append(np.sqrt(np.mean((u - ue) ** 2)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates.min() > 1.8, (errs, rates)
+
+
+@pytest.mark.parametrize("space", ["p2", "i4"])
+def test_superconductivity_decomposition_a_reproduces_sga(space):
+    """Decomposition (a): nu K u + M3 : (u x c~) with c~ = u^2 + 1, written as sigma M u (the +1)
+    plus the product reaction int c u phi_i with c = u^2.  P2 holds u^2 exactly and I_4 integrates
+    u^3 phi_i exactly, so both equal the standard Galerkin approach, and the residual equals that
+    of decomposition (b) (nu K u + M u + M^c u^3 on P3)."""
+    mesh = wl.unit_square_mesh(6)
+    u = wl.random_vector(mesh.n_nodes, 95, 0.8)
+    b = wl.random_vector(mesh.n_nodes, 96) * 1e-3
+    kw = dict(c_deg=2) if space == "p2" else dict(c_deg=4, c_space="quad")
+    A = oracle.Problem(mesh, a=None, a_deg=1, kappa=0.01, c=("pow", 2.0), gamma=1.0, sigma=1.0, c_product=True, **kw)
+    rs = A.residual(u, b, method="sga")
+    assert np.abs(A.residual(u, b) - rs).max() <= 1e-13 * np.abs(rs).max()
+    Js = A.jacobian(u, method="sga")
+    assert abs(A.jacobian(u) - Js).max() <= 1e-13 * abs(Js).max()
+    B = _supercond(mesh, 0.01, c_deg=3)
+    assert np.abs(B.residual(u, b) - A.residual(u, b)).max() <= 1e-13 * np.abs(rs).max()
+
+
+def test_product_reaction_jacobian_matches_finite_differences():
+    """Case 2 (exp interpolated in P2) for the product form: the Jacobian against central
+    differences of the residual (both terms of d(c u)/du)."""
+    mesh = wl.unit_square_mesh(5)
+    P = oracle.Problem(mesh, a=None, a_deg=1, kappa=0.5, c=("exp",), c_deg=2, gamma=0.7, c_product=True)
+    u = wl.random_vector(mesh.n_nodes, 97, 0.8)
+    b = wl.random_vector(mesh.n_nodes, 98)
+    J = P.jacobian(u).toarray()
+    free = np.where(mesh.dirichlet == 0)[0]
+    h = 1e-6
+    for l in free[::2]:
+        e = np.zeros(mesh.n_nodes)
+        e[l] = h
+        fd = (P.residual(u + e, b) - P.residual(u - e, b)) / (2 * h)
+        assert np.abs(fd[free] - J[free, l]).max() <= 1e-8 * max(1.0, np.abs(J).max())
