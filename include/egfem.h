@@ -120,6 +120,10 @@ typedef struct {
     double sigma;        /* linear reaction sigma int u phi_i = sigma (M u)_i, M the P1 mass
                             matrix (the M u term of the superconductivity decomposition (b),
                             Sec. 5); nonzero needs EGFEM_OP_MATRIX_FREE                   */
+    int32_t c_product;   /* nonzero: the reaction is gamma int c u phi_i = gamma M3 : (u x c), with
+                            the trilinear mass form M3_imk = int eta_m phi_k phi_i on W_c
+                            (decomposition (a) of the superconductivity example, Sec. 5);
+                            needs EGFEM_OP_MATRIX_FREE                                  */
 } egfem_problem;
 
 /* The approximation space W of a nonlinearity (Sec. 3.1).  EGFEM_W_QUADRATURE is Case 3's

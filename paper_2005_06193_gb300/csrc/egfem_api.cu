@@ -576,18 +576,24 @@ egfem_status lagrange_local(int d, int p, MfLocal &L) {
         const int l = L.nw++;
         for (int a = 0; a < 4; ++a) L.w[l][a] = a < nv ? double(alpha[a]) / double(p) : 0.0;
         L.iota[l] = basis_integral(d, p, kind);
-        for (int a = 0; a < 4; ++a) {
+        // int_K lambda^beta / |K| for beta = e + extra (exponent vectors)
+        auto moment = [&](int a, int b) {
             double m = 0.0;
-            for (int e = 0; a < nv && e < 625; ++e) {
+            for (int e = 0; e < 625; ++e) {
                 if (poly[e] == 0.0) continue;
                 int ex[4] = {e % 5, (e / 5) % 5, (e / 25) % 5, e / 125};
-                ex[a] += 1;
+                if (a >= 0) ex[a] += 1;
+                if (b >= 0) ex[b] += 1;
                 double num = fact(d);
                 int tot = 0;
                 for (int j = 0; j < nv; ++j) { num *= fact(ex[j]); tot += ex[j]; }
                 m += poly[e] * num / fact(tot + d);
             }
-            L.mu[l][a] = m;
+            return m;
+        };
+        for (int a = 0; a < 4; ++a) {
+            L.mu[l][a] = a < nv ? moment(a, -1) : 0.0;
+            for (int b = 0; b < 4; ++b) L.mu3[l][a][b] = (a < nv && b < nv) ? moment(a, b) : 0.0;
         }
     };
     for (int a = 0; a < nv; ++a) { int al[4] = {0, 0, 0, 0}; al[a] = p; add(al, W_VERTEX); }
@@ -645,7 +651,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     if (prob->c_kind == EGFEM_G_GRADPOW) { g_last_error = "c: the gradient nonlinearity is a coefficient"; return EGFEM_ERR_INVALID_ARG; }
     const bool gradc = prob->a_kind == EGFEM_G_GRADPOW;
     // a Lagrange W_c of degree 2 or 3 (evaluated by the element-local operator)
-    const bool lag_c = !quad_c && prob->c_kind != EGFEM_G_NONE && prob->c_degree > 1;
+    const bool lag_c = !quad_c && prob->c_kind != EGFEM_G_NONE && (prob->c_degree > 1 || prob->c_product);
+    if (prob->c_product && prob->c_kind == EGFEM_G_NONE) { g_last_error = "c_product needs a reaction nonlinearity"; return EGFEM_ERR_INVALID_ARG; }
     if (!std::isfinite(prob->sigma)) { g_last_error = "sigma must be finite"; return EGFEM_ERR_INVALID_ARG; }
     if (gradc) {
         // (shift + s)^q on s = ||grad u||^2 >= 0: finite with its derivative at s = 0 when
@@ -662,7 +669,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     if (opts) h->opts = *opts;
     if (h->opts.precision != EGFEM_PREC_FP64 && h->opts.precision != EGFEM_PREC_MIXED) { g_last_error = "bad precision"; return EGFEM_ERR_INVALID_ARG; }
     if (h->opts.op != EGFEM_OP_CSF && h->opts.op != EGFEM_OP_MATRIX_FREE) { g_last_error = "unknown operator variant"; return EGFEM_ERR_INVALID_ARG; }
-    if ((gradc || quad_a || quad_c || lag_c || prob->sigma != 0.0) && h->opts.op != EGFEM_OP_MATRIX_FREE) {
+    if ((gradc || quad_a || quad_c || lag_c || prob->sigma != 0.0 || prob->c_product) && h->opts.op != EGFEM_OP_MATRIX_FREE) {
         // the P0 and I_k forms are multiples of the cell stiffness S^K, and the reaction forms
         // on I_k or P2/P3 and the linear mass term are per-cell products: the element-local
         // operator evaluates them without a stored tensor
@@ -794,6 +801,8 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
                         Lc.w[l][a] = a < nv ? qc_bary[l][a] : 0.0;
                         Lc.mu[l][a] = qc_w[l] * Lc.w[l][a];
                     }
+                    for (int a = 0; a < 4; ++a)
+                        for (int b = 0; b < 4; ++b) Lc.mu3[l][a][b] = qc_w[l] * Lc.w[l][a] * Lc.w[l][b];
                     Lc.iota[l] = qc_w[l];
                 }
                 Lc.nw = nqc;
@@ -807,6 +816,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
     h->nl.c_kind = prob->c_kind; h->nl.c_pi = int32_t(prob->c_p); h->nl.c_scale = prob->c_scale;
     h->nl.gamma = prob->gamma; h->nl.kappa = prob->kappa; h->nl.kappa_field = nullptr;
     h->nl.sigma = prob->sigma;
+    h->nl.c_product = prob->c_product ? 1 : 0;
     // workspace
     h->n_pad = int64_t(H.n_slices) * SLICE;
     auto grid_for = [&](int64_t per_block) {

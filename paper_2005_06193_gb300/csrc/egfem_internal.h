@@ -117,6 +117,7 @@ struct Nonlin {
     int32_t picard;              // nonzero: the Picard matrix (no g' terms) instead of the Jacobian
     double a_preal, a_shift;     // EGFEM_G_GRADPOW: g = a_scale (a_shift + |grad u|^2)^a_preal
     double sigma;                // linear reaction sigma M u (element-local operator only)
+    int32_t c_product;           // reaction gamma int c u phi_i (element-local operator only)
 };
 
 // Host-side assembly entry points (egfem_build.cpp).

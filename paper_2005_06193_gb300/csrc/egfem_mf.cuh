@@ -29,6 +29,7 @@ struct MfLocal {
     double w[MF_MAXW][4];               // barycentric weights on the cell's vertices
     double iota[MF_MAXW];               // int_K eta_l / |K|
     double mu[MF_MAXW][4];              // int_K lambda_a eta_l / |K| (reaction spaces)
+    double mu3[MF_MAXW][4][4];          // int_K lambda_a lambda_b eta_l / |K| (product reaction)
 };
 
 struct MfArgs {
@@ -150,7 +151,11 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
         for (int a = 0; a < NV; ++a) rho[a] = 0.0;
 #pragma unroll
         for (int q = 0; q < NV * NV; ++q) R[q] = 0.0;
+        // The product form (decomposition (a), Sec. 5), gamma int c u phi_a = gamma |K| sum_l c_l
+        // sum_k mu3_lak u_k, has R_ab = gamma |K| sum_l [c_l mu3_lab + (mu3_la. u) c'_l Pi_lb].
+        // The g' terms are left out of the Picard matrix (the product's c_l mu3 term stays).
         const double gv = M.nl.gamma * M.vol[c];
+        const bool prod = M.nl.c_product != 0, newton = !M.nl.picard;
         for (int l = 0; l < M.loc_c.nw; ++l) {
             double uq = 0.0;
 #pragma unroll
@@ -160,11 +165,20 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
             const double wg = gv * g, wd = gv * gp;
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
-                const double ma = M.loc_c.mu[l][a];
-                rho[a] += wg * ma;
-                const double md = wd * ma;
+                double ma = M.loc_c.mu[l][a];
+                if (prod) {
+                    ma = 0.0;
 #pragma unroll
-                for (int b = 0; b < NV; ++b) R[a * NV + b] += md * M.loc_c.w[l][b];
+                    for (int k = 0; k < NV; ++k) ma += M.loc_c.mu3[l][a][k] * uk[k];
+#pragma unroll
+                    for (int b = 0; b < NV; ++b) R[a * NV + b] += wg * M.loc_c.mu3[l][a][b];
+                }
+                rho[a] += wg * ma;
+                if (newton) {
+                    const double md = wd * ma;
+#pragma unroll
+                    for (int b = 0; b < NV; ++b) R[a * NV + b] += md * M.loc_c.w[l][b];
+                }
             }
         }
 #pragma unroll
@@ -252,12 +266,11 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             }
         }
         if (nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
-            // gamma M^c c with W_c = I_k, P2 or P3: the cell pass's rho_a and R_ab (see there)
+            // gamma M^c c with W_c = I_k, P2 or P3 (or the product form): the cell pass's rho_a
+            // and R_ab, the latter already without the g' terms for the Picard matrix
             r += E[1 + 2 * NV + a];
-            if (!nl.picard) {
 #pragma unroll
-                for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + a * NV + b];
-            }
+            for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + a * NV + b];
         } else if (nl.c_kind != EGFEM_G_NONE) {
             // gamma M^c c with W_c = P1: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
             const double m0 = M.vol[cell] / double((DIM + 1) * (DIM + 2));

@@ -45,7 +45,7 @@ class Problem(ctypes.Structure):
                 ("a_degree", ctypes.c_int32), ("c_kind", ctypes.c_int32), ("c_p", ctypes.c_double),
                 ("c_scale", ctypes.c_double), ("c_degree", ctypes.c_int32), ("gamma", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("a_shift", ctypes.c_double), ("a_space", ctypes.c_int32),
-                ("c_space", ctypes.c_int32), ("sigma", ctypes.c_double)]
+                ("c_space", ctypes.c_int32), ("sigma", ctypes.c_double), ("c_product", ctypes.c_int32)]
 
 
 class Options(ctypes.Structure):
@@ -162,11 +162,12 @@ def selftest_grid_barrier(blocks: int, arrive: int, wait_ms: float):
 
 
 def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_scale=1.0, gamma=0.0, kappa=1.0,
-                 a_space="lagrange", c_space="lagrange", sigma=0.0) -> Problem:
+                 a_space="lagrange", c_space="lagrange", sigma=0.0, c_product=False) -> Problem:
     """a = (kind, exponent[, shift]): ("pow", p), ("exp",), ("gradpow", q, shift) for the gradient
     coefficient (shift + |grad u|^2)^q (with a_degree=0); c likewise for the reaction.
     a_space / c_space = "quad" selects the quadrature space I_k with k = a_degree / c_degree;
-    sigma adds the linear reaction sigma * int u phi_i."""
+    sigma adds the linear reaction sigma * int u phi_i; c_product makes the reaction
+    gamma * int c u phi_i (trilinear mass form) instead of gamma * int c phi_i."""
     spaces = {"lagrange": W_LAGRANGE, "quad": W_QUADRATURE}
     kinds = {None: G_NONE, "none": G_NONE, "pow": G_POW, "exp": G_EXP, "gradpow": G_GRADPOW}
     p = Problem()
@@ -180,6 +181,7 @@ def make_problem(a=("pow", 2), a_degree=2, a_scale=1.0, c=None, c_degree=1, c_sc
     p.gamma, p.kappa = float(gamma), float(kappa)
     p.a_space, p.c_space = spaces[a_space], spaces[c_space]
     p.sigma = float(sigma)
+    p.c_product = int(bool(c_product))
     return p
 
 

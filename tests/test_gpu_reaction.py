@@ -98,3 +98,48 @@ def test_superconductivity_newton_matches_sga(P, space, nu, prec):
     torch.cuda.synchronize()
     assert st.status == 0
     assert rel(u.cpu().numpy(), u_sga) <= (1e-8 if mixed else 1e-11)
+
+
+# product reaction gamma int c u phi_i (decomposition (a)): (dim, W_c degree, space, kind)
+PRODUCT = [(2, 1, "lagrange", ("exp",)), (2, 2, "lagrange", ("pow", 2)), (2, 4, "quad", ("pow", 2)),
+           (3, 2, "lagrange", ("exp",)), (3, 3, "quad", ("pow", 2))]
+
+
+@pytest.mark.parametrize("iteration", ["newton", "picard"])
+@pytest.mark.parametrize("dim,deg,space,c", PRODUCT)
+def test_product_reaction_parity(P, dim, deg, space, c, iteration):
+    mesh = wl.unit_square_mesh(9) if dim == 2 else wl.unit_cube_mesh(3)
+    orc = oracle.Problem(mesh, a=None, a_deg=1, c=(c[0], float(c[1])) if len(c) > 1 else c, c_deg=deg, c_space=space,
+                         gamma=0.9, kappa=0.3, sigma=0.5, c_product=True)
+    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, c=c, c_degree=deg, c_space=space, gamma=0.9, kappa=0.3,
+                                      sigma=0.5, c_product=True),
+                 P.default_options(op=P.OP_MATRIX_FREE, iteration=P.ITER_PICARD if iteration == "picard" else P.ITER_NEWTON))
+    b = wl.random_vector(mesh.n_nodes, 13) * (1 - mesh.dirichlet)
+    u = wl.random_vector(mesh.n_nodes, 14, 0.8)
+    r = torch.empty(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    h.residual(cuda(u), cuda(b), r)
+    torch.cuda.synchronize()
+    assert rel(r.cpu().numpy(), orc.residual(u, b)) <= 1e-12
+    A, Ao = _jac(h, u, mesh.n_nodes), orc.jacobian(u, method="picard" if iteration == "picard" else "egfem")
+    assert abs(A - Ao).max() <= 1e-12 * abs(Ao).max()
+
+
+@pytest.mark.parametrize("space,nu", [("p2", 1.0), ("i4", 1.0), ("p2", 1e-2)])
+def test_superconductivity_decomposition_a_newton_matches_sga(P, space, nu):
+    """Decomposition (a) on the 32 x 32 grid: sigma M u plus the product reaction with c = u^2 on
+    P2 or I_4 reproduces the standard Galerkin discretisation of -nu lap u + u^3 + u = d."""
+    mesh = wl.unit_square_mesh(32)
+    ue = wl.supercond_exact(mesh.coords[:, 0], mesh.coords[:, 1])
+    uD = ue * mesh.dirichlet
+    sga = oracle.Problem(mesh, a=None, a_deg=1, kappa=nu, c=("pow", 3.0), c_deg=3, gamma=1.0, sigma=1.0)
+    b = sga.load_vector(lambda xx, yy: wl.supercond_source(xx, yy, nu)) * (1 - mesh.dirichlet)
+    u_sga, _, _, _ = sga.newton(b, u0=uD, uD=uD, method="sga", rtol=1e-13)
+    deg, cs = (2, "lagrange") if space == "p2" else (4, "quad")
+    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, kappa=nu, c=("pow", 2), c_degree=deg, c_space=cs, gamma=1.0,
+                                      sigma=1.0, c_product=True),
+                 P.default_options(op=P.OP_MATRIX_FREE, newton_rtol=1e-13))
+    u = cuda(uD)
+    st = h.newton_solve(u, cuda(b + uD))
+    torch.cuda.synchronize()
+    assert st.status == 0
+    assert rel(u.cpu().numpy(), u_sga) <= 1e-11
