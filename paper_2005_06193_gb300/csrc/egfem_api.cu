@@ -183,7 +183,8 @@ int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     MfArgs M{};
     M.n_cells = h->ncells; M.n_rows = h->n; M.dim = DIM;
     M.verts = h->cell_verts; M.S = h->cell_S; M.vol = h->cell_vol; M.v2c_ptr = h->v2c_ptr; M.v2c = h->v2c;
-    M.E = h->cell_E; M.ne = h->mf_ne; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c; M.nl = h->nl;
+    M.E = h->cell_E; M.ne = h->mf_ne; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c;
+    M.nl = A.nl;   // this call's record: it carries the Picard flag
     mf_cell_kernel<DIM><<<unsigned((h->ncells + 255) / 256), 256, 0, s>>>(M, A.u);
     const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
     switch (h->maxc_tpl) {
