@@ -355,22 +355,27 @@ def quadrature_setup(torch, P, dev, n):
     return h, d, torch.tensor(uD, device=dev, dtype=torch.float64)
 
 
-# Table 1 (Sec. 5, superconductivity, decomposition (b)): the paper's own solve times in seconds
+# Table 1 (Sec. 5, superconductivity, decompositions (a), (b)): the paper's own solve times in seconds
 # (Matlab R2019b on an i7-8700, Picard iteration) for context only; None where its Picard
 # iteration did not converge
-TABLE1_B_SECONDS = {("p3", 1.0): 0.076, ("i4", 1.0): 0.077, ("p3", 1e-2): 0.599, ("i4", 1e-2): 0.579,
-                    ("p3", 1e-3): None, ("i4", 1e-3): None}
+TABLE1_SECONDS = {("b", "p3", 1.0): 0.076, ("b", "i4", 1.0): 0.077, ("b", "p3", 1e-2): 0.599,
+                  ("b", "i4", 1e-2): 0.579, ("b", "p3", 1e-3): None, ("b", "i4", 1e-3): None,
+                  ("a", "p2", 1.0): 0.146, ("a", "i4", 1.0): 0.182, ("a", "p2", 1e-2): 0.577,
+                  ("a", "i4", 1e-2): 0.702, ("a", "p2", 1e-3): 1.185, ("a", "i4", 1e-3): 1.425}
 
 
-def supercond_setup(torch, P, dev, n, nu, space):
-    """Superconductivity decomposition (b) on the n x n square (Sec. 5): nu K u + M u + M^c c with
-    c = u^3 on W_c = P3 or I_4, u_D = sin(2 pi x) sin(2 pi y) e^(2x) / 6, manufactured source at
-    cell centroids, Newton from the boundary data.  Returns (handle, d, u0)."""
+def supercond_setup(torch, P, dev, n, nu, space, decomp="b"):
+    """Superconductivity example on the n x n square (Sec. 5), decomposition (b): nu K u + M u +
+    M^c c with c = u^3 on W_c = P3 or I_4; or (a): nu K u + M3 : (u x c~), c~ = u^2 + 1, written as
+    sigma M u plus the product reaction with c = u^2 on W_c = P2 or I_4.  u_D = sin(2 pi x)
+    sin(2 pi y) e^(2x) / 6, manufactured source at cell centroids, Newton from the boundary data.
+    Returns (handle, d, u0)."""
     import workloads as wl
     mesh = wl.unit_square_mesh(n)
-    deg, cs = (3, "lagrange") if space == "p3" else (4, "quad")
-    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, kappa=nu, c=("pow", 3), c_degree=deg, c_space=cs,
-                                      gamma=1.0, sigma=1.0), P.default_options(op=P.OP_MATRIX_FREE, newton_maxit=100))
+    deg, cs = {"p3": (3, "lagrange"), "p2": (2, "lagrange"), "i4": (4, "quad")}[space]
+    h = P.Handle(mesh, P.make_problem(a=None, a_degree=1, kappa=nu, c=("pow", 2 if decomp == "a" else 3), c_degree=deg,
+                                      c_space=cs, gamma=1.0, sigma=1.0, c_product=decomp == "a"),
+                 P.default_options(op=P.OP_MATRIX_FREE, newton_maxit=100))
     x, y = mesh.coords[:, 0], mesh.coords[:, 1]
     uD = wl.supercond_exact(x, y) * mesh.dirichlet
     xc = wl.cell_centroids(mesh)
@@ -383,28 +388,29 @@ def supercond_setup(torch, P, dev, n, nu, space):
 
 def supercond_extra(torch, P, dev, steps, barrier, hbm, fp64_peak, n_big):
     rows = []
-    for nu in (1.0, 1e-2, 1e-3):
-        for space in ("p3", "i4"):
-            h, d, u0 = supercond_setup(torch, P, dev, 64, nu, space)
-            u = u0.clone()
-            h.newton_solve(u, d)
-            torch.cuda.synchronize()
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = max(steps, 5)
-            e0.record()
-            for _ in range(reps):
-                u.copy_(u0)
-                st = h.newton_solve(u, d)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            rows.append({"nu": nu, "w_c": space, "unknowns": h.sizes.n_nodes + h.sizes.n_wc,
-                         "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "newton_iters": st.newton_iters,
-                         "krylov_iters": int(st.krylov_iters), "status": int(st.status),
-                         "paper_seconds_context": TABLE1_B_SECONDS[(space, nu)]})
-            h.close()
-    out = {"workload": "superconductivity decomposition (b), 64x64 grid (Table 1), Newton to 1e-10",
+    cases = [(dec, sp, nu) for dec, sps in (("a", ("p2", "i4")), ("b", ("p3", "i4"))) for nu in (1.0, 1e-2, 1e-3)
+             for sp in sps]
+    for decomp, space, nu in cases:
+        h, d, u0 = supercond_setup(torch, P, dev, 64, nu, space, decomp)
+        u = u0.clone()
+        h.newton_solve(u, d)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(steps, 5)
+        e0.record()
+        for _ in range(reps):
+            u.copy_(u0)
+            st = h.newton_solve(u, d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        rows.append({"decomposition": decomp, "nu": nu, "w_c": space, "unknowns": h.sizes.n_nodes + h.sizes.n_wc,
+                     "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "newton_iters": st.newton_iters,
+                     "krylov_iters": int(st.krylov_iters), "status": int(st.status),
+                     "paper_seconds_context": TABLE1_SECONDS[(decomp, space, nu)]})
+        h.close()
+    out = {"workload": "superconductivity decompositions (a) and (b), 64x64 grid (Table 1), Newton to 1e-10",
            "table1": rows}
     if n_big:
         out["large"] = next_row_extra(torch, P, dev, n_big, min(steps, 3), barrier,
