@@ -186,12 +186,12 @@ int launch_mf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     M.E = h->cell_E; M.ne = h->mf_ne; M.loc = h->mf_loc; M.loc_c = h->mf_loc_c;
     M.nl = A.nl;   // this call's record: it carries the Picard flag
     mf_cell_kernel<DIM><<<unsigned((h->ncells + 255) / 256), 256, 0, s>>>(M, A.u);
-    const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
+    auto grid = [&](int blk) { return unsigned((h->n + blk - 1) / blk); };
     switch (h->maxc_tpl) {
-        case 8: mf_row_kernel<DIM, 8><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
-        case 16: mf_row_kernel<DIM, 16><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
-        case 32: mf_row_kernel<DIM, 32><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
-        default: mf_row_kernel<DIM, 64><<<grid, CSF_BLOCK, 0, s>>>(M, A); break;
+        case 8: mf_row_kernel<DIM, 8><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(M, A); break;
+        case 16: mf_row_kernel<DIM, 16><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(M, A); break;
+        case 32: mf_row_kernel<DIM, 32><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(M, A); break;
+        default: mf_row_kernel<DIM, 64><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(M, A); break;
     }
     return 2;
 }
@@ -240,22 +240,22 @@ int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
         B.wc_val = h->wc_val; B.wc_gp = h->wc_gp;
         ++launched;
     }
-    const unsigned grid = unsigned((h->n + CSF_BLOCK - 1) / CSF_BLOCK);
+    auto grid = [&](int blk) { return unsigned((h->n + blk - 1) / blk); };
     if (mix) {
         B.leaf_val32 = h->leaf_val32;
         switch (h->maxc_tpl) {
-            case 8: csf_mixed_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-            case 16: csf_mixed_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-            case 32: csf_mixed_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-            default: csf_mixed_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+            case 8: csf_mixed_kernel<8><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(B); break;
+            case 16: csf_mixed_kernel<16><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(B); break;
+            case 32: csf_mixed_kernel<32><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(B); break;
+            default: csf_mixed_kernel<64><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(B); break;
         }
         return launched;
     }
     switch (h->maxc_tpl) {
-        case 8: csf_fused_kernel<8><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-        case 16: csf_fused_kernel<16><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-        case 32: csf_fused_kernel<32><<<grid, CSF_BLOCK, 0, s>>>(B); break;
-        default: csf_fused_kernel<64><<<grid, CSF_BLOCK, 0, s>>>(B); break;
+        case 8: csf_fused_kernel<8><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(B); break;
+        case 16: csf_fused_kernel<16><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(B); break;
+        case 32: csf_fused_kernel<32><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(B); break;
+        default: csf_fused_kernel<64><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(B); break;
     }
     return launched;
 }

@@ -16,6 +16,9 @@
 namespace egfem {
 
 constexpr int CSF_BLOCK = 128;
+// Threads per block of the row kernels for MAXC local columns: their per-thread shared arrays
+// (up to 16 B per column) keep to 32 KB, below the 48 KB static limit.
+template <int MAXC> __host__ __device__ constexpr int csf_block() { return MAXC <= 16 ? CSF_BLOCK : 2048 / MAXC; }
 
 struct CsfArgs {
     int64_t n_rows;
@@ -101,13 +104,14 @@ __device__ __forceinline__ void scatter_pi32(uint32_t info, float e, float *J, i
 
 // Fused pointwise nonlinearity + residual + Jacobian fill (one thread per row).
 // MAXC bounds the local columns of a row; du and J live in shared memory, one column
-// of CSF_BLOCK entries per local column.
+// of csf_block<MAXC>() entries per local column.
 template <int MAXC>
-__global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
-    __shared__ double s_du[MAXC * CSF_BLOCK];
-    __shared__ double s_J[MAXC * CSF_BLOCK];
+__global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A) {
+    constexpr int BLK = csf_block<MAXC>();
+    __shared__ double s_du[MAXC * BLK];
+    __shared__ double s_J[MAXC * BLK];
     const int tid = threadIdx.x;
-    const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
+    const int64_t row = int64_t(blockIdx.x) * BLK + tid;
     if (row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     const int lane = int(row % SLICE);
@@ -133,8 +137,8 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     }
     for (int c = 0; c < M.ncol; ++c) {
         const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
-        du[c * CSF_BLOCK] = A.u[g] - ui;
-        J[c * CSF_BLOCK] = 0.0;
+        du[c * BLK] = A.u[g] - ui;
+        J[c * BLK] = 0.0;
     }
     const Nonlin nl = A.nl;
     double r = 0.0, j1d = 0.0, D = 0.0, a = 0.0, gp = 0.0;
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
-                if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, CSF_BLOCK);
+                if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, BLK);
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
                 a = A.wa_val[m];
                 gp = A.wa_gp[m];
             } else {
-                const double pu = ui + interp_du(info, du, CSF_BLOCK);
+                const double pu = ui + interp_du(info, du, BLK);
                 double w;
                 g_eval(nl.a_kind, nl.a_pi, nl.a_scale, pu, w, gp);
                 a = (nl.kappa_field ? nl.kappa_field[A.fib_m[fq]] : nl.kappa) + w;
@@ -174,13 +178,13 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
         }
         const int c = lc & LEAF_PAD;
         if (c != LEAF_PAD) {
-            D += T * du[c * CSF_BLOCK];
-            J[c * CSF_BLOCK] += T * a;
+            D += T * du[c * BLK];
+            J[c * BLK] += T * a;
         }
     }
     if (f >= 0) {
         r += a * D;
-        if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, CSF_BLOCK);
+        if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, BLK);
     }
     // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
     for (int j = 0; j < M.nrx; ++j) {
@@ -194,11 +198,11 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
             cv = A.wc_val[m];
             cp = A.wc_gp[m];
         } else {
-            const double pc = ui + interp_du(xi, du, CSF_BLOCK);
+            const double pc = ui + interp_du(xi, du, BLK);
             g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
         }
         r += nl.gamma * mv * cv;
-        if (!nl.picard) scatter_pi(xi, nl.gamma * mv * cp, J, CSF_BLOCK);
+        if (!nl.picard) scatter_pi(xi, nl.gamma * mv * cp, J, BLK);
     }
     const double diag = j1d + J[0];
     const double res = r - di;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
     for (int c = 0; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int32_t slot = A.col_slot[q];
-        const double v = (c == 0) ? diag : J[c * CSF_BLOCK];
+        const double v = (c == 0) ? diag : J[c * BLK];
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
         const double sv = slot >= 0 ? dinv * v : 0.0;
@@ -237,12 +241,13 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_fused_kernel(CsfArgs A) {
 // per leaf and one per fibre.  Needs wa_val/wa_val32 (or a constant coefficient), wc_val for
 // a reaction, leaf_val32, r, q64 and a32.
 template <int MAXC>
-__global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
-    __shared__ double s_du[MAXC * CSF_BLOCK];
-    __shared__ float s_du32[MAXC * CSF_BLOCK];
-    __shared__ float s_J[MAXC * CSF_BLOCK];
+__global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A) {
+    constexpr int BLK = csf_block<MAXC>();
+    __shared__ double s_du[MAXC * BLK];
+    __shared__ float s_du32[MAXC * BLK];
+    __shared__ float s_J[MAXC * BLK];
     const int tid = threadIdx.x;
-    const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
+    const int64_t row = int64_t(blockIdx.x) * BLK + tid;
     if (row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     const int lane = int(row % SLICE);
@@ -261,9 +266,9 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     for (int c = 0; c < M.ncol; ++c) {
         const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
         const double d = A.u[g] - ui;
-        du[c * CSF_BLOCK] = d;
-        du32[c * CSF_BLOCK] = float(d);
-        J[c * CSF_BLOCK] = 0.0f;
+        du[c * BLK] = d;
+        du32[c * BLK] = float(d);
+        J[c * BLK] = 0.0f;
     }
     const Nonlin nl = A.nl;
     // FP64: the residual (D, r).  FP32: the Jacobian (D32, J, s1) and its row sum (rs_hi + rs_lo,
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
                 r += a * D;
                 if (gp32 != 0.0f && !nl.picard) {
                     const float e = D32 * gp32;
-                    scatter_pi32(info, e, J, CSF_BLOCK);
+                    scatter_pi32(info, e, J, BLK);
                     rs_add(e);
                 }
             }
@@ -311,11 +316,11 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         }
         const int c = lc & LEAF_PAD;
         if (c != LEAF_PAD) {
-            D += __ldg(A.leaf_val + q) * du[c * CSF_BLOCK];
+            D += __ldg(A.leaf_val + q) * du[c * BLK];
             const float T32 = __ldg(A.leaf_val32 + q);
-            D32 += T32 * du32[c * CSF_BLOCK];
+            D32 += T32 * du32[c * BLK];
             const float t = T32 * a32;
-            J[c * CSF_BLOCK] += t;
+            J[c * BLK] += t;
             s1 += t;
         }
     }
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         r += a * D;
         if (gp32 != 0.0f && !nl.picard) {
             const float e = D32 * gp32;
-            scatter_pi32(info, e, J, CSF_BLOCK);
+            scatter_pi32(info, e, J, BLK);
             rs_add(e);
         }
     }
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
         r += nl.gamma * mv * A.wc_val[m];
         if (!nl.picard) {
             const float e = float(nl.gamma * mv * A.wc_gp[m]);
-            scatter_pi32(A.rx_info[q], e, J, CSF_BLOCK);
+            scatter_pi32(A.rx_info[q], e, J, BLK);
             rs_add(e);
         }
     }
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) csf_mixed_kernel(CsfArgs A) {
     A.q64[row] = double(dinv) * res;
     for (int c = 1; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
-        const float v = J[c * CSF_BLOCK];
+        const float v = J[c * BLK];
         if (A.col_slot[q] >= 0) {
             A.a32[q] = dinv * v;
         } else {

@@ -190,12 +190,13 @@ __global__ void __launch_bounds__(256) mf_cell_kernel(MfArgs M, const double *u)
 
 // pass 2: per row, gather the cells' contributions; outputs as the CSF kernel's
 template <int DIM, int MAXC>
-__global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) {
+__global__ void __launch_bounds__(csf_block<MAXC>()) mf_row_kernel(MfArgs M, CsfArgs A) {
+    constexpr int BLK = csf_block<MAXC>();
     constexpr int NV = DIM + 1, NS = NV * (NV + 1) / 2;
-    __shared__ double s_J[MAXC * CSF_BLOCK];
-    __shared__ int32_t s_col[MAXC * CSF_BLOCK];
+    __shared__ double s_J[MAXC * BLK];
+    __shared__ int32_t s_col[MAXC * BLK];
     const int tid = threadIdx.x;
-    const int64_t row = int64_t(blockIdx.x) * CSF_BLOCK + tid;
+    const int64_t row = int64_t(blockIdx.x) * BLK + tid;
     if (row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     if (A.inst_mask && !A.inst_mask[A.slice_inst[sl]]) return;
@@ -221,8 +222,8 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
         return;
     }
     for (int c = 0; c < Ms.ncol; ++c) {
-        C[c * CSF_BLOCK] = A.col_idx[Ms.col_base + int64_t(c) * SLICE + lane];
-        J[c * CSF_BLOCK] = 0.0;
+        C[c * BLK] = A.col_idx[Ms.col_base + int64_t(c) * SLICE + lane];
+        J[c * BLK] = 0.0;
     }
     const Nonlin nl = A.nl;
     double r = 0.0, diag_extra = 0.0;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
 #pragma unroll
         for (int b = 0; b < NV; ++b) {
             lcb[b] = 0;
-            for (int c = 0; c < Ms.ncol; ++c) if (C[c * CSF_BLOCK] == vk[b]) { lcb[b] = c; break; }
+            for (int c = 0; c < Ms.ncol; ++c) if (C[c * BLK] == vk[b]) { lcb[b] = c; break; }
         }
         const double *E = M.E + cell * M.ne;
         const double abar = E[0], su = E[1 + a];
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
                 v += t;
                 diag_extra -= t;
             }
-            J[lc * CSF_BLOCK] += v;
+            J[lc * BLK] += v;
         }
         if (nl.sigma != 0.0) {
             // linear reaction sigma M^K: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             for (int b = 0; b < NV; ++b) {
                 const double mab = (b == a) ? 2.0 * m0 : m0;
                 r += mab * A.u[vk[b]];
-                J[lcb[b] * CSF_BLOCK] += mab;
+                J[lcb[b] * BLK] += mab;
             }
         }
         if (nl.c_kind != EGFEM_G_NONE && M.loc_c.nw > 0) {
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
             // and R_ab, the latter already without the g' terms for the Picard matrix
             r += E[1 + 2 * NV + a];
 #pragma unroll
-            for (int b = 0; b < NV; ++b) J[lcb[b] * CSF_BLOCK] += E[1 + 3 * NV + a * NV + b];
+            for (int b = 0; b < NV; ++b) J[lcb[b] * BLK] += E[1 + 3 * NV + a * NV + b];
         } else if (nl.c_kind != EGFEM_G_NONE) {
             // gamma M^c c with W_c = P1: M_ab = |K| (1 + delta_ab) / ((d+1)(d+2))
             const double m0 = M.vol[cell] / double((DIM + 1) * (DIM + 2));
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
                 g_eval(nl.c_kind, nl.c_pi, nl.c_scale, A.u[vk[b]], g, gp);
                 const double mab = (b == a) ? 2.0 * m0 : m0;
                 r += nl.gamma * mab * g;
-                if (!nl.picard) J[lcb[b] * CSF_BLOCK] += nl.gamma * mab * gp;
+                if (!nl.picard) J[lcb[b] * BLK] += nl.gamma * mab * gp;
             }
         }
     }
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(CSF_BLOCK) mf_row_kernel(MfArgs M, CsfArgs A) 
     for (int c = 0; c < Ms.ncol; ++c) {
         const int64_t q = Ms.col_base + int64_t(c) * SLICE + lane;
         const int32_t slot = A.col_slot[q];
-        const double v = (c == 0) ? diag : J[c * CSF_BLOCK];
+        const double v = (c == 0) ? diag : J[c * BLK];
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
         const double sv = slot >= 0 ? dinv * v : 0.0;

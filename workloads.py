@@ -133,6 +133,25 @@ def unit_disk_mesh(n: int) -> Mesh:
     return Mesh(2, coords, cells, dirichlet)
 
 
+def fan_mesh(k: int) -> Mesh:
+    """A high-valence test mesh: a centre vertex, a free ring of k vertices at radius 1/2 and a
+    Dirichlet ring of k vertices at radius 1, with k centre triangles and 2k between the rings.
+    The centre has k neighbours, so k > 31 exercises the 64-column row kernels."""
+    if k < 3:
+        raise ValueError("k must be >= 3")
+    t = 2.0 * np.pi * np.arange(k) / k
+    coords = np.concatenate([np.zeros((1, 2)), 0.5 * np.stack([np.cos(t), np.sin(t)], 1),
+                             np.stack([np.cos(t + np.pi / k), np.sin(t + np.pi / k)], 1)]).astype(np.float64)
+    cells = []
+    for j in range(k):
+        a, b = 1 + j, 1 + (j + 1) % k            # inner ring
+        c, d = 1 + k + j, 1 + k + (j + 1) % k    # outer ring
+        cells += [[0, a, b], [a, c, b], [b, c, d]]
+    dirichlet = np.zeros(coords.shape[0], dtype=np.uint8)
+    dirichlet[1 + k:] = 1
+    return Mesh(2, coords, np.array(cells, dtype=np.int32), dirichlet)
+
+
 def plaplace_disk_exact(x: np.ndarray, y: np.ndarray, p: float) -> np.ndarray:
     """The closed-form solution of -div(|grad u|^(p-2) grad u) = 1 on the unit disk with u = 0
     on its boundary (Sec. 5, p-Laplace example): 2^(-1/(p-1)) (p-1)/p (1 - |x|^(p/(p-1)))."""
