@@ -35,8 +35,8 @@ def rel(a, b):
 @pytest.mark.parametrize("k", [20, 48])
 def test_high_valence_parity_and_solve(P, k, op, prec):
     mesh = wl.fan_mesh(k)
-    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2, c=("exp",), c_deg=1, gamma=-0.5)
-    h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2, c=("exp",), c_degree=1, gamma=-0.5),
+    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2, c=("exp",), c_deg=1, gamma=0.5)
+    h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2, c=("exp",), c_degree=1, gamma=0.5),
                  P.default_options(op=P.OP_MATRIX_FREE if op == "mf" else P.OP_CSF, newton_rtol=1e-12,
                                    precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64))
     u = wl.random_vector(mesh.n_nodes, 3, 0.7)
