@@ -218,3 +218,12 @@ def test_bad_quadrature_space_is_rejected_before_any_cuda_call(egf):
     h = ctypes.c_void_p()
     assert egf.lib().egfem_build(ctypes.byref(m), ctypes.byref(bad), ctypes.byref(mf), ctypes.byref(h)) == 1
     del keep
+
+
+def test_empty_mesh_is_rejected(egf):
+    """A mesh without nodes or cells is an invalid argument, reported before any device work."""
+    import numpy as np
+    empty = wl.Mesh(2, np.zeros((0, 2)), np.zeros((0, 3), dtype=np.int32), np.zeros(0, dtype=np.uint8))
+    with pytest.raises(egf.EgfemError) as e:
+        egf.inspect_tensor(empty, egf.make_problem())
+    assert e.value.status == 1
