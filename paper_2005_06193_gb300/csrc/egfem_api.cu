@@ -19,6 +19,7 @@
 #include "egfem_mf.cuh"
 #include "egfem_persist.cuh"
 #include "egfem_cluster.cuh"
+#include "egfem_gnewton.cuh"
 
 using namespace egfem;
 
@@ -154,6 +155,17 @@ struct egfem_t {
     double *bpart2 = nullptr;           // tile partials of the persistent batched solve
     void *bsc = nullptr;                // PkScal<V> per instance (room for the larger V)
     int bgraph_chunk = 0, bgraph_tiles = 0;
+    // graph-resident batched Newton loop (egfem_gnewton.cuh): device state, the instantiated
+    // graph and the vectors and path it was captured for
+    GNState *gn_state = nullptr;
+    egfem_stats *gn_stats = nullptr;
+    int32_t *gn_loops = nullptr;
+    cudaGraphExec_t gn_exec = nullptr;
+    const double *gn_u = nullptr, *gn_d = nullptr;
+    int gn_mixed = -1;
+    int gn_nodes = 0;                   // kernels one body execution launches
+    bool gn_failed = false;             // capture or instantiation failed once: host loop only
+    bool gn_used = false;               // the last batched solve ran the graph loop
 };
 
 namespace {
@@ -902,6 +914,7 @@ void egfem_default_options(egfem_options *o) {
     o->iteration = EGFEM_ITER_NEWTON;
     o->krylov_block_rows = 0;
     o->krylov_cluster = 0;
+    o->newton_graph = 1;
 }
 
 egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
@@ -943,6 +956,8 @@ void egfem_destroy(egfem_handle h) {
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
     dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bsys_t0); dfree(h->bpart2);
     if (h->bsc) cudaFree(h->bsc);
+    if (h->gn_exec) cudaGraphExecDestroy(h->gn_exec);
+    dfree(h->gn_state); dfree(h->gn_stats); dfree(h->gn_loops);
     if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
     if (h->bgraph32) cudaGraphExecDestroy(h->bgraph32);
     for (void *q : {(void *)h->h_mask, (void *)h->h_eta, (void *)h->h_lam, (void *)h->h_norm2, (void *)h->h_bst})
@@ -962,6 +977,9 @@ egfem_status egfem_set_options(egfem_handle h, const egfem_options *opts) {
         return EGFEM_ERR_INVALID_ARG;
     }
     h->opts = *opts;
+    // the graph Newton loop bakes the options in: capture it again at the next batched solve
+    if (h->gn_exec) { cudaGraphExecDestroy(h->gn_exec); h->gn_exec = nullptr; }
+    h->gn_failed = false;
     return EGFEM_OK;
 }
 
@@ -1797,6 +1815,115 @@ egfem_status batch_norms(egfem_t *h) {
     return EGFEM_OK;
 }
 
+// Capture the body of the graph-resident batched Newton loop (see egfem_gnewton.cuh) for the
+// vectors d_u, d_d and the FP64 (V = double) or mixed (V = df64) path, under a conditional
+// WHILE node; the graph is kept for later calls with the same vectors and path.
+template <typename V>
+egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, int pg) {
+    constexpr bool mixed = std::is_same<V, df64>::value;
+    if (h->gn_exec && h->gn_u == d_u && h->gn_d == d_d && h->gn_mixed == int(mixed)) return EGFEM_OK;
+    if (h->gn_exec) { cudaGraphExecDestroy(h->gn_exec); h->gn_exec = nullptr; }
+    if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));   // no allocation may happen inside the capture
+    if (!h->gn_state) {
+        EG_TRY(dalloc(h->gn_state, size_t(h->nb)));
+        EG_TRY(dalloc(h->gn_stats, size_t(h->nb)));
+        EG_TRY(dalloc(h->gn_loops, 1));
+    }
+    cudaGraph_t g = nullptr;
+    EG_CUDA(cudaGraphCreate(&g, 0));
+    egfem_status st = EGFEM_OK;
+    cudaError_t e = cudaSuccess;
+    cudaGraphConditionalHandle cond{};
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node = nullptr;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->hs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        g_last_error = std::string("graph Newton loop: ") + cudaGetErrorString(e);
+        return EGFEM_ERR_CUDA;
+    }
+    GNArgs G{};
+    G.nb = h->nb; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
+    G.lam = h->inst_lam; G.kst = h->bst; G.norm2 = h->inst_norm2; G.loops = h->gn_loops;
+    G.max_loops = h->opts.newton_maxit + 2; G.newton_maxit = h->opts.newton_maxit; G.fixed_eta = h->opts.fixed_eta;
+    G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
+    const unsigned gu = unsigned((h->n + 255) / 256);
+    int nodes = 0;
+    gn_pre<<<1, 256, 0, h->hs>>>(G);
+    st = launch_batch_persistent(h, W, pg, h->opts.krylov_maxit, mixed ? kMixedStall : 0);
+    gn_mid<<<1, 256, 0, h->hs>>>(G);
+    kb_update<V><<<gu, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, W.x);
+    CsfArgs A = csf_args(h, d_u, d_d);
+    A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
+    if (mixed) A.a32 = h->k32.A;
+    A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
+    nodes += launch_csf(h, A, h->hs);
+    if (mixed) { cast_kernel<double, df64><<<gu, 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b); ++nodes; }
+    kb_norm2<<<int(std::max<int64_t>(1, std::min<int64_t>(h->ntiles, int64_t(h->sms) * 8))), KRY_BLOCK, 0, h->hs>>>(
+        h->ntiles, h->tiles, h->bst, h->bpart, h->r, h->csf.dir, h->n, h->inst_norm2);
+    gn_post<<<1, 256, 0, h->hs>>>(G);
+    kb_update<V><<<gu, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, W.x);
+    nodes += 7;
+    cudaGraph_t body = nullptr;
+    e = cudaStreamEndCapture(h->hs, &body);
+    if (st == EGFEM_OK && e == cudaSuccess) e = cudaGetLastError();
+    if (st == EGFEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->gn_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (st != EGFEM_OK || e != cudaSuccess) {
+        if (e != cudaSuccess) g_last_error = std::string("graph Newton loop: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        h->gn_exec = nullptr;
+        return st != EGFEM_OK ? st : EGFEM_ERR_CUDA;
+    }
+    h->gn_u = d_u; h->gn_d = d_d; h->gn_mixed = int(mixed); h->gn_nodes = nodes;
+    return EGFEM_OK;
+}
+
+// Run the graph-resident Newton loop from the host driver's state (after its first residual
+// evaluation) and take its state back: instances it handed back, and any it did not finish,
+// continue in the host loop.  Returns false when the graph is unavailable (the host loop then
+// does everything).
+template <typename V>
+bool gn_run(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, std::vector<double> &rn, std::vector<double> &rprev,
+            std::vector<double> &eta, const std::vector<double> &target, std::vector<int32_t> &st,
+            std::vector<egfem_stats> &S, int64_t *launches) {
+    if (!h->opts.newton_graph || h->gn_failed) return false;
+    const int pg = pk_batch_grid<V>(h);
+    if (pg <= 0) return false;
+    if (gn_build<V>(h, W, d_u, d_d, pg) != EGFEM_OK) { h->gn_failed = true; return false; }
+    h->gn_used = true;
+    const int nb = h->nb;
+    std::vector<GNState> G(nb);
+    for (int b = 0; b < nb; ++b) G[b] = GNState{rn[b], rprev[b], rn[b], target[b], eta[b], 0, 0};
+    if (cudaMemcpyAsync(h->gn_state, G.data(), sizeof(GNState) * size_t(nb), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
+        cudaMemcpyAsync(h->gn_stats, S.data(), sizeof(egfem_stats) * size_t(nb), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
+        cudaMemsetAsync(h->gn_loops, 0, sizeof(int32_t), h->hs) != cudaSuccess ||
+        cudaGraphLaunch(h->gn_exec, h->hs) != cudaSuccess) {
+        cudaGetLastError();
+        h->gn_failed = true;
+        return false;
+    }
+    int32_t loops = 0;
+    cudaMemcpyAsync(G.data(), h->gn_state, sizeof(GNState) * size_t(nb), cudaMemcpyDeviceToHost, h->hs);
+    cudaMemcpyAsync(S.data(), h->gn_stats, sizeof(egfem_stats) * size_t(nb), cudaMemcpyDeviceToHost, h->hs);
+    cudaMemcpyAsync(&loops, h->gn_loops, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs);
+    if (cudaStreamSynchronize(h->hs) != cudaSuccess) return true;   // the caller's next CUDA call reports it
+    for (int b = 0; b < nb; ++b) {
+        rn[b] = G[b].rn; rprev[b] = G[b].rprev; eta[b] = G[b].eta;
+        st[b] = S[b].status;
+    }
+    *launches += int64_t(loops) * h->gn_nodes;
+    return true;
+}
+
 egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stats *stats) {
     const int nb = h->nb;
     const bool mixed = h->opts.precision == EGFEM_PREC_MIXED;
@@ -1852,6 +1979,24 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         S[b].res0 = rn[b];
         target[b] = std::max(h->opts.newton_rtol * rn[b], h->opts.newton_atol);
         rprev[b] = rn[b];
+    }
+    // the Newton loop on the device (full steps); the host loop below finishes what it hands back
+    h->gn_used = false;
+    const bool ran = mixed ? gn_run<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, st, S, &launches)
+                           : gn_run<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, st, S, &launches);
+    if (!ran && h->opts.newton_graph == 2) {
+        g_last_error = "graph Newton loop required (newton_graph = 2) but unavailable: " + g_last_error;
+        return EGFEM_ERR_UNSUPPORTED;
+    }
+    if (ran) {
+        EG_CUDA(cudaGetLastError());
+        std::vector<int> left(nb, 0);
+        bool any = false;
+        for (int b = 0; b < nb; ++b) {
+            left[b] = st[b] == EGFEM_OK && !(rn[b] <= target[b]);
+            any = any || left[b];
+        }
+        if (any) EG_TRY(eval(left));   // their residual and operator at the current u
     }
     for (int step = 0; step <= h->opts.newton_maxit; ++step) {
         bool any = false;

@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double), ("krylov_maxit", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("op", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
                 ("fixed_eta", ctypes.c_int32), ("krylov_persistent", ctypes.c_int32), ("iteration", ctypes.c_int32),
-                ("krylov_block_rows", ctypes.c_int32), ("krylov_cluster", ctypes.c_int32)]
+                ("krylov_block_rows", ctypes.c_int32), ("krylov_cluster", ctypes.c_int32),
+                ("newton_graph", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -1,0 +1,106 @@
+"""GPU checks of the graph-resident batched Newton loop (a conditional WHILE node in one CUDA
+graph; option newton_graph): with the graph required (newton_graph = 2) every instance's
+solution equals the oracle's and the host loop's, with the same Newton step counts; a second
+call reuses the graph; Picard runs in it too; and instances whose full step fails the decrease
+test are handed back to the host loop and still converge."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2005_06193_gb300 as P
+    return P
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    inst = wl.batch_instances(count=5, seed=7, n_lo=6, n_hi=24)
+    meshes = [wl.unit_square_mesh(n) for n, _ in inst]
+    loads, refs = [], []
+    for (n, src), mesh in zip(inst, meshes):
+        orc = oracle.Problem(mesh, a=("pow", 3.0), a_deg=3)
+        b = orc.load_vector(src) * (1 - mesh.dirichlet)
+        u_ref, _, _, _ = orc.newton(b, rtol=1e-13)
+        loads.append(b)
+        refs.append(u_ref)
+    return meshes, loads, refs
+
+
+def _solve(P, meshes, loads, graph, prec, **kw):
+    opts = P.default_options(newton_graph=graph, newton_rtol=1e-13 if prec == "fp64" else 1e-10,
+                             precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64, **kw)
+    h = P.BatchHandle(meshes, P.make_problem(a=("pow", 3), a_degree=3), opts)
+    d = h.scatter(loads)
+    u = torch.zeros_like(d)
+    stats = h.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    return h, d, u, stats
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_newton_matches_host_loop_and_oracle(P, batch, prec):
+    meshes, loads, refs = batch
+    sizes = [m.n_nodes for m in meshes]
+    hg, dg, ug, sg = _solve(P, meshes, loads, 2, prec)
+    hh, dh, uh, sh = _solve(P, meshes, loads, 0, prec)
+    tol = 1e-11 if prec == "fp64" else 1e-6
+    for b, (x, y, ref) in enumerate(zip(hg.gather(ug, sizes), hh.gather(uh, sizes), refs)):
+        assert sg[b].status == 0 and sh[b].status == 0, b
+        assert rel(x, ref) <= tol and rel(y, ref) <= tol, b
+        assert sg[b].newton_iters == sh[b].newton_iters, b
+    # a second call with the same tensors runs the captured graph again
+    ug.zero_()
+    sg2 = hg.batch_newton_solve(ug, dg)
+    torch.cuda.synchronize()
+    for b, (x, ref) in enumerate(zip(hg.gather(ug, sizes), refs)):
+        assert sg2[b].status == 0 and rel(x, ref) <= tol, b
+
+
+def test_graph_picard_matches_oracle(P, batch):
+    meshes, loads, refs = batch
+    h, d, u, st = _solve(P, meshes, loads, 2, "fp64", iteration=P.ITER_PICARD, newton_maxit=300)
+    for b, (x, ref) in enumerate(zip(h.gather(u, [m.n_nodes for m in meshes]), refs)):
+        assert st[b].status == 0 and st[b].newton_iters > 5, b
+        assert rel(x, ref) <= 1e-10, b
+
+
+def test_graph_hands_back_steps_that_need_damping(P):
+    """Minimal surface from the boundary data (full Newton steps overshoot there): the graph
+    hands those instances back, the host loop shortens their steps, and every instance reaches
+    the oracle's discrete solution."""
+    meshes = [wl.unit_square_mesh(n) for n in (24, 32)]
+    loads, refs, starts = [], [], []
+    for mesh in meshes:
+        orc = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
+        x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+        ue = wl.minsurf_exact(x, y)
+        uD = ue * mesh.dirichlet
+        b = orc.load_vector(wl.minsurf_source) * (1 - mesh.dirichlet)
+        u_ref, _, _, _ = orc.newton(b, u0=ue + 0.2 * np.sin(np.pi * x) * np.sin(np.pi * y), uD=uD, rtol=1e-12)
+        loads.append(b + uD)
+        refs.append(u_ref)
+        starts.append(uD)
+    h = P.BatchHandle(meshes, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
+                      P.default_options(op=P.OP_MATRIX_FREE, newton_graph=2, newton_rtol=1e-12))
+    d = h.scatter(loads)
+    u = h.scatter(starts)
+    st = h.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    for b, (x, ref) in enumerate(zip(h.gather(u, [m.n_nodes for m in meshes]), refs)):
+        assert st[b].status == 0, b
+        assert rel(x, ref) <= 1e-10, b
