@@ -419,6 +419,43 @@ def supercond_extra(torch, P, dev, steps, barrier, hbm, fp64_peak, n_big):
     return out
 
 
+def bratu_extra(torch, P, dev, steps, barrier, hbm, fp64_peak, n=64):
+    """Bratu -lap u = 2 e^u on the n^3 cube (6 Kuhn tetrahedra per cube; e^u interpolated in P1,
+    GFEM), f = 0, Newton from 0: FP64 and mixed (FP32 operator and Krylov, FP64 residual)
+    solves, the mixed error against the FP64 solution, and each path's tensor action."""
+    import workloads as wl
+    mesh = wl.unit_cube_mesh(n)
+    prob = P.make_problem(a=None, a_degree=1, c=("exp",), c_degree=1, gamma=-2.0)
+    d = torch.zeros(mesh.n_nodes, device=dev, dtype=torch.float64)
+    out, sols = {"workload": f"bratu_3d_{n}^3_gfem_p1", "n_nodes": mesh.n_nodes, "n_cells": mesh.n_cells}, {}
+    for prec in ("fp64", "mixed"):
+        h = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64))
+        u = torch.zeros_like(d)
+        h.newton_solve(u, d)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            u.zero_()
+            st = h.newton_solve(u, d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = h.profile_kernels(u, d, reps=20)
+        ta = next(p for p in prof if p["name"] in ("csf_fused", "csf_mixed"))
+        out[prec] = {"value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "newton_iters": st.newton_iters,
+                     "krylov_iters": int(st.krylov_iters), "final_rel_residual": st.res_final / st.res0,
+                     "tensor_action": {"kernel": ta["name"], "ms": ta["ms"],
+                                       "achieved_gbs": ta["bytes"] / (ta["ms"] / 1e3) / 1e9,
+                                       "frac_hbm": ta["bytes"] / (ta["ms"] / 1e3) / 1e9 / hbm}}
+        sols[prec] = u.clone()
+        h.close()
+    out["mixed_rel_error_vs_fp64"] = float(torch.linalg.norm(sols["mixed"] - sols["fp64"]) / torch.linalg.norm(sols["fp64"]))
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def next_row_extra(torch, P, dev, n, steps, barrier, setup, workload, hbm, fp64_peak):
     h, d, u0 = setup(torch, P, dev, n)
     u = u0.clone()
@@ -475,6 +512,7 @@ def main():
     ap.add_argument("--no-picard", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the gradient-coefficient and I_k lines")
+    ap.add_argument("--no-bratu", action="store_true", help="skip the 64^3 Bratu line")
     ap.add_argument("--batch-instances", type=int, default=16)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--p3-instances", type=int, default=32)
@@ -668,6 +706,9 @@ def main():
         out["quadrature_i3"] = next_row_extra(torch, P, dev, args.n, min(args.steps, 3), barrier, quadrature_setup,
                                               f"quadratic_reaction_i3_{args.n}x{args.n}", hbm, fp64_peak)
         out["superconductivity"] = supercond_extra(torch, P, dev, args.steps, barrier, hbm, fp64_peak, args.n)
+
+    if not args.no_bratu:
+        out["bratu_3d"] = bratu_extra(torch, P, dev, min(args.steps, 3), barrier, hbm, fp64_peak)
 
     if not args.no_batch:
         out["batched_adjoint"] = batched_adjoint_extra(torch, P, dev, args.batch_instances, args.batch_n, barrier)
