@@ -241,14 +241,15 @@ int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     if (h->wa_val) {
         float *v32 = mix ? h->wa_val32 : nullptr, *g32 = mix ? h->wa_gp32 : nullptr;
         wnode_kernel<<<unsigned((h->nwa + 255) / 256), 256, 0, s>>>(h->nwa, h->wa_kind, h->wa_sup, A.u, h->nl.a_kind, h->nl.a_pi,
-                                                                  h->nl.a_scale, h->nl.kappa, h->nl.kappa_field, h->wa_val, h->wa_gp,
-                                                                  v32, g32);
+                                                                  h->nl.a_scale, h->nl.a_scale * h->nl.a_pi, h->nl.kappa,
+                                                                  h->nl.kappa_field, h->wa_val, h->wa_gp, v32, g32);
         B.wa_val = h->wa_val; B.wa_gp = h->wa_gp; B.wa_val32 = v32; B.wa_gp32 = g32;
         ++launched;
     }
     if (h->wc_val) {
         wnode_kernel<<<unsigned((h->nwc + 255) / 256), 256, 0, s>>>(h->nwc, h->wc_kind, h->wc_sup, A.u, h->nl.c_kind, h->nl.c_pi,
-                                                                  h->nl.c_scale, 0.0, nullptr, h->wc_val, h->wc_gp, nullptr, nullptr);
+                                                                  h->nl.c_scale, h->nl.c_scale * h->nl.c_pi, 0.0, nullptr,
+                                                                  h->wc_val, h->wc_gp, nullptr, nullptr);
         B.wc_val = h->wc_val; B.wc_gp = h->wc_gp;
         ++launched;
     }

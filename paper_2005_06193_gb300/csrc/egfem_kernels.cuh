@@ -368,11 +368,13 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A)
 // Nodal values of one nonlinearity on its W space (Sec. 3.1 eq. (5), Sec. 3.2), one thread
 // per W node, each node evaluated once: val_m = base_m + g((Pi u)_m), gp_m = g'((Pi u)_m),
 // with base = kappa (constant, or the field when base_field is set) for the coefficient
-// space and 0 for the reaction space.
+// space and 0 for the reaction space.  Every FP64 operation costs a slot of GB300's narrow
+// FP64 pipe, so the integer power is written with the fewest: t = s^(p-1),
+// gp = (scale p) t with scale p from the host, val = (scale s) t + base as one FMA.
 __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u,
-                                                    int32_t g_kind, int32_t g_p, double g_scale, double base,
-                                                    const double *base_field, double *val, double *gp, float *val32,
-                                                    float *gp32) {
+                                                    int32_t g_kind, int32_t g_p, double g_scale, double g_scale_p,
+                                                    double base, const double *base_field, double *val, double *gp,
+                                                    float *val32, float *gp32) {
     const int64_t m = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (m >= n_w) return;
     const uint32_t k = kind[m];
@@ -380,11 +382,21 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
     double pu;
     if (k == W_VERTEX) pu = u0;
     else if (k == W_MID) pu = 0.5 * (u0 + u[sup[3 * m + 1]]);
-    else if (k == W_THIRD) pu = (2.0 * u0 + u[sup[3 * m + 1]]) * (1.0 / 3.0);
+    else if (k == W_THIRD) pu = fma(2.0, u0, u[sup[3 * m + 1]]) * (1.0 / 3.0);
     else pu = (u0 + u[sup[3 * m + 1]] + u[sup[3 * m + 2]]) * (1.0 / 3.0);
-    double g, d;
-    g_eval(g_kind, g_p, g_scale, pu, g, d);
-    const double v = (base_field ? base_field[m] : base) + g;
+    const double b0 = base_field ? base_field[m] : base;
+    double v, d;
+    if (g_kind == EGFEM_G_POW) {
+        double t = 1.0;                       // pu^(p-1)
+        if (g_p >= 2) t = pu;
+        for (int32_t k = 2; k < g_p; ++k) t *= pu;
+        d = g_p == 1 ? g_scale : g_scale_p * t;
+        v = fma(g_scale * pu, t, b0);
+    } else {
+        double g;
+        g_eval(g_kind, g_p, g_scale, pu, g, d);
+        v = b0 + g;
+    }
     val[m] = v;
     gp[m] = d;
     if (val32) {   // FP32 copies for the mixed-precision Jacobian
