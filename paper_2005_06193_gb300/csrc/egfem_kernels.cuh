@@ -87,7 +87,8 @@ __device__ __forceinline__ void scatter_pi(uint32_t info, double e, double *J, i
     const uint32_t kind = (info >> 24) & 0xF;
     const uint32_t c0 = info & 0xFF, c1 = (info >> 8) & 0xFF, c2 = (info >> 16) & 0xFF;
     if (kind == W_VERTEX) { J[c0 * stride] += e; return; }
-    if (kind == W_MID) { const double h = 0.5 * e; J[c0 * stride] += h; J[c1 * stride] += h; return; }
+    // 0.5 e is exact, so the FMA adds the same value as h = 0.5 e, J += h, in one FP64 operation
+    if (kind == W_MID) { J[c0 * stride] = fma(0.5, e, J[c0 * stride]); J[c1 * stride] = fma(0.5, e, J[c1 * stride]); return; }
     if (kind == W_THIRD) { const double h = e * (1.0 / 3.0); J[c0 * stride] += 2.0 * h; J[c1 * stride] += h; return; }
     if (kind == W_FACE) { const double h = e * (1.0 / 3.0); J[c0 * stride] += h; J[c1 * stride] += h; J[c2 * stride] += h; }
 }
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
     const Nonlin nl = A.nl;
     double r = 0.0, j1d = 0.0, D = 0.0, a = 0.0, gp = 0.0;
     uint32_t info = 0;
+    bool j2 = false;
     int f = -1;
     // tensor data are read-only (non-coherent loads); unrolling lets the next leaves' loads
     // issue ahead of this leaf's arithmetic
@@ -154,12 +156,14 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
-                if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, BLK);
+                if (j2) scatter_pi(info, D * gp, J, BLK);
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
             info = __ldg(A.fib_info + fq);
             const double td = __ldg(A.fib_tdiag + fq);
+            // the J2 scatter is tested on integers (an FP64 compare would take an FP64 slot)
+            j2 = !nl.picard && ((info >> 24) & 0xF) != W_CONST;
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 gp = 0.0;
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
     }
     if (f >= 0) {
         r += a * D;
-        if (gp != 0.0 && !nl.picard) scatter_pi(info, D * gp, J, BLK);
+        if (j2) scatter_pi(info, D * gp, J, BLK);
     }
     // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
     for (int j = 0; j < M.nrx; ++j) {
@@ -221,9 +225,8 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
         const double sv = slot >= 0 ? dinv * v : 0.0;
-        rowsum += sv;
         if (A.a64) A.a64[q] = sv;
-        if (A.a32) A.a32[q] = float(sv);
+        if (A.a32) { rowsum += sv; A.a32[q] = float(sv); }
     }
     // the FP32 operator keeps its row sum in column 0 (difference-form SpMV)
     if (A.a32) A.a32[M.col_base + lane] = float(rowsum);
