@@ -372,8 +372,8 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A)
 // per W node, each node evaluated once: val_m = base_m + g((Pi u)_m), gp_m = g'((Pi u)_m),
 // with base = kappa (constant, or the field when base_field is set) for the coefficient
 // space and 0 for the reaction space.  Every FP64 operation costs a slot of GB300's narrow
-// FP64 pipe, so the integer power is written with the fewest: t = s^(p-1),
-// gp = (scale p) t with scale p from the host, val = (scale s) t + base as one FMA.
+// FP64 pipe, so the integer power is written with few: t = s^(p-1), gp = (scale p) t with
+// scale p from the host, val = base + (scale t) s.
 __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u,
                                                     int32_t g_kind, int32_t g_p, double g_scale, double g_scale_p,
                                                     double base, const double *base_field, double *val, double *gp,
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
         if (g_p >= 2) t = pu;
         for (int32_t k = 2; k < g_p; ++k) t *= pu;
         d = g_p == 1 ? g_scale : g_scale_p * t;
-        v = fma(g_scale * pu, t, b0);
+        v = b0 + (g_scale * t) * pu;   // rounded as scale s^(p-1) s + base, the oracle's order
     } else {
         double g;
         g_eval(g_kind, g_p, g_scale, pu, g, d);
