@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
         if (g_p >= 2) t = pu;
         for (int32_t k = 2; k < g_p; ++k) t *= pu;
         d = g_p == 1 ? g_scale : g_scale_p * t;
-        v = b0 + (g_scale * t) * pu;   // rounded as scale s^(p-1) s + base, the oracle's order
+        v = b0 + (g_scale * t) * pu;   // this rounding order: the Krylov iteration counts follow a's last bit
     } else {
         double g;
         g_eval(g_kind, g_p, g_scale, pu, g, d);
