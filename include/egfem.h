@@ -159,7 +159,7 @@ typedef struct {
                                   up to 32); the grid is min(rows / this, resident blocks).
                                   0 (default) picks the library's value; read at the first
                                   solve of a handle                                          */
-    int32_t krylov_cluster;  /* FP64 single-system solve in one thread-block cluster (the Krylov
+    int32_t krylov_cluster;  /* single-system solve (FP64 or mixed) in one thread-block cluster (the Krylov
                                 vectors in distributed shared memory; systems up to about
                                 16 x 3904 rows): 0 (default) when it fits, with the cluster
                                 size chosen by the library; 1..16 that cluster size; -1

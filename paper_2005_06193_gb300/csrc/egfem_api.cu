@@ -309,21 +309,23 @@ int one_wave(const egfem_t *h, const void *func) {
     return int(std::max<int64_t>(1, std::min<int64_t>(work, int64_t(nb) * h->sms)));
 }
 
-// Cluster solve plan for one FP64 system: the rows must fit the Krylov vectors of the cluster's
+// Cluster solve plan for one system (FP64 or double-float vectors): the rows must fit the Krylov
+// vectors of the cluster's
 // CTAs in shared memory (PKC_NVEC doubles per row); the cluster size is the smallest power of two
 // giving at most kPkcTargetRows rows per CTA (or the krylov_cluster option), and the launch
 // configuration must be schedulable (cudaOccupancyMaxActiveClusters).  Leaves W.pkc_cluster = 0
 // when any of this fails: the grid-wide persistent solve is used instead.
 constexpr int64_t kPkcTargetRows = 128;
 
-egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
+template <typename V>
+egfem_status pkc_plan(egfem_t *h, KWork<V> &W) {
     W.pkc_cluster = 0;
     if (h->opts.krylov_cluster < 0 || !h->opts.krylov_persistent) return EGFEM_OK;
     int smem_optin = 0;
     EG_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const int64_t static_smem = 12288;  // the kernel's static shared memory (8.4 KB), rounded up
     const int mc = h->csf.max_cols;     // ELL columns of the shared-memory operator copy
-    auto rows_max = [&](int op) { return (int64_t(smem_optin) - static_smem) / pkc_row_bytes(op) / SLICE * SLICE; };
+    auto rows_max = [&](int op) { return (int64_t(smem_optin) - static_smem) / pkc_row_bytes<V>(op) / SLICE * SLICE; };
     auto rows_for = [&](int64_t c) { return (h->n_pad + c * SLICE - 1) / (c * SLICE) * SLICE; };
     int64_t c = h->opts.krylov_cluster > 0 ? h->opts.krylov_cluster : 1;
     if (h->opts.krylov_cluster == 0)
@@ -332,9 +334,9 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     const int64_t rows = rows_for(c);
     // the operator goes to shared memory when it fits (column codes hold 16-bit offsets)
     const int op = (mc <= 255 && rows <= 65535 && rows <= rows_max(mc)) ? mc : 0;
-    const size_t smem = size_t((rows * pkc_row_bytes(op) + 15) / 16 * 16);
-    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const size_t smem = size_t((rows * pkc_row_bytes<V>(op) + 15) / 16 * 16);
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkc_solve<V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -342,7 +344,7 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     cfg.gridDim = dim3(unsigned(c)); cfg.blockDim = dim3(PKC_BLOCK); cfg.dynamicSmemBytes = smem;
     cfg.stream = h->hs; cfg.attrs = attr; cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)pkc_solve, &cfg) != cudaSuccess || nclusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)pkc_solve<V>, &cfg) != cudaSuccess || nclusters < 1) {
         cudaGetLastError();
         return EGFEM_OK;
     }
@@ -353,8 +355,9 @@ egfem_status pkc_plan(egfem_t *h, KWork<double> &W) {
     return EGFEM_OK;
 }
 
-egfem_status launch_pkc(egfem_t *h, KWork<double> &W, double rtol, int32_t maxit, int32_t stall) {
-    PkcArgs P{};
+template <typename V>
+egfem_status launch_pkc(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
+    PkcArgs<V> P{};
     P.K = kvecs(h, W);
     P.st = h->st; P.n_pad = h->n_pad; P.rows_cta = W.pkc_rows; P.op_cols = W.pkc_op;
     P.rtol = rtol; P.maxit = maxit; P.stall = stall;
@@ -365,7 +368,7 @@ egfem_status launch_pkc(egfem_t *h, KWork<double> &W, double rtol, int32_t maxit
     cfg.gridDim = dim3(unsigned(W.pkc_cluster)); cfg.blockDim = dim3(PKC_BLOCK);
     cfg.dynamicSmemBytes = W.pkc_smem;
     cfg.stream = h->hs; cfg.attrs = attr; cfg.numAttrs = 1;
-    EG_CUDA(cudaLaunchKernelEx(&cfg, pkc_solve, P));
+    EG_CUDA(cudaLaunchKernelEx(&cfg, pkc_solve<V>, P));
     return EGFEM_OK;
 }
 
@@ -408,7 +411,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
         }
     }
-    if constexpr (std::is_same<V, double>::value) EG_TRY(pkc_plan(h, W));
+    EG_TRY(pkc_plan<V>(h, W));
     if constexpr (std::is_same<V, df64>::value) {
         W.g_vp = one_wave<V>(h, (const void *)kry_vp<V>);
         W.g_st = one_wave<V>(h, (const void *)kry_st<V>);
@@ -480,8 +483,7 @@ egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, in
 
 template <typename V>
 egfem_status launch_pk_single(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
-    if constexpr (std::is_same<V, double>::value)
-        if (W.pkc_cluster > 0) return launch_pkc(h, W, rtol, maxit, stall);
+    if (W.pkc_cluster > 0) return launch_pkc<V>(h, W, rtol, maxit, stall);
     return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, nullptr, nullptr, rtol,
                      W.bar, maxit, stall);
 }
@@ -1477,8 +1479,7 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         // the operator is read twice.
         const int32_t iters = 40;
         cudaError_t le = cudaSuccess;
-        bool cl = false;
-        if constexpr (std::is_same<V, double>::value) cl = W.pkc_cluster > 0;
+        const bool cl = W.pkc_cluster > 0;
         EG_TRY(timeit(cl ? "kry_cluster" : "kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
             if (launch_pk_single(h, W, 0.0, iters, 0) != EGFEM_OK) le = cudaErrorLaunchFailure;
         }));

@@ -20,6 +20,9 @@
 // (forming p and s inside the SpMV for each gathered neighbour would save two barriers but
 // triple the SpMV's FP64 work).
 //
+// V = double (the FP64 path) or df64 (the mixed path: double-float vectors, the FP32 operator
+// applied in difference form with its row sum in column 0, compensated as in pk_solve).
+//
 // The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve.
 // When it fits beside the vectors, each CTA copies its rows of it to shared memory at the
 // start (ELL values and column codes naming the owning CTA and offset), and the iterations
@@ -37,8 +40,9 @@ constexpr int PKC_MAX_CLUSTER = 16;     // non-portable cluster size (one GPC ho
 
 enum { PV_P = 0, PV_V, PV_S, PV_T, PV_R, PV_RH, PV_X };
 
+template <typename V>
 struct PkcArgs {
-    KVecs<double> K;        // operator, b (rhs) and x (solution out) in global memory
+    KVecs<V> K;             // operator, b (rhs) and x (solution out) in global memory
     KState *st;             // final state (written by rank 0)
     int64_t n_pad;          // rows (whole slices)
     int32_t rows_cta;       // rows per CTA (a multiple of SLICE); the last CTA may own fewer
@@ -49,8 +53,10 @@ struct PkcArgs {
 
 // Shared-memory bytes per row: the Krylov vectors, and with the operator copy its ELL values,
 // column codes (owning rank << 16 | offset in that CTA) and the row's column count.
+template <typename V>
 __host__ __device__ constexpr int64_t pkc_row_bytes(int op_cols) {
-    return int64_t(PKC_NVEC) * 8 + (op_cols > 0 ? int64_t(op_cols) * 12 + 1 : 0);
+    return int64_t(PKC_NVEC) * int64_t(sizeof(V)) +
+           (op_cols > 0 ? int64_t(op_cols) * int64_t(sizeof(typename VecT<V>::mat) + 4) + 1 : 0);
 }
 
 __device__ __forceinline__ void pkc_cluster_barrier() {
@@ -114,42 +120,73 @@ __device__ __forceinline__ void pkc_reduce_update(const double *cta, uint32_t nr
     __syncthreads();
 }
 
+// a df64 in CTA `rank`'s shared memory (its two words)
+__device__ __forceinline__ df64 pkc_ld_remote(const df64 *p, uint32_t rank) {
+    uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p)), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    df64 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.hi), "=f"(v.lo) : "r"(ra));
+    return v;
+}
+
+// Row accumulator of the SpMV: FP64 y = a0 x_g + sum a_c x_c, or for df64 the difference form
+// y = s_g x_g + sum a_c (x_c - x_g) (column 0 holds the row sum s_g) in a compensated pair.
+template <typename V> struct PkcRow;
+template <> struct PkcRow<double> {
+    double y, xg;
+    __device__ __forceinline__ PkcRow(double a0, double x) : y(a0 * x), xg(x) {}
+    __device__ __forceinline__ void add(double a, double xc) { y = fma(a, xc, y); }
+    __device__ __forceinline__ double value() const { return y; }
+};
+template <> struct PkcRow<df64> {
+    float hi, lo;
+    df64 xg;
+    __device__ __forceinline__ PkcRow(float a0, df64 x) : xg(x) {
+        hi = __fmul_rn(a0, x.hi);
+        lo = __fmaf_rn(a0, x.lo, __fmaf_rn(a0, x.hi, -hi));
+    }
+    __device__ __forceinline__ void add(float a, df64 xc) { df_acc_diff(hi, lo, a, xc, xg); }
+    __device__ __forceinline__ df64 value() const { return df_fast_two_sum(hi, lo); }
+};
+
 // y_g = (A x)_g for the owned row g; x is vector `vec` of the cluster, xg its value at g
-__device__ __forceinline__ double pkc_spmv_row(const KVecs<double> &K, const double *xv, int64_t g, int64_t base,
-                                               int64_t rows_here, int64_t rc, double xg) {
+template <typename V>
+__device__ __forceinline__ V pkc_spmv_row(const KVecs<V> &K, const V *xv, int64_t g, int64_t base, int64_t rows_here,
+                                          int64_t rc, V xg) {
     const SliceMeta M = K.meta[g / SLICE];
     const int lane = int(g % SLICE);
-    double y = __ldg(K.A + M.col_base + lane) * xg;
+    PkcRow<V> y(__ldg(K.A + M.col_base + lane), xg);
 #pragma unroll 4
     for (int c = 1; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
-        const double a = __ldg(K.A + q);
+        const auto a = __ldg(K.A + q);
         const int64_t col = M.off_base >= 0 ? g + __ldg(K.slice_off + M.off_base + c) : int64_t(__ldg(K.col_idx + q));
-        double xc;
+        V xc;
         if (col >= base && col < base + rows_here) {
             xc = xv[col - base];
         } else {
             const uint32_t o = uint32_t(col / rc);
             xc = pkc_ld_remote(xv + (col - int64_t(o) * rc), o);
         }
-        y = fma(a, xc, y);
+        y.add(a, xc);
     }
-    return y;
+    return y.value();
 }
 
 // the same product from the shared-memory copy of the operator (row l of this CTA)
-__device__ __forceinline__ double pkc_spmv_row_smem(const double *opv, const uint32_t *opc, const uint8_t *opn,
-                                                    const double *xv, int64_t l, int64_t rc, uint32_t rank, double xg) {
-    double y = opv[l] * xg;
+template <typename V, typename M_t>
+__device__ __forceinline__ V pkc_spmv_row_smem(const M_t *opv, const uint32_t *opc, const uint8_t *opn, const V *xv,
+                                               int64_t l, int64_t rc, uint32_t rank, V xg) {
+    PkcRow<V> y(opv[l], xg);
     const int nc = opn[l];
 #pragma unroll 4
     for (int c = 1; c < nc; ++c) {
         const uint32_t code = opc[int64_t(c) * rc + l];
         const uint32_t o = code >> 16, off = code & 0xFFFFu;
-        const double xc = o == rank ? xv[off] : pkc_ld_remote(xv + off, o);
-        y = fma(opv[int64_t(c) * rc + l], xc, y);
+        const V xc = o == rank ? xv[off] : pkc_ld_remote(xv + off, o);
+        y.add(opv[int64_t(c) * rc + l], xc);
     }
-    return y;
+    return y.value();
 }
 
 #define PKC_ROWS for (int64_t l = threadIdx.x; l < rows_here; l += PKC_BLOCK)
@@ -158,8 +195,12 @@ __device__ __forceinline__ double pkc_spmv_row_smem(const double *opv, const uin
 // cap, divergence or (stall > 0) stagnation.  One cluster; grid = the cluster.  The phases and
 // their order are those of pk_solve<double>: A v = A p | B1 s = r - alpha v | B2 t = A s |
 // C x, r | D p, with a cluster barrier after each.
-__global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
-    extern __shared__ double sv[];              // [PKC_NVEC][rows_cta]
+template <typename V>
+__global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs<V> P) {
+    using Op = PkOps<V>;
+    using M_t = typename VecT<V>::mat;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sv = reinterpret_cast<V *>(smem_raw);     // [PKC_NVEC][rows_cta]
     __shared__ double th[2][PKC_BLOCK];         // per-thread partials of the reduction in progress
     __shared__ double cta_0[1], cta_a[1], cta_o[2], cta_r[2];
     __shared__ KState S;                        // this CTA's copy of the state (warp 0 writes it)
@@ -168,12 +209,12 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
     const int64_t base = int64_t(rank) * RC;
     const int64_t rows_here = base >= P.n_pad ? 0 : (P.n_pad - base < RC ? P.n_pad - base : RC);
     const int nact = int(rows_here < PKC_BLOCK ? rows_here : PKC_BLOCK);   // threads that own rows
-    double *p = sv + PV_P * RC, *v = sv + PV_V * RC, *s = sv + PV_S * RC, *t = sv + PV_T * RC;
-    double *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
-    const KVecs<double> &K = P.K;
+    V *p = sv + PV_P * RC, *v = sv + PV_V * RC, *s = sv + PV_S * RC, *t = sv + PV_T * RC;
+    V *r = sv + PV_R * RC, *rh = sv + PV_RH * RC, *x = sv + PV_X * RC;
+    const KVecs<V> &K = P.K;
     // the operator copy (when P.op_cols > 0): values [op_cols][RC], codes [op_cols][RC], counts [RC]
     const int MC = P.op_cols;
-    double *opv = sv + PKC_NVEC * RC;
+    M_t *opv = reinterpret_cast<M_t *>(sv + PKC_NVEC * RC);
     uint32_t *opc = reinterpret_cast<uint32_t *>(opv + int64_t(MC) * RC);
     uint8_t *opn = reinterpret_cast<uint8_t *>(opc + int64_t(MC) * RC);
     if (MC > 0) {
@@ -183,7 +224,7 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
             const int lane = int(g % SLICE);
             opn[l] = uint8_t(M.ncol < MC ? M.ncol : MC);
             for (int c = 0; c < MC; ++c) {
-                double a = 0.0;
+                M_t a = M_t(0);
                 uint32_t code = (rank << 16) | uint32_t(l);
                 if (c < M.ncol) {
                     const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
@@ -197,17 +238,22 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
             }
         }
     }
+    auto spmv = [&](const V *xv, int64_t l, V xg) -> V {
+        return MC > 0 ? pkc_spmv_row_smem<V, M_t>(opv, opc, opn, xv, l, RC, rank, xg)
+                      : pkc_spmv_row<V>(K, xv, base + l, base, rows_here, RC, xg);
+    };
 
     // setup: x = v = 0, r = rh = p = b, (b, b)
-    double acc0 = 0.0;
+    DotAcc<V> acc0;
+    const V zero = cvt<V>(0.0);
     PKC_ROWS {
-        const double b = __ldg(K.b + base + l);
-        x[l] = 0.0; v[l] = 0.0; s[l] = 0.0; t[l] = 0.0;
+        const V b = K.b[base + l];
+        x[l] = zero; v[l] = zero; s[l] = zero; t[l] = zero;
         r[l] = b; rh[l] = b; p[l] = b;
-        acc0 = fma(b, b, acc0);
+        acc0.add(b, b);
     }
     {
-        const double a1[1] = {acc0};
+        const double a1[1] = {acc0.value()};
         pkc_cta_partial<1>(a1, th, nact, cta_0);
     }
     pkc_cluster_barrier();   // also: every CTA of the cluster has started before any remote access
@@ -223,15 +269,14 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
 
     while (S.done == K_RUNNING) {
         // A: v = A p, (rh, v)
-        double acc = 0.0;
+        DotAcc<V> acc;
         PKC_ROWS {
-            const double y = MC > 0 ? pkc_spmv_row_smem(opv, opc, opn, p, l, RC, rank, p[l])
-                                    : pkc_spmv_row(K, p, base + l, base, rows_here, RC, p[l]);
+            const V y = spmv(p, l, p[l]);
             v[l] = y;
-            acc = fma(rh[l], y, acc);
+            acc.add(rh[l], y);
         }
         {
-            const double a1[1] = {acc};
+            const double a1[1] = {acc.value()};
             pkc_cta_partial<1>(a1, th, nact, cta_a);
         }
         pkc_cluster_barrier();
@@ -242,22 +287,21 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         if (S.done != K_RUNNING) break;
 
         // B1: s = r - alpha v (every CTA's s is complete before the SpMV gathers it)
-        const double al = S.alpha;
-        PKC_ROWS s[l] = r[l] - al * v[l];
+        const V al = cvt<V>(S.alpha);
+        PKC_ROWS s[l] = Op::sub(r[l], al * v[l]);
         pkc_cluster_barrier();
 
         // B2: t = A s, (t, s), (t, t)
-        double ts = 0.0, tt = 0.0;
+        DotAcc<V> ts, tt;
         PKC_ROWS {
-            const double sl = s[l];
-            const double y = MC > 0 ? pkc_spmv_row_smem(opv, opc, opn, s, l, RC, rank, sl)
-                                    : pkc_spmv_row(K, s, base + l, base, rows_here, RC, sl);
+            const V sl = s[l];
+            const V y = spmv(s, l, sl);
             t[l] = y;
-            ts = fma(y, sl, ts);
-            tt = fma(y, y, tt);
+            ts.add(y, sl);
+            tt.add(y, y);
         }
         {
-            const double a2[2] = {ts, tt};
+            const double a2[2] = {ts.value(), tt.value()};
             pkc_cta_partial<2>(a2, th, nact, cta_o);
         }
         pkc_cluster_barrier();
@@ -268,17 +312,17 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         if (S.done != K_RUNNING) break;
 
         // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
-        const double om = S.omega;
-        double rr1 = 0.0, rr2 = 0.0;
+        const V om = cvt<V>(S.omega);
+        DotAcc<V> rr1, rr2;
         PKC_ROWS {
-            x[l] = x[l] + (al * p[l] + om * s[l]);
-            const double rn = s[l] - om * t[l];
+            x[l] = Op::add(x[l], Op::add(al * p[l], om * s[l]));
+            const V rn = Op::sub(s[l], om * t[l]);
             r[l] = rn;
-            rr1 = fma(rh[l], rn, rr1);
-            rr2 = fma(rn, rn, rr2);
+            rr1.add(rh[l], rn);
+            rr2.add(rn, rn);
         }
         {
-            const double a2[2] = {rr1, rr2};
+            const double a2[2] = {rr1.value(), rr2.value()};
             pkc_cta_partial<2>(a2, th, nact, cta_r);
         }
         pkc_cluster_barrier();
@@ -288,8 +332,8 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs P) {
         if (S.done != K_RUNNING) break;
 
         // D: p = r + beta (p - omega v)
-        const double be = S.beta;
-        PKC_ROWS p[l] = r[l] + be * (p[l] - om * v[l]);
+        const V be = cvt<V>(S.beta);
+        PKC_ROWS p[l] = Op::add(r[l], be * Op::sub(p[l], om * v[l]));
         pkc_cluster_barrier();
     }
 

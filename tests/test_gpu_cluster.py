@@ -1,6 +1,7 @@
 """GPU checks of the cluster BiCGStab solve (one thread-block cluster, the Krylov vectors in
-distributed shared memory): for every cluster size, the Newton solution equals the oracle's and
-the grid-wide persistent solve's, with the same number of Newton steps."""
+distributed shared memory): for every cluster size and both precisions (FP64; double-float
+vectors with the FP32 operator), the Newton solution equals the oracle's and the grid-wide
+persistent solve's (FP64: with the same number of Newton steps)."""
 import numpy as np
 import pytest
 
@@ -38,13 +39,16 @@ def case():
     return mesh, b, u_orc
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16, 0])
-def test_cluster_solve_matches_oracle_and_grid_solve(P, case, cluster):
+def test_cluster_solve_matches_oracle_and_grid_solve(P, case, cluster, prec):
     mesh, b, u_orc = case
     prob = P.make_problem(a=("pow", 2), a_degree=2)
+    mixed = prec == "mixed"
     out = {}
     for name, c in (("cluster", cluster), ("grid", -1)):
-        h = P.Handle(mesh, prob, P.default_options(newton_rtol=1e-13, krylov_cluster=c))
+        h = P.Handle(mesh, prob, P.default_options(newton_rtol=1e-10 if mixed else 1e-13, krylov_cluster=c,
+                                                   precision=P.PREC_MIXED if mixed else P.PREC_FP64))
         u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
         st = h.newton_solve(u, cuda(b))
         torch.cuda.synchronize()
@@ -53,9 +57,11 @@ def test_cluster_solve_matches_oracle_and_grid_solve(P, case, cluster):
         kernels = {p["name"] for p in h.profile_kernels(u, cuda(b), reps=1)}
         assert ("kry_cluster" in kernels) == (name == "cluster"), kernels
         h.close()
-    assert rel(out["cluster"][0], u_orc) <= 1e-11
-    assert rel(out["cluster"][0], out["grid"][0]) <= 1e-11
-    assert out["cluster"][1] == out["grid"][1]
+    tol = 1e-8 if mixed else 1e-11
+    assert rel(out["cluster"][0], u_orc) <= tol
+    assert rel(out["cluster"][0], out["grid"][0]) <= tol
+    if not mixed:
+        assert out["cluster"][1] == out["grid"][1]
 
 
 def test_cluster_solve_too_large_falls_back_to_the_grid_solve(P):
