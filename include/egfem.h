@@ -164,11 +164,12 @@ typedef struct {
                                 16 x 3904 rows): 0 (default) when it fits, with the cluster
                                 size chosen by the library; 1..16 that cluster size; -1
                                 never.  Read at the first solve of a handle                   */
-    int32_t newton_graph;    /* nonzero (default): egfem_batch_newton_solve runs its Newton loop
-                                as one CUDA graph (a conditional WHILE node over controller
-                                kernels, the batched persistent BiCGStab, the update and the
-                                tensor action) taking full steps; instances that need a
-                                shortened step or an FP64 redo are finished by the host loop.
+    int32_t newton_graph;    /* nonzero (default): egfem_newton_solve and egfem_batch_newton_solve
+                                run their Newton loop as one CUDA graph (a conditional WHILE
+                                node over controller kernels, the persistent or cluster
+                                BiCGStab, the update and the tensor action) taking full steps;
+                                systems that need a shortened step or an FP64 redo are finished
+                                by the host loop (needs krylov_persistent).
                                 0: the host loop only; 2: the graph loop is required (the
                                 solve returns EGFEM_ERR_UNSUPPORTED where it is unavailable) */
 } egfem_options;

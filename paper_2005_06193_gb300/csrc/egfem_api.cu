@@ -163,6 +163,7 @@ struct egfem_t {
     cudaGraphExec_t gn_exec = nullptr;
     const double *gn_u = nullptr, *gn_d = nullptr;
     int gn_mixed = -1;
+    int gn_one = -1;                    // 1: captured for egfem_newton_solve, 0: for the batched solve
     int gn_nodes = 0;                   // kernels one body execution launches
     bool gn_failed = false;             // capture or instantiation failed once: host loop only
     bool gn_used = false;               // the last batched solve ran the graph loop
@@ -356,11 +357,12 @@ egfem_status pkc_plan(egfem_t *h, KWork<V> &W) {
 }
 
 template <typename V>
-egfem_status launch_pkc(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
+egfem_status launch_pkc(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall,
+                        const uint8_t *active = nullptr, const double *rtol_ptr = nullptr) {
     PkcArgs<V> P{};
     P.K = kvecs(h, W);
     P.st = h->st; P.n_pad = h->n_pad; P.rows_cta = W.pkc_rows; P.op_cols = W.pkc_op;
-    P.rtol = rtol; P.maxit = maxit; P.stall = stall;
+    P.rtol = rtol; P.maxit = maxit; P.stall = stall; P.active = active; P.rtol_ptr = rtol_ptr;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -861,6 +863,118 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
 
 }  // namespace
 
+namespace {
+
+// Single-system graph Newton loop (egfem_gnewton.cuh with one instance): the body is the
+// controller, the persistent or cluster BiCGStab with its tolerance and activity read from
+// device memory, the controller, u -= x, the tensor action and the free-row norm, the
+// controller and the revert.  Kept for later calls with the same vectors and path.
+template <typename V>
+egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d) {
+    constexpr bool mixed = std::is_same<V, df64>::value;
+    if (h->gn_exec && h->gn_u == d_u && h->gn_d == d_d && h->gn_mixed == int(mixed) && h->gn_one == 1) return EGFEM_OK;
+    if (h->gn_exec) { cudaGraphExecDestroy(h->gn_exec); h->gn_exec = nullptr; }
+    if (h->nb > 0) return EGFEM_ERR_UNSUPPORTED;   // a batch handle solves through the batched loop
+    if (!h->gn_state) {
+        EG_TRY(dalloc(h->gn_state, 1));
+        EG_TRY(dalloc(h->gn_stats, 1));
+        EG_TRY(dalloc(h->gn_loops, 1));
+        EG_TRY(dalloc(h->inst_mask, 1));
+        EG_TRY(dalloc(h->inst_eta, 1));
+        EG_TRY(dalloc(h->inst_lam, 1));
+    }
+    if (!W.bar && W.pkc_cluster == 0) return EGFEM_ERR_UNSUPPORTED;
+    cudaGraph_t g = nullptr;
+    EG_CUDA(cudaGraphCreate(&g, 0));
+    cudaError_t e = cudaSuccess;
+    cudaGraphConditionalHandle cond{};
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node = nullptr;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->hs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        g_last_error = std::string("graph Newton loop: ") + cudaGetErrorString(e);
+        return EGFEM_ERR_CUDA;
+    }
+    GNArgs G{};
+    G.nb = 1; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
+    G.lam = h->inst_lam; G.kst = h->st; G.norm2 = h->scal; G.loops = h->gn_loops;
+    G.max_loops = h->opts.newton_maxit + 2; G.newton_maxit = h->opts.newton_maxit; G.fixed_eta = h->opts.fixed_eta;
+    G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
+    const unsigned gu = unsigned((h->n + 255) / 256);
+    const int32_t stall = mixed ? kMixedStall : 0;
+    int nodes = 0;
+    egfem_status st = EGFEM_OK;
+    gn_pre<<<1, 32, 0, h->hs>>>(G);
+    if (W.pkc_cluster > 0) st = launch_pkc<V>(h, W, 0.0, h->opts.krylov_maxit, stall, h->inst_mask, h->inst_eta);
+    else st = launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, h->inst_mask,
+                        h->inst_eta, 0.0, W.bar, h->opts.krylov_maxit, stall);
+    gn_mid<<<1, 32, 0, h->hs>>>(G);
+    gn_update_one<V><<<gu, 256, 0, h->hs>>>(h->n, h->inst_mask, h->inst_lam, d_u, W.x);
+    CsfArgs A = csf_args(h, d_u, d_d);
+    A.r = h->r; A.q64 = h->k64.b;
+    if (mixed) A.a32 = h->k32.A;
+    else A.a64 = h->k64.A;
+    nodes += launch_csf(h, A, h->hs);
+    if (mixed) { cast_kernel<double, df64><<<gu, 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b); ++nodes; }
+    norm2_free_kernel<<<h->kgrid, KRY_BLOCK, 0, h->hs>>>(h->n, h->r, h->csf.dir, h->part, h->ticket, h->scal);
+    gn_post<<<1, 32, 0, h->hs>>>(G);
+    gn_update_one<V><<<gu, 256, 0, h->hs>>>(h->n, h->inst_mask, h->inst_lam, d_u, W.x);
+    nodes += 7;
+    cudaGraph_t body = nullptr;
+    e = cudaStreamEndCapture(h->hs, &body);
+    if (st == EGFEM_OK && e == cudaSuccess) e = cudaGetLastError();
+    if (st == EGFEM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->gn_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (st != EGFEM_OK || e != cudaSuccess) {
+        if (e != cudaSuccess) g_last_error = std::string("graph Newton loop: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        h->gn_exec = nullptr;
+        return st != EGFEM_OK ? st : EGFEM_ERR_CUDA;
+    }
+    h->gn_u = d_u; h->gn_d = d_d; h->gn_mixed = int(mixed); h->gn_nodes = nodes; h->gn_one = 1;
+    return EGFEM_OK;
+}
+
+// Run it from the host driver's state after the first evaluation; false when unavailable.
+template <typename V>
+bool gn_run_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, double &rn, double &rprev, double &eta,
+                double target, egfem_stats &S, bool &handed_back) {
+    handed_back = false;
+    if (!h->opts.newton_graph || h->gn_failed || !h->opts.krylov_persistent || h->nb > 0) return false;
+    if (W.g_pk <= 0 && W.pkc_cluster <= 0) return false;
+    if (gn_build_one<V>(h, W, d_u, d_d) != EGFEM_OK) { h->gn_failed = true; return false; }
+    GNState G{rn, rprev, rn, target, eta, 0, 0};
+    if (cudaMemcpyAsync(h->gn_state, &G, sizeof(GNState), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
+        cudaMemcpyAsync(h->gn_stats, &S, sizeof(egfem_stats), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
+        cudaMemsetAsync(h->gn_loops, 0, sizeof(int32_t), h->hs) != cudaSuccess ||
+        cudaGraphLaunch(h->gn_exec, h->hs) != cudaSuccess) {
+        cudaGetLastError();
+        h->gn_failed = true;
+        return false;
+    }
+    int32_t loops = 0;
+    cudaMemcpyAsync(&G, h->gn_state, sizeof(GNState), cudaMemcpyDeviceToHost, h->hs);
+    cudaMemcpyAsync(&S, h->gn_stats, sizeof(egfem_stats), cudaMemcpyDeviceToHost, h->hs);
+    cudaMemcpyAsync(&loops, h->gn_loops, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs);
+    if (cudaStreamSynchronize(h->hs) != cudaSuccess) return true;   // the caller's next CUDA call reports it
+    rn = G.rn; rprev = G.rprev; eta = G.eta;
+    handed_back = G.host != 0;
+    S.kernel_launches += int64_t(loops) * h->gn_nodes;
+    h->gn_used = true;
+    return true;
+}
+
+}  // namespace
+
 extern "C" {
 
 egfem_status egfem_selftest_grid_barrier(int32_t blocks, int32_t arrive, double wait_ms, int32_t *ok_host,
@@ -1150,7 +1264,27 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     double eta = h->opts.eta_max, rprev = rn;
     int k = 0;
     status = EGFEM_OK;
-    while (true) {
+    // the Newton loop on the device (full steps); the host loop below resumes from its state
+    h->gn_used = false;
+    if (rn > target && std::isfinite(rn)) {
+        bool back = false;
+        const bool ran = mixed ? gn_run_one<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, S, back)
+                               : gn_run_one<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, S, back);
+        if (!ran && h->opts.newton_graph == 2) {
+            g_last_error = "graph Newton loop required (newton_graph = 2) but unavailable: " + g_last_error;
+            status = EGFEM_ERR_UNSUPPORTED;
+        } else if (ran) {
+            EG_CUDA(cudaGetLastError());
+            k = S.newton_iters;
+            const egfem_status ws = check_status_word(h);   // a zero Jacobi diagonal on the way
+            if (ws != EGFEM_OK) status = ws;
+            else if (S.status != EGFEM_OK) status = egfem_status(S.status);
+            // residual and operator at the current u for the host loop (it may have stopped at
+            // a rejected, reverted step, or at the iteration cap)
+            else if (back || rn > target) status = eval(&rn);
+        }
+    }
+    while (status == EGFEM_OK) {
         if (!std::isfinite(rn)) { status = EGFEM_ERR_NONFINITE; break; }
         if (rn <= target) break;
         if (k >= h->opts.newton_maxit) { status = EGFEM_ERR_NOT_CONVERGED; g_last_error = "Newton iteration cap"; break; }
@@ -1823,11 +1957,11 @@ egfem_status batch_norms(egfem_t *h) {
 template <typename V>
 egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, int pg) {
     constexpr bool mixed = std::is_same<V, df64>::value;
-    if (h->gn_exec && h->gn_u == d_u && h->gn_d == d_d && h->gn_mixed == int(mixed)) return EGFEM_OK;
+    if (h->gn_exec && h->gn_u == d_u && h->gn_d == d_d && h->gn_mixed == int(mixed) && h->gn_one == 0) return EGFEM_OK;
     if (h->gn_exec) { cudaGraphExecDestroy(h->gn_exec); h->gn_exec = nullptr; }
     if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));   // no allocation may happen inside the capture
     if (!h->gn_state) {
-        EG_TRY(dalloc(h->gn_state, size_t(h->nb)));
+        EG_TRY(dalloc(h->gn_state, size_t(std::max<int32_t>(h->nb, 1))));
         EG_TRY(dalloc(h->gn_stats, size_t(h->nb)));
         EG_TRY(dalloc(h->gn_loops, 1));
     }
@@ -1885,7 +2019,7 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
         h->gn_exec = nullptr;
         return st != EGFEM_OK ? st : EGFEM_ERR_CUDA;
     }
-    h->gn_u = d_u; h->gn_d = d_d; h->gn_mixed = int(mixed); h->gn_nodes = nodes;
+    h->gn_u = d_u; h->gn_d = d_d; h->gn_mixed = int(mixed); h->gn_nodes = nodes; h->gn_one = 0;
     return EGFEM_OK;
 }
 

@@ -49,6 +49,8 @@ struct PkcArgs {
     int32_t op_cols;        // > 0: the operator is copied to shared memory as op_cols ELL columns
     double rtol;
     int32_t maxit, stall;
+    const uint8_t *active;  // nullable: the solve does nothing when *active == 0 (graph Newton loop)
+    const double *rtol_ptr; // nullable: the tolerance read from device memory instead of rtol
 };
 
 // Shared-memory bytes per row: the Krylov vectors, and with the operator copy its ELL values,
@@ -204,6 +206,9 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs<V> P) {
     __shared__ double th[2][PKC_BLOCK];         // per-thread partials of the reduction in progress
     __shared__ double cta_0[1], cta_a[1], cta_o[2], cta_r[2];
     __shared__ KState S;                        // this CTA's copy of the state (warp 0 writes it)
+    // an inactive solve (graph Newton loop, nothing to do) returns at once in every CTA
+    if (P.active && !*P.active) return;
+    const double rtol = P.rtol_ptr ? *P.rtol_ptr : P.rtol;
     const uint32_t rank = pkc_rank(), nranks = pkc_nranks();
     const int64_t RC = P.rows_cta;
     const int64_t base = int64_t(rank) * RC;
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs<V> P) {
         Q.iter = 0; Q.last_improve = 0; Q.maxit = P.maxit; Q.stall = P.stall; Q.ticket = 0u;
         Q.alpha = 1.0; Q.omega = 1.0; Q.beta = 0.0; Q.scratch[0] = Q.scratch[1] = 0.0;
         Q.rho = Q.rr = Q.rr0 = Q.best_rr = bb;
-        Q.tol2 = P.rtol * P.rtol * bb;
+        Q.tol2 = rtol * rtol * bb;
         Q.stall_rr = 4e-6 * bb;
         Q.done = (bb == 0.0) ? K_CONVERGED : (!isfinite(bb) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
     });

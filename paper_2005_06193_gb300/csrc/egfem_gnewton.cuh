@@ -8,9 +8,11 @@
 // An instance whose full step fails the sufficient-decrease test, or whose Krylov solve broke
 // down, has the step reverted and is handed back (host = 1): the host driver then finishes it
 // with step halving and, on the mixed path, an FP64 redo -- the graph only takes full steps.
+// A single system uses the same controllers with one instance (nb = 1).
 #pragma once
 
 #include "egfem_kernels.cuh"
+#include "egfem_krylov.cuh"
 
 namespace egfem {
 
@@ -116,6 +118,14 @@ __global__ void gn_post(GNArgs G) {
             G.lam[b] = -1.0;
         }
     }
+}
+
+// u -= lam x on every row when the single system's mask is set (the graph loop's step and
+// revert for one system)
+template <typename V>
+__global__ void gn_update_one(int64_t n, const uint8_t *mask, const double *lam, double *u, const V *x) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n && *mask) u[i] -= *lam * to_d(x[i]);
 }
 
 }  // namespace egfem

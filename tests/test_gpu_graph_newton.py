@@ -106,3 +106,50 @@ def test_graph_hands_back_steps_that_need_damping(P):
     for b, (x, ref) in enumerate(zip(h.gather(u, [m.n_nodes for m in meshes]), refs)):
         assert st[b].status == 0, b
         assert rel(x, ref) <= 1e-10, b
+
+
+@pytest.mark.parametrize("prec,cluster", [("fp64", 0), ("fp64", -1), ("mixed", 0), ("mixed", -1)])
+def test_single_system_graph_newton_matches_host_loop(P, prec, cluster):
+    """egfem_newton_solve with the graph loop required equals the host loop (same Newton steps)
+    and the oracle, for the cluster and the grid-wide BiCGStab and both precisions."""
+    mesh = wl.unit_square_mesh(40)
+    orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+    b = orc.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
+    u_ref, _, _, _ = orc.newton(b, rtol=1e-13)
+    mixed = prec == "mixed"
+    out = []
+    for graph in (2, 0):
+        h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2),
+                     P.default_options(newton_graph=graph, krylov_cluster=cluster, newton_rtol=1e-10 if mixed else 1e-13,
+                                       precision=P.PREC_MIXED if mixed else P.PREC_FP64))
+        u = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+        d = torch.tensor(b, device="cuda", dtype=torch.float64)
+        st = h.newton_solve(u, d)
+        u2 = torch.zeros_like(u)
+        st2 = h.newton_solve(u2, d) if graph == 2 else st   # a second call reuses the captured graph
+        torch.cuda.synchronize()
+        assert st.status == 0 and st2.status == 0
+        out.append((u.cpu().numpy(), st.newton_iters))
+        if graph == 2:
+            assert np.array_equal(u.cpu().numpy(), u2.cpu().numpy())
+        h.close()
+    tol = 1e-8 if mixed else 1e-11
+    assert rel(out[0][0], u_ref) <= tol and rel(out[1][0], u_ref) <= tol
+    assert out[0][1] == out[1][1]
+
+
+def test_single_system_graph_hands_back_damped_steps(P):
+    mesh = wl.unit_square_mesh(32)
+    orc = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    ue = wl.minsurf_exact(x, y)
+    uD = ue * mesh.dirichlet
+    b = orc.load_vector(wl.minsurf_source) * (1 - mesh.dirichlet)
+    u_ref, _, _, _ = orc.newton(b, u0=ue + 0.2 * np.sin(np.pi * x) * np.sin(np.pi * y), uD=uD, rtol=1e-12)
+    h = P.Handle(mesh, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
+                 P.default_options(op=P.OP_MATRIX_FREE, newton_graph=2, newton_rtol=1e-12))
+    u = torch.tensor(uD, device="cuda", dtype=torch.float64)
+    st = h.newton_solve(u, torch.tensor(b + uD, device="cuda", dtype=torch.float64))
+    torch.cuda.synchronize()
+    assert st.status == 0
+    assert rel(u.cpu().numpy(), u_ref) <= 1e-10
