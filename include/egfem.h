@@ -167,9 +167,9 @@ typedef struct {
     int32_t newton_graph;    /* nonzero (default): egfem_newton_solve and egfem_batch_newton_solve
                                 run their Newton loop as one CUDA graph (a conditional WHILE
                                 node over controller kernels, the persistent or cluster
-                                BiCGStab, the update and the tensor action) taking full steps;
-                                systems that need a shortened step or an FP64 redo are finished
-                                by the host loop (needs krylov_persistent).
+                                BiCGStab, the update and the tensor action), step halving
+                                included; a step that needs the FP64 redo of the mixed path is
+                                finished by the host loop (needs krylov_persistent).
                                 0: the host loop only; 2: the graph loop is required (the
                                 solve returns EGFEM_ERR_UNSUPPORTED where it is unavailable) */
 } egfem_options;

@@ -907,7 +907,8 @@ egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_
     GNArgs G{};
     G.nb = 1; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
     G.lam = h->inst_lam; G.kst = h->st; G.norm2 = h->scal; G.loops = h->gn_loops;
-    G.max_loops = h->opts.newton_maxit + 2; G.newton_maxit = h->opts.newton_maxit; G.fixed_eta = h->opts.fixed_eta;
+    G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
+    G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
     G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
     const unsigned gu = unsigned((h->n + 255) / 256);
     const int32_t stall = mixed ? kMixedStall : 0;
@@ -944,15 +945,17 @@ egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_
     return EGFEM_OK;
 }
 
-// Run it from the host driver's state after the first evaluation; false when unavailable.
+// Run it from the host driver's state after the first evaluation; false when unavailable.  On a
+// hand-back (handed_back) the current step awaits its FP64 redo: rbefore is its starting norm
+// and eta its forcing term.
 template <typename V>
 bool gn_run_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, double &rn, double &rprev, double &eta,
-                double target, egfem_stats &S, bool &handed_back) {
+                double target, egfem_stats &S, bool &handed_back, double &rbefore) {
     handed_back = false;
     if (!h->opts.newton_graph || h->gn_failed || !h->opts.krylov_persistent || h->nb > 0) return false;
     if (W.g_pk <= 0 && W.pkc_cluster <= 0) return false;
     if (gn_build_one<V>(h, W, d_u, d_d) != EGFEM_OK) { h->gn_failed = true; return false; }
-    GNState G{rn, rprev, rn, target, eta, 0, 0};
+    GNState G{rn, rprev, rn, target, eta, 1.0, 0, 0, 0, 0};
     if (cudaMemcpyAsync(h->gn_state, &G, sizeof(GNState), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
         cudaMemcpyAsync(h->gn_stats, &S, sizeof(egfem_stats), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
         cudaMemsetAsync(h->gn_loops, 0, sizeof(int32_t), h->hs) != cudaSuccess ||
@@ -966,7 +969,7 @@ bool gn_run_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, double 
     cudaMemcpyAsync(&S, h->gn_stats, sizeof(egfem_stats), cudaMemcpyDeviceToHost, h->hs);
     cudaMemcpyAsync(&loops, h->gn_loops, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs);
     if (cudaStreamSynchronize(h->hs) != cudaSuccess) return true;   // the caller's next CUDA call reports it
-    rn = G.rn; rprev = G.rprev; eta = G.eta;
+    rn = G.rn; rprev = G.rprev; eta = G.eta; rbefore = G.rbefore;
     handed_back = G.host != 0;
     S.kernel_launches += int64_t(loops) * h->gn_nodes;
     h->gn_used = true;
@@ -1264,12 +1267,14 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     double eta = h->opts.eta_max, rprev = rn;
     int k = 0;
     status = EGFEM_OK;
-    // the Newton loop on the device (full steps); the host loop below resumes from its state
+    // the Newton loop on the device (damping included); the host loop below resumes from its state
     h->gn_used = false;
+    bool resume64 = false;   // the graph handed back its current step for the FP64 redo
+    double rb_resume = rn;
     if (rn > target && std::isfinite(rn)) {
         bool back = false;
-        const bool ran = mixed ? gn_run_one<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, S, back)
-                               : gn_run_one<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, S, back);
+        const bool ran = mixed ? gn_run_one<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, S, back, rb_resume)
+                               : gn_run_one<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, S, back, rb_resume);
         if (!ran && h->opts.newton_graph == 2) {
             g_last_error = "graph Newton loop required (newton_graph = 2) but unavailable: " + g_last_error;
             status = EGFEM_ERR_UNSUPPORTED;
@@ -1278,10 +1283,17 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             k = S.newton_iters;
             const egfem_status ws = check_status_word(h);   // a zero Jacobi diagonal on the way
             if (ws != EGFEM_OK) status = ws;
-            else if (S.status != EGFEM_OK) status = egfem_status(S.status);
-            // residual and operator at the current u for the host loop (it may have stopped at
-            // a rejected, reverted step, or at the iteration cap)
-            else if (back || rn > target) status = eval(&rn);
+            else if (S.status != EGFEM_OK) {
+                status = egfem_status(S.status);
+                if (status == EGFEM_ERR_NOT_CONVERGED)
+                    g_last_error = k >= h->opts.newton_maxit ? "Newton iteration cap"
+                                                             : "Newton step failed to decrease the residual after 6 halvings";
+            } else if (back || rn > target) {
+                // residual and operator at the current u for the host loop: the undone step
+                // of a hand-back (its FP64 redo follows), or the graph's loop cap
+                status = eval(&rn);
+                resume64 = back;
+            }
         }
     }
     while (status == EGFEM_OK) {
@@ -1290,8 +1302,9 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
         if (k >= h->opts.newton_maxit) { status = EGFEM_ERR_NOT_CONVERGED; g_last_error = "Newton iteration cap"; break; }
         egfem_status ws = check_status_word(h);
         if (ws != EGFEM_OK) { status = ws; break; }
-        // Eisenstat-Walker forcing term (choice 2, gamma = 0.9, alpha = 2), safeguarded
-        if (k > 0 && !h->opts.fixed_eta) {
+        // Eisenstat-Walker forcing term (choice 2, gamma = 0.9, alpha = 2), safeguarded; a step
+        // resumed from the graph keeps its forcing term and starting norm
+        if (k > 0 && !h->opts.fixed_eta && !resume64) {
             double e = 0.9 * (rn / rprev) * (rn / rprev);
             const double sg = 0.9 * eta * eta;
             if (sg > 0.1) e = std::max(e, sg);
@@ -1299,9 +1312,10 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             eta = std::max(eta, 0.5 * target / rn);
         }
         eta = std::max(eta, h->opts.eta_min);
-        bool fp32 = mixed, stepped = false;
-        const double rbefore = rn;
-        int32_t its_step = 0;
+        bool fp32 = mixed && !resume64, stepped = false;
+        const double rbefore = resume64 ? rb_resume : rn;
+        int32_t its_step = k < EGFEM_HIST ? S.krylov_hist[k] : 0;   // the graph's share of this step
+        resume64 = false;
         while (!stepped) {
             int32_t done = 0, it = 0;
             if (!fp32 && !have64) {   // an FP64 rescue needs the FP64 operator at this u
@@ -1989,7 +2003,8 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
     GNArgs G{};
     G.nb = h->nb; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
     G.lam = h->inst_lam; G.kst = h->bst; G.norm2 = h->inst_norm2; G.loops = h->gn_loops;
-    G.max_loops = h->opts.newton_maxit + 2; G.newton_maxit = h->opts.newton_maxit; G.fixed_eta = h->opts.fixed_eta;
+    G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
+    G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
     G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
     const unsigned gu = unsigned((h->n + 255) / 256);
     int nodes = 0;
@@ -2024,13 +2039,14 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
 }
 
 // Run the graph-resident Newton loop from the host driver's state (after its first residual
-// evaluation) and take its state back: instances it handed back, and any it did not finish,
-// continue in the host loop.  Returns false when the graph is unavailable (the host loop then
-// does everything).
+// evaluation) and take its state back: instances it handed back (resume64: their current step
+// awaits the FP64 redo, from rbefore with forcing term eta), and any it did not finish, continue
+// in the host loop.  Returns false when the graph is unavailable (the host loop then does
+// everything).
 template <typename V>
 bool gn_run(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, std::vector<double> &rn, std::vector<double> &rprev,
             std::vector<double> &eta, const std::vector<double> &target, std::vector<int32_t> &st,
-            std::vector<egfem_stats> &S, int64_t *launches) {
+            std::vector<egfem_stats> &S, std::vector<double> &rbefore, std::vector<int> &resume64, int64_t *launches) {
     if (!h->opts.newton_graph || h->gn_failed) return false;
     const int pg = pk_batch_grid<V>(h);
     if (pg <= 0) return false;
@@ -2038,7 +2054,7 @@ bool gn_run(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, std::vector
     h->gn_used = true;
     const int nb = h->nb;
     std::vector<GNState> G(nb);
-    for (int b = 0; b < nb; ++b) G[b] = GNState{rn[b], rprev[b], rn[b], target[b], eta[b], 0, 0};
+    for (int b = 0; b < nb; ++b) G[b] = GNState{rn[b], rprev[b], rn[b], target[b], eta[b], 1.0, 0, 0, 0, 0};
     if (cudaMemcpyAsync(h->gn_state, G.data(), sizeof(GNState) * size_t(nb), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
         cudaMemcpyAsync(h->gn_stats, S.data(), sizeof(egfem_stats) * size_t(nb), cudaMemcpyHostToDevice, h->hs) != cudaSuccess ||
         cudaMemsetAsync(h->gn_loops, 0, sizeof(int32_t), h->hs) != cudaSuccess ||
@@ -2053,7 +2069,8 @@ bool gn_run(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, std::vector
     cudaMemcpyAsync(&loops, h->gn_loops, sizeof(int32_t), cudaMemcpyDeviceToHost, h->hs);
     if (cudaStreamSynchronize(h->hs) != cudaSuccess) return true;   // the caller's next CUDA call reports it
     for (int b = 0; b < nb; ++b) {
-        rn[b] = G[b].rn; rprev[b] = G[b].rprev; eta[b] = G[b].eta;
+        rn[b] = G[b].rn; rprev[b] = G[b].rprev; eta[b] = G[b].eta; rbefore[b] = G[b].rbefore;
+        resume64[b] = G[b].host != 0;
         st[b] = S[b].status;
     }
     *launches += int64_t(loops) * h->gn_nodes;
@@ -2079,7 +2096,7 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
     std::vector<egfem_stats> S(nb);
     for (auto &x : S) std::memset(&x, 0, sizeof(x));
     std::vector<double> rn(nb), rprev(nb), rbefore(nb), target(nb), eta(nb, h->opts.eta_max), lam(nb, 1.0);
-    std::vector<int> active(nb, 0), fp32(nb, 0), pending(nb, 0);
+    std::vector<int> active(nb, 0), fp32(nb, 0), pending(nb, 0), resume64(nb, 0);
     std::vector<int32_t> st(nb, EGFEM_OK);
     int64_t launches = 0;
     // evaluate residual/operator for instances with mask m
@@ -2116,10 +2133,10 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         target[b] = std::max(h->opts.newton_rtol * rn[b], h->opts.newton_atol);
         rprev[b] = rn[b];
     }
-    // the Newton loop on the device (full steps); the host loop below finishes what it hands back
+    // the Newton loop on the device (damping included); the host loop below finishes what it hands back
     h->gn_used = false;
-    const bool ran = mixed ? gn_run<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, st, S, &launches)
-                           : gn_run<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, st, S, &launches);
+    const bool ran = mixed ? gn_run<df64>(h, h->k32, d_u, d_d, rn, rprev, eta, target, st, S, rbefore, resume64, &launches)
+                           : gn_run<double>(h, h->k64, d_u, d_d, rn, rprev, eta, target, st, S, rbefore, resume64, &launches);
     if (!ran && h->opts.newton_graph == 2) {
         g_last_error = "graph Newton loop required (newton_graph = 2) but unavailable: " + g_last_error;
         return EGFEM_ERR_UNSUPPORTED;
@@ -2144,6 +2161,11 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
             if (S[b].newton_iters >= h->opts.newton_maxit) { st[b] = EGFEM_ERR_NOT_CONVERGED; continue; }
             active[b] = 1;
             any = true;
+            if (resume64[b]) {   // the graph's step, handed back for its FP64 redo
+                fp32[b] = 0;
+                resume64[b] = 0;
+                continue;
+            }
             if (S[b].newton_iters > 0 && !h->opts.fixed_eta) {
                 double e = 0.9 * (rn[b] / rprev[b]) * (rn[b] / rprev[b]);
                 const double sg = 0.9 * eta[b] * eta[b];
@@ -2174,7 +2196,7 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
                 const KState &K = h->h_bst[b];
                 S[b].krylov_iters += K.iter;
                 if (S[b].newton_iters < EGFEM_HIST) S[b].krylov_hist[S[b].newton_iters] += K.iter;
-                const bool failed = K.done == K_NONFINITE || K.done == K_BREAKDOWN;
+                const bool failed = K.done == K_NONFINITE || (K.done == K_BREAKDOWN && (p32 || K.iter == 0));
                 if (failed) {
                     if (p32) { fp32[b] = 0; ++S[b].fp64_rescues; }
                     else { st[b] = K.done == K_NONFINITE ? EGFEM_ERR_NONFINITE : EGFEM_ERR_BREAKDOWN; active[b] = 0; }

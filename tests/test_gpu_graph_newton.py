@@ -1,8 +1,9 @@
-"""GPU checks of the graph-resident batched Newton loop (a conditional WHILE node in one CUDA
-graph; option newton_graph): with the graph required (newton_graph = 2) every instance's
-solution equals the oracle's and the host loop's, with the same Newton step counts; a second
-call reuses the graph; Picard runs in it too; and instances whose full step fails the decrease
-test are handed back to the host loop and still converge."""
+"""GPU checks of the graph-resident Newton loop (a conditional WHILE node in one CUDA graph;
+option newton_graph), batched and for one system: with the graph required (newton_graph = 2)
+every solution equals the oracle's and the host loop's, with the same Newton step counts (for
+one system the same Krylov counts step by step); a second call reuses the graph; Picard runs in
+it too; and steps that fail the sufficient-decrease test are halved inside the graph exactly as
+the host loop halves them."""
 import numpy as np
 import pytest
 
@@ -63,6 +64,8 @@ def test_graph_newton_matches_host_loop_and_oracle(P, batch, prec):
         assert sg[b].status == 0 and sh[b].status == 0, b
         assert rel(x, ref) <= tol and rel(y, ref) <= tol, b
         assert sg[b].newton_iters == sh[b].newton_iters, b
+        for s_ in (sg[b], sh[b]):   # every Krylov iteration is counted once, in its step
+            assert s_.krylov_iters == sum(s_.krylov_hist[:s_.newton_iters]), b
     # a second call with the same tensors runs the captured graph again
     ug.zero_()
     sg2 = hg.batch_newton_solve(ug, dg)
@@ -81,10 +84,11 @@ def test_graph_picard_matches_oracle(P, batch):
         assert rel(x, ref) <= 1e-10, b
 
 
-def test_graph_hands_back_steps_that_need_damping(P):
-    """Minimal surface from the boundary data (full Newton steps overshoot there): the graph
-    hands those instances back, the host loop shortens their steps, and every instance reaches
-    the oracle's discrete solution."""
+@pytest.mark.parametrize("graph", [2, 0])
+def test_batched_steps_that_need_damping(P, graph):
+    """Minimal surface from the boundary data (full Newton steps overshoot there): the step
+    halving (in the graph, or in the host loop) brings every instance to the oracle's discrete
+    solution."""
     meshes = [wl.unit_square_mesh(n) for n in (24, 32)]
     loads, refs, starts = [], [], []
     for mesh in meshes:
@@ -98,7 +102,7 @@ def test_graph_hands_back_steps_that_need_damping(P):
         refs.append(u_ref)
         starts.append(uD)
     h = P.BatchHandle(meshes, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
-                      P.default_options(op=P.OP_MATRIX_FREE, newton_graph=2, newton_rtol=1e-12))
+                      P.default_options(op=P.OP_MATRIX_FREE, newton_graph=graph, newton_rtol=1e-12))
     d = h.scatter(loads)
     u = h.scatter(starts)
     st = h.batch_newton_solve(u, d)
@@ -106,12 +110,16 @@ def test_graph_hands_back_steps_that_need_damping(P):
     for b, (x, ref) in enumerate(zip(h.gather(u, [m.n_nodes for m in meshes]), refs)):
         assert st[b].status == 0, b
         assert rel(x, ref) <= 1e-10, b
+        assert st[b].krylov_iters == sum(st[b].krylov_hist[:st[b].newton_iters]), b
 
 
 @pytest.mark.parametrize("prec,cluster", [("fp64", 0), ("fp64", -1), ("mixed", 0), ("mixed", -1)])
 def test_single_system_graph_newton_matches_host_loop(P, prec, cluster):
-    """egfem_newton_solve with the graph loop required equals the host loop (same Newton steps)
-    and the oracle, for the cluster and the grid-wide BiCGStab and both precisions."""
+    """egfem_newton_solve with the graph loop required equals the host loop (the same Newton
+    steps with the same Krylov counts and residual norms: both run the same kernels) and the
+    oracle, for the cluster and the grid-wide BiCGStab and both precisions.  From u = 0 the
+    first full step of this problem fails the sufficient-decrease test, so the halving runs
+    too."""
     mesh = wl.unit_square_mesh(40)
     orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
     b = orc.load_vector(wl.mms_source) * (1 - mesh.dirichlet)
@@ -129,16 +137,25 @@ def test_single_system_graph_newton_matches_host_loop(P, prec, cluster):
         st2 = h.newton_solve(u2, d) if graph == 2 else st   # a second call reuses the captured graph
         torch.cuda.synchronize()
         assert st.status == 0 and st2.status == 0
-        out.append((u.cpu().numpy(), st.newton_iters))
+        out.append((u.cpu().numpy(), st))
+        assert st.krylov_iters == sum(st.krylov_hist[:st.newton_iters])
         if graph == 2:
             assert np.array_equal(u.cpu().numpy(), u2.cpu().numpy())
         h.close()
     tol = 1e-8 if mixed else 1e-11
     assert rel(out[0][0], u_ref) <= tol and rel(out[1][0], u_ref) <= tol
-    assert out[0][1] == out[1][1]
+    sg, sh = out[0][1], out[1][1]
+    k = sg.newton_iters
+    assert k == sh.newton_iters and sg.krylov_iters == sh.krylov_iters
+    assert list(sg.krylov_hist[:k]) == list(sh.krylov_hist[:k])
+    assert np.allclose(sg.res_hist[:k], sh.res_hist[:k], rtol=1e-12, atol=0.0)
+    assert sg.fp64_rescues == sh.fp64_rescues
 
 
-def test_single_system_graph_hands_back_damped_steps(P):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_system_graph_damped_steps_match_host_loop(P, prec):
+    """Minimal surface from the boundary data: the graph's halvings reproduce the host loop's
+    iteration step by step, and both reach the oracle's discrete solution."""
     mesh = wl.unit_square_mesh(32)
     orc = oracle.Problem(mesh, a=("gradpow", -0.5, 1.0), a_deg=0, kappa=0.0)
     x, y = mesh.coords[:, 0], mesh.coords[:, 1]
@@ -146,10 +163,19 @@ def test_single_system_graph_hands_back_damped_steps(P):
     uD = ue * mesh.dirichlet
     b = orc.load_vector(wl.minsurf_source) * (1 - mesh.dirichlet)
     u_ref, _, _, _ = orc.newton(b, u0=ue + 0.2 * np.sin(np.pi * x) * np.sin(np.pi * y), uD=uD, rtol=1e-12)
-    h = P.Handle(mesh, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
-                 P.default_options(op=P.OP_MATRIX_FREE, newton_graph=2, newton_rtol=1e-12))
-    u = torch.tensor(uD, device="cuda", dtype=torch.float64)
-    st = h.newton_solve(u, torch.tensor(b + uD, device="cuda", dtype=torch.float64))
-    torch.cuda.synchronize()
-    assert st.status == 0
-    assert rel(u.cpu().numpy(), u_ref) <= 1e-10
+    mixed = prec == "mixed"
+    res = []
+    for graph in (2, 0):
+        h = P.Handle(mesh, P.make_problem(a=("gradpow", -0.5, 1.0), a_degree=0, kappa=0.0),
+                     P.default_options(op=P.OP_MATRIX_FREE, newton_graph=graph, newton_rtol=1e-10 if mixed else 1e-12,
+                                       precision=P.PREC_MIXED if mixed else P.PREC_FP64))
+        u = torch.tensor(uD, device="cuda", dtype=torch.float64)
+        st = h.newton_solve(u, torch.tensor(b + uD, device="cuda", dtype=torch.float64))
+        torch.cuda.synchronize()
+        assert st.status == 0
+        assert rel(u.cpu().numpy(), u_ref) <= (1e-8 if mixed else 1e-10)
+        assert st.krylov_iters == sum(st.krylov_hist[:st.newton_iters])
+        res.append(st)
+        h.close()
+    k = res[0].newton_iters
+    assert k == res[1].newton_iters and list(res[0].krylov_hist[:k]) == list(res[1].krylov_hist[:k])
