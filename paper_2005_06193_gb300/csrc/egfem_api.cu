@@ -394,8 +394,11 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     if (h->coop) {
         // every block of a cooperative launch must be resident: at most occupancy x SMs; each
         // block owns one contiguous, slice-aligned tile of rows
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) == cudaSuccess && nb >= 1) {
+        int nb = 0, nb1 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, (const void *)pk_solve1<V>, PK_BLOCK, 0) == cudaSuccess &&
+            std::min(nb, nb1) >= 1) {
+            nb = std::min(nb, nb1);   // the same grid serves both kernels
             const int64_t min_rows = (int64_t(h->opts.krylov_block_rows > 0 ? h->opts.krylov_block_rows : kPkBlockRows) +
                                       SLICE - 1) / SLICE * SLICE;
             const int64_t g = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::min(nb, 8)) * h->sms, h->n_pad / min_rows));
@@ -483,11 +486,30 @@ egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, in
     return EGFEM_OK;
 }
 
+// One system in one cooperative launch of pk_solve1 (one tile per block; every block keeps the
+// solver state); active and rtol_ptr as for launch_pk with one system.
+template <typename V>
+egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall, const uint8_t *active = nullptr,
+                        const double *rtol_ptr = nullptr) {
+    PkArgs<V> P{};
+    P.K = kvecs(h, W);
+    P.tiles = W.pk_tiles; P.ntiles = W.pk_ntiles; P.sys_t0 = W.pk_sys_t0; P.nsys = 1; P.st = h->st; P.sc = W.pk_sc;
+    P.part = W.pk_part; P.active = active; P.rtol = rtol_ptr; P.rtol0 = rtol; P.bar = W.bar; P.maxit = maxit; P.stall = stall;
+    if (W.pk_ntiles < 1)   // no rows: the general kernel (its blocks find no tile)
+        return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, active, rtol_ptr,
+                         rtol, W.bar, maxit, stall);
+    void *args[] = {(void *)&P};
+    EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
+    // one block per tile (at most the resident grid W.g_pk)
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solve1<V>, dim3(unsigned(W.pk_ntiles)), dim3(PK_BLOCK), args, 0,
+                                        h->hs));
+    return EGFEM_OK;
+}
+
 template <typename V>
 egfem_status launch_pk_single(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int32_t stall) {
     if (W.pkc_cluster > 0) return launch_pkc<V>(h, W, rtol, maxit, stall);
-    return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, nullptr, nullptr, rtol,
-                     W.bar, maxit, stall);
+    return launch_pk1<V>(h, W, rtol, maxit, stall);
 }
 
 // Run BiCGStab on W.A x = W.b (already filled) on the internal stream; returns the
@@ -907,6 +929,7 @@ egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_
     GNArgs G{};
     G.nb = 1; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
     G.lam = h->inst_lam; G.kst = h->st; G.norm2 = h->scal; G.loops = h->gn_loops;
+    G.kerr = W.pkc_cluster > 0 ? nullptr : &W.bar->err;
     G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
     G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
     G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
@@ -916,8 +939,7 @@ egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_
     egfem_status st = EGFEM_OK;
     gn_pre<<<1, 32, 0, h->hs>>>(G);
     if (W.pkc_cluster > 0) st = launch_pkc<V>(h, W, 0.0, h->opts.krylov_maxit, stall, h->inst_mask, h->inst_eta);
-    else st = launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, h->inst_mask,
-                        h->inst_eta, 0.0, W.bar, h->opts.krylov_maxit, stall);
+    else st = launch_pk1<V>(h, W, 0.0, h->opts.krylov_maxit, stall, h->inst_mask, h->inst_eta);
     gn_mid<<<1, 32, 0, h->hs>>>(G);
     gn_update_one<V><<<gu, 256, 0, h->hs>>>(h->n, h->inst_mask, h->inst_lam, d_u, W.x);
     CsfArgs A = csf_args(h, d_u, d_d);
@@ -2003,6 +2025,7 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
     GNArgs G{};
     G.nb = h->nb; G.state = h->gn_state; G.stats = h->gn_stats; G.mask = h->inst_mask; G.eta_out = h->inst_eta;
     G.lam = h->inst_lam; G.kst = h->bst; G.norm2 = h->inst_norm2; G.loops = h->gn_loops;
+    G.kerr = &h->bbar->err;
     G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
     G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
     G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;

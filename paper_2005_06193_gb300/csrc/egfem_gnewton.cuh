@@ -16,6 +16,7 @@
 
 #include "egfem_kernels.cuh"
 #include "egfem_krylov.cuh"
+#include "egfem_persist.cuh"
 
 namespace egfem {
 
@@ -42,6 +43,7 @@ struct GNArgs {
     double *lam;                 // increment factor per instance: u -= lam x
     const KState *kst;           // final Krylov state per instance
     const double *norm2;         // ||r||^2 per instance after the tensor action
+    const int32_t *kerr;         // nonzero: a grid-barrier wait of the persistent solve ran out (nullable)
     int32_t *loops;              // body executions so far
     int32_t max_loops;
     int32_t newton_maxit, fixed_eta, mixed;
@@ -113,6 +115,11 @@ __global__ void gn_mid(GNArgs G) {
             continue;
         }
         const KState &K = G.kst[b];
+        if (K.done == K_TIMEOUT || (G.kerr && *G.kerr)) {
+            T.status = EGFEM_ERR_TIMEOUT;
+            G.mask[b] = 0;
+            continue;
+        }
         T.krylov_iters += K.iter;
         if (T.newton_iters < EGFEM_HIST) T.krylov_hist[T.newton_iters] += K.iter;
         if (K.done == K_NONFINITE || (K.done == K_BREAKDOWN && (G.mixed || K.iter == 0))) {

@@ -628,6 +628,216 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve(PkArgs<V> P)
 #undef PK_TILES
 #undef PK_ROWS
 
+// ---------------------------------------------------------------------------------
+// One system: every block keeps the solver state
+// ---------------------------------------------------------------------------------
+
+// Grid-wide barrier on an arrival counter that only grows within a launch: the k-th barrier
+// completes when the counter reaches k x gridDim.x.  No block is singled out, so a barrier is
+// one arrival atomic and one wait (two L2 round trips) instead of the arrival, the last
+// block's release and the waiters' reads.  false when the wait ran out or another block gave up.
+__device__ __forceinline__ bool pk1_sync(PGrid *g, uint32_t &nbar, unsigned long long limit_ns = PK_WAIT_NS) {
+    __shared__ int s_ok;
+    ++nbar;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t target = nbar * gridDim.x;
+        int ok = 1;
+        if (atom_add_acq_rel_gpu(&g->count, 1u) + 1u < target) {
+            const unsigned long long t0 = pk_clock_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_gpu(&g->count) < target) {
+                if (ld_relaxed_gpu(&g->err)) { ok = 0; break; }
+                if ((++spins & 255u) == 0u && pk_clock_ns() - t0 > limit_ns) {
+                    atomicExch(&g->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sums of NV dot products over the grid, the same in every block: the block's partials go to
+// part[k * G + block], and after the barrier every block adds all G partials in one fixed order
+// (threads over partials, warp sums, then the warps in order -- the order of the batched
+// kernel's last-block sum for one system, so both kernels compute the same iterates).
+template <typename V, int NV>
+__device__ __forceinline__ bool pk1_allreduce(const PkArgs<V> &P, const DotAcc<V> (&acc)[NV], uint32_t &nbar,
+                                              double (&tot)[NV]) {
+    __shared__ double s_w[2][PK_BLOCK / 32];
+    const int64_t G = gridDim.x;
+    pk_tile_partial<V, NV>(acc, P.part, G, blockIdx.x);
+    if (!pk1_sync(P.bar, nbar)) return false;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = 0.0;
+        for (int64_t q = threadIdx.x; q < G; q += PK_BLOCK) x += __ldcg(P.part + k * G + q);
+        x = warp_sum(x);
+        if (lane == 0) s_w[k][w] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = s_w[k][0];
+        for (int q = 1; q < PK_BLOCK / 32; ++q) x += s_w[k][q];
+        tot[k] = x;
+    }
+    return true;
+}
+
+#define PK1_ROWS \
+    _Pragma("unroll 1") for (int64_t r0 = T.r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < T.r_end; r0 += int64_t(PK_BLOCK) * VecT<V>::R)
+
+// The solve of one system, one tile per block (P.ntiles == gridDim.x): the phases, their
+// arithmetic and their order are pk_solve's, but every block computes the scalars itself from
+// all partials and keeps the state in shared memory, so the iteration needs no last block, no
+// published scalars and no state in global memory.  Block 0 writes the final state to P.st
+// (done = K_TIMEOUT when a barrier wait ran out; P.bar->err is then set too).  An inactive
+// system (P.active[0] == 0) returns at once.
+template <typename V>
+__global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P) {
+    using Op = PkOps<V>;
+    constexpr int R = VecT<V>::R;
+    __shared__ KState S;
+    if (P.active && !P.active[0]) return;
+    const KVecs<V> &K = P.K;
+    __shared__ BTile T;   // the block's rows (in shared memory: fewer live registers in the phases)
+    if (threadIdx.x == 0) T = P.tiles[blockIdx.x];
+    __syncthreads();
+    uint32_t nbar = 0;
+    bool ok;
+    {
+        // setup: x = v = 0, r = rh = p = b, (b, b)
+        Pack<V> z;
+#pragma unroll
+        for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
+        DotAcc<V> acc[1];
+        PK1_ROWS {
+            const Pack<V> b = ldv(K.b + r0);
+            stv(K.x + r0, z); stv(K.v + r0, z);
+            stv(K.r + r0, b); stv(K.rh + r0, b); stv(K.p + r0, b);
+#pragma unroll
+            for (int j = 0; j < R; ++j) acc[0].add(b.v[j], b.v[j]);
+        }
+        double tot[1];
+        ok = pk1_allreduce<V, 1>(P, acc, nbar, tot);
+        if (threadIdx.x == 0) {
+            const double x = ok ? tot[0] : 0.0, rt = P.rtol ? P.rtol[0] : P.rtol0;
+            S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
+            S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+            S.rho = S.rr = S.rr0 = S.best_rr = x;
+            S.tol2 = rt * rt * x;
+            S.stall_rr = 4e-6 * x;
+            S.done = (x == 0.0) ? K_CONVERGED : (!isfinite(x) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
+        }
+        __syncthreads();
+    }
+
+    while (ok && S.done == K_RUNNING) {
+        // A: v = A p, (rh, v)
+        {
+            DotAcc<V> acc[1];
+            PK1_ROWS {
+                const Pack<V> p = ldcv(K.p + r0);
+                const Pack<V> y = pk_spmv(K, r0, K.p, p);
+                stv(K.v + r0, y);
+                const Pack<V> rh = ldcv(K.rh + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) acc[0].add(rh.v[j], y.v[j]);
+            }
+            double tot[1];
+            if (!(ok = pk1_allreduce<V, 1>(P, acc, nbar, tot))) break;
+            if (threadIdx.x == 0) {
+                if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
+                else S.alpha = S.rho / tot[0];
+            }
+            __syncthreads();
+            if (S.done != K_RUNNING) break;
+        }
+
+        // B1: s = r - alpha v
+        const V al = cvt<V>(S.alpha);
+        PK1_ROWS {
+            const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
+            Pack<V> s;
+#pragma unroll
+            for (int j = 0; j < R; ++j) s.v[j] = Op::sub(r.v[j], al * v.v[j]);
+            stv(K.s + r0, s);
+        }
+        if (!(ok = pk1_sync(P.bar, nbar))) break;
+
+        // B2: t = A s, (t, s), (t, t)
+        {
+            DotAcc<V> acc[2];
+            PK1_ROWS {
+                const Pack<V> s = ldcv(K.s + r0);
+                const Pack<V> y = pk_spmv(K, r0, K.s, s);
+                stv(K.t + r0, y);
+#pragma unroll
+                for (int j = 0; j < R; ++j) { acc[0].add(y.v[j], s.v[j]); acc[1].add(y.v[j], y.v[j]); }
+            }
+            double tot[2];
+            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, tot))) break;
+            if (threadIdx.x == 0) {
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
+                else S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+            }
+            __syncthreads();
+            if (S.done != K_RUNNING) break;
+        }
+
+        // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
+        {
+            const V om = cvt<V>(S.omega);
+            DotAcc<V> acc[2];
+            PK1_ROWS {
+                const Pack<V> s = ldcv(K.s + r0), p = ldcv(K.p + r0), tv = ldcv(K.t + r0), rh = ldcv(K.rh + r0);
+                Pack<V> x = ldcv(K.x + r0), r;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    x.v[j] = Op::add(x.v[j], Op::add(al * p.v[j], om * s.v[j]));
+                    r.v[j] = Op::sub(s.v[j], om * tv.v[j]);
+                    acc[0].add(rh.v[j], r.v[j]);
+                    acc[1].add(r.v[j], r.v[j]);
+                }
+                stv(K.x + r0, x);
+                stv(K.r + r0, r);
+            }
+            double tot[2];
+            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, tot))) break;
+            if (threadIdx.x == 0) pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
+            __syncthreads();
+            if (S.done != K_RUNNING) break;
+        }
+
+        // D: p = r + beta (p - omega v)
+        {
+            const V be = cvt<V>(S.beta), om = cvt<V>(S.omega);
+            PK1_ROWS {
+                const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
+                Pack<V> p = ldcv(K.p + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) p.v[j] = Op::add(r.v[j], be * Op::sub(p.v[j], om * v.v[j]));
+                stv(K.p + r0, p);
+            }
+        }
+        if (!(ok = pk1_sync(P.bar, nbar))) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        KState F = S;
+        if (!ok) F.done = K_TIMEOUT;
+        *P.st = F;
+    }
+}
+
+#undef PK1_ROWS
+
 // Self-test of the barrier's bounded wait: blocks with index >= arrive leave without
 // arriving, so with arrive < gridDim.x the barrier cannot complete and the waiting blocks
 // must give up after limit_ns.  ok[b] = 1 when block b passed the barrier, 0 when it gave up,
