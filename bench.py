@@ -38,10 +38,10 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 SMS = 152                 # GB300 streaming multiprocessors
 DFMA_PER_SM_CLK = 2       # FP64 FMAs per SM per clock on GB300 (nominal 1.25 TFLOP/s FP64)
-# DRAM bytes (read + write) per launch (per iteration for the persistent solve) from ncu
-# captures of the current kernels; the captures and their commands are summarised in
-# profiles/pk_solve_fp64_1024x1024_ncu.md.  Valid for the FP64 1024 x 1024 workload only.
-NCU_TRAFFIC = {"kry_persistent": 144.8e6}
+# DRAM bytes (read + write) per launch (per iteration for the persistent solve, pk_solve1) from
+# ncu captures of the current kernels; the captures and their commands are summarised in
+# profiles/pk_solve1_fp64_1024x1024_ncu.md.  Valid for the FP64 1024 x 1024 workload only.
+NCU_TRAFFIC = {"kry_persistent": 149.0e6}
 
 
 def load_peaks():
@@ -484,15 +484,31 @@ def next_row_extra(torch, P, dev, n, steps, barrier, setup, workload, hbm, fp64_
     return out
 
 
-def timed_solves(torch, h, d, u, steps, rank_barrier):
+def perturbed_loads(d, count):
+    """count copies of the load vector d scaled by 1 + k 2^-44 (k = 0 .. count-1): the same
+    workload to about 13 digits.  The BiCGStab iteration count of a solve moves by up to about
+    20 % under such perturbations (rounding decides when the erratic residual history crosses
+    its tolerance), so each timed step solves its own copy and the rate reflects the mean count
+    rather than one draw."""
+    return [d * (1.0 + k * 2.0 ** -44) for k in range(count)]
+
+
+def mean_iters(stats):
+    k = [int(s.krylov_iters) for s in stats]
+    return {"krylov_iters": round(sum(k) / len(k), 1), "krylov_iters_range": [min(k), max(k)],
+            "newton_iters": round(sum(s.newton_iters for s in stats) / len(stats), 2)}
+
+
+def timed_solves(torch, h, ds, u, steps, rank_barrier):
+    """steps Newton solves from u = 0, step i on the load vector ds[i % len(ds)]"""
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
     rank_barrier()
     torch.cuda.synchronize()
     ev0.record()
-    for _ in range(steps):
+    for i in range(steps):
         u.zero_()
-        stats.append(h.newton_solve(u, d))
+        stats.append(h.newton_solve(u, ds[i % len(ds)]))
     ev1.record()
     torch.cuda.synchronize()
     rank_barrier()
@@ -562,18 +578,21 @@ def main():
         print(json.dumps(hp.profile_kernels(u, d, reps=1)), flush=True)
         hp.close()
         return
-    h = P.Handle(mesh, prob, P.default_options())
+    # the host Newton loop (newton_graph = 0): at this size it is as fast as the graph-resident
+    # loop (timed below), and ncu sees every kernel of it (not those inside a conditional node)
+    h = P.Handle(mesh, prob, P.default_options(newton_graph=0))
     dev = torch.device("cuda", local)
     f = torch.tensor(f_cell, device=dev, dtype=torch.float64)
     d = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
     h.load_cellwise(f, d)
+    ds = perturbed_loads(d, args.steps)
     u = torch.zeros(mesh.n_nodes, device=dev, dtype=torch.float64)
-    for _ in range(args.warmup):
+    for i in range(args.warmup):
         u.zero_()
-        h.newton_solve(u, d)
+        h.newton_solve(u, ds[i % len(ds)])
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms, stats = timed_solves(torch, h, d, u, args.steps, barrier)
+        ms, stats = timed_solves(torch, h, ds, u, args.steps, barrier)
     clocks = clk.summary()
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if world > 1:
@@ -581,18 +600,19 @@ def main():
     ms_max = float(t.item())
     value = world * args.steps / (ms_max / 1e3)
     st = stats[-1]
+    its = mean_iters(stats)
     launches = int(sum(s.kernel_launches for s in stats))
 
     # end to end through the public API with host buffers
-    d_host = d.cpu().pin_memory()
+    d_hosts = [x.cpu().pin_memory() for x in ds]
     u_host = torch.empty(mesh.n_nodes, dtype=torch.float64).pin_memory()
     d_dev = torch.empty_like(d)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        d_dev.copy_(d_host, non_blocking=True)
+    for i in range(args.steps):
+        d_dev.copy_(d_hosts[i % len(d_hosts)], non_blocking=True)
         u.zero_()
         h.newton_solve(u, d_dev)
         u_host.copy_(u, non_blocking=True)
@@ -609,9 +629,9 @@ def main():
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     fp64_peak = fp64_peak_tflops(peaks)
-    counts = {"csf_fused": st.newton_iters + 1}
+    counts = {"csf_fused": its["newton_iters"] + 1}
     for k in ("kry_v", "kry_s", "kry_t", "kry_x", "kry_p", "kry_persistent", "kry_cluster"):
-        counts[k] = int(st.krylov_iters)
+        counts[k] = its["krylov_iters"]
     share = {p["name"]: p["ms"] * counts.get(p["name"], 0) for p in prof}
     total_share = sum(share.values())
     dom = max(prof, key=lambda p: share[p["name"]])
@@ -632,9 +652,9 @@ def main():
     hg = P.Handle(mesh, prob, P.default_options(krylov_persistent=0))
     u.zero_()
     hg.newton_solve(u, d)
-    msg, sg = timed_solves(torch, hg, d, u, min(args.steps, 3), barrier)
+    msg, sg = timed_solves(torch, hg, ds, u, min(args.steps, 3), barrier)
     graph_driver = {"value": world * min(args.steps, 3) / (msg / 1e3), "unit": "solves/s",
-                    "ms_per_step": msg / min(args.steps, 3), "krylov_iters": int(sg[-1].krylov_iters),
+                    "ms_per_step": msg / min(args.steps, 3), **mean_iters(sg),
                     "gpu_launches_per_solve": int(sg[-1].kernel_launches)}
     hg.close()
 
@@ -644,8 +664,11 @@ def main():
            "config": {"workload": f"egfem_newton_2d_p1p2_u2_{args.n}x{args.n}", "grid": args.n, "n_p1": mesh.n_nodes,
                       "n_p2": h.sizes.n_wa, "newton_rtol": 1e-10, "precision": "fp64", "operator": "csf",
                       "parallelism": "replicas" if world > 1 else "single", "l2": "inputs larger than L2 (no flush)",
-                      "krylov_driver": "persistent" if h.options.krylov_persistent else "graph"},
-           "newton_iters": st.newton_iters, "krylov_iters": int(st.krylov_iters),
+                      "krylov_driver": "persistent" if h.options.krylov_persistent else "graph",
+                      "newton_loop": "host",
+                      "rhs": "step k solves with the load vector scaled by 1 + k 2^-44 (the iteration count's "
+                             "sensitivity to rounding averaged over the steps)"},
+           **its,
            "final_rel_residual": st.res_final / st.res0,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * mesh.n_nodes,
                    "d2h_bytes_per_step": 8 * mesh.n_nodes},
@@ -653,18 +676,27 @@ def main():
            "kernels": [{**p, "share": share[p["name"]] / total_share} for p in prof],
            "fp64_graph_driver": graph_driver}
 
+    # the same FP64 solve with the graph-resident Newton loop (the library's default)
+    hgl = P.Handle(mesh, prob, P.default_options())
+    u.zero_()
+    hgl.newton_solve(u, d)
+    msl, sgl = timed_solves(torch, hgl, ds, u, args.steps, barrier)
+    out["graph_newton_loop"] = {"value": world * args.steps / (msl / 1e3), "unit": "solves/s",
+                                "ms_per_step": msl / args.steps, **mean_iters(sgl),
+                                "gpu_launches_per_solve": int(sgl[-1].kernel_launches)}
+    hgl.close()
+
     if not args.no_mixed:
-        hm = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED))
-        for _ in range(max(1, args.warmup)):
+        hm = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED, newton_graph=0))
+        for i in range(max(1, args.warmup)):
             u.zero_()
-            hm.newton_solve(u, d)
-        msm, sm = timed_solves(torch, hm, d, u, args.steps, barrier)
+            hm.newton_solve(u, ds[i % len(ds)])
+        msm, sm = timed_solves(torch, hm, ds, u, args.steps, barrier)
         sl = sm[-1]
         mprof = hm.profile_kernels(u, d, reps=20)
         out["mixed"] = {"value": world * args.steps / (msm / 1e3), "unit": "solves/s", "ms_per_step": msm / args.steps,
-                        "newton_iters": sl.newton_iters, "krylov_iters": int(sl.krylov_iters),
-                        "final_rel_residual": sl.res_final / sl.res0, "speedup_vs_fp64": (ms_max / msm),
-                        "fp64_rescues": sl.fp64_rescues,
+                        **mean_iters(sm), "final_rel_residual": sl.res_final / sl.res0,
+                        "speedup_vs_fp64": (ms_max / msm), "fp64_rescues": int(sum(x.fp64_rescues for x in sm)),
                         "kernels": [{"name": p["name"], "ms": p["ms"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9,
                                      "frac_hbm": p["bytes"] / (p["ms"] / 1e3) / 1e9 / hbm} for p in mprof]}
         out["mixed"]["gpu_launches"] = int(sum(s.kernel_launches for s in sm))
@@ -682,7 +714,7 @@ def main():
         hpi = P.Handle(mesh, prob, P.default_options(iteration=P.ITER_PICARD, newton_maxit=200))
         u.zero_()
         hpi.newton_solve(u, d)
-        msp, spi = timed_solves(torch, hpi, d, u, min(args.steps, 2), barrier)
+        msp, spi = timed_solves(torch, hpi, ds, u, min(args.steps, 2), barrier)
         sl = spi[-1]
         out["picard"] = {"value": world * min(args.steps, 2) / (msp / 1e3), "unit": "solves/s",
                          "ms_per_step": msp / min(args.steps, 2), "picard_iters": sl.newton_iters,
@@ -715,7 +747,7 @@ def main():
         out["batched_p3"] = batched_p3_extra(torch, P, dev, args.p3_instances, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_solve, cpu_s, sample = oracle_sample(args.n, st.newton_iters, int(st.krylov_iters))
+        per_solve, cpu_s, sample = oracle_sample(args.n, int(round(its["newton_iters"])), int(round(its["krylov_iters"])))
         out["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                "sample": sample, "sample_cpu_seconds": cpu_s}
     if rank == 0:

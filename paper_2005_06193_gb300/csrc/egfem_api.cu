@@ -62,12 +62,11 @@ struct KWork {
     typename VecT<V>::mat *A = nullptr;   // Jacobi-scaled operator (SELL layout)
     V *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     V *p2 = nullptr, *v2 = nullptr;       // second p / v buffers of the fused double-float iteration
-    // persistent solve (pk_solve): one tile of rows per block
+    // persistent solve (pk_solve1): one tile of rows per block
     int g_pk = 0;                         // blocks (0: not available)
     BTile *pk_tiles = nullptr;
     int64_t pk_ntiles = 0;
     int64_t *pk_sys_t0 = nullptr;         // [1] = {0}
-    PkScal<V> *pk_sc = nullptr;           // [1]
     double *pk_part = nullptr;            // [2 * pk_ntiles]
     PGrid *bar = nullptr;
     // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
@@ -153,7 +152,6 @@ struct egfem_t {
     PGrid *bbar = nullptr;              // grid barrier of the persistent batched solve
     int64_t *bsys_t0 = nullptr;         // first tile of each instance
     double *bpart2 = nullptr;           // tile partials of the persistent batched solve
-    void *bsc = nullptr;                // PkScal<V> per instance (room for the larger V)
     int bgraph_chunk = 0, bgraph_tiles = 0;
     // graph-resident batched Newton loop (egfem_gnewton.cuh): device state, the instantiated
     // graph and the vectors and path it was captured for
@@ -395,7 +393,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
         // every block of a cooperative launch must be resident: at most occupancy x SMs; each
         // block owns one contiguous, slice-aligned tile of rows
         int nb = 0, nb1 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PK_BLOCK, 0) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, (const void *)pk_solve1<V>, PK_BLOCK, 0) == cudaSuccess &&
             std::min(nb, nb1) >= 1) {
             nb = std::min(nb, nb1);   // the same grid serves both kernels
@@ -410,7 +408,6 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
             W.pk_ntiles = int64_t(T.size());
             EG_TRY(upload(W.pk_tiles, T));
             EG_TRY(upload(W.pk_sys_t0, std::vector<int64_t>(1, 0)));
-            EG_TRY(dalloc(W.pk_sc, 1));
             EG_TRY(dalloc(W.pk_part, size_t(2 * W.pk_ntiles)));
             EG_TRY(dalloc(W.bar, 1));
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
@@ -471,18 +468,18 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
     return EGFEM_OK;
 }
 
-// Cooperative launch of pk_solve over the given tiles and systems.
+// Cooperative launch of pk_solveb over the given tiles and systems.
 template <typename V>
 egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, int64_t ntiles, const int64_t *sys_t0,
-                       int32_t nsys, KState *st, PkScal<V> *sc, double *part, const uint8_t *active, const double *rtol,
+                       int32_t nsys, KState *st, double *part, const uint8_t *active, const double *rtol,
                        double rtol0, PGrid *bar, int32_t maxit, int32_t stall) {
     PkArgs<V> P{};
     P.K = kvecs(h, W);
-    P.tiles = tiles; P.ntiles = ntiles; P.sys_t0 = sys_t0; P.nsys = nsys; P.st = st; P.sc = sc; P.part = part;
+    P.tiles = tiles; P.ntiles = ntiles; P.sys_t0 = sys_t0; P.nsys = nsys; P.st = st; P.part = part;
     P.active = active; P.rtol = rtol; P.rtol0 = rtol0; P.bar = bar; P.maxit = maxit; P.stall = stall;
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(bar, 0, sizeof(PGrid), h->hs));
-    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solve<V>, dim3(grid), dim3(PK_BLOCK), args, 0, h->hs));
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solveb<V>, dim3(grid), dim3(PK_BLOCK), args, 0, h->hs));
     return EGFEM_OK;
 }
 
@@ -493,10 +490,10 @@ egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
                         const double *rtol_ptr = nullptr) {
     PkArgs<V> P{};
     P.K = kvecs(h, W);
-    P.tiles = W.pk_tiles; P.ntiles = W.pk_ntiles; P.sys_t0 = W.pk_sys_t0; P.nsys = 1; P.st = h->st; P.sc = W.pk_sc;
+    P.tiles = W.pk_tiles; P.ntiles = W.pk_ntiles; P.sys_t0 = W.pk_sys_t0; P.nsys = 1; P.st = h->st;
     P.part = W.pk_part; P.active = active; P.rtol = rtol_ptr; P.rtol0 = rtol; P.bar = W.bar; P.maxit = maxit; P.stall = stall;
-    if (W.pk_ntiles < 1)   // no rows: the general kernel (its blocks find no tile)
-        return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_sc, W.pk_part, active, rtol_ptr,
+    if (W.pk_ntiles < 1 || W.pk_ntiles > PK1_MAXG)   // no rows, or more blocks than it sums: the general kernel
+        return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_part, active, rtol_ptr,
                          rtol, W.bar, maxit, stall);
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
@@ -1088,16 +1085,15 @@ void egfem_destroy(egfem_handle h) {
     for (KWork<double> *W : {&h->k64}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_sc); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_part);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_sc); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_part);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
     dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bsys_t0); dfree(h->bpart2);
-    if (h->bsc) cudaFree(h->bsc);
     if (h->gn_exec) cudaGraphExecDestroy(h->gn_exec);
     dfree(h->gn_state); dfree(h->gn_stats); dfree(h->gn_loops);
     if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
@@ -1792,7 +1788,7 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     // tiles near that size, so blocks get nearly equal work whatever the instance sizes
     constexpr int R = VecT<V>::R;
     int nbk = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, (const void *)pk_solve<V>, PK_BLOCK, 0) != cudaSuccess || nbk < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, (const void *)pk_solveb<V>, PK_BLOCK, 0) != cudaSuccess || nbk < 1)
         nbk = 1;
     const int64_t blocks = int64_t(std::min(nbk, 8)) * h->sms;
     const int64_t target = std::max<int64_t>(SLICE, (h->inst_off[h->nb] + blocks * factor - 1) / (blocks * factor));
@@ -1814,7 +1810,6 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     EG_TRY(upload(h->tiles, T));
     EG_TRY(upload(h->bsys_t0, sys_t0));
     EG_TRY(dalloc(h->bpart2, size_t(2 * T.size())));
-    if (!h->bsc) EG_CUDA(cudaMalloc(&h->bsc, size_t(h->nb) * std::max(sizeof(PkScal<double>), sizeof(PkScal<df64>))));
     h->ntiles = int64_t(T.size());
     // 3 slots x 2 values per tile, then one running count per block of the persistent solve
     EG_TRY(dalloc(h->bpart, size_t(6 * h->ntiles + int64_t(h->sms) * 8)));
@@ -1872,7 +1867,7 @@ template <typename V>
 int pk_batch_grid(const egfem_t *h) {
     if (!h->coop || !h->opts.krylov_persistent || h->ntiles < 1) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve<V>, PK_BLOCK, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PK_BLOCK, 0) != cudaSuccess || nb < 1)
         return 0;
     const int64_t g = std::min<int64_t>(h->ntiles, std::min<int64_t>(int64_t(nb), 8) * h->sms);
     if ((h->ntiles + g - 1) / g > PK_MAXT) return 0;
@@ -1882,7 +1877,7 @@ int pk_batch_grid(const egfem_t *h) {
 template <typename V>
 egfem_status launch_batch_persistent(egfem_t *h, KWork<V> &W, int grid, int32_t maxit, int32_t stall) {
     if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));
-    return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bsys_t0, h->nb, h->bst, static_cast<PkScal<V> *>(h->bsc), h->bpart2,
+    return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bsys_t0, h->nb, h->bst, h->bpart2,
                      h->inst_mask, h->inst_eta, 0.0, h->bbar, maxit, stall);
 }
 

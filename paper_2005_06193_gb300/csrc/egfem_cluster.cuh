@@ -21,13 +21,13 @@
 // triple the SpMV's FP64 work).
 //
 // V = double (the FP64 path) or df64 (the mixed path: double-float vectors, the FP32 operator
-// applied in difference form with its row sum in column 0, compensated as in pk_solve).
+// applied in difference form with its row sum in column 0, compensated as in pk_solve1).
 //
 // The operator (the Jacobi-scaled Jacobian in SELL layout) is read-only during the solve.
 // When it fits beside the vectors, each CTA copies its rows of it to shared memory at the
 // start (ELL values and column codes naming the owning CTA and offset), and the iterations
 // touch no global memory; otherwise it is read from global memory.  Arithmetic and stopping
-// rules are those of pk_solve<double>.
+// rules are those of pk_solve1<double>.
 #pragma once
 
 #include "egfem_persist.cuh"
@@ -195,7 +195,7 @@ __device__ __forceinline__ V pkc_spmv_row_smem(const M_t *opv, const uint32_t *o
 
 // The solve: x = 0 start, BiCGStab until (r, r) <= rtol^2 (b, b), a breakdown, the iteration
 // cap, divergence or (stall > 0) stagnation.  One cluster; grid = the cluster.  The phases and
-// their order are those of pk_solve<double>: A v = A p | B1 s = r - alpha v | B2 t = A s |
+// their order are those of pk_solve1<double>: A v = A p | B1 s = r - alpha v | B2 t = A s |
 // C x, r | D p, with a cluster barrier after each.
 template <typename V>
 __global__ void __launch_bounds__(PKC_BLOCK, 1) pkc_solve(PkcArgs<V> P) {

@@ -17,23 +17,25 @@
 //
 // Each block writes one partial (double) per owned tile and inner product; double-float
 // accumulators are summed within the block in double-float arithmetic on the FP32 pipe
-// (GB300 executes FP64 at about 1/58 of the FP32 rate).  At a summing barrier the LAST block
-// to arrive, before it releases the others, sums every system's tile partials in tile order,
-// updates the systems' BiCGStab scalars and states once, and publishes them (in the vector
-// type) with the count of systems still iterating; every block then reads the scalars of its
-// tiles' systems, so no block repeats the FP64 scalar work.  The results are deterministic
-// (fixed summation order), and the loop ends in all blocks at once.
+// (GB300 executes FP64 at about 1/58 of the FP32 rate).  No block is singled out at a summing
+// barrier: after it, EVERY block sums the partials it needs (all of them for one system,
+// pk_solve1; all tiles of each owned tile's system for a batch, pk_solveb) in one fixed order
+// and updates its own copy of the BiCGStab state in shared memory.  The copies agree bit for
+// bit (same inputs, same order), so the loop ends in all blocks at once, and a barrier costs
+// one arrival atomic and one wait -- not the arrival, a last block's sums, fence and release,
+// and every block's read of the published scalars (about 7 round trips to L2 against 3).
 //
-// The barrier is an arrival counter and a generation word.  The cooperative launch guarantees
-// that all blocks are resident (the host sizes the grid from the occupancy calculator), so
-// every wait ends; each wait is bounded all the same (PK_WAIT_NS of %globaltimer), after which
-// the block raises the error word, the other blocks leave their waits, and the host reports a
-// timeout instead of hanging.
+// The barriers count arrivals (pk1_sync: one counter that only grows within a launch;
+// pkb_sync: a ring of three 64-bit slots that also count the blocks still owning a running
+// system, which ends the batched loop).  The cooperative launch guarantees that all blocks are
+// resident (the host sizes the grid from the occupancy calculator), so every wait ends; each
+// wait is bounded all the same (PK_WAIT_NS of %globaltimer), after which the block raises the
+// error word, the other blocks leave their waits, and the host reports a timeout instead of
+// hanging.
 //
 // Vectors written during the launch are read with plain loads, ordered by the barriers; the
 // operator, its index data and the right-hand side are read-only for the launch and use the
-// non-coherent path; scalars and partials rewritten during the launch are read at L2
-// (ld.global.cg).
+// non-coherent path; partials rewritten during the launch are read at L2 (ld.global.cg).
 //
 // Double-float (df64) vectors take compensated arithmetic in the operator application: the
 // difference x_c - x_i by TwoSum of the high words, the product with the FP32 operator value
@@ -56,6 +58,7 @@ struct PGrid {
     uint32_t gen;       // barriers completed
     int32_t err;        // nonzero: a wait ran out; every block leaves
     int32_t running;    // systems still iterating (published at each summing barrier)
+    unsigned long long slot[3];   // pk_solveb: barrier k counts on slot k % 3 (arrivals | live blocks << 32)
 };
 
 constexpr unsigned long long PK_WAIT_NS = 2000000000ull;   // longest wait at one barrier
@@ -86,6 +89,19 @@ __device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
 }
 __device__ __forceinline__ void st_relaxed_gpu(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu_u64(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Loads of vectors written during the launch: plain (weak, L1-cached) loads.  The barrier's
@@ -241,13 +257,6 @@ constexpr int32_t K_TIMEOUT = 6;   // a grid-barrier wait ran out (KDone extensi
 // against 74 and 293 us with 5 blocks and no unrolling; FP64 unchanged (97 us).
 constexpr int PK_MIN_BLOCKS = 4;
 
-// scalars of one system as the vector loops use them
-template <typename V>
-struct PkScal {
-    V alpha, omega, beta;
-    int32_t done, pad;
-};
-
 template <typename V>
 struct PkArgs {
     KVecs<V> K;               // vectors and operator (K.st and K.part unused)
@@ -256,7 +265,6 @@ struct PkArgs {
     const int64_t *sys_t0;    // [nsys]: first tile of each system
     int32_t nsys;
     KState *st;               // [nsys] BiCGStab state (final state for the host)
-    PkScal<V> *sc;            // [nsys] scalars published at the summing barriers
     double *part;             // [2 * ntiles] tile partials
     const uint8_t *active;    // [nsys] systems to solve, or null (all)
     const double *rtol;       // [nsys] tolerances, or null (rtol0 for all)
@@ -265,49 +273,6 @@ struct PkArgs {
     int32_t maxit, stall;
 };
 
-// Grid barrier in two halves: every block arrives; the last block to arrive runs work()
-// with all its threads, then releases the others.  false when a wait ran out.
-template <typename F>
-__device__ __forceinline__ bool pk_barrier(PGrid *g, uint32_t &gen, F &&work, unsigned long long limit_ns = PK_WAIT_NS) {
-    __shared__ int s_last, s_ok;
-    const uint32_t target = gen + 1u;
-    gen = target;
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atom_add_acq_rel_gpu(&g->count, 1u) + 1u == gridDim.x);
-    __syncthreads();
-    if (s_last) {
-        work();
-        __threadfence();   // the results are visible at L2 before the release
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            st_relaxed_gpu(&g->count, 0u);
-            st_release_gpu(&g->gen, target);
-        }
-        return true;
-    }
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned long long t0 = pk_clock_ns();
-        uint32_t spins = 0;
-        while (ld_acquire_gpu(&g->gen) != target) {
-            if (ld_relaxed_gpu(&g->err)) { ok = 0; break; }
-            if ((++spins & 255u) == 0u && pk_clock_ns() - t0 > limit_ns) {
-                atomicExch(&g->err, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-__device__ __forceinline__ df64 ldcg_df(const float2 *p) {
-    const float2 t = __ldcg(p);
-    return {t.x, t.y};
-}
 
 __device__ __forceinline__ df64 shfl_xor_df(df64 a, int o) {
     return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
@@ -350,283 +315,9 @@ __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], doub
     }
 }
 
-// state of a system, read at L2 (another SM may have written it at an earlier barrier)
-__device__ __forceinline__ KState pk_load_state(const KState *g) {
-    KState S;
-    S.rho = __ldcg(&g->rho); S.alpha = __ldcg(&g->alpha); S.omega = __ldcg(&g->omega); S.beta = __ldcg(&g->beta);
-    S.rr = __ldcg(&g->rr); S.rr0 = __ldcg(&g->rr0); S.tol2 = __ldcg(&g->tol2); S.best_rr = __ldcg(&g->best_rr);
-    S.stall_rr = __ldcg(&g->stall_rr); S.scratch[0] = 0.0; S.scratch[1] = 0.0;
-    S.iter = __ldcg(&g->iter); S.maxit = __ldcg(&g->maxit); S.done = __ldcg(&g->done);
-    S.last_improve = __ldcg(&g->last_improve); S.stall = __ldcg(&g->stall); S.ticket = 0u;
-    return S;
-}
-
-// Last-block work of a summing barrier: for every system to update (SETUP: every active
-// system; else every running one), the sums of its tile partials (one warp per system, lanes
-// over tiles, df64), then update(S, tot) on a copy of its state, which is stored back with the
-// published scalars; the count of systems still running goes to the barrier word.
-template <bool SETUP, typename V, int NV, typename U>
-__device__ __forceinline__ void pk_sum_update(const PkArgs<V> &P, U &&update) {
-    __shared__ int s_run;
-    __shared__ double s_w[2][PK_BLOCK / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_run = 0;
-    // one system: all warps share its tiles, then the warp sums are added in order
-    const bool one = P.nsys == 1;
-    if (one) {
-        const int32_t nt = P.tiles[0].ntiles_inst;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-            for (int q = threadIdx.x; q < nt; q += PK_BLOCK) x += __ldcg(P.part + k * P.ntiles + q);
-            x = warp_sum(x);
-            if (lane == 0) s_w[k][w] = x;
-        }
-    }
-    __syncthreads();
-    int run = 0;
-    for (int b = w; b < P.nsys; b += PK_BLOCK / 32) {
-        KState S;
-        if constexpr (SETUP) {
-            S.done = (!P.active || P.active[b]) ? K_RUNNING : K_CONVERGED;
-            S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
-            S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
-            S.rho = S.rr = S.rr0 = S.best_rr = S.tol2 = S.stall_rr = 0.0;
-            if (S.done != K_RUNNING) {
-                if (lane == 0) {
-                    P.st[b] = S;
-                    P.sc[b] = PkScal<V>{cvt<V>(1.0), cvt<V>(1.0), cvt<V>(0.0), S.done, 0};
-                }
-                continue;
-            }
-        } else {
-            if (__ldcg(&P.st[b].done) != K_RUNNING) continue;
-            S = pk_load_state(P.st + b);
-        }
-        double x[NV];
-        if (one) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                x[k] = s_w[k][0];
-                for (int q = 1; q < PK_BLOCK / 32; ++q) x[k] += s_w[k][q];
-            }
-        } else {
-            const int64_t t0 = P.sys_t0[b];
-            const int32_t nt = P.tiles[t0].ntiles_inst;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                x[k] = 0.0;
-                for (int q = lane; q < nt; q += 32) x[k] += __ldcg(P.part + k * P.ntiles + t0 + q);
-                x[k] = warp_sum(x[k]);
-            }
-        }
-        if (lane == 0) {
-            update(S, b, x);
-            P.st[b] = S;
-            P.sc[b] = PkScal<V>{cvt<V>(S.alpha), cvt<V>(S.omega), cvt<V>(S.beta), S.done, 0};
-            run += (S.done == K_RUNNING);
-        }
-    }
-    if (lane == 0 && run) atomicAdd(&s_run, run);
-    __syncthreads();
-    if (threadIdx.x == 0) P.bar->running = s_run;
-}
-
-// every owned tile's system scalars -> shared memory; returns the running-system count
-template <typename V>
-__device__ __forceinline__ int pk_read_scalars(const PkArgs<V> &P, int nt, const int32_t *inst, PkScal<V> *sc) {
-    __shared__ int s_running;
-    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
-        const PkScal<V> *c = P.sc + inst[t];
-        PkScal<V> v;
-        if constexpr (std::is_same<V, df64>::value) {
-            v.alpha = ldcg_df(reinterpret_cast<const float2 *>(&c->alpha));
-            v.omega = ldcg_df(reinterpret_cast<const float2 *>(&c->omega));
-            v.beta = ldcg_df(reinterpret_cast<const float2 *>(&c->beta));
-        } else {
-            v.alpha = __ldcg(&c->alpha); v.omega = __ldcg(&c->omega); v.beta = __ldcg(&c->beta);
-        }
-        v.done = __ldcg(&c->done);
-        v.pad = 0;
-        sc[t] = v;
-    }
-    if (threadIdx.x == 0) s_running = __ldcg(&P.bar->running);
-    __syncthreads();
-    return s_running;
-}
-
 #define PK_TILES(nt) for (int t = 0; t < (nt); ++t)
 #define PK_ROWS(T) \
     _Pragma("unroll 1") for (int64_t r0 = (T).r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < (T).r_end; r0 += int64_t(PK_BLOCK) * VecT<V>::R)
-
-// The solve: x = 0 start for every active system, BiCGStab until (r, r) <= rtol^2 (b, b),
-// a breakdown, the iteration cap, divergence or (stall > 0) stagnation, all systems in one
-// launch.  Final states in P.st; P.bar->err set when a barrier wait ran out.
-template <typename V>
-__global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve(PkArgs<V> P) {
-    using Op = PkOps<V>;
-    constexpr int R = VecT<V>::R;
-    __shared__ int32_t s_inst[PK_MAXT];
-    __shared__ PkScal<V> s_sc[PK_MAXT];
-    const int64_t G = gridDim.x;
-    if (P.ntiles > G * PK_MAXT) {   // the host keeps to the limit; every block leaves at once
-        if (blockIdx.x == 0 && threadIdx.x == 0) P.bar->err = 2;
-        return;
-    }
-    const int nt = int64_t(blockIdx.x) < P.ntiles ? int((P.ntiles - blockIdx.x + G - 1) / G) : 0;
-    const KVecs<V> &K = P.K;
-    uint32_t gen = 0;
-
-    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
-        const int32_t b = P.tiles[blockIdx.x + int64_t(t) * G].inst;
-        s_inst[t] = b;
-        s_sc[t].done = (!P.active || P.active[b]) ? K_RUNNING : K_CONVERGED;
-    }
-    __syncthreads();
-
-    // setup: x = v = 0, r = rh = p = b, (b, b)
-    {
-        Pack<V> z;
-#pragma unroll
-        for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const int64_t tile = blockIdx.x + int64_t(t) * G;
-            const BTile T = P.tiles[tile];
-            DotAcc<V> acc[1];
-            PK_ROWS(T) {
-                const Pack<V> b = ldv(K.b + r0);
-                stv(K.x + r0, z); stv(K.v + r0, z);
-                stv(K.r + r0, b); stv(K.rh + r0, b); stv(K.p + r0, b);
-#pragma unroll
-                for (int j = 0; j < R; ++j) acc[0].add(b.v[j], b.v[j]);
-            }
-            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, tile);
-        }
-    }
-    bool ok = pk_barrier(P.bar, gen, [&] {
-        // active systems start with (b, b); inactive ones are done
-        pk_sum_update<true, V, 1>(P, [&](KState &S, int b, const double *tot) {
-            const double x = tot[0], rt = P.rtol ? P.rtol[b] : P.rtol0;
-            S.rho = S.rr = S.rr0 = S.best_rr = x;
-            S.tol2 = rt * rt * x;
-            S.stall_rr = 4e-6 * x;   // the stagnation guard waits for a 500x reduction
-            S.done = (x == 0.0) ? K_CONVERGED : (!isfinite(x) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
-        });
-    });
-    int running = ok ? pk_read_scalars(P, nt, s_inst, s_sc) : 0;
-
-    while (running > 0) {
-        // A: v = A p, (rh, v)
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const int64_t tile = blockIdx.x + int64_t(t) * G;
-            const BTile T = P.tiles[tile];
-            DotAcc<V> acc[1];
-            PK_ROWS(T) {
-                const Pack<V> p = ldcv(K.p + r0);
-                const Pack<V> y = pk_spmv(K, r0, K.p, p);
-                stv(K.v + r0, y);
-                const Pack<V> rh = ldcv(K.rh + r0);
-#pragma unroll
-                for (int j = 0; j < R; ++j) acc[0].add(rh.v[j], y.v[j]);
-            }
-            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, tile);
-        }
-        ok = pk_barrier(P.bar, gen, [&] {
-            pk_sum_update<false, V, 1>(P, [&](KState &S, int, const double *tot) {
-                if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
-                else S.alpha = S.rho / tot[0];
-            });
-        });
-        if (!ok || (running = pk_read_scalars(P, nt, s_inst, s_sc)) == 0) break;
-
-        // B1: s = r - alpha v
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const BTile T = P.tiles[blockIdx.x + int64_t(t) * G];
-            const V al = s_sc[t].alpha;
-            PK_ROWS(T) {
-                const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
-                Pack<V> s;
-#pragma unroll
-                for (int j = 0; j < R; ++j) s.v[j] = Op::sub(r.v[j], al * v.v[j]);
-                stv(K.s + r0, s);
-            }
-        }
-        if (!pk_barrier(P.bar, gen, [] {})) break;
-
-        // B2: t = A s, (t, s), (t, t)
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const int64_t tile = blockIdx.x + int64_t(t) * G;
-            const BTile T = P.tiles[tile];
-            DotAcc<V> acc[2];
-            PK_ROWS(T) {
-                const Pack<V> s = ldcv(K.s + r0);
-                const Pack<V> y = pk_spmv(K, r0, K.s, s);
-                stv(K.t + r0, y);
-#pragma unroll
-                for (int j = 0; j < R; ++j) { acc[0].add(y.v[j], s.v[j]); acc[1].add(y.v[j], y.v[j]); }
-            }
-            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, tile);
-        }
-        ok = pk_barrier(P.bar, gen, [&] {
-            pk_sum_update<false, V, 2>(P, [&](KState &S, int, const double *tot) {
-                if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
-                else S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
-            });
-        });
-        if (!ok || (running = pk_read_scalars(P, nt, s_inst, s_sc)) == 0) break;
-
-        // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const int64_t tile = blockIdx.x + int64_t(t) * G;
-            const BTile T = P.tiles[tile];
-            const V al = s_sc[t].alpha, om = s_sc[t].omega;
-            DotAcc<V> acc[2];
-            PK_ROWS(T) {
-                const Pack<V> s = ldcv(K.s + r0), p = ldcv(K.p + r0), tv = ldcv(K.t + r0), rh = ldcv(K.rh + r0);
-                Pack<V> x = ldcv(K.x + r0), r;
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    x.v[j] = Op::add(x.v[j], Op::add(al * p.v[j], om * s.v[j]));
-                    r.v[j] = Op::sub(s.v[j], om * tv.v[j]);
-                    acc[0].add(rh.v[j], r.v[j]);
-                    acc[1].add(r.v[j], r.v[j]);
-                }
-                stv(K.x + r0, x);
-                stv(K.r + r0, r);
-            }
-            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, tile);
-        }
-        ok = pk_barrier(P.bar, gen, [&] {
-            pk_sum_update<false, V, 2>(P, [&](KState &S, int, const double *tot) {
-                pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
-            });
-        });
-        if (!ok || (running = pk_read_scalars(P, nt, s_inst, s_sc)) == 0) break;
-
-        // D: p = r + beta (p - omega v)
-        PK_TILES(nt) {
-            if (s_sc[t].done != K_RUNNING) continue;
-            const BTile T = P.tiles[blockIdx.x + int64_t(t) * G];
-            const V be = s_sc[t].beta, om = s_sc[t].omega;
-            PK_ROWS(T) {
-                const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
-                Pack<V> p = ldcv(K.p + r0);
-#pragma unroll
-                for (int j = 0; j < R; ++j) p.v[j] = Op::add(r.v[j], be * Op::sub(p.v[j], om * v.v[j]));
-                stv(K.p + r0, p);
-            }
-        }
-        if (!pk_barrier(P.bar, gen, [] {})) break;
-    }
-}
-
-#undef PK_TILES
-#undef PK_ROWS
 
 // ---------------------------------------------------------------------------------
 // One system: every block keeps the solver state
@@ -662,42 +353,46 @@ __device__ __forceinline__ bool pk1_sync(PGrid *g, uint32_t &nbar, unsigned long
     return s_ok != 0;
 }
 
+// Most blocks the single-system kernel sums over (8 resident blocks on each of 152 SMs; the
+// host launches the general kernel beyond it)
+constexpr int PK1_MAXG = 8 * 152;
+
 // Sums of NV dot products over the grid, the same in every block: the block's partials go to
-// part[k * G + block], and after the barrier every block adds all G partials in one fixed order
-// (threads over partials, warp sums, then the warps in order -- the order of the batched
-// kernel's last-block sum for one system, so both kernels compute the same iterates).
+// part[k * G + block]; after the barrier every block loads all G partials into shared memory
+// (one round of parallel L2 loads), and warp k adds those of value k in one fixed order (lanes
+// over partials, then the warp's tree); s_p is the kernel's [2][PK1_MAXG] shared buffer.  One warp per sum keeps the FP64 work of the redundant
+// sums small: GB300 retires about two FP64 operations per SM and clock.
 template <typename V, int NV>
 __device__ __forceinline__ bool pk1_allreduce(const PkArgs<V> &P, const DotAcc<V> (&acc)[NV], uint32_t &nbar,
-                                              double (&tot)[NV]) {
-    __shared__ double s_w[2][PK_BLOCK / 32];
-    const int64_t G = gridDim.x;
+                                              double (*s_p)[PK1_MAXG], double (&tot)[NV]) {
+    __shared__ double s_tot[2];
+    const int G = int(gridDim.x);
     pk_tile_partial<V, NV>(acc, P.part, G, blockIdx.x);
     if (!pk1_sync(P.bar, nbar)) return false;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
+    for (int k = 0; k < NV; ++k)
+        for (int q = threadIdx.x; q < G; q += PK_BLOCK) s_p[k][q] = __ldcg(P.part + int64_t(k) * G + q);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < NV) {
         double x = 0.0;
-        for (int64_t q = threadIdx.x; q < G; q += PK_BLOCK) x += __ldcg(P.part + k * G + q);
+        for (int q = lane; q < G; q += 32) x += s_p[w][q];
         x = warp_sum(x);
-        if (lane == 0) s_w[k][w] = x;
+        if (lane == 0) s_tot[w] = x;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double x = s_w[k][0];
-        for (int q = 1; q < PK_BLOCK / 32; ++q) x += s_w[k][q];
-        tot[k] = x;
-    }
+    for (int k = 0; k < NV; ++k) tot[k] = s_tot[k];
     return true;
 }
 
 #define PK1_ROWS \
     _Pragma("unroll 1") for (int64_t r0 = T.r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < T.r_end; r0 += int64_t(PK_BLOCK) * VecT<V>::R)
 
-// The solve of one system, one tile per block (P.ntiles == gridDim.x): the phases, their
-// arithmetic and their order are pk_solve's, but every block computes the scalars itself from
-// all partials and keeps the state in shared memory, so the iteration needs no last block, no
-// published scalars and no state in global memory.  Block 0 writes the final state to P.st
+// The solve of one system, one tile per block (P.ntiles == gridDim.x), in the phases A, B1,
+// B2, C, D above from x = 0 until (r, r) <= rtol^2 (b, b), a breakdown, the iteration cap,
+// divergence or (stall > 0) stagnation; every block computes the scalars itself from all
+// partials and keeps the state in shared memory.  Block 0 writes the final state to P.st
 // (done = K_TIMEOUT when a barrier wait ran out; P.bar->err is then set too).  An inactive
 // system (P.active[0] == 0) returns at once.
 template <typename V>
@@ -705,6 +400,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
     using Op = PkOps<V>;
     constexpr int R = VecT<V>::R;
     __shared__ KState S;
+    __shared__ double s_p[2][PK1_MAXG];   // partials of the sums in progress
     if (P.active && !P.active[0]) return;
     const KVecs<V> &K = P.K;
     __shared__ BTile T;   // the block's rows (in shared memory: fewer live registers in the phases)
@@ -726,7 +422,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
             for (int j = 0; j < R; ++j) acc[0].add(b.v[j], b.v[j]);
         }
         double tot[1];
-        ok = pk1_allreduce<V, 1>(P, acc, nbar, tot);
+        ok = pk1_allreduce<V, 1>(P, acc, nbar, s_p, tot);
         if (threadIdx.x == 0) {
             const double x = ok ? tot[0] : 0.0, rt = P.rtol ? P.rtol[0] : P.rtol0;
             S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
@@ -752,7 +448,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
                 for (int j = 0; j < R; ++j) acc[0].add(rh.v[j], y.v[j]);
             }
             double tot[1];
-            if (!(ok = pk1_allreduce<V, 1>(P, acc, nbar, tot))) break;
+            if (!(ok = pk1_allreduce<V, 1>(P, acc, nbar, s_p, tot))) break;
             if (threadIdx.x == 0) {
                 if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
                 else S.alpha = S.rho / tot[0];
@@ -783,7 +479,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
                 for (int j = 0; j < R; ++j) { acc[0].add(y.v[j], s.v[j]); acc[1].add(y.v[j], y.v[j]); }
             }
             double tot[2];
-            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, tot))) break;
+            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, s_p, tot))) break;
             if (threadIdx.x == 0) {
                 if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
                 else S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
@@ -810,7 +506,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
                 stv(K.r + r0, r);
             }
             double tot[2];
-            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, tot))) break;
+            if (!(ok = pk1_allreduce<V, 2>(P, acc, nbar, s_p, tot))) break;
             if (threadIdx.x == 0) pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
             __syncthreads();
             if (S.done != K_RUNNING) break;
@@ -838,17 +534,259 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P
 
 #undef PK1_ROWS
 
-// Self-test of the barrier's bounded wait: blocks with index >= arrive leave without
-// arriving, so with arrive < gridDim.x the barrier cannot complete and the waiting blocks
-// must give up after limit_ns.  ok[b] = 1 when block b passed the barrier, 0 when it gave up,
-// -1 when it did not arrive.
+// ---------------------------------------------------------------------------------
+// Many systems (a batch): every block keeps the states of its tiles' systems
+// ---------------------------------------------------------------------------------
+
+// Barrier number nbar of pk_solveb: thread 0 counts the block on slot nbar % 3 (low word:
+// arrivals; high word: blocks that still own a running tile) and waits until all gridDim.x
+// blocks have arrived; live = the high word then, the same in every block.  Block 0 clears
+// slot (nbar - 1) % 3 after passing: every block has read it before arriving here, and none
+// adds to it again before barrier nbar + 2, which needs block 0's next arrival.  false when
+// the wait ran out or another block gave up.
+__device__ __forceinline__ bool pkb_sync(PGrid *g, uint32_t &nbar, int has_live, uint32_t &live,
+                                         unsigned long long limit_ns = PK_WAIT_NS) {
+    __shared__ int s_ok;
+    __shared__ uint32_t s_live;
+    ++nbar;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *sl = &g->slot[nbar % 3u];
+        const unsigned long long add = 1ull | (has_live ? (1ull << 32) : 0ull);
+        unsigned long long v = atom_add_acq_rel_gpu_u64(sl, add) + add;
+        int ok = 1;
+        const unsigned long long t0 = pk_clock_ns();
+        uint32_t spins = 0;
+        while (uint32_t(v & 0xffffffffull) < gridDim.x) {
+            if (ld_relaxed_gpu(&g->err)) { ok = 0; break; }
+            if ((++spins & 255u) == 0u && pk_clock_ns() - t0 > limit_ns) {
+                atomicExch(&g->err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+            v = ld_acquire_gpu_u64(sl);
+        }
+        if (blockIdx.x == 0) st_relaxed_gpu_u64(&g->slot[(nbar + 2u) % 3u], 0ull);
+        s_ok = ok;
+        s_live = uint32_t(v >> 32);
+    }
+    __syncthreads();
+    live = s_live;
+    return s_ok != 0;
+}
+
+// The sums of a barrier: for each owned tile whose system runs, warp (tile mod 8) adds the NV
+// partials of all tiles of that system in one fixed order (lanes over tiles, then the warp's
+// tree), so every block holding a tile of the system computes the same sums, and lane 0 calls
+// update(state, system, sums) on the block's copy of the state.
+template <typename V, int NV, typename U>
+__device__ __forceinline__ void pkb_sums(const PkArgs<V> &P, int nt, KState *st, const BTile *tl, U &&update) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = w; t < nt; t += PK_BLOCK / 32) {
+        if (st[t].done != K_RUNNING) continue;
+        const int64_t t0 = tl[t].tile0;
+        const int32_t n = tl[t].ntiles_inst;
+        double x[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = 0.0;
+            for (int q = lane; q < n; q += 32) a += __ldcg(P.part + k * P.ntiles + t0 + q);
+            x[k] = warp_sum(a);
+        }
+        if (lane == 0) update(st[t], tl[t].inst, x);
+    }
+    __syncthreads();
+}
+
+// The batched solve: every active system from x = 0, BiCGStab until (r, r) <= rtol^2 (b, b),
+// a breakdown, the iteration cap, divergence or (stall > 0) stagnation; the phases and their
+// arithmetic are pk_solve1's.  Tiles are dealt to blocks round-robin (tile = block + t G); a
+// block keeps the state of each owned tile's system in shared memory, computed from all of
+// that system's partials, and the loop ends at the first barrier at which no block owns a
+// running tile.  The block owning a system's first tile writes its final state to P.st
+// (done = K_TIMEOUT when a barrier wait ran out; P.bar->err is then set too).
+template <typename V>
+__global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P) {
+    using Op = PkOps<V>;
+    constexpr int R = VecT<V>::R;
+    __shared__ KState s_st[PK_MAXT];
+    __shared__ BTile s_tl[PK_MAXT];
+    const int64_t G = gridDim.x;
+    if (P.ntiles > G * PK_MAXT) {   // the host keeps to the limit; every block leaves at once
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.bar->err = 2;
+        return;
+    }
+    const int nt = int64_t(blockIdx.x) < P.ntiles ? int((P.ntiles - blockIdx.x + G - 1) / G) : 0;
+    const KVecs<V> &K = P.K;
+    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
+        const BTile T = P.tiles[blockIdx.x + int64_t(t) * G];
+        s_tl[t] = T;
+        KState &S = s_st[t];
+        S.done = (!P.active || P.active[T.inst]) ? K_RUNNING : K_CONVERGED;
+        S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
+        S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+        S.rho = S.rr = S.rr0 = S.best_rr = S.tol2 = S.stall_rr = 0.0;
+    }
+    __syncthreads();
+    auto running = [&]() {
+        int a = 0;
+        for (int t = 0; t < nt; ++t) a |= (s_st[t].done == K_RUNNING);
+        return a;
+    };
+    uint32_t nbar = 0, live = 0;
+
+    // setup: x = v = 0, r = rh = p = b, (b, b)
+    {
+        Pack<V> z;
+#pragma unroll
+        for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            DotAcc<V> acc[1];
+            PK_ROWS(T) {
+                const Pack<V> b = ldv(K.b + r0);
+                stv(K.x + r0, z); stv(K.v + r0, z);
+                stv(K.r + r0, b); stv(K.rh + r0, b); stv(K.p + r0, b);
+#pragma unroll
+                for (int j = 0; j < R; ++j) acc[0].add(b.v[j], b.v[j]);
+            }
+            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+        }
+    }
+    bool ok = pkb_sync(P.bar, nbar, running(), live);
+    if (ok && live)
+        pkb_sums<V, 1>(P, nt, s_st, s_tl, [&](KState &S, int b, const double *tot) {
+            const double x = tot[0], rt = P.rtol ? P.rtol[b] : P.rtol0;
+            S.rho = S.rr = S.rr0 = S.best_rr = x;
+            S.tol2 = rt * rt * x;
+            S.stall_rr = 4e-6 * x;
+            S.done = (x == 0.0) ? K_CONVERGED : (!isfinite(x) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
+        });
+
+    while (ok && live) {
+        // A: v = A p, (rh, v)
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            DotAcc<V> acc[1];
+            PK_ROWS(T) {
+                const Pack<V> p = ldcv(K.p + r0);
+                const Pack<V> y = pk_spmv(K, r0, K.p, p);
+                stv(K.v + r0, y);
+                const Pack<V> rh = ldcv(K.rh + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) acc[0].add(rh.v[j], y.v[j]);
+            }
+            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+        pkb_sums<V, 1>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
+            if (tot[0] == 0.0 || !isfinite(tot[0])) S.done = isfinite(tot[0]) ? K_BREAKDOWN : K_NONFINITE;
+            else S.alpha = S.rho / tot[0];
+        });
+
+        // B1: s = r - alpha v
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            const V al = cvt<V>(s_st[t].alpha);
+            PK_ROWS(T) {
+                const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
+                Pack<V> s;
+#pragma unroll
+                for (int j = 0; j < R; ++j) s.v[j] = Op::sub(r.v[j], al * v.v[j]);
+                stv(K.s + r0, s);
+            }
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+
+        // B2: t = A s, (t, s), (t, t)
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            DotAcc<V> acc[2];
+            PK_ROWS(T) {
+                const Pack<V> s = ldcv(K.s + r0);
+                const Pack<V> y = pk_spmv(K, r0, K.s, s);
+                stv(K.t + r0, y);
+#pragma unroll
+                for (int j = 0; j < R; ++j) { acc[0].add(y.v[j], s.v[j]); acc[1].add(y.v[j], y.v[j]); }
+            }
+            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+        pkb_sums<V, 2>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) S.done = K_NONFINITE;
+            else S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+        });
+
+        // C: x += alpha p + omega s, r = s - omega t, (rh, r), (r, r)
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            const V al = cvt<V>(s_st[t].alpha), om = cvt<V>(s_st[t].omega);
+            DotAcc<V> acc[2];
+            PK_ROWS(T) {
+                const Pack<V> s = ldcv(K.s + r0), p = ldcv(K.p + r0), tv = ldcv(K.t + r0), rh = ldcv(K.rh + r0);
+                Pack<V> x = ldcv(K.x + r0), r;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    x.v[j] = Op::add(x.v[j], Op::add(al * p.v[j], om * s.v[j]));
+                    r.v[j] = Op::sub(s.v[j], om * tv.v[j]);
+                    acc[0].add(rh.v[j], r.v[j]);
+                    acc[1].add(r.v[j], r.v[j]);
+                }
+                stv(K.x + r0, x);
+                stv(K.r + r0, r);
+            }
+            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+        pkb_sums<V, 2>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
+            pk_after_c(S, tot[0], tot[1], P.maxit, P.stall);
+        });
+
+        // D: p = r + beta (p - omega v)
+        PK_TILES(nt) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &T = s_tl[t];
+            const V be = cvt<V>(s_st[t].beta), om = cvt<V>(s_st[t].omega);
+            PK_ROWS(T) {
+                const Pack<V> r = ldcv(K.r + r0), v = ldcv(K.v + r0);
+                Pack<V> p = ldcv(K.p + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) p.v[j] = Op::add(r.v[j], be * Op::sub(p.v[j], om * v.v[j]));
+                stv(K.p + r0, p);
+            }
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+    }
+    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
+        if (blockIdx.x + int64_t(t) * G != s_tl[t].tile0) continue;
+        KState F = s_st[t];
+        if (!ok) F.done = K_TIMEOUT;
+        P.st[s_tl[t].inst] = F;
+    }
+}
+
+#undef PK_TILES
+#undef PK_ROWS
+
+// Self-test of the barriers' bounded waits: blocks with index >= arrive leave without
+// arriving, so with arrive < gridDim.x the batched solve's barrier (pkb_sync) cannot complete
+// and the waiting blocks must give up after limit_ns; when it completes, its live count must
+// equal the arrivals, and the single-system barrier (pk1_sync) follows.  ok[b] = 1 when block
+// b passed both, 0 when it gave up, -1 when it did not arrive.
 __global__ void pk_barrier_selftest(PGrid *g, int32_t arrive, unsigned long long limit_ns, int32_t *ok) {
-    uint32_t gen = 0;
+    uint32_t nb = 0, n1 = 0, live = 0;
     if (int32_t(blockIdx.x) >= arrive) {
         if (threadIdx.x == 0) ok[blockIdx.x] = -1;
         return;
     }
-    const bool passed = pk_barrier(g, gen, [] {}, limit_ns);
+    bool passed = pkb_sync(g, nb, 1, live, limit_ns) && live == uint32_t(arrive);
+    passed = passed && pk1_sync(g, n1, limit_ns);
     if (threadIdx.x == 0) ok[blockIdx.x] = passed ? 1 : 0;
 }
 
