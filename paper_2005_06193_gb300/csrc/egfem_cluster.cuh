@@ -2,8 +2,9 @@
 // shared memory of one thread-block cluster (up to 16 CTAs, one per SM).
 //
 // The grid-wide persistent solve (egfem_persist.cuh) pays, at every one of its five grid
-// barriers per iteration, a chain of dependent L2 round trips (arrival atomic, last-block sum,
-// fence, release, poll, scalar read): about 30 us per iteration however few rows there are.
+// barriers per iteration, a chain of dependent L2 round trips (arrival atomic, wait, and at the
+// summing barriers one round of partial loads): about 19 us per iteration however few rows
+// there are.
 // Here the cluster's CTAs own contiguous slice-aligned row ranges; the seven Krylov vectors of
 // those rows stay in each CTA's shared memory for the whole solve; the SpMV gathers its
 // neighbours' entries from the owning CTA's shared memory (mapa + ld.shared::cluster); and the
