@@ -392,11 +392,11 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     if (h->coop) {
         // every block of a cooperative launch must be resident: at most occupancy x SMs; each
         // block owns one contiguous, slice-aligned tile of rows
-        int nb = 0, nb1 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PK_BLOCK, 0) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, (const void *)pk_solve1<V>, PK_BLOCK, 0) == cudaSuccess &&
-            std::min(nb, nb1) >= 1) {
-            nb = std::min(nb, nb1);   // the same grid serves both kernels
+        int nb = 0, nbb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solve1<V>, PK1_BLOCK, 0) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbb, (const void *)pk_solveb<V>, PKB_BLOCK, 0) == cudaSuccess &&
+            std::min(nb, nbb) >= 1) {
+            nb = std::min(nb, nbb);   // the grid of pk_solve1, which pk_solveb (more blocks per SM) also holds
             const int64_t min_rows = (int64_t(h->opts.krylov_block_rows > 0 ? h->opts.krylov_block_rows : kPkBlockRows) +
                                       SLICE - 1) / SLICE * SLICE;
             const int64_t g = std::max<int64_t>(1, std::min<int64_t>(int64_t(std::min(nb, 8)) * h->sms, h->n_pad / min_rows));
@@ -479,7 +479,7 @@ egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, in
     P.active = active; P.rtol = rtol; P.rtol0 = rtol0; P.bar = bar; P.maxit = maxit; P.stall = stall;
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(bar, 0, sizeof(PGrid), h->hs));
-    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solveb<V>, dim3(grid), dim3(PK_BLOCK), args, 0, h->hs));
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solveb<V>, dim3(grid), dim3(PKB_BLOCK), args, 0, h->hs));
     return EGFEM_OK;
 }
 
@@ -498,7 +498,7 @@ egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
     // one block per tile (at most the resident grid W.g_pk)
-    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solve1<V>, dim3(unsigned(W.pk_ntiles)), dim3(PK_BLOCK), args, 0,
+    EG_CUDA(cudaLaunchCooperativeKernel((const void *)pk_solve1<V>, dim3(unsigned(W.pk_ntiles)), dim3(PK1_BLOCK), args, 0,
                                         h->hs));
     return EGFEM_OK;
 }
@@ -1788,7 +1788,7 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     // tiles near that size, so blocks get nearly equal work whatever the instance sizes
     constexpr int R = VecT<V>::R;
     int nbk = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, (const void *)pk_solveb<V>, PK_BLOCK, 0) != cudaSuccess || nbk < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbk, (const void *)pk_solveb<V>, PKB_BLOCK, 0) != cudaSuccess || nbk < 1)
         nbk = 1;
     const int64_t blocks = int64_t(std::min(nbk, 8)) * h->sms;
     const int64_t target = std::max<int64_t>(SLICE, (h->inst_off[h->nb] + blocks * factor - 1) / (blocks * factor));
@@ -1867,7 +1867,7 @@ template <typename V>
 int pk_batch_grid(const egfem_t *h) {
     if (!h->coop || !h->opts.krylov_persistent || h->ntiles < 1) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PK_BLOCK, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PKB_BLOCK, 0) != cudaSuccess || nb < 1)
         return 0;
     const int64_t g = std::min<int64_t>(h->ntiles, std::min<int64_t>(int64_t(nb), 8) * h->sms);
     if ((h->ntiles + g - 1) / g > PK_MAXT) return 0;

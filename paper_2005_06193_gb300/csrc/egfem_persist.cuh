@@ -50,7 +50,8 @@
 
 namespace egfem {
 
-constexpr int PK_BLOCK = 256;   // threads per block of the persistent kernel
+constexpr int PK1_BLOCK = 512;  // threads per block of the single-system kernel (2 resident per SM)
+constexpr int PKB_BLOCK = 256;  // threads per block of the batched kernel (4 resident per SM)
 constexpr int PK_MAXT = 64;     // tiles per block
 
 struct PGrid {
@@ -251,11 +252,16 @@ __device__ __forceinline__ void pk_after_c(KState &S, double rho1, double rr, in
 
 constexpr int32_t K_TIMEOUT = 6;   // a grid-barrier wait ran out (KDone extension)
 
-// Resident blocks per SM the kernel is compiled for: 4 (64 registers per thread), with the
-// operator's column loop unrolled 4 times (its loads then issue ahead of the arithmetic):
-// measured fastest -- double-float 69 us per iteration at 1M rows and 242 us at 4.2M rows,
-// against 74 and 293 us with 5 blocks and no unrolling; FP64 unchanged (97 us).
-constexpr int PK_MIN_BLOCKS = 4;
+// Resident blocks per SM the kernels are compiled for, 64 registers per thread either way, with
+// the operator's column loop unrolled 4 times (its loads then issue ahead of the arithmetic).
+// Every block sums all partials of a reduction, so for one system fewer, larger blocks shorten
+// the sums and the barriers: per iteration, 512 x 2 against 256 x 4 at 66 k / 1 M / 4.2 M rows,
+// FP64 24.0 / 87.7 / 265 us against 26.8 / 89.1 / 268, double-float 26.7 / 62.0 / 234 against
+// 29.7 / 65.5 / 235 (1024 x 1 loses at 4.2 M rows: 278 / 243).  The batched kernel keeps
+// 256 x 4: its blocks hold tiles of uneven instances, and 512 x 2 took the 32-instance P3 batch
+// from 123.7 to 109.8 solves/s.
+constexpr int PK1_MIN_BLOCKS = 2;
+constexpr int PKB_MIN_BLOCKS = 4;
 
 template <typename V>
 struct PkArgs {
@@ -279,13 +285,13 @@ __device__ __forceinline__ df64 shfl_xor_df(df64 a, int o) {
 }
 
 // Block sum of NV per-thread accumulators for one tile -> part[k * ntiles + tile].
-template <typename V, int NV>
+template <typename V, int NV, int BLOCK>
 __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], double *part, int64_t ntiles, int64_t tile) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();   // the previous tile's readers of the shared arrays are done
     if constexpr (std::is_same<V, df64>::value) {
         // warp and block sums in double-float arithmetic (FP32 pipe), one conversion per tile
-        __shared__ float2 shf[2][PK_BLOCK / 32];
+        __shared__ float2 shf[2][BLOCK / 32];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             df64 x = df_two_sum(acc[k].hi, acc[k].lo);
@@ -297,18 +303,18 @@ __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], doub
         if (threadIdx.x < NV) {
             const int k = threadIdx.x;
             df64 x = {shf[k][0].x, shf[k][0].y};
-            for (int q = 1; q < PK_BLOCK / 32; ++q) x = df_add(x, df64{shf[k][q].x, shf[k][q].y});
+            for (int q = 1; q < BLOCK / 32; ++q) x = df_add(x, df64{shf[k][q].x, shf[k][q].y});
             part[k * ntiles + tile] = df_to_double(x);
         }
     } else {
-        __shared__ double shd[2][PK_BLOCK];
+        __shared__ double shd[2][BLOCK];
 #pragma unroll
         for (int k = 0; k < NV; ++k) shd[k][threadIdx.x] = acc[k].value();
         __syncthreads();
         if (w < NV) {
             double x = 0.0;
 #pragma unroll
-            for (int q = 0; q < PK_BLOCK / 32; ++q) x += shd[w][lane + 32 * q];
+            for (int q = 0; q < BLOCK / 32; ++q) x += shd[w][lane + 32 * q];
             x = warp_sum(x);
             if (lane == 0) part[w * ntiles + tile] = x;
         }
@@ -317,7 +323,7 @@ __device__ __forceinline__ void pk_tile_partial(const DotAcc<V> (&acc)[NV], doub
 
 #define PK_TILES(nt) for (int t = 0; t < (nt); ++t)
 #define PK_ROWS(T) \
-    _Pragma("unroll 1") for (int64_t r0 = (T).r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < (T).r_end; r0 += int64_t(PK_BLOCK) * VecT<V>::R)
+    _Pragma("unroll 1") for (int64_t r0 = (T).r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < (T).r_end; r0 += int64_t(PKB_BLOCK) * VecT<V>::R)
 
 // ---------------------------------------------------------------------------------
 // One system: every block keeps the solver state
@@ -367,11 +373,11 @@ __device__ __forceinline__ bool pk1_allreduce(const PkArgs<V> &P, const DotAcc<V
                                               double (*s_p)[PK1_MAXG], double (&tot)[NV]) {
     __shared__ double s_tot[2];
     const int G = int(gridDim.x);
-    pk_tile_partial<V, NV>(acc, P.part, G, blockIdx.x);
+    pk_tile_partial<V, NV, PK1_BLOCK>(acc, P.part, G, blockIdx.x);
     if (!pk1_sync(P.bar, nbar)) return false;
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-        for (int q = threadIdx.x; q < G; q += PK_BLOCK) s_p[k][q] = __ldcg(P.part + int64_t(k) * G + q);
+        for (int q = threadIdx.x; q < G; q += PK1_BLOCK) s_p[k][q] = __ldcg(P.part + int64_t(k) * G + q);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w < NV) {
@@ -387,7 +393,7 @@ __device__ __forceinline__ bool pk1_allreduce(const PkArgs<V> &P, const DotAcc<V
 }
 
 #define PK1_ROWS \
-    _Pragma("unroll 1") for (int64_t r0 = T.r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < T.r_end; r0 += int64_t(PK_BLOCK) * VecT<V>::R)
+    _Pragma("unroll 1") for (int64_t r0 = T.r_begin + int64_t(threadIdx.x) * VecT<V>::R; r0 < T.r_end; r0 += int64_t(PK1_BLOCK) * VecT<V>::R)
 
 // The solve of one system, one tile per block (P.ntiles == gridDim.x), in the phases A, B1,
 // B2, C, D above from x = 0 until (r, r) <= rtol^2 (b, b), a breakdown, the iteration cap,
@@ -396,7 +402,7 @@ __device__ __forceinline__ bool pk1_allreduce(const PkArgs<V> &P, const DotAcc<V
 // (done = K_TIMEOUT when a barrier wait ran out; P.bar->err is then set too).  An inactive
 // system (P.active[0] == 0) returns at once.
 template <typename V>
-__global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solve1(PkArgs<V> P) {
+__global__ void __launch_bounds__(PK1_BLOCK, PK1_MIN_BLOCKS) pk_solve1(PkArgs<V> P) {
     using Op = PkOps<V>;
     constexpr int R = VecT<V>::R;
     __shared__ KState S;
@@ -583,7 +589,7 @@ __device__ __forceinline__ bool pkb_sync(PGrid *g, uint32_t &nbar, int has_live,
 template <typename V, int NV, typename U>
 __device__ __forceinline__ void pkb_sums(const PkArgs<V> &P, int nt, KState *st, const BTile *tl, U &&update) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int t = w; t < nt; t += PK_BLOCK / 32) {
+    for (int t = w; t < nt; t += PKB_BLOCK / 32) {
         if (st[t].done != K_RUNNING) continue;
         const int64_t t0 = tl[t].tile0;
         const int32_t n = tl[t].ntiles_inst;
@@ -607,7 +613,7 @@ __device__ __forceinline__ void pkb_sums(const PkArgs<V> &P, int nt, KState *st,
 // running tile.  The block owning a system's first tile writes its final state to P.st
 // (done = K_TIMEOUT when a barrier wait ran out; P.bar->err is then set too).
 template <typename V>
-__global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P) {
+__global__ void __launch_bounds__(PKB_BLOCK, PKB_MIN_BLOCKS) pk_solveb(PkArgs<V> P) {
     using Op = PkOps<V>;
     constexpr int R = VecT<V>::R;
     __shared__ KState s_st[PK_MAXT];
@@ -619,7 +625,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
     }
     const int nt = int64_t(blockIdx.x) < P.ntiles ? int((P.ntiles - blockIdx.x + G - 1) / G) : 0;
     const KVecs<V> &K = P.K;
-    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
+    for (int t = threadIdx.x; t < nt; t += PKB_BLOCK) {
         const BTile T = P.tiles[blockIdx.x + int64_t(t) * G];
         s_tl[t] = T;
         KState &S = s_st[t];
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
 #pragma unroll
                 for (int j = 0; j < R; ++j) acc[0].add(b.v[j], b.v[j]);
             }
-            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+            pk_tile_partial<V, 1, PKB_BLOCK>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
         }
     }
     bool ok = pkb_sync(P.bar, nbar, running(), live);
@@ -679,7 +685,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
 #pragma unroll
                 for (int j = 0; j < R; ++j) acc[0].add(rh.v[j], y.v[j]);
             }
-            pk_tile_partial<V, 1>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+            pk_tile_partial<V, 1, PKB_BLOCK>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
         }
         if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
         pkb_sums<V, 1>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
 #pragma unroll
                 for (int j = 0; j < R; ++j) { acc[0].add(y.v[j], s.v[j]); acc[1].add(y.v[j], y.v[j]); }
             }
-            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+            pk_tile_partial<V, 2, PKB_BLOCK>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
         }
         if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
         pkb_sums<V, 2>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
@@ -741,7 +747,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
                 stv(K.x + r0, x);
                 stv(K.r + r0, r);
             }
-            pk_tile_partial<V, 2>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
+            pk_tile_partial<V, 2, PKB_BLOCK>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G);
         }
         if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
         pkb_sums<V, 2>(P, nt, s_st, s_tl, [&](KState &S, int, const double *tot) {
@@ -763,7 +769,7 @@ __global__ void __launch_bounds__(PK_BLOCK, PK_MIN_BLOCKS) pk_solveb(PkArgs<V> P
         }
         if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
     }
-    for (int t = threadIdx.x; t < nt; t += PK_BLOCK) {
+    for (int t = threadIdx.x; t < nt; t += PKB_BLOCK) {
         if (blockIdx.x + int64_t(t) * G != s_tl[t].tile0) continue;
         KState F = s_st[t];
         if (!ok) F.done = K_TIMEOUT;
