@@ -92,3 +92,52 @@ def test_newton_parity_both_krylov_drivers(P, prec, persistent):
     # one kernel per BiCGStab solve on the persistent driver
     if persistent:
         assert st.kernel_launches < 20 * st.newton_iters + 10
+
+
+def test_single_system_grid_solve_with_ragged_tiles(P):
+    """The grid-wide persistent solve on 40 401 rows: about 250 row tiles, fewer than the
+    resident grid, the last one short; every block sums all partials itself.  The solution of
+    J x = b equals a direct solve."""
+    mesh, orc, h = _setup(P, 200, krylov_cluster=-1)
+    u = wl.random_vector(mesh.n_nodes, 15, 0.5) * (1 - mesh.dirichlet)
+    rp, cl = h.pattern()
+    vals = torch.empty(h.sizes.jac_nnz, device="cuda", dtype=torch.float64)
+    h.jacobian(cuda(u), vals)
+    torch.cuda.synchronize()
+    J = sp.csr_matrix((vals.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=(mesh.n_nodes, mesh.n_nodes))
+    rhs = wl.random_vector(mesh.n_nodes, 16)
+    sol = torch.zeros(mesh.n_nodes, device="cuda", dtype=torch.float64)
+    its = h.bicgstab(vals, cuda(rhs), sol, rtol=1e-12)
+    torch.cuda.synchronize()
+    ref = spla.spsolve(J.tocsc(), rhs)
+    assert its > 100
+    assert rel(sol.cpu().numpy(), ref) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_solve_with_many_tiles_per_instance(P, prec):
+    """Two instances cut into hundreds of tiles each (the batched solve's per-system sums run
+    over many tiles per lane) and a small third one: every instance's Newton solution equals
+    the single-system solve of that instance."""
+    ns = (150, 190, 12)
+    meshes = [wl.unit_square_mesh(n) for n in ns]
+    prob = P.make_problem(a=("pow", 2), a_degree=2)
+    mixed = prec == "mixed"
+    opts = dict(newton_rtol=1e-12 if not mixed else 1e-10, precision=P.PREC_MIXED if mixed else P.PREC_FP64)
+    loads = [oracle.Problem(m, a=("pow", 2), a_deg=2).load_vector(wl.mms_source) * (1 - m.dirichlet) for m in meshes]
+    hb = P.BatchHandle(meshes, prob, P.default_options(**opts))
+    d = hb.scatter(loads)
+    u = torch.zeros_like(d)
+    st = hb.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    got = hb.gather(u, [m.n_nodes for m in meshes])
+    for b, (m, ld) in enumerate(zip(meshes, loads)):
+        assert st[b].status == 0, b
+        h = P.Handle(m, prob, P.default_options(newton_rtol=1e-12))
+        ub = torch.zeros(m.n_nodes, device="cuda", dtype=torch.float64)
+        s1 = h.newton_solve(ub, cuda(ld))
+        torch.cuda.synchronize()
+        assert s1.status == 0
+        assert rel(got[b], ub.cpu().numpy()) <= (1e-8 if mixed else 1e-10), b
+        h.close()
+    hb.close()
