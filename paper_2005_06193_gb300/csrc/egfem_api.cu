@@ -1412,7 +1412,7 @@ __global__ void transpose_scaled_kernel(int64_t n, const SliceMeta *meta, const 
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int64_t t = tmap[q];
         if (t < 0) continue;
-        AT[t] = M_t(jsell[q] * dinv[col_idx[q]]);
+        AT[t] = (c == 0 && dinv[row] != 0.0) ? M_t(1) : M_t(jsell[q] * dinv[col_idx[q]]);   // unit diagonal
     }
 }
 

@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         const double v = (c == 0) ? diag : J[c * BLK];
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
-        const double sv = slot >= 0 ? dinv * v : 0.0;
+        // the scaled diagonal is stored as exactly 1 (the persistent FP64 solve relies on it)
+        const double sv = slot >= 0 ? (c == 0 && dinv != 0.0 ? 1.0 : dinv * v) : 0.0;
         if (A.a64) A.a64[q] = sv;
         if (A.a32) { rowsum += sv; A.a32[q] = float(sv); }
     }

@@ -472,7 +472,7 @@ __global__ void csr_to_sell_kernel(int64_t n, const SliceMeta *meta, const int32
     for (int c = 0; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int32_t s = col_slot[q];
-        const double a = s >= 0 ? vals[s] * dinv : 0.0;
+        const double a = s >= 0 ? (c == 0 && dinv != 0.0 ? 1.0 : vals[s] * dinv) : 0.0;   // unit diagonal
         rs += a;
         A[q] = M_t(a);
     }

@@ -175,20 +175,23 @@ __device__ __forceinline__ Pack<V> pk_spmv(const KVecs<V> &K, int64_t r0, const 
     using M_t = typename VecT<V>::mat;
     const SliceMeta M = K.meta[r0 / SLICE];
     const int lane = int(r0 % SLICE);
-    M_t a0[R];
-    ldm(K.A + M.col_base + lane, a0);
     // accumulators: FP64 y, or the double-float pair (hi, lo) in the difference form
-    // (column 0 holds the row sum s_i)
+    // (column 0 holds the row sum s_i).  The FP64 operator's column 0 is the Jacobi-scaled
+    // diagonal, stored as exactly 1 by every builder, so y starts at x_i without a load or a
+    // multiply (the same value a0 x_i would give).
     double y64[R];
     float hi[R], lo[R];
+    if constexpr (DF) {
+        M_t a0[R];
+        ldm(K.A + M.col_base + lane, a0);
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        if constexpr (DF) {
+        for (int j = 0; j < R; ++j) {
             hi[j] = __fmul_rn(a0[j], xi.v[j].hi);
             lo[j] = __fmaf_rn(a0[j], xi.v[j].lo, __fmaf_rn(a0[j], xi.v[j].hi, -hi[j]));
-        } else {
-            y64[j] = a0[j] * xi.v[j];
         }
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) y64[j] = xi.v[j];
     }
 #pragma unroll 4
     for (int c0 = 1; c0 < M.ncol; c0 += CH) {
