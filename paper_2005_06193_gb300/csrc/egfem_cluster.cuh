@@ -137,7 +137,8 @@ __device__ __forceinline__ df64 pkc_ld_remote(const df64 *p, uint32_t rank) {
 template <typename V> struct PkcRow;
 template <> struct PkcRow<double> {
     double y, xg;
-    __device__ __forceinline__ PkcRow(double a0, double x) : y(a0 * x), xg(x) {}
+    // column 0 is the Jacobi-scaled diagonal, stored as exactly 1: y starts at x (= a0 x)
+    __device__ __forceinline__ PkcRow(double, double x) : y(x), xg(x) {}
     __device__ __forceinline__ void add(double a, double xc) { y = fma(a, xc, y); }
     __device__ __forceinline__ double value() const { return y; }
 };
