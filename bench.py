@@ -41,7 +41,7 @@ DFMA_PER_SM_CLK = 2       # FP64 FMAs per SM per clock on GB300 (nominal 1.25 TF
 # DRAM bytes (read + write) per launch (per iteration for the persistent solve, pk_solve1) from
 # ncu captures of the current kernels; the captures and their commands are summarised in
 # profiles/pk_solve1_fp64_1024x1024_ncu.md.  Valid for the FP64 1024 x 1024 workload only.
-NCU_TRAFFIC = {"kry_persistent": 142.2e6}
+NCU_TRAFFIC = {"kry_persistent": 95.5e6}
 
 
 def load_peaks():

@@ -1646,7 +1646,9 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         const int32_t iters = 40;
         cudaError_t le = cudaSuccess;
         const bool cl = W.pkc_cluster > 0;
-        EG_TRY(timeit(cl ? "kry_cluster" : "kry_persistent", 2 * (CE * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CE + 22 * N, fp, [&] {
+        // the FP64 operator's unit diagonal is neither read nor multiplied (column 0 of each row)
+        const double CEo = std::is_same<V, double>::value ? CE - N : CE;
+        EG_TRY(timeit(cl ? "kry_cluster" : "kry_persistent", 2 * (CEo * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CEo + 22 * N, fp, [&] {
             if (launch_pk_single(h, W, 0.0, iters, 0) != EGFEM_OK) le = cudaErrorLaunchFailure;
         }));
         EG_CUDA(le);
