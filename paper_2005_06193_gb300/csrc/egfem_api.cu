@@ -66,7 +66,6 @@ struct KWork {
     int g_pk = 0;                         // blocks (0: not available)
     BTile *pk_tiles = nullptr;
     int64_t pk_ntiles = 0;
-    int64_t *pk_sys_t0 = nullptr;         // [1] = {0}
     double *pk_part = nullptr;            // [2 * pk_ntiles]
     PGrid *bar = nullptr;
     // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
@@ -150,7 +149,6 @@ struct egfem_t {
     double *bpart = nullptr;
     cudaGraphExec_t bgraph64 = nullptr, bgraph32 = nullptr;
     PGrid *bbar = nullptr;              // grid barrier of the persistent batched solve
-    int64_t *bsys_t0 = nullptr;         // first tile of each instance
     double *bpart2 = nullptr;           // tile partials of the persistent batched solve
     int bgraph_chunk = 0, bgraph_tiles = 0;
     // graph-resident batched Newton loop (egfem_gnewton.cuh): device state, the instantiated
@@ -407,7 +405,6 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
             W.g_pk = int(g);
             W.pk_ntiles = int64_t(T.size());
             EG_TRY(upload(W.pk_tiles, T));
-            EG_TRY(upload(W.pk_sys_t0, std::vector<int64_t>(1, 0)));
             EG_TRY(dalloc(W.pk_part, size_t(2 * W.pk_ntiles)));
             EG_TRY(dalloc(W.bar, 1));
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
@@ -470,12 +467,12 @@ egfem_status ensure_graph(egfem_t *h, KWork<V> &W) {
 
 // Cooperative launch of pk_solveb over the given tiles and systems.
 template <typename V>
-egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, int64_t ntiles, const int64_t *sys_t0,
-                       int32_t nsys, KState *st, double *part, const uint8_t *active, const double *rtol,
+egfem_status launch_pk(egfem_t *h, KWork<V> &W, int grid, const BTile *tiles, int64_t ntiles, KState *st, double *part,
+                       const uint8_t *active, const double *rtol,
                        double rtol0, PGrid *bar, int32_t maxit, int32_t stall) {
     PkArgs<V> P{};
     P.K = kvecs(h, W);
-    P.tiles = tiles; P.ntiles = ntiles; P.sys_t0 = sys_t0; P.nsys = nsys; P.st = st; P.part = part;
+    P.tiles = tiles; P.ntiles = ntiles; P.st = st; P.part = part;
     P.active = active; P.rtol = rtol; P.rtol0 = rtol0; P.bar = bar; P.maxit = maxit; P.stall = stall;
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(bar, 0, sizeof(PGrid), h->hs));
@@ -490,10 +487,10 @@ egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
                         const double *rtol_ptr = nullptr) {
     PkArgs<V> P{};
     P.K = kvecs(h, W);
-    P.tiles = W.pk_tiles; P.ntiles = W.pk_ntiles; P.sys_t0 = W.pk_sys_t0; P.nsys = 1; P.st = h->st;
+    P.tiles = W.pk_tiles; P.ntiles = W.pk_ntiles; P.st = h->st;
     P.part = W.pk_part; P.active = active; P.rtol = rtol_ptr; P.rtol0 = rtol; P.bar = W.bar; P.maxit = maxit; P.stall = stall;
     if (W.pk_ntiles < 1 || W.pk_ntiles > PK1_MAXG)   // no rows, or more blocks than it sums: the general kernel
-        return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, W.pk_sys_t0, 1, h->st, W.pk_part, active, rtol_ptr,
+        return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, h->st, W.pk_part, active, rtol_ptr,
                          rtol, W.bar, maxit, stall);
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
@@ -1085,15 +1082,15 @@ void egfem_destroy(egfem_handle h) {
     for (KWork<double> *W : {&h->k64}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_sys_t0); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
-    dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bsys_t0); dfree(h->bpart2);
+    dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bpart2);
     if (h->gn_exec) cudaGraphExecDestroy(h->gn_exec);
     dfree(h->gn_state); dfree(h->gn_stats); dfree(h->gn_loops);
     if (h->bgraph64) cudaGraphExecDestroy(h->bgraph64);
@@ -1795,10 +1792,8 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     const int64_t blocks = int64_t(std::min(nbk, 8)) * h->sms;
     const int64_t target = std::max<int64_t>(SLICE, (h->inst_off[h->nb] + blocks * factor - 1) / (blocks * factor));
     std::vector<BTile> T;
-    std::vector<int64_t> sys_t0(size_t(h->nb));
     for (int32_t b = 0; b < h->nb; ++b) {
         const int64_t t0 = int64_t(T.size());
-        sys_t0[size_t(b)] = t0;
         const int64_t lo = h->inst_off[b], hi = h->inst_off[b + 1];
         const int64_t nt = std::max<int64_t>(1, (hi - lo + target / 2) / target);
         const int64_t rows = ((hi - lo + nt - 1) / nt + SLICE - 1) / SLICE * SLICE;
@@ -1807,10 +1802,8 @@ egfem_status batch_tiles(egfem_t *h, int factor) {
     }
     dfree(h->tiles);
     dfree(h->bpart);
-    dfree(h->bsys_t0);
     dfree(h->bpart2);
     EG_TRY(upload(h->tiles, T));
-    EG_TRY(upload(h->bsys_t0, sys_t0));
     EG_TRY(dalloc(h->bpart2, size_t(2 * T.size())));
     h->ntiles = int64_t(T.size());
     // 3 slots x 2 values per tile, then one running count per block of the persistent solve
@@ -1879,7 +1872,7 @@ int pk_batch_grid(const egfem_t *h) {
 template <typename V>
 egfem_status launch_batch_persistent(egfem_t *h, KWork<V> &W, int grid, int32_t maxit, int32_t stall) {
     if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));
-    return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bsys_t0, h->nb, h->bst, h->bpart2,
+    return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bst, h->bpart2,
                      h->inst_mask, h->inst_eta, 0.0, h->bbar, maxit, stall);
 }
 

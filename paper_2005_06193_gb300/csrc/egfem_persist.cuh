@@ -55,10 +55,8 @@ constexpr int PKB_BLOCK = 256;  // threads per block of the batched kernel (4 re
 constexpr int PK_MAXT = 64;     // tiles per block
 
 struct PGrid {
-    uint32_t count;     // blocks arrived at the current barrier
-    uint32_t gen;       // barriers completed
-    int32_t err;        // nonzero: a wait ran out; every block leaves
-    int32_t running;    // systems still iterating (published at each summing barrier)
+    uint32_t count;     // pk_solve1: arrivals so far in this launch (the k-th barrier ends at k x blocks)
+    int32_t err;        // nonzero: a wait ran out (1) or too many tiles (2); every block leaves
     unsigned long long slot[3];   // pk_solveb: barrier k counts on slot k % 3 (arrivals | live blocks << 32)
 };
 
@@ -269,14 +267,12 @@ constexpr int PKB_MIN_BLOCKS = 4;
 template <typename V>
 struct PkArgs {
     KVecs<V> K;               // vectors and operator (K.st and K.part unused)
-    const BTile *tiles;       // tiles grouped by system, in row order
+    const BTile *tiles;       // tiles grouped by system, in row order (each knows its system and first tile)
     int64_t ntiles;
-    const int64_t *sys_t0;    // [nsys]: first tile of each system
-    int32_t nsys;
-    KState *st;               // [nsys] BiCGStab state (final state for the host)
+    KState *st;               // [systems] BiCGStab state (final state for the host)
     double *part;             // [2 * ntiles] tile partials
-    const uint8_t *active;    // [nsys] systems to solve, or null (all)
-    const double *rtol;       // [nsys] tolerances, or null (rtol0 for all)
+    const uint8_t *active;    // [systems] systems to solve, or null (all)
+    const double *rtol;       // [systems] tolerances, or null (rtol0 for all)
     double rtol0;
     PGrid *bar;
     int32_t maxit, stall;
