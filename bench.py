@@ -279,7 +279,7 @@ def p3_instances(count):
 
 def p3_batch(torch, P, dev, meshes, fs, **opts):
     prob = P.make_problem(a=("pow", 3), a_degree=3)
-    hb = P.BatchHandle(meshes, prob, P.default_options(precision=P.PREC_MIXED, **opts))
+    hb = P.BatchHandle(meshes, prob, P.default_options(**{"precision": P.PREC_MIXED, **opts}))
     d = torch.empty(hb.sizes.n_nodes, device=dev, dtype=torch.float64)
     hb.load_cellwise(torch.tensor(np.concatenate(fs), device=dev), d)
     return hb, d
