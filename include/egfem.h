@@ -142,13 +142,16 @@ typedef struct {
     double newton_rtol;      /* stop when ||r||_2 <= newton_rtol * ||r(u0)||_2 (default 1e-10) */
     double newton_atol;      /* ... or ||r||_2 <= newton_atol (default 0)                     */
     int32_t newton_maxit;    /* Newton step cap (default 50)                                  */
-    double eta_max;          /* largest Krylov forcing term (default 1e-2)                    */
+    double eta_max;          /* largest Krylov forcing term, and the first step's; 0 (default):
+                                0.9 for Newton (the cap Eisenstat and Walker give for choice
+                                2), 1e-2 for Picard                                           */
     double eta_min;          /* smallest Krylov forcing term (default 1e-12; mixed: 1e-6)     */
     int32_t krylov_maxit;    /* BiCGStab iteration cap per Newton step (default 100000)       */
     int32_t precision;       /* egfem_precision (default EGFEM_PREC_FP64)                    */
     int32_t op;              /* egfem_operator  (default EGFEM_OP_CSF)                       */
     int32_t graph_chunk;     /* BiCGStab iterations per captured CUDA graph (default 32)     */
-    int32_t fixed_eta;       /* nonzero: use eta_max for every step (no Eisenstat-Walker)    */
+    int32_t fixed_eta;       /* nonzero: use eta_max for every step (no Eisenstat-Walker; set
+                                eta_max to the wanted constant term)                          */
     int32_t krylov_persistent; /* nonzero (default): each BiCGStab solve is one cooperative
                                   launch with grid barriers; 0: graph-captured iteration
                                   kernels (graph_chunk iterations per graph launch)          */

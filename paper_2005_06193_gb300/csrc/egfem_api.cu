@@ -270,6 +270,14 @@ int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
     return launched;
 }
 
+// Largest Krylov forcing term, also the first step's: the option when set, else 0.9 for Newton
+// (Eisenstat and Walker's cap for choice 2) and 1e-2 for Picard, whose frozen-coefficient step
+// is no Newton direction and needs its linear solves tighter to decrease the residual.
+double eta_cap(const egfem_t *h) {
+    if (h->opts.eta_max > 0.0) return h->opts.eta_max;
+    return h->opts.iteration == EGFEM_ITER_PICARD ? 1e-2 : 0.9;
+}
+
 CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
     CsfArgs A{};
     A.n_rows = h->n;
@@ -926,7 +934,7 @@ egfem_status gn_build_one(egfem_t *h, KWork<V> &W, double *d_u, const double *d_
     G.kerr = W.pkc_cluster > 0 ? nullptr : &W.bar->err;
     G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
     G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
-    G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
+    G.eta_max = eta_cap(h); G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
     const unsigned gu = unsigned((h->n + 255) / 256);
     const int32_t stall = mixed ? kMixedStall : 0;
     int nodes = 0;
@@ -1039,7 +1047,7 @@ void egfem_default_options(egfem_options *o) {
     o->newton_rtol = 1e-10;
     o->newton_atol = 0.0;
     o->newton_maxit = 50;
-    o->eta_max = 1e-2;
+    o->eta_max = 0.0;   // the library's cap: eta_cap()
     o->eta_min = 1e-12;
     o->krylov_maxit = 100000;
     o->precision = EGFEM_PREC_FP64;
@@ -1279,7 +1287,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
     const double r0 = rn;
     S.res0 = r0;
     const double target = std::max(h->opts.newton_rtol * r0, h->opts.newton_atol);
-    double eta = h->opts.eta_max, rprev = rn;
+    double eta = eta_cap(h), rprev = rn;
     int k = 0;
     status = EGFEM_OK;
     // the Newton loop on the device (damping included); the host loop below resumes from its state
@@ -1323,7 +1331,7 @@ egfem_status egfem_newton_solve(egfem_handle h, double *d_u, const double *d_d, 
             double e = 0.9 * (rn / rprev) * (rn / rprev);
             const double sg = 0.9 * eta * eta;
             if (sg > 0.1) e = std::max(e, sg);
-            eta = std::min(h->opts.eta_max, e);
+            eta = std::min(eta_cap(h), e);
             eta = std::max(eta, 0.5 * target / rn);
         }
         eta = std::max(eta, h->opts.eta_min);
@@ -2018,7 +2026,7 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
     G.kerr = &h->bbar->err;
     G.max_loops = gn_max_loops(h->opts.newton_maxit); G.newton_maxit = h->opts.newton_maxit;
     G.fixed_eta = h->opts.fixed_eta; G.mixed = int(mixed);
-    G.eta_max = h->opts.eta_max; G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
+    G.eta_max = eta_cap(h); G.eta_min = h->opts.eta_min; G.eta_floor = mixed ? kMixedEtaFloor : 0.0; G.cond = cond;
     const unsigned gu = unsigned((h->n + 255) / 256);
     int nodes = 0;
     gn_pre<<<1, 256, 0, h->hs>>>(G);
@@ -2108,7 +2116,7 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<egfem_stats> S(nb);
     for (auto &x : S) std::memset(&x, 0, sizeof(x));
-    std::vector<double> rn(nb), rprev(nb), rbefore(nb), target(nb), eta(nb, h->opts.eta_max), lam(nb, 1.0);
+    std::vector<double> rn(nb), rprev(nb), rbefore(nb), target(nb), eta(nb, eta_cap(h)), lam(nb, 1.0);
     std::vector<int> active(nb, 0), fp32(nb, 0), pending(nb, 0), resume64(nb, 0);
     std::vector<int32_t> st(nb, EGFEM_OK);
     int64_t launches = 0;
@@ -2183,7 +2191,7 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
                 double e = 0.9 * (rn[b] / rprev[b]) * (rn[b] / rprev[b]);
                 const double sg = 0.9 * eta[b] * eta[b];
                 if (sg > 0.1) e = std::max(e, sg);
-                eta[b] = std::max(std::min(h->opts.eta_max, e), 0.5 * target[b] / rn[b]);
+                eta[b] = std::max(std::min(eta_cap(h), e), 0.5 * target[b] / rn[b]);
             }
             eta[b] = std::max(eta[b], h->opts.eta_min);
             fp32[b] = mixed ? 1 : 0;
