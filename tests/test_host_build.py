@@ -227,3 +227,17 @@ def test_empty_mesh_is_rejected(egf):
     with pytest.raises(egf.EgfemError) as e:
         egf.inspect_tensor(empty, egf.make_problem())
     assert e.value.status == 1
+
+
+def test_default_options_leave_the_choices_to_the_library(egf):
+    """The defaults the C library fills in (no GPU needed): the forcing-term cap 0 (the library
+    picks 0.9 for Newton, 1e-2 for Picard), Newton iteration, FP64, the CSF operator, the
+    persistent Krylov driver, the cluster solve where it fits and the graph Newton loop on."""
+    o = egf.default_options()
+    assert o.eta_max == 0.0 and o.eta_min == 1e-12
+    assert o.newton_rtol == 1e-10 and o.newton_maxit == 50 and o.krylov_maxit == 100000
+    assert o.iteration == egf.ITER_NEWTON and o.precision == egf.PREC_FP64 and o.op == egf.OP_CSF
+    assert o.krylov_persistent == 1 and o.krylov_cluster == 0 and o.newton_graph == 1 and o.fixed_eta == 0
+    # keyword overrides reach the structure
+    o2 = egf.default_options(eta_max=0.3, iteration=egf.ITER_PICARD)
+    assert o2.eta_max == 0.3 and o2.iteration == egf.ITER_PICARD
