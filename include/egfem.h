@@ -330,13 +330,14 @@ egfem_status egfem_inspect_tensor(const egfem_mesh *mesh, const egfem_problem *p
                                   int64_t *I, int64_t *M, int64_t *K, double *V, int64_t *n_wa, double *wa_coords);
 
 /* Self-test of the bounded device-side wait of the persistent BiCGStab solve (no handle).
- * Launches `blocks` blocks (1..64) of which the first `arrive` (0..blocks) enter one grid
- * barrier.  With arrive == blocks the launch is cooperative and every block must pass; with
- * arrive < blocks the barrier cannot complete and each waiting block gives up after wait_ms
- * milliseconds (0 < wait_ms <= 2000) and raises the barrier's error word.  ok_host (host,
- * [blocks]) receives 1 for a block that passed, 0 for one that gave up, -1 for one that did
- * not arrive; *err_host (host, optional) the error word.  Synchronous; allocates and frees
- * its own 0.3 KB of device memory.  Errors: EGFEM_ERR_INVALID_ARG for sizes out of range,
+ * Launches `blocks` blocks (1..64) of which the first `arrive` (0..blocks) enter the batched
+ * solve's grid barrier and then, if it completed with every block counted as live, the
+ * single-system solve's barrier.  With arrive == blocks the launch is cooperative and every
+ * block must pass both; with arrive < blocks the first barrier cannot complete and each waiting
+ * block gives up after wait_ms milliseconds (0 < wait_ms <= 2000) and raises the barriers' error
+ * word.  ok_host (host, [blocks]) receives 1 for a block that passed, 0 for one that gave up, -1
+ * for one that did not arrive; *err_host (host, optional) the error word.  Synchronous;
+ * allocates and frees its own device memory (under 0.5 KB).  Errors: EGFEM_ERR_INVALID_ARG for sizes out of range,
  * EGFEM_ERR_CUDA for a failed launch.  The paper has no counterpart: this checks the
  * library's own failure handling. */
 egfem_status egfem_selftest_grid_barrier(int32_t blocks, int32_t arrive, double wait_ms, int32_t *ok_host,
