@@ -20,15 +20,18 @@ from .egfem import BatchHandle
 class _NewtonSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, d, kappa, handle):
-        if kappa is not None:
-            handle.set_kappa(kappa.detach().contiguous())
+        # The handle holds one kappa state, which later forwards may change.  Record the field
+        # this solve used (None: the handle's constant kappa) and set it again before the adjoint,
+        # so the backward pass linearises at the coefficient that produced u*.
+        k_used = None if kappa is None else kappa.detach().contiguous().clone()
+        handle.set_kappa(k_used)
         u = torch.zeros_like(d)
         if isinstance(handle, BatchHandle):
             stats = handle.batch_newton_solve(u, d.detach().contiguous())
         else:
             stats = [handle.newton_solve(u, d.detach().contiguous())]
         ctx.handle = handle
-        ctx.has_kappa = kappa is not None
+        ctx.k_used = k_used
         ctx.stats = stats
         ctx.save_for_backward(u)
         return u
@@ -37,8 +40,9 @@ class _NewtonSolve(torch.autograd.Function):
     def backward(ctx, gu):
         (u,) = ctx.saved_tensors
         h = ctx.handle
+        h.set_kappa(ctx.k_used)
         lam = torch.zeros_like(u)
-        gk = torch.zeros(h.sizes.n_wa, device=u.device, dtype=u.dtype) if ctx.has_kappa else None
+        gk = torch.zeros(h.sizes.n_wa, device=u.device, dtype=u.dtype) if ctx.k_used is not None else None
         h.adjoint(u, gu.contiguous(), lam, gk)
         return lam, gk, None
 

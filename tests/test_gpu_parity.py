@@ -355,6 +355,47 @@ def test_autograd_adjoint_matches_central_differences_and_oracle(P, prec):
     assert rel(gk[perm], gk_ref) <= (1e-10 if prec == "fp64" else 1e-7)
 
 
+def test_autograd_interleaved_forwards_use_their_own_kappa(P):
+    """Two forwards on ONE handle with different kappa fields, then both backwards (the
+    second first): each gradient equals the gradient from a handle that saw only its own
+    forward (1e-12 relative).  A forward with kappa=None after a kappa field runs with the
+    handle's constant kappa again."""
+    mesh, pc, ud_np, opts = _adjoint_setup(P, 12, 4, None)
+    prob = P.make_problem(a=("pow", 2), a_degree=2)
+    h = P.Handle(mesh, prob, opts)
+    free, ud = cuda(1.0 - mesh.dirichlet), cuda(ud_np)
+    pc_t = torch.tensor(pc, device="cuda", dtype=torch.int64)
+    theta0 = cuda(wl.adjoint_theta(3, 4))
+    kappas = [1.0 + 0.5 * torch.rand(h.sizes.n_wa, device="cuda", dtype=torch.float64, generator=torch.Generator(
+        device="cuda").manual_seed(s)) for s in (1, 2)]
+
+    def grads(handle, ka):
+        th = theta0.clone().requires_grad_(True)
+        k = ka.clone().requires_grad_(True)
+        J, _ = _objective(P, handle, th, pc_t, ud, free, k)
+        return J, th, k
+
+    runs = [grads(h, ka) for ka in kappas]          # both forwards first
+    for J, _, _ in reversed(runs):                  # then the backwards, last forward first
+        J.backward()
+    for (J, th, k), ka in zip(runs, kappas):
+        hs = P.Handle(mesh, prob, opts)
+        Js, ths, ks = grads(hs, ka)
+        Js.backward()
+        assert rel(th.grad.cpu().numpy(), ths.grad.cpu().numpy()) <= 1e-12
+        assert rel(k.grad.cpu().numpy(), ks.grad.cpu().numpy()) <= 1e-12
+        hs.close()
+    # kappa=None after a field: the constant kappa (= 1) again, as on a fresh handle
+    from paper_2005_06193_gb300 import autograd as ag
+    d = ag.load_cellwise(theta0.reshape(-1)[pc_t], h)
+    u_none = ag.newton_solve(d, None, h)
+    hf = P.Handle(mesh, prob, opts)
+    u_fresh = ag.newton_solve(ag.load_cellwise(theta0.reshape(-1)[pc_t], hf), None, hf)
+    assert rel(u_none.detach().cpu().numpy(), u_fresh.detach().cpu().numpy()) <= 1e-12
+    h.close()
+    hf.close()
+
+
 def test_batched_adjoint_gradients_equal_single_instance(P):
     """Three instances on one mesh with different theta: the batched forward solve and the
     block-diagonal adjoint give each instance the gradient of its own single solve."""
