@@ -153,7 +153,10 @@ typedef struct {
     int32_t fixed_eta;       /* nonzero: use eta_max for every step (no Eisenstat-Walker; set
                                 eta_max to the wanted constant term)                          */
     int32_t krylov_persistent; /* nonzero (default): each BiCGStab solve is one cooperative
-                                  launch with grid barriers; 0: graph-captured iteration
+                                  launch with grid barriers; for one system it takes two grid
+                                  reductions per iteration, each block holding its rows' stencil
+                                  window in shared memory, where the windows fit (1: default);
+                                  2: the five-barrier form instead; 0: graph-captured iteration
                                   kernels (graph_chunk iterations per graph launch)          */
     int32_t iteration;       /* egfem_iteration of egfem_newton_solve / batch solve and the
                                 matrix egfem_jacobian returns (default EGFEM_ITER_NEWTON);
@@ -351,11 +354,14 @@ egfem_status egfem_selftest_grid_barrier(int32_t blocks, int32_t arrive, double 
  * completion ticket live in a fixed static device array of 65.8 KB that every GPU which
  * loads the library holds until the process exits.  At most 134,217,728 rows
  * (8192 blocks of 16384 rows); larger n returns EGFEM_ERR_INVALID_ARG.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU (different streams, or host threads) race and may
- * return wrong sums; the ticket is reset at the start of every call.  Asynchronous on
- * stream.  The paper has no counterpart: this is a deployment variant of the library's
+ * on a device (and the first after a cudaDeviceReset) looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  The sum is deterministic from call to call but is not bit-identical to the
+ * handle's own norm (different row partition; they agree to rounding).  All calls share the
+ * one array: calls that overlap on the GPU (different streams, or host threads) race, and
+ * may write a wrong sum or leave *d_out unwritten (stale), because one call's ticket reset
+ * can hide another call's last block; order the calls, for example on one stream.  The
+ * ticket is reset at the start of every call.  Asynchronous on stream.  The paper has no counterpart: this is a deployment variant of the library's
  * own residual-norm reduction. */
 egfem_status egfem_free_norm2_noalloc(int64_t n, const double *d_r, const uint8_t *d_dirichlet, double *d_out,
                                       egfem_stream stream);

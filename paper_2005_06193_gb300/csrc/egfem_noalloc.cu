@@ -4,10 +4,12 @@
 // all device memory to their own pool up front, or real-time loops where cudaMalloc's
 // implicit device synchronisation and latency are not acceptable.  This entry point
 // computes sum_{i : dirichlet[i] == 0} r_i^2 (the quantity of the Newton convergence test)
-// with the same deterministic two-stage reduction as the library's own norm kernel, but
-// its block partials and completion ticket live in a file-scope __device__ array that
+// by a deterministic two-stage reduction: repeatable from call to call, but not bit-identical
+// to the handle's own norm, which partitions the rows differently (the two agree to rounding).
+// Its block partials and completion ticket live in a file-scope __device__ array that
 // exists as soon as the library is loaded (every GPU that loads it holds the array until
 // the process exits).  It allocates nothing and needs no handle.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,11 +27,64 @@ constexpr int NA_MAX_BLOCKS = 8192;                              // block partia
 // (kept 256-byte aligned at the front of its own 256-byte slot)
 static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_BLOCKS + 32];
 
-// One set-up per device: the host-side name of the array is not a device address, so
-// the kernel receives the address that cudaGetSymbolAddress returns for the device.
+// Set-up once per device context: the host-side name of the array is not a device address,
+// so the kernel receives the address that cudaGetSymbolAddress returns with the device
+// current.  The address is cached with the id of the context it belongs to: after a
+// cudaDeviceReset the module is loaded into a new context (new id) and the address is looked
+// up again instead of reusing one that may now be unmapped or belong to another allocation.
+// The two driver calls come through the runtime's entry-point query, so the library does not
+// link the driver library itself.
 std::mutex g_na_mutex;
 constexpr int NA_MAX_DEVICES = 64;
-double *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+struct NaSlot { double *ptr; unsigned long long ctx_id; };
+NaSlot g_na[NA_MAX_DEVICES] = {};
+
+typedef CUresult (*NaCtxGetCurrent)(CUcontext *);
+typedef CUresult (*NaCtxGetId)(CUcontext, unsigned long long *);
+
+// id of the calling thread's current context; false when it cannot be read (no context yet,
+// or the driver does not offer the query), in which case nothing is cached
+bool na_current_ctx_id(unsigned long long &id) {
+    static NaCtxGetCurrent get_cur = nullptr;
+    static NaCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<NaCtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<NaCtxGetId>(f);
+    });
+    if (!get_cur || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, &id) == CUDA_SUCCESS;
+}
+
+// device address of the scratch array in the current device's context
+egfem_status na_scratch(int dev, double *&scratch) {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    unsigned long long id = 0;
+    const bool have_id = na_current_ctx_id(id);
+    if (have_id && g_na[dev].ptr && g_na[dev].ctx_id == id) {
+        scratch = g_na[dev].ptr;
+        return EGFEM_OK;
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        egfem::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return EGFEM_ERR_CUDA;
+    }
+    scratch = static_cast<double *>(p);
+    unsigned long long id2 = 0;   // the lookup above creates the context if none was current
+    g_na[dev] = na_current_ctx_id(id2) ? NaSlot{scratch, id2} : NaSlot{nullptr, 0ull};
+    return EGFEM_OK;
+}
 
 __device__ __forceinline__ double na_warp_sum(double x) {
 #pragma unroll
@@ -88,16 +143,8 @@ extern "C" egfem_status egfem_free_norm2_noalloc(int64_t n, const double *d_r, c
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) { egfem::set_last_error("no usable current device"); return EGFEM_ERR_CUDA; }
     double *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[dev]) {
-            void *p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) { egfem::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)); return EGFEM_ERR_CUDA; }
-            g_na_ptr[dev] = static_cast<double *>(p);
-        }
-        scratch = g_na_ptr[dev];
-    }
+    const egfem_status st = na_scratch(dev, scratch);
+    if (st != EGFEM_OK) return st;
     // the ticket must start at zero: a previous call may have been interrupted
     if (cudaMemsetAsync(scratch + NA_MAX_BLOCKS, 0, sizeof(uint32_t), (cudaStream_t)stream) != cudaSuccess) {
         egfem::set_last_error("cudaMemsetAsync of the ticket failed");

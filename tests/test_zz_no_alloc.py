@@ -47,7 +47,11 @@ def test_noalloc_norm_equals_newton_initial_residual_norm_twice():
         vals.append(float(out.item()))
         out.fill_(-1.0)
     assert st.res0 > 0
+    # independent check: the host's sum over the copied-back residual's free rows
+    rn = r.cpu().numpy()
+    host = float(np.sum(rn[mesh.dirichlet == 0] ** 2))
     for v in vals:
+        assert abs(v - host) <= 1e-12 * host
         assert abs(np.sqrt(v) - st.res0) <= 1e-12 * st.res0
     assert vals[0] == vals[1]
 
