@@ -671,7 +671,7 @@ def main():
     hbm = float(peaks["hbm_gbs"])
     fp64_peak = fp64_peak_tflops(peaks)
     counts = {"csf_fused": its["newton_iters"] + 1}
-    for k in ("kry_v", "kry_s", "kry_t", "kry_x", "kry_p", "kry_persistent", "kry_cluster"):
+    for k in ("kry_v", "kry_s", "kry_t", "kry_x", "kry_p", "kry_persistent", "kry_window", "kry_cluster"):
         counts[k] = its["krylov_iters"]
     share = {p["name"]: p["ms"] * counts.get(p["name"], 0) for p in prof}
     total_share = sum(share.values())
@@ -680,7 +680,7 @@ def main():
     if args.n != 1024:
         roofline["traffic"] = None   # the ncu capture is of the 1024 x 1024 workload
     roofline["share_of_solve"] = share[dom["name"]] / (ms_max / args.steps)
-    if dom["name"] in ("kry_persistent", "kry_cluster"):
+    if dom["name"] in ("kry_persistent", "kry_window", "kry_cluster"):
         roofline["units_per_launch"] = f"one launch runs a whole BiCGStab solve; ms and bytes are per iteration"
     csf = next(p for p in prof if p["name"] == "csf_fused")
     tensor_action = {"kernel": "csf_fused", "ms": csf["ms"], "achieved_gbs": csf["bytes"] / (csf["ms"] / 1e3) / 1e9,

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libegfem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["egfem_api.cu", "egfem_build.cpp", "egfem_noalloc.cu"]
-HEADERS = ["egfem_internal.h", "egfem_kernels.cuh", "egfem_krylov.cuh", "egfem_batch.cuh", "egfem_df64.cuh", "egfem_mf.cuh", "egfem_persist.cuh", "egfem_cluster.cuh", "egfem_gnewton.cuh"]
+HEADERS = ["egfem_internal.h", "egfem_kernels.cuh", "egfem_krylov.cuh", "egfem_batch.cuh", "egfem_df64.cuh", "egfem_mf.cuh", "egfem_persist.cuh", "egfem_window.cuh", "egfem_cluster.cuh", "egfem_gnewton.cuh"]
 
 
 def _nvcc() -> str:

@@ -18,6 +18,7 @@
 #include "egfem_batch.cuh"
 #include "egfem_mf.cuh"
 #include "egfem_persist.cuh"
+#include "egfem_window.cuh"
 #include "egfem_cluster.cuh"
 #include "egfem_gnewton.cuh"
 
@@ -66,8 +67,11 @@ struct KWork {
     int g_pk = 0;                         // blocks (0: not available)
     BTile *pk_tiles = nullptr;
     int64_t pk_ntiles = 0;
-    double *pk_part = nullptr;            // [2 * pk_ntiles]
+    double *pk_part = nullptr;            // [4 * pk_ntiles]
     PGrid *bar = nullptr;
+    // windowed single-system solve (pkw_solve): one window per tile; 0 bytes: not available
+    PkWin *pkw_win = nullptr;
+    size_t pkw_smem = 0;
     // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
     int pkc_cluster = 0;
     int32_t pkc_rows = 0;
@@ -378,6 +382,36 @@ egfem_status launch_pkc(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
     return EGFEM_OK;
 }
 
+// Windowed single-system solve plan: each tile's window (its rows and every column they touch)
+// must fit the shared memory of a block while all W.pk_ntiles blocks stay resident; leaves
+// W.pkw_smem = 0 (the five-barrier pk_solve1 is used) when it does not.
+template <typename V>
+egfem_status pkw_plan(egfem_t *h, KWork<V> &W) {
+    W.pkw_smem = 0;
+    if (W.pk_ntiles < 1 || W.pk_ntiles > PK1_MAXG) return EGFEM_OK;
+    EG_TRY(dalloc(W.pkw_win, size_t(W.pk_ntiles)));
+    pkw_window_kernel<V><<<unsigned(W.pk_ntiles), 256, 0, h->hs>>>(kvecs(h, W), h->n, W.pk_tiles, W.pkw_win);
+    EG_CUDA(cudaGetLastError());
+    std::vector<PkWin> win(size_t(W.pk_ntiles));
+    EG_CUDA(cudaMemcpyAsync(win.data(), W.pkw_win, win.size() * sizeof(PkWin), cudaMemcpyDeviceToHost, h->hs));
+    EG_CUDA(cudaStreamSynchronize(h->hs));
+    int64_t wmax = 0;
+    for (const PkWin &w : win) wmax = std::max(wmax, w.hi - w.lo);
+    const size_t smem = size_t(wmax) * sizeof(V);
+    int optin = 0;
+    EG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (smem == 0 || smem + 4096 > size_t(optin)) return EGFEM_OK;
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkw_solve<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pkw_solve<V>, PKW_BLOCK, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return EGFEM_OK;
+    }
+    if (int64_t(nb) * h->sms < W.pk_ntiles) return EGFEM_OK;
+    W.pkw_smem = smem;
+    return EGFEM_OK;
+}
+
 template <typename V>
 egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     if (W.ready) return EGFEM_OK;
@@ -390,7 +424,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
     EG_TRY(dalloc(W.A, size_t(h->csf.n_colentries)));
     EG_CUDA(cudaMemset(W.A, 0, size_t(h->csf.n_colentries) * sizeof(*W.A)));
     V **vec[] = {&W.b, &W.x, &W.r, &W.rh, &W.p, &W.v, &W.s, &W.t, &W.p2, &W.v2};
-    const int nvec = std::is_same<V, df64>::value ? 10 : 8;
+    const int nvec = 10;
     for (int k = 0; k < nvec; ++k) {
         EG_TRY(dalloc(*vec[k], size_t(h->n_pad)));
         EG_CUDA(cudaMemset(*vec[k], 0, size_t(h->n_pad) * sizeof(V)));
@@ -413,9 +447,10 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
             W.g_pk = int(g);
             W.pk_ntiles = int64_t(T.size());
             EG_TRY(upload(W.pk_tiles, T));
-            EG_TRY(dalloc(W.pk_part, size_t(2 * W.pk_ntiles)));
+            EG_TRY(dalloc(W.pk_part, size_t(4 * W.pk_ntiles)));
             EG_TRY(dalloc(W.bar, 1));
             EG_CUDA(cudaMemset(W.bar, 0, sizeof(PGrid)));
+            EG_TRY(pkw_plan<V>(h, W));
         }
     }
     EG_TRY(pkc_plan<V>(h, W));
@@ -500,6 +535,18 @@ egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
     if (W.pk_ntiles < 1 || W.pk_ntiles > PK1_MAXG)   // no rows, or more blocks than it sums: the general kernel
         return launch_pk(h, W, W.g_pk, W.pk_tiles, W.pk_ntiles, h->st, W.pk_part, active, rtol_ptr,
                          rtol, W.bar, maxit, stall);
+    if (W.pkw_smem > 0 && h->opts.krylov_persistent != 2) {
+        // two reductions per iteration, halo rows recomputed in shared-memory windows
+        PkwArgs<V> Q{};
+        Q.K = P.K; Q.p2 = W.p2; Q.v2 = W.v2; Q.tiles = W.pk_tiles; Q.win = W.pkw_win; Q.st = h->st;
+        Q.part = W.pk_part; Q.active = active; Q.rtol = rtol_ptr; Q.rtol0 = rtol; Q.bar = W.bar; Q.n = h->n; Q.maxit = maxit;
+        Q.stall = stall;
+        void *qargs[] = {(void *)&Q};
+        EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
+        EG_CUDA(cudaLaunchCooperativeKernel((const void *)pkw_solve<V>, dim3(unsigned(W.pk_ntiles)), dim3(PKW_BLOCK), qargs,
+                                            W.pkw_smem, h->hs));
+        return EGFEM_OK;
+    }
     void *args[] = {(void *)&P};
     EG_CUDA(cudaMemsetAsync(W.bar, 0, sizeof(PGrid), h->hs));
     // one block per tile (at most the resident grid W.g_pk)
@@ -1090,12 +1137,12 @@ void egfem_destroy(egfem_handle h) {
     for (KWork<double> *W : {&h->k64}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part); dfree(W->pkw_win);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
-        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part);
+        dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part); dfree(W->pkw_win);
     }
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
     dfree(h->bst); dfree(h->tiles); dfree(h->bpart); dfree(h->bbar); dfree(h->bpart2);
@@ -1651,9 +1698,15 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         const int32_t iters = 40;
         cudaError_t le = cudaSuccess;
         const bool cl = W.pkc_cluster > 0;
+        // windowed solve (pkw_solve): per row and iteration A reads s, t, p, v (window) and x, b,
+        // writes x, r, p, v; B reads r, v (window) and b, writes s, t (15 vector passes); the
+        // updates take 12 FP64 flops per row, the inner products run on the FP32 pipe
+        const bool win = !cl && W.pkw_smem > 0 && h->opts.krylov_persistent != 2 && W.pk_ntiles <= PK1_MAXG;
         // the FP64 operator's unit diagonal is neither read nor multiplied (column 0 of each row)
         const double CEo = std::is_same<V, double>::value ? CE - N : CE;
-        EG_TRY(timeit(cl ? "kry_cluster" : "kry_persistent", 2 * (CEo * mb + ce_nonuni * 4 + SM) + 19 * N * vb, 4 * CEo + 22 * N, fp, [&] {
+        const double kbytes = 2 * (CEo * mb + ce_nonuni * 4 + SM) + (win ? 15 : 19) * N * vb;
+        const double kflops = 4 * CEo + (win && fp ? 12 : 22) * N;
+        EG_TRY(timeit(cl ? "kry_cluster" : (win ? "kry_window" : "kry_persistent"), kbytes, kflops, fp, [&] {
             if (launch_pk_single(h, W, 0.0, iters, 0) != EGFEM_OK) le = cudaErrorLaunchFailure;
         }));
         EG_CUDA(le);

@@ -1,0 +1,463 @@
+// egfem_window.cuh -- BiCGStab (van der Vorst 1992) on one Jacobi-scaled system as one
+// persistent cooperative kernel with TWO grid-wide reductions per iteration.
+//
+// pk_solve1 separates its phases by five grid barriers per iteration: three for the inner
+// products and two because each operator application needs its neighbours' rows of the
+// vector it multiplies (s after B1, p after D).  Each barrier waits for the slowest block,
+// and the block sums that follow are a chain of L2 round trips, so at 1 M rows the FP64
+// iteration stalls on barriers about as long as it computes.
+//
+// Here block b owns one contiguous tile of rows [r_begin, r_end) and the WINDOW [w_lo, w_hi)
+// of every column its rows touch (the tile plus the stencil halo; 2D structured meshes in
+// lexicographic order: one grid line of the mesh on each side).  Before each operator
+// application the block evaluates the vector it multiplies on its whole window into shared
+// memory, recomputing the halo rows from vectors that every block finished before the last
+// reduction, with the same instructions the owners use, so the halo values are bit-identical
+// to the owners' values.  No barrier is then needed before an operator application, and the
+// inner products are regrouped so that each iteration has two reductions:
+//
+//   A_k (after G2 of k-1):  window: r_k = s - w t,  p_k = r_k + b (p_{k-1} - w v_{k-1})
+//                           tile:   x_k = x_{k-1} + a p_{k-1} + w s;  v_k = A p_k
+//                           sums:   (r_k, r_k), (rh, v_k)                       -> G1
+//       after G1: the convergence and failure tests on r_k (pk_solve1's, with the same
+//       quantities), then alpha_k = rho_k / (rh, v_k)
+//   B_k:                    window: s = r_k - alpha_k v_k
+//                           tile:   t = A s
+//                           sums:   (t, s), (t, t), (rh, s), (rh, t)            -> G2
+//       after G2: omega_k = (t, s) / (t, t), rho_{k+1} = (rh, s) - omega_k (rh, t) (equal to
+//       (rh, r_{k+1}) in exact arithmetic; r_{k+1} itself is formed only in A_{k+1}),
+//       beta_k = (rho_{k+1} / rho_k) (alpha_k / omega_k)
+//
+// x_0 = 0, so r_0 = p_0 = b and the shadow residual rh is b itself (not stored).  The
+// iteration count and the stopping decisions are those of the five-barrier form: the tests
+// on r_k run at G1 of step k, before alpha_k is used, and x_k is complete by then.  p and v
+// alternate between two buffers (a block reads p_{k-1} and v_{k-1} at its halo rows while
+// their owners write p_k and v_k); r, s and t are read at halo rows only after the reduction
+// that follows their writes.
+//
+// The barrier, its bounded wait and the timeout path are pk_solve1's (pk1_sync): every wait
+// ends after PK_WAIT_NS of %globaltimer at the latest, and the host reports the timeout.
+#pragma once
+
+#include "egfem_persist.cuh"
+
+namespace egfem {
+
+constexpr int PKW_BLOCK = 512;   // threads per block (2 resident per SM)
+constexpr int PKW_MIN_BLOCKS = 2;
+
+struct PkWin {
+    int64_t lo, hi;   // window rows [lo, hi), multiples of the thread row count
+};
+
+template <typename V>
+struct PkwArgs {
+    KVecs<V> K;               // x, r, p (p_k, even k), v (even k), s, t, b; K.rh unused (rh = b)
+    V *p2, *v2;               // p and v of odd k
+    const BTile *tiles;       // one tile per block
+    const PkWin *win;         // one window per block
+    KState *st;
+    double *part;             // [4 * gridDim.x] block partials
+    const uint8_t *active;    // [1] or null
+    const double *rtol;       // [1] or null (rtol0)
+    double rtol0;
+    PGrid *bar;
+    int64_t n;                // rows of the system (K.n_pad - n padding rows follow)
+    int32_t maxit, stall;
+};
+
+// Column indices of local column c for the R rows at r0, as row_cols, except that a padding row
+// (index >= n, all of its operator values zero) names itself: the builder gives padding rows
+// column 0, which lies outside any window but the first.
+template <typename V>
+__device__ __forceinline__ void pkw_cols(const KVecs<V> &K, const SliceMeta &M, int64_t r0, int64_t q, int c, int64_t n,
+                                         int32_t (&col)[VecT<V>::R]) {
+    row_cols(K, M, r0, q, c, col);
+    if (M.off_base < 0) {
+#pragma unroll
+        for (int j = 0; j < VecT<V>::R; ++j)
+            if (r0 + j >= n) col[j] = int32_t(r0 + j);
+    }
+}
+
+// y = A x for the R rows at r0, with x gathered from the shared-memory window xw (row j at
+// xw[j - lo]); xi = x at those rows; n = the system's rows (padding rows follow).  Arithmetic as
+// pk_spmv.
+template <typename V>
+__device__ __forceinline__ Pack<V> pkw_spmv(const KVecs<V> &K, int64_t r0, const V *xw, int64_t lo, int64_t n,
+                                            const Pack<V> &xi) {
+    constexpr int R = VecT<V>::R;
+    constexpr bool DF = std::is_same<V, df64>::value;
+    using M_t = typename VecT<V>::mat;
+    const SliceMeta M = K.meta[r0 / SLICE];
+    const int lane = int(r0 % SLICE);
+    double y64[R];
+    float hi[R], lo_[R];
+    if constexpr (DF) {
+        M_t a0[R];
+        ldm(K.A + M.col_base + lane, a0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            hi[j] = __fmul_rn(a0[j], xi.v[j].hi);
+            lo_[j] = __fmaf_rn(a0[j], xi.v[j].lo, __fmaf_rn(a0[j], xi.v[j].hi, -hi[j]));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) y64[j] = xi.v[j];
+    }
+#pragma unroll 4
+    for (int c = 1; c < M.ncol; ++c) {
+        const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
+        M_t a[R];
+        int32_t col[R];
+        ldm(K.A + q, a);
+        pkw_cols(K, M, r0, q, c, n, col);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const V xc = xw[col[j] - int32_t(lo)];
+            if constexpr (DF) df_acc_diff(hi[j], lo_[j], a[j], xc, xi.v[j]);
+            else y64[j] = fma(a[j], xc, y64[j]);
+        }
+    }
+    Pack<V> y;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if constexpr (DF) y.v[j] = df_fast_two_sum(hi[j], lo_[j]);
+        else y.v[j] = y64[j];
+    }
+    return y;
+}
+
+// x 2^-sc as a pair of floats (hi, lo) built from the bit pattern with integer operations (no
+// FP64 instruction): hi holds the leading 24 significand bits, lo the next 23 (lo = 0 below 2^-80
+// after scaling), so hi + lo equals x 2^-sc to a relative error below 2^-46.  Zero and values
+// below 2^-126 after scaling give (0, 0); infinities, NaN and values beyond the float range after
+// scaling give a non-finite hi, so a non-finite vector still makes the sums non-finite.
+__device__ __forceinline__ df64 split_dbl(double x, int sc) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned hi32 = unsigned(b >> 32), lo32 = unsigned(b);
+    const unsigned sign = hi32 & 0x80000000u;
+    const int eb = int((hi32 >> 20) & 0x7ffu);
+    const int e = eb - sc;
+    df64 r;
+    if (eb == 0x7ff || e > 1150) {
+        const bool nan = eb == 0x7ff && ((hi32 & 0xfffffu) | lo32) != 0u;
+        r.hi = __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+        r.lo = 0.f;
+    } else if (e < 897) {
+        r.hi = 0.f;
+        r.lo = 0.f;
+    } else {
+        r.hi = __uint_as_float(sign | (unsigned(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+        const float f = __fsub_rn(__uint_as_float(0x4B000000u | ((lo32 >> 6) & 0x7fffffu)), 8388608.0f);
+        r.lo = e >= 943 ? __fmul_rn(f, __uint_as_float(sign | (unsigned(e - 942) << 23))) : 0.f;
+    }
+    return r;
+}
+
+// Inner products of the solve: double-float accumulators on the FP32 pipe.  FP64 vectors enter
+// through split_dbl with the solve's scale (a power of two near the root mean square of b, so
+// that every product stays in the float range); double-float vectors enter as they are.
+template <typename V> struct PkwIn;
+template <> struct PkwIn<double> {
+    static __device__ __forceinline__ df64 get(double x, int sc) { return split_dbl(x, sc); }
+};
+template <> struct PkwIn<df64> {
+    static __device__ __forceinline__ df64 get(df64 x, int) { return x; }
+};
+
+// Grid sums of NV (2 or 4) accumulators (DotAcc<df64>, or DotAcc<double> for the first sums of an
+// FP64 solve), the same in every block: the block's per-thread values go to shared memory, warp w
+// adds chunk w / NV of value w % NV, and warp k < NV adds the chunk sums of value k and stores the
+// block partial in part[k * G + block] (double-float pairs in the 8-byte slots, or doubles); after
+// the barrier warp k adds the G partials of value k (lanes over partials in one fixed order, then
+// the warp's tree).  Every block thus computes the same sums in the same order, on the FP32 pipe
+// for double-float values.  false when the barrier's wait ran out.
+template <typename A, int NV>
+__device__ __forceinline__ bool pkw_allreduce(PGrid *bar, double *part, const A (&acc)[NV], uint32_t &nbar,
+                                              double (&tot)[NV]) {
+    constexpr bool DF = std::is_same<A, DotAcc<df64>>::value;
+    using T = typename std::conditional<DF, df64, double>::type;
+    constexpr int NW = PKW_BLOCK / 32, CH = NW / NV, PER = PKW_BLOCK / CH;
+    static_assert(NV == 2 || NV == 4, "two or four sums");
+    __shared__ __align__(16) T s_acc[NV * PKW_BLOCK];
+    __shared__ T s_ch[NV][CH];
+    __shared__ double s_tot[4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int G = int(gridDim.x);
+    auto add = [](T a, T b) -> T {
+        if constexpr (DF) return df_add(a, b);
+        else return a + b;
+    };
+    auto shfl = [](T a, int o) -> T {
+        if constexpr (DF) return shfl_xor_df(a, o);
+        else return __shfl_xor_sync(0xffffffffu, a, o);
+    };
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if constexpr (DF) s_acc[k * PKW_BLOCK + threadIdx.x] = df_two_sum(acc[k].hi, acc[k].lo);
+        else s_acc[k * PKW_BLOCK + threadIdx.x] = acc[k].value();
+    }
+    __syncthreads();
+    {
+        const int k = w % NV, c = w / NV;
+        T x = s_acc[k * PKW_BLOCK + c * PER + lane];
+#pragma unroll
+        for (int q = lane + 32; q < PER; q += 32) x = add(x, s_acc[k * PKW_BLOCK + c * PER + q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = add(x, shfl(x, o));
+        if (lane == 0) s_ch[k][c] = x;
+    }
+    __syncthreads();
+    if (w < NV && lane == 0) {
+        T x = s_ch[w][0];
+#pragma unroll
+        for (int c = 1; c < CH; ++c) x = add(x, s_ch[w][c]);
+        if constexpr (DF) reinterpret_cast<float2 *>(part)[int64_t(w) * G + blockIdx.x] = make_float2(x.hi, x.lo);
+        else part[int64_t(w) * G + blockIdx.x] = x;
+    }
+    if (!pk1_sync(bar, nbar)) return false;
+    if (w < NV) {
+        T x;
+        if constexpr (DF) x = df64{0.f, 0.f};
+        else x = 0.0;
+        for (int q = lane; q < G; q += 32) {
+            if constexpr (DF) {
+                const float2 t = __ldcg(reinterpret_cast<const float2 *>(part) + int64_t(w) * G + q);
+                x = df_add(x, df64{t.x, t.y});
+            } else {
+                x = x + __ldcg(part + int64_t(w) * G + q);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = add(x, shfl(x, o));
+        if constexpr (DF) { if (lane == 0) s_tot[w] = df_to_double(x); }
+        else { if (lane == 0) s_tot[w] = x; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s_tot[k];
+    return true;
+}
+
+// x + (a p + w s): two FMAs in FP64, the sloppy double-float sums for double-float vectors
+__device__ __forceinline__ double pkw_xupd(double x, double a, double p, double w, double s) { return fma(w, s, fma(a, p, x)); }
+__device__ __forceinline__ df64 pkw_xupd(df64 x, df64 a, df64 p, df64 w, df64 s) { return dfs_add(x, dfs_add(a * p, w * s)); }
+
+template <typename V>
+__global__ void __launch_bounds__(PKW_BLOCK, PKW_MIN_BLOCKS) pkw_solve(PkwArgs<V> P) {
+    using Op = PkOps<V>;
+    using In = PkwIn<V>;
+    constexpr int R = VecT<V>::R;
+    constexpr bool F64 = std::is_same<V, double>::value;
+    extern __shared__ __align__(16) unsigned char pkw_dyn[];
+    V *xw = reinterpret_cast<V *>(pkw_dyn);   // the window of the vector being multiplied
+    __shared__ KState S;
+    __shared__ double s_rho_next;
+    __shared__ int s_sc;                       // scale of the split inner products (FP64 solve)
+    __shared__ BTile T;
+    __shared__ PkWin Wn;
+    if (P.active && !P.active[0]) return;
+    const KVecs<V> &K = P.K;
+    if (threadIdx.x == 0) { T = P.tiles[blockIdx.x]; Wn = P.win[blockIdx.x]; s_sc = 0; }
+    __syncthreads();
+    const int64_t rb = T.r_begin, re = T.r_end, lo = Wn.lo, hi = Wn.hi;
+    uint32_t nbar = 0;
+    bool ok = true;
+    for (int32_t k = 0;; ++k) {
+        V *const p_old = (k & 1) ? K.p : P.p2, *const v_old = (k & 1) ? K.v : P.v2;
+        V *const p_new = (k & 1) ? P.p2 : K.p, *const v_new = (k & 1) ? P.v2 : K.v;
+        const int sc = s_sc;
+        // ---- A_k: r_k and p_k on the window, x_k on the tile; v_k = A p_k; (r_k, r_k), (rh, v_k)
+        {
+            const V al = cvt<V>(k ? S.alpha : 0.0), om = cvt<V>(k ? S.omega : 0.0), be = cvt<V>(k ? S.beta : 0.0);
+            DotAcc<df64> acc[2];
+            DotAcc<double> acc0[2];   // the first sums of an FP64 solve, which fix its scale
+#pragma unroll 1
+            for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(PKW_BLOCK) * R) {
+                Pack<V> rk, pk;
+                const bool own = j0 >= rb && j0 < re;
+                if (k == 0) {
+                    rk = ldv(K.b + j0);
+                    pk = rk;
+                    if (own) {
+                        Pack<V> z;
+#pragma unroll
+                        for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
+                        stv(K.x + j0, z);
+                    }
+                } else {
+                    const Pack<V> s = ldcv(K.s + j0), tv = ldcv(K.t + j0), po = ldcv(p_old + j0), vo = ldcv(v_old + j0);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        rk.v[j] = Op::sub(s.v[j], om * tv.v[j]);
+                        pk.v[j] = Op::add(rk.v[j], be * Op::sub(po.v[j], om * vo.v[j]));
+                    }
+                    if (own) {
+                        Pack<V> x = ldcv(K.x + j0);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) x.v[j] = pkw_xupd(x.v[j], al, po.v[j], om, s.v[j]);
+                        stv(K.x + j0, x);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) xw[j0 - lo + j] = pk.v[j];
+                if (own) {
+                    stv(K.r + j0, rk);
+                    stv(p_new + j0, pk);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        if (F64 && k == 0) acc0[0].add(to_d(rk.v[j]), to_d(rk.v[j]));
+                        else { const df64 q = In::get(rk.v[j], sc); acc[0].add(q, q); }
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(PKW_BLOCK) * R) {
+                Pack<V> pi;
+#pragma unroll
+                for (int j = 0; j < R; ++j) pi.v[j] = xw[r0 - lo + j];
+                const Pack<V> y = pkw_spmv(K, r0, xw, lo, P.n, pi);
+                stv(v_new + r0, y);
+                const Pack<V> rh = ldv(K.b + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (F64 && k == 0) acc0[1].add(to_d(rh.v[j]), to_d(y.v[j]));
+                    else acc[1].add(In::get(rh.v[j], sc), In::get(y.v[j], sc));
+                }
+            }
+            double tot[2];
+            if (F64 && k == 0) ok = pkw_allreduce<DotAcc<double>, 2>(P.bar, P.part, acc0, nbar, tot);
+            else ok = pkw_allreduce<DotAcc<df64>, 2>(P.bar, P.part, acc, nbar, tot);
+            if (!ok) break;
+            if (threadIdx.x == 0) {
+                const double f = F64 ? ldexp(1.0, sc) : 1.0;   // sums of split products carry 2^-2sc
+                const double rr = tot[0] * f * f, rv = tot[1] * f * f;
+                if (k == 0) {
+                    const double rt = P.rtol ? P.rtol[0] : P.rtol0;
+                    S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
+                    S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+                    S.rho = S.rr = S.rr0 = S.best_rr = rr;
+                    S.tol2 = rt * rt * rr;
+                    S.stall_rr = 4e-6 * rr;
+                    S.done = (rr == 0.0) ? K_CONVERGED : (!isfinite(rr) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
+                    // scale of the later inner products: 2^sc near the root mean square of b
+                    if (F64 && S.done == K_RUNNING) {
+                        int ex = 0;
+                        frexp(sqrt(rr / double(P.n > 0 ? P.n : 1)), &ex);
+                        s_sc = ex;
+                    }
+                } else {
+                    // the tests of pk_after_c on r_k; beta was formed at G2 and is used only if running
+                    const double rho1 = s_rho_next, beta = S.beta;
+                    pk_after_c(S, rho1, rr, P.maxit, P.stall);
+                    S.beta = beta;
+                }
+                if (S.done == K_RUNNING) {
+                    if (rv == 0.0 || !isfinite(rv)) S.done = isfinite(rv) ? K_BREAKDOWN : K_NONFINITE;
+                    else S.alpha = S.rho / rv;
+                }
+            }
+            __syncthreads();
+            if (S.done != K_RUNNING) break;
+        }
+        // ---- B_k: s on the window; t = A s; (t, s), (t, t), (rh, s), (rh, t)
+        {
+            const V al = cvt<V>(S.alpha);
+            const int scb = s_sc;
+            DotAcc<df64> acc[4];
+#pragma unroll 1
+            for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(PKW_BLOCK) * R) {
+                const Pack<V> r = ldcv(K.r + j0), v = ldcv(v_new + j0);
+                Pack<V> s;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    s.v[j] = Op::sub(r.v[j], al * v.v[j]);
+                    xw[j0 - lo + j] = s.v[j];
+                }
+                if (j0 >= rb && j0 < re) stv(K.s + j0, s);
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(PKW_BLOCK) * R) {
+                Pack<V> si;
+#pragma unroll
+                for (int j = 0; j < R; ++j) si.v[j] = xw[r0 - lo + j];
+                const Pack<V> y = pkw_spmv(K, r0, xw, lo, P.n, si);
+                stv(K.t + r0, y);
+                const Pack<V> rh = ldv(K.b + r0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const df64 qt = In::get(y.v[j], scb), qs = In::get(si.v[j], scb), qb = In::get(rh.v[j], scb);
+                    acc[0].add(qt, qs);
+                    acc[1].add(qt, qt);
+                    acc[2].add(qb, qs);
+                    acc[3].add(qb, qt);
+                }
+            }
+            double tot[4];
+            if (!(ok = pkw_allreduce<DotAcc<df64>, 4>(P.bar, P.part, acc, nbar, tot))) break;
+            if (threadIdx.x == 0) {
+                const double f = F64 ? ldexp(1.0, scb) : 1.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tot[q] = tot[q] * f * f;
+                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                    S.done = K_NONFINITE;
+                } else {
+                    S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+                    const double rho1 = tot[2] - S.omega * tot[3];
+                    s_rho_next = rho1;
+                    // a zero omega or rho ends the solve at the next tests, before beta is used
+                    S.beta = (S.omega != 0.0 && S.rho != 0.0) ? (rho1 / S.rho) * (S.alpha / S.omega) : 0.0;
+                }
+            }
+            __syncthreads();
+            if (S.done != K_RUNNING) break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        KState F = S;
+        if (!ok) F.done = K_TIMEOUT;
+        *P.st = F;
+    }
+}
+
+// Window of each tile: the smallest and largest column its rows touch, widened to the tile and
+// rounded to whole thread row groups.  One block per tile.
+template <typename V>
+__global__ void pkw_window_kernel(KVecs<V> K, int64_t n, const BTile *tiles, PkWin *win) {
+    __shared__ int64_t s_lo[8], s_hi[8];
+    const BTile T = tiles[blockIdx.x];
+    int64_t lo = T.r_begin, hi = T.r_end;
+    for (int64_t r = T.r_begin + threadIdx.x; r < T.r_end; r += blockDim.x) {
+        const SliceMeta M = K.meta[r / SLICE];
+        const int lane = int(r % SLICE);
+        for (int c = 0; c < M.ncol; ++c) {
+            int64_t col;
+            if (M.off_base >= 0) col = r + K.slice_off[M.off_base + c];
+            else col = r >= n ? r : K.col_idx[M.col_base + int64_t(c) * SLICE + lane];   // as pkw_cols
+            lo = col < lo ? col : lo;
+            hi = col + 1 > hi ? col + 1 : hi;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const int64_t a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) { s_lo[threadIdx.x >> 5] = lo; s_hi[threadIdx.x >> 5] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < int(blockDim.x >> 5); ++q) { lo = s_lo[q] < lo ? s_lo[q] : lo; hi = s_hi[q] > hi ? s_hi[q] : hi; }
+        if (lo > s_lo[0]) lo = s_lo[0];
+        if (hi < s_hi[0]) hi = s_hi[0];
+        constexpr int R = VecT<V>::R;
+        lo = lo / R * R;
+        hi = (hi + R - 1) / R * R;
+        if (hi > K.n_pad) hi = K.n_pad;
+        win[blockIdx.x] = PkWin{lo, hi};
+    }
+}
+
+}  // namespace egfem
