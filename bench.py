@@ -38,10 +38,6 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 SMS = 152                 # GB300 streaming multiprocessors
 DFMA_PER_SM_CLK = 2       # FP64 FMAs per SM per clock on GB300 (nominal 1.25 TFLOP/s FP64)
-# DRAM bytes (read + write) per launch (per iteration for the persistent solve, pk_solve1) from
-# ncu captures of the current kernels; the captures and their commands are summarised in
-# profiles/pk_solve1_fp64_1024x1024_ncu.md.  Valid for the FP64 1024 x 1024 workload only.
-NCU_TRAFFIC = {"kry_persistent": 95.5e6}
 
 
 def load_peaks():
@@ -63,9 +59,11 @@ def roofline_of(k, hbm, peak_kind, fp64_peak):
     sec = k["ms"] / 1e3
     gbs = k["bytes"] / sec / 1e9
     tf = k["flops"] / sec / 1e12
+    # DRAM traffic needs ncu counters, which a timed run does not collect: null here; the ncu
+    # captures of the kernels give it separately
     r = {"kernel": k["name"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
          "hbm_peak_kind": f"{peak_kind} (hbm_gbs, copy)",
-         "traffic": NCU_TRAFFIC.get(k["name"]), "bytes_per_launch": k["bytes"], "flops_per_launch": k["flops"]}
+         "traffic": None, "bytes_per_launch": k["bytes"], "flops_per_launch": k["flops"]}
     if k["fp64"] and tf / fp64_peak > gbs / hbm:
         r.update({"bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s", "frac": tf / fp64_peak,
                   "peak_kind": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock"})
@@ -145,38 +143,47 @@ def make_workload(n):
 # CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(n, newton_steps, krylov_iters, strip_rows=None, kry_sample=60):
-    """Seconds per Newton solve of the FP64 oracle on the n x n workload, estimated from a
-    strip of the grid: time the oracle's residual, Jacobian and BiCGStab iterations on the
-    strip's rows and scale by (all rows / strip rows) and by the Newton and Krylov
-    iteration counts of the solve being compared."""
-    import oracle
-    import workloads as wl
-    full = wl.unit_square_mesh(n)
-    rows = strip_rows or max(4, n // 4)
-    keep = np.where(wl.cell_centroids(full)[:, 1] < rows / n)[0]
-    cells = full.cells[keep]
-    nodes = np.unique(cells)
-    remap = -np.ones(full.n_nodes, dtype=np.int64)
-    remap[nodes] = np.arange(len(nodes))
-    mesh = wl.Mesh(2, full.coords[nodes], remap[cells].astype(np.int32), full.dirichlet[nodes])
-    P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
-    cen = wl.cell_centroids(mesh)
-    b = P.load_vector_cellwise(wl.mms_source(cen[:, 0], cen[:, 1])) * (1 - mesh.dirichlet)
-    u = wl.random_vector(mesh.n_nodes, 1, 0.5) * (1 - mesh.dirichlet)
-    t0 = time.perf_counter()
-    P.residual(u, b, form="diff")
-    J = P.jacobian(u)
-    t_step = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.bicgstab(J, b, rtol=0.0, maxit=kry_sample)
-    t_kry = (time.perf_counter() - t0) / kry_sample
-    scale = full.n_nodes / mesh.n_nodes
-    per_solve = scale * ((newton_steps + 1) * t_step + krylov_iters * t_kry)
-    sample = (f"{rows}-row strip of the {n}x{n} grid ({mesh.n_nodes} of {full.n_nodes} nodes): residual+Jacobian once "
-              f"and {kry_sample} BiCGStab iterations timed, scaled by node count to {newton_steps} Newton steps and "
-              f"{krylov_iters} BiCGStab iterations per solve")
-    return per_solve, t_step + kry_sample * t_kry, sample
+class OracleSample:
+    """The FP64 CPU oracle on a bounded sample of the n x n workload: a strip of `strip_rows`
+    grid rows (set up once, untimed).  step() times the oracle's residual and Jacobian once and
+    `kry_sample` BiCGStab iterations on the strip and returns (seconds the step took, the
+    estimated seconds of one whole Newton solve): the strip's times scaled by (all nodes / strip
+    nodes) and by the Newton and Krylov iteration counts of the solve being compared.  The
+    BiCGStab loops run on the oracle's OpenMP threads (results independent of their number);
+    the residual and Jacobian assembly are single-threaded."""
+
+    def __init__(self, n, newton_steps, krylov_iters, strip_rows=64, kry_sample=60):
+        import oracle
+        import workloads as wl
+        self.oracle = oracle
+        full = wl.unit_square_mesh(n)
+        keep = np.where(wl.cell_centroids(full)[:, 1] < strip_rows / n)[0]
+        cells = full.cells[keep]
+        nodes = np.unique(cells)
+        remap = -np.ones(full.n_nodes, dtype=np.int64)
+        remap[nodes] = np.arange(len(nodes))
+        mesh = wl.Mesh(2, full.coords[nodes], remap[cells].astype(np.int32), full.dirichlet[nodes])
+        self.P = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2)
+        cen = wl.cell_centroids(mesh)
+        self.b = self.P.load_vector_cellwise(wl.mms_source(cen[:, 0], cen[:, 1])) * (1 - mesh.dirichlet)
+        self.u = wl.random_vector(mesh.n_nodes, 1, 0.5) * (1 - mesh.dirichlet)
+        self.scale = full.n_nodes / mesh.n_nodes
+        self.newton_steps, self.krylov_iters, self.kry_sample = newton_steps, krylov_iters, kry_sample
+        self.desc = (f"{strip_rows}-row strip of the {n}x{n} grid ({mesh.n_nodes} of {full.n_nodes} nodes): residual, "
+                     f"Jacobian and {kry_sample} BiCGStab iterations timed per step, scaled by node count to "
+                     f"{newton_steps} Newton steps and {krylov_iters} BiCGStab iterations per solve")
+
+    def step(self, threads):
+        self.oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        self.P.residual(self.u, self.b, form="diff")
+        J = self.P.jacobian(self.u)
+        t1 = time.perf_counter()
+        self.oracle.bicgstab(J, self.b, rtol=0.0, maxit=self.kry_sample)
+        t2 = time.perf_counter()
+        t_kry = (t2 - t1) / self.kry_sample
+        per_solve = self.scale * ((self.newton_steps + 1) * (t1 - t0) + self.krylov_iters * t_kry)
+        return t2 - t0, per_solve
 
 
 def run_reference(args):
@@ -185,23 +192,27 @@ def run_reference(args):
         return
     n = args.n
     # Newton/Krylov counts of the FP64 solve on this workload (the means of the library's timed
-    # steps on the GPU: 7 Newton steps and about 2935 BiCGStab iterations per solve)
+    # steps on the GPU)
     steps, kry = args.ref_newton_steps, args.ref_krylov_iters
-    times = []
+    threads = os.cpu_count() or 1
+    S = OracleSample(n, steps, kry)
     for _ in range(args.warmup):
-        oracle_sample(n, steps, kry)
-    sample = ""
+        S.step(threads)
+    secs, per = [], []
     for _ in range(args.steps):
-        per_solve, _, sample = oracle_sample(n, steps, kry)
-        times.append(per_solve)
-    mean = float(np.mean(times))
-    value = 1.0 / mean
+        a, b = S.step(threads)
+        secs.append(a)
+        per.append(b)
+    value = 1.0 / float(np.mean(per))
     line = {"impl": "reference", "metric": "newton_solves_per_s", "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"egfem_newton_2d_p1p2_u2_{n}x{n}", "grid": n, "w_space": "P2",
-                       "newton_rtol": 1e-10, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+                       "newton_rtol": 1e-10, "parallelism": "replicas",
+                       "step": "one bounded sample of the solve (see cpu_baseline.sample); value = solves/s "
+                               "extrapolated from the samples"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "nproc": os.cpu_count(),
+                             "kind": "oracle", "sample": S.desc},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -337,7 +348,8 @@ def batched_p3_extra(torch, P, dev, count, barrier):
         t_plain += time.perf_counter() - t0
         h.close()
     hb.close()
-    return {"workload": f"first {count} of the 256 seeded instances, n in [64, 512], P1/P3 u^3",
+    return {"workload": (f"the 256 seeded instances, n in [64, 512], P1/P3 u^3" if count == 256 else
+                         f"first {count} of the 256 seeded instances, n in [64, 512], P1/P3 u^3"),
             "unit": "solves/s", "plain_fp64_sequential": count / t_plain, "batched_mixed": count / t_batch,
             "speedup": t_plain / t_batch, "all_converged_1e-10": ok,
             "rows": int(hb.sizes.n_nodes)}
@@ -517,6 +529,28 @@ def next_row_extra(torch, P, dev, n, steps, barrier, setup, workload, hbm, fp64_
     return out
 
 
+def latency_c1(torch, P, dev, reps, barrier, n=32):
+    """The 32 x 32 workload (1089 P1, 4225 P2 nodes; the whole problem sits in L2): FP64 Newton
+    solves per second with the library's defaults (one-cluster BiCGStab, graph-resident Newton
+    loop), same source and target as the 1024 x 1024 line."""
+    mesh, f_cell = make_workload(n)
+    h = P.Handle(mesh, P.make_problem(a=("pow", 2), a_degree=2), P.default_options())
+    f = torch.tensor(f_cell, device=dev, dtype=torch.float64)
+    d = torch.empty(mesh.n_nodes, device=dev, dtype=torch.float64)
+    h.load_cellwise(f, d)
+    u = torch.zeros_like(d)
+    for _ in range(3):
+        u.zero_()
+        h.newton_solve(u, d)
+    ms, stats = timed_solves(torch, h, [d], u, reps, barrier)
+    st = stats[-1]
+    out = {"workload": f"egfem_newton_2d_p1p2_u2_{n}x{n}", "value": reps / (ms / 1e3), "unit": "solves/s",
+           "ms_per_step": ms / reps, **mean_iters(stats), "final_rel_residual": st.res_final / st.res0,
+           "krylov_driver": "cluster" if h.options.krylov_cluster >= 0 else "grid", "newton_loop": "graph"}
+    h.close()
+    return out
+
+
 def whole_job_rate(dist, world, units, ms, device):
     """Units per second for the whole job: every rank's `units` over the slowest rank's time
     (`ms` is this rank's time; the maximum over ranks is taken with an all-reduce).  Returns
@@ -574,9 +608,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the gradient-coefficient and I_k lines")
     ap.add_argument("--no-bratu", action="store_true", help="skip the 64^3 Bratu line")
-    ap.add_argument("--batch-instances", type=int, default=16)
+    ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-n", type=int, default=512)
-    ap.add_argument("--p3-instances", type=int, default=32)
+    ap.add_argument("--p3-instances", type=int, default=256)
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=2935)
     ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch"],
@@ -677,12 +711,19 @@ def main():
     total_share = sum(share.values())
     dom = max(prof, key=lambda p: share[p["name"]])
     roofline = roofline_of(dom, hbm, peak_kind, fp64_peak)
-    if args.n != 1024:
-        roofline["traffic"] = None   # the ncu capture is of the 1024 x 1024 workload
     roofline["share_of_solve"] = share[dom["name"]] / (ms_max / args.steps)
     if dom["name"] in ("kry_persistent", "kry_window", "kry_cluster"):
         roofline["units_per_launch"] = f"one launch runs a whole BiCGStab solve; ms and bytes are per iteration"
     csf = next(p for p in prof if p["name"] == "csf_fused")
+    # second half of the metric: the tensor action (nodal pass + fused residual / Jacobian fill)
+    # against HBM, with the FP64 pipe (its binding unit) beside it
+    ta_gbs = csf["bytes"] / (csf["ms"] / 1e3) / 1e9
+    ta_tf = csf["flops"] / (csf["ms"] / 1e3) / 1e12
+    roofline_ta = {"kernel": "wnode_kernel + csf_fused_kernel (residual + Jacobian fill, FP64)", "bound": "hbm",
+                   "achieved": ta_gbs, "peak": hbm, "unit": "GB/s", "frac": ta_gbs / hbm, "traffic": None,
+                   "peak_kind": f"{peak_kind} (hbm_gbs, copy)", "bytes_per_launch": csf["bytes"], "ms": csf["ms"],
+                   "fp64_tflops": ta_tf, "fp64_frac": ta_tf / fp64_peak,
+                   "fp64_peak_kind": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}
     tensor_action = {"kernel": "csf_fused", "ms": csf["ms"], "achieved_gbs": csf["bytes"] / (csf["ms"] / 1e3) / 1e9,
                      "frac_hbm": csf["bytes"] / (csf["ms"] / 1e3) / 1e9 / hbm,
                      "fp64_tflops": csf["flops"] / (csf["ms"] / 1e3) / 1e12,
@@ -713,7 +754,8 @@ def main():
            "final_rel_residual": st.res_final / st.res0,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * mesh.n_nodes,
                    "d2h_bytes_per_step": 8 * mesh.n_nodes},
-           "gpu_launches": launches, "roofline": roofline, "tensor_action": tensor_action, "clocks": clocks,
+           "gpu_launches": launches, "roofline": roofline, "roofline_tensor_action": roofline_ta,
+           "tensor_action": tensor_action, "clocks": clocks,
            "kernels": [{**p, "share": share[p["name"]] / total_share} for p in prof],
            "fp64_graph_driver": graph_driver}
 
@@ -726,6 +768,8 @@ def main():
                                 "ms_per_step": msl / args.steps, **mean_iters(sgl),
                                 "gpu_launches_per_solve": int(sgl[-1].kernel_launches)}
     hgl.close()
+
+    out["latency_32x32"] = latency_c1(torch, P, dev, max(args.steps, 20), barrier)
 
     if not args.no_mixed:
         hm = P.Handle(mesh, prob, P.default_options(precision=P.PREC_MIXED, newton_graph=0))
@@ -788,9 +832,13 @@ def main():
         out["batched_p3"] = batched_p3_extra(torch, P, dev, args.p3_instances, barrier)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_solve, cpu_s, sample = oracle_sample(args.n, int(round(its["newton_iters"])), int(round(its["krylov_iters"])))
-        out["cpu_baseline"] = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                               "sample": sample, "sample_cpu_seconds": cpu_s}
+        S = OracleSample(args.n, int(round(its["newton_iters"])), int(round(its["krylov_iters"])))
+        threads = os.cpu_count() or 1
+        s_all, per_all = S.step(threads)
+        s_one, per_one = S.step(1)
+        out["cpu_baseline"] = {"value": 1.0 / per_all, "unit": "solves/s", "cores": threads, "nproc": os.cpu_count(),
+                               "kind": "oracle", "sample": S.desc, "sample_seconds": s_all,
+                               "value_1_thread": 1.0 / per_one, "sample_seconds_1_thread": s_one}
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()

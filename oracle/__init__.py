@@ -51,11 +51,12 @@ _c_lp = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags only) into oracle/_build/liborc.so."""
+    """Compile the oracle with gcc (portable flags only, OpenMP for the BiCGStab loops) into
+    oracle/_build/liborc.so."""
     os.makedirs(os.path.dirname(_LIBPATH), exist_ok=True)
     if force or not os.path.exists(_LIBPATH) or os.path.getmtime(_LIBPATH) < os.path.getmtime(_SRC):
         tmp = _LIBPATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-fopenmp", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIBPATH)
     return _LIBPATH
 
@@ -110,6 +111,8 @@ def lib():
             L.orc_bicgstab.argtypes = [ctypes.c_int, ctypes.c_int64, _c_lp, _c_lp, _c_dp, _c_dp, _c_dp,
                                        ctypes.c_double, ctypes.c_int, _c_ip, _c_dp]
             L.orc_bicgstab.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_get_threads.restype = ctypes.c_int
             L.orc_newton.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_dp, _c_dp, _c_dp,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, _c_dp, _c_dp, _c_ip]
             L.orc_newton.restype = ctypes.c_int
@@ -350,6 +353,17 @@ def band_solve(A, rhs):
     if st != 0:
         raise RuntimeError(f"band solve failed with code {st}")
     return x
+
+
+def set_threads(n: int) -> int:
+    """Use n OpenMP threads in the oracle's BiCGStab (its results do not depend on n); returns
+    the thread count now in effect."""
+    lib().orc_set_threads(int(n))
+    return int(lib().orc_get_threads())
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def bicgstab(A, rhs, rtol=1e-12, maxit=100000, x0=None):

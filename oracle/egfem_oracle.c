@@ -48,6 +48,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 3
 #define ORC_MAXNB 20   /* P3 in 3D has 20 local basis functions */
@@ -1173,14 +1176,47 @@ int orc_band_solve(int n, int kl, int ku, int64_t nnz, const int64_t *I, const i
     return 0;
 }
 
-static double dot(int n, const double *a, const double *b) { double s = 0; for (int i = 0; i < n; ++i) s += a[i] * b[i]; return s; }
+/* Inner product as ORC_DOT_CHUNKS contiguous partial sums added in chunk order: the same
+ * result for any number of OpenMP threads (the chunks, not the threads, fix the order). */
+#define ORC_DOT_CHUNKS 64
+static double dot(int n, const double *a, const double *b) {
+    double part[ORC_DOT_CHUNKS];
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < ORC_DOT_CHUNKS; ++c) {
+        const int lo = (int)((int64_t)n * c / ORC_DOT_CHUNKS), hi = (int)((int64_t)n * (c + 1) / ORC_DOT_CHUNKS);
+        double s = 0;
+        for (int i = lo; i < hi; ++i) s += a[i] * b[i];
+        part[c] = s;
+    }
+    double s = 0;
+    for (int c = 0; c < ORC_DOT_CHUNKS; ++c) s += part[c];
+    return s;
+}
 
+/* y = A x, one row at a time (rows split across OpenMP threads; each row summed in order) */
 static void csr_matvec(int n, const int64_t *rp, const int64_t *ci, const double *v, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) { double s = 0; for (int64_t t = rp[i]; t < rp[i + 1]; ++t) s += v[t] * x[ci[t]]; y[i] = s; }
 }
 
 /* Right-preconditioned BiCGStab (van der Vorst 1992) with M = diag(A)^{-1}.
  * A in sorted COO (row-major).  Stops when ||b - A x|| <= rtol ||b||.  x in: guess. */
+/* OpenMP threads of the oracle's parallel loops (results do not depend on it) */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 int orc_bicgstab(int n, int64_t nnz, const int64_t *I, const int64_t *L, const double *V,
                  const double *b, double *x, double rtol, int maxit, int *iters, double *relres) {
     int64_t *rp = calloc(n + 1, sizeof(int64_t));
@@ -1203,15 +1239,18 @@ int orc_bicgstab(int n, int64_t nnz, const int64_t *I, const int64_t *L, const d
         double rho1 = dot(n, rh, r);
         if (rho1 == 0.0) { status = -5; break; }
         double beta = (rho1 / rho) * (alpha / omega);
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) { p[i] = r[i] + beta * (p[i] - omega * v[i]); ph[i] = D[i] * p[i]; }
         csr_matvec(n, rp, L, V, ph, v);
         double rv = dot(n, rh, v);
         if (rv == 0.0) { status = -5; break; }
         alpha = rho1 / rv;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) { s[i] = r[i] - alpha * v[i]; sh[i] = D[i] * s[i]; }
         csr_matvec(n, rp, L, V, sh, t);
         double tt = dot(n, t, t);
         omega = tt == 0.0 ? 0.0 : dot(n, t, s) / tt;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) { x[i] += alpha * ph[i] + omega * sh[i]; r[i] = s[i] - omega * t[i]; }
         rho = rho1;
         ++it;
