@@ -286,10 +286,17 @@ egfem_status egfem_profile_kernels(egfem_handle h, const double *d_u, const doub
  * motivated by the repeated forward/backward solves of optimal control, Sec. 6):
  *   J(u*)^T lambda = dj/du  on free rows, lambda = 0 on Dirichlet rows;
  *   dj/dd_i = lambda_i (free rows);  dj/dkappa_m = -sum_{i,k} lambda_i T_imk u_k.
- * The transposed system is solved by FP64 Jacobi-BiCGStab to 1e-13 relative in either
- * precision of the handle; on a batch handle every instance runs its own BiCGStab (own
- * scalars and convergence test) within one persistent launch.  d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa]
- * out (may be NULL).  Synchronises the stream. */
+ * The Jacobi-scaled transposed system (D J^T) lambda = D dj/du is solved by FP64 Jacobi-
+ * BiCGStab in either precision of the handle, with true-residual restarts: each round forms
+ * res = D dj/du - D J^T lambda in FP64 and solves for the correction with a fresh shadow
+ * residual, until ||res|| <= 1e-13 ||D dj/du|| or a round no longer halves ||res|| (its FP64
+ * floor, about eps |D J^T| |lambda|), at most 5 rounds; on a batch handle every instance
+ * runs its own BiCGStab (own scalars, convergence test and rounds) within one persistent
+ * launch per round.  stats->res0 and stats->res_final receive ||D dj/du|| and the final true
+ * ||res|| (over all instances), stats->krylov_iters the iterations of all rounds.
+ * EGFEM_ERR_NOT_CONVERGED when the rounds end above 1e-10 relative while still improving.
+ * d_dJdu[n_nodes] in; d_lambda[n_nodes] out; d_grad_kappa[n_wa] out (may be NULL).
+ * Synchronises the stream. */
 egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJdu, double *d_lambda,
                            double *d_grad_kappa, egfem_stats *stats, egfem_stream stream);
 
