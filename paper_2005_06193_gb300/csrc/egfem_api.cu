@@ -72,6 +72,14 @@ struct KWork {
     // windowed single-system solve (pkw_solve): one window per tile; 0 bytes: not available
     PkWin *pkw_win = nullptr;
     size_t pkw_smem = 0;
+    // windowed batched solve (pkwb_solve): its own tiles (inside instances) and windows
+    BTile *pkwb_tiles = nullptr;
+    PkWin *pkwb_win = nullptr;
+    double *pkwb_part = nullptr;          // [4 * pkwb_ntiles]
+    int64_t pkwb_ntiles = 0;
+    int pkwb_grid = 0;
+    size_t pkwb_smem = 0;                 // 0: not available
+    bool pkwb_planned = false;            // planned with the batch layout in place
     // cluster solve (pkc_solve, FP64): CTAs in the cluster (0: not used) and rows per CTA
     int pkc_cluster = 0;
     int32_t pkc_rows = 0;
@@ -409,7 +417,7 @@ egfem_status pkw_plan(egfem_t *h, KWork<V> &W) {
         if (tl[t].r_end > tl[t].r_begin) tile_min = std::min(tile_min, tl[t].r_end - tl[t].r_begin);
     }
     if (halo_max > 2 * tile_min && W.pk_ntiles > 1) return EGFEM_OK;
-    const size_t smem = size_t(wmax) * sizeof(V);
+    const size_t smem = std::max(size_t(wmax) * sizeof(V), PKW_STAGE_BYTES);
     int optin = 0;
     EG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     if (smem == 0 || smem + 4096 > size_t(optin)) return EGFEM_OK;
@@ -424,9 +432,69 @@ egfem_status pkw_plan(egfem_t *h, KWork<V> &W) {
     return EGFEM_OK;
 }
 
+// Windowed batched solve plan: tiles of 1024 to 4096 rows (about four per block, equal within an
+// instance), each tile's window in shared memory with every block resident and a halo of at
+// most twice the tile; leaves W.pkwb_smem = 0 (pk_solveb is used) when it does not fit.
+template <typename V>
+egfem_status pkwb_plan(egfem_t *h, KWork<V> &W) {
+    W.pkwb_smem = 0;
+    if (h->nb < 1) return EGFEM_OK;   // egfem_batch_build sets the layout after the first allocation
+    W.pkwb_planned = true;
+    if (!h->coop || h->opts.krylov_persistent != 1) return EGFEM_OK;
+    int optin = 0;
+    EG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const int64_t G0 = int64_t(PKWB_MIN_BLOCKS) * h->sms;
+    const int64_t total = h->inst_off[h->nb];
+    const int64_t target = std::min<int64_t>(4096, std::max<int64_t>(1024, (total + 4 * G0 - 1) / (4 * G0)));
+    std::vector<BTile> T;
+    for (int32_t b = 0; b < h->nb; ++b) {
+        const int64_t t0 = int64_t(T.size());
+        const int64_t lo = h->inst_off[b], hi = h->inst_off[b + 1];
+        const int64_t nt = std::max<int64_t>(1, (hi - lo + target - 1) / target);
+        const int64_t rows = ((hi - lo + nt - 1) / nt + SLICE - 1) / SLICE * SLICE;
+        for (int64_t r = lo; r < hi; r += rows) T.push_back(BTile{r, std::min(hi, r + rows), t0, b, 0});
+        for (size_t q = size_t(t0); q < T.size(); ++q) T[q].ntiles_inst = int32_t(T.size() - size_t(t0));
+    }
+    const int64_t nt = int64_t(T.size());
+    const int64_t G = std::min<int64_t>(G0, nt);
+    if ((nt + G - 1) / G > PKWB_MAXT) return EGFEM_OK;
+    for (void *q : {(void *)W.pkwb_tiles, (void *)W.pkwb_win, (void *)W.pkwb_part}) if (q) cudaFree(q);
+    W.pkwb_tiles = nullptr; W.pkwb_win = nullptr; W.pkwb_part = nullptr;
+    EG_TRY(upload(W.pkwb_tiles, T));
+    EG_TRY(dalloc(W.pkwb_win, size_t(nt)));
+    EG_TRY(dalloc(W.pkwb_part, size_t(4 * nt)));
+    pkw_window_kernel<V><<<unsigned(nt), 256, 0, h->hs>>>(kvecs(h, W), h->n, W.pkwb_tiles, W.pkwb_win);
+    EG_CUDA(cudaGetLastError());
+    std::vector<PkWin> win(static_cast<size_t>(nt));
+    EG_CUDA(cudaMemcpyAsync(win.data(), W.pkwb_win, win.size() * sizeof(PkWin), cudaMemcpyDeviceToHost, h->hs));
+    EG_CUDA(cudaStreamSynchronize(h->hs));
+    int64_t wmax = 0;
+    for (size_t t = 0; t < win.size(); ++t) {
+        const int64_t w = win[t].hi - win[t].lo, own = T[t].r_end - T[t].r_begin;
+        wmax = std::max(wmax, w);
+        if (w - own > 2 * own && T[t].ntiles_inst > 1) return EGFEM_OK;
+    }
+    const size_t smem = std::max(size_t(wmax) * sizeof(V), PKW_STAGE_BYTES);
+    if (smem + 4096 > size_t(optin)) return EGFEM_OK;
+    EG_CUDA(cudaFuncSetAttribute((const void *)pkwb_solve<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pkwb_solve<V>, PKWB_BLOCK, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return EGFEM_OK;
+    }
+    if (int64_t(nb) * h->sms < G) return EGFEM_OK;
+    W.pkwb_ntiles = nt;
+    W.pkwb_grid = int(G);
+    W.pkwb_smem = smem;
+    return EGFEM_OK;
+}
+
 template <typename V>
 egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
-    if (W.ready) return EGFEM_OK;
+    if (W.ready) {
+        if (h->nb > 0 && !W.pkwb_planned) EG_TRY(pkwb_plan<V>(h, W));
+        return EGFEM_OK;
+    }
     W.g_setup = one_wave<V>(h, (const void *)kry_setup<V>);
     W.g_v = one_wave<V>(h, (const void *)kry_v<V>);
     W.g_s = one_wave<V>(h, (const void *)kry_s<V>);
@@ -466,6 +534,7 @@ egfem_status kwork_alloc(egfem_t *h, KWork<V> &W) {
         }
     }
     EG_TRY(pkc_plan<V>(h, W));
+    EG_TRY(pkwb_plan<V>(h, W));
     if constexpr (std::is_same<V, df64>::value) {
         W.g_vp = one_wave<V>(h, (const void *)kry_vp<V>);
         W.g_st = one_wave<V>(h, (const void *)kry_st<V>);
@@ -550,7 +619,7 @@ egfem_status launch_pk1(egfem_t *h, KWork<V> &W, double rtol, int32_t maxit, int
     if (W.pkw_smem > 0 && h->opts.krylov_persistent != 2) {
         // two reductions per iteration, halo rows recomputed in shared-memory windows
         PkwArgs<V> Q{};
-        Q.K = P.K; Q.p2 = W.p2; Q.v2 = W.v2; Q.tiles = W.pk_tiles; Q.win = W.pkw_win; Q.st = h->st;
+        Q.K = P.K; Q.p2 = W.p2; Q.v2 = W.v2; Q.tiles = W.pk_tiles; Q.win = W.pkw_win; Q.ntiles = W.pk_ntiles; Q.st = h->st;
         Q.part = W.pk_part; Q.active = active; Q.rtol = rtol_ptr; Q.rtol0 = rtol; Q.bar = W.bar; Q.n = h->n; Q.maxit = maxit;
         Q.stall = stall;
         void *qargs[] = {(void *)&Q};
@@ -1150,11 +1219,13 @@ void egfem_destroy(egfem_handle h) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
         dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part); dfree(W->pkw_win);
+        dfree(W->pkwb_tiles); dfree(W->pkwb_win); dfree(W->pkwb_part);
     }
     for (KWork<df64> *W : {&h->k32}) {
         if (W->graph) cudaGraphExecDestroy(W->graph);
         dfree(W->A); dfree(W->b); dfree(W->x); dfree(W->r); dfree(W->rh); dfree(W->p); dfree(W->v); dfree(W->s); dfree(W->t);
         dfree(W->p2); dfree(W->v2); dfree(W->bar); dfree(W->pk_tiles); dfree(W->pk_part); dfree(W->pkw_win);
+        dfree(W->pkwb_tiles); dfree(W->pkwb_win); dfree(W->pkwb_part);
     }
     dfree(h->adj_b0); dfree(h->adj_acc); dfree(h->adj_ss);
     dfree(h->slice_inst); dfree(h->inst_mask); dfree(h->inst_eta); dfree(h->inst_lam); dfree(h->inst_norm2);
@@ -2043,7 +2114,15 @@ egfem_status batch_graph(egfem_t *h, KWork<V> &W, cudaGraphExec_t &G) {
 // tiles; 0 when that solve cannot run (no cooperative launch, option off, or more than
 // PK_MAXT tiles per block at the current tile size).
 template <typename V>
+const KWork<V> &kwork_of(const egfem_t *h);
+template <>
+const KWork<double> &kwork_of<double>(const egfem_t *h) { return h->k64; }
+template <>
+const KWork<df64> &kwork_of<df64>(const egfem_t *h) { return h->k32; }
+
+template <typename V>
 int pk_batch_grid(const egfem_t *h) {
+    if (kwork_of<V>(h).pkwb_smem > 0 && h->opts.krylov_persistent == 1) return kwork_of<V>(h).pkwb_grid;   // windowed
     if (!h->coop || !h->opts.krylov_persistent || h->ntiles < 1) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)pk_solveb<V>, PKB_BLOCK, 0) != cudaSuccess || nb < 1)
@@ -2056,6 +2135,18 @@ int pk_batch_grid(const egfem_t *h) {
 template <typename V>
 egfem_status launch_batch_persistent(egfem_t *h, KWork<V> &W, int grid, int32_t maxit, int32_t stall) {
     if (!h->bbar) EG_TRY(dalloc(h->bbar, 1));
+    if (W.pkwb_smem > 0 && h->opts.krylov_persistent == 1) {
+        // two reductions per iteration, each tile's halo recomputed in a shared-memory window
+        PkwArgs<V> Q{};
+        Q.K = kvecs(h, W); Q.p2 = W.p2; Q.v2 = W.v2; Q.tiles = W.pkwb_tiles; Q.win = W.pkwb_win;
+        Q.ntiles = W.pkwb_ntiles; Q.st = h->bst; Q.part = W.pkwb_part; Q.active = h->inst_mask; Q.rtol = h->inst_eta;
+        Q.rtol0 = 0.0; Q.bar = h->bbar; Q.n = h->n; Q.maxit = maxit; Q.stall = stall;
+        void *qargs[] = {(void *)&Q};
+        EG_CUDA(cudaMemsetAsync(h->bbar, 0, sizeof(PGrid), h->hs));
+        EG_CUDA(cudaLaunchCooperativeKernel((const void *)pkwb_solve<V>, dim3(unsigned(W.pkwb_grid)), dim3(PKWB_BLOCK),
+                                            qargs, W.pkwb_smem, h->hs));
+        return EGFEM_OK;
+    }
     return launch_pk(h, W, grid, h->tiles, h->ntiles, h->bst, h->bpart2,
                      h->inst_mask, h->inst_eta, 0.0, h->bbar, maxit, stall);
 }
@@ -2286,8 +2377,9 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
         if (mixed) A0.a32 = h->k32.A;
         launch_csf(h, A0, h->hs);
         if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
-        if (mixed) EG_TRY(autotune_tiles<df64>(h, h->k32));
-        else EG_TRY(autotune_tiles<double>(h, h->k64));
+        // the tile autotuner times the five-barrier batched solve; the windowed one plans its own tiles
+        if (mixed) EG_TRY(h->k32.pkwb_smem > 0 ? batch_tiles<df64>(h, 4) : autotune_tiles<df64>(h, h->k32));
+        else EG_TRY(h->k64.pkwb_smem > 0 ? batch_tiles<double>(h, 4) : autotune_tiles<double>(h, h->k64));
     }
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<egfem_stats> S(nb);

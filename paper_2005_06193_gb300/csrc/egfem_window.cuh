@@ -37,14 +37,26 @@
 //
 // The barrier, its bounded wait and the timeout path are pk_solve1's (pk1_sync): every wait
 // ends after PK_WAIT_NS of %globaltimer at the latest, and the host reports the timeout.
+//
+// pkwb_solve is the same iteration for a batch of independent systems (block-diagonal
+// operator, instances of uneven size), as pk_solveb is for pk_solve1: tiles lie inside one
+// instance and are dealt to blocks round-robin; a block takes its tiles one after another in
+// each phase (one window in shared memory at a time), keeps the state of each owned tile's
+// system, and after each barrier adds all partials of that system (pkb_sync's barrier, which
+// also counts the blocks that still own a running tile and so ends the loop).
 #pragma once
 
 #include "egfem_persist.cuh"
 
 namespace egfem {
 
-constexpr int PKW_BLOCK = 512;   // threads per block (2 resident per SM)
+constexpr int PKW_BLOCK = 512;    // threads per block of the one-system kernel (2 resident per SM)
 constexpr int PKW_MIN_BLOCKS = 2;
+constexpr int PKWB_BLOCK = 512;   // threads per block of the batched kernel (2 resident per SM)
+constexpr int PKWB_MIN_BLOCKS = 2;
+// shared memory of a block's reduction staging, carved from the window buffer (free while a tile's
+// partials are formed): the window allocation is at least this large
+constexpr size_t PKW_STAGE_BYTES = 4 * PKW_BLOCK * sizeof(double);
 
 struct PkWin {
     int64_t lo, hi;   // window rows [lo, hi), multiples of the thread row count
@@ -54,15 +66,16 @@ template <typename V>
 struct PkwArgs {
     KVecs<V> K;               // x, r, p (p_k, even k), v (even k), s, t, b; K.rh unused (rh = b)
     V *p2, *v2;               // p and v of odd k
-    const BTile *tiles;       // one tile per block
-    const PkWin *win;         // one window per block
-    KState *st;
-    double *part;             // [4 * gridDim.x] block partials
-    const uint8_t *active;    // [1] or null
-    const double *rtol;       // [1] or null (rtol0)
+    const BTile *tiles;       // pkw_solve: one tile per block; pkwb_solve: tiles grouped by system
+    const PkWin *win;         // one window per tile
+    int64_t ntiles;
+    KState *st;               // [systems] final states
+    double *part;             // [4 * G] (pkw_solve) or [4 * ntiles] (pkwb_solve) partials
+    const uint8_t *active;    // [systems] or null (all)
+    const double *rtol;       // [systems] or null (rtol0)
     double rtol0;
     PGrid *bar;
-    int64_t n;                // rows of the system (K.n_pad - n padding rows follow)
+    int64_t n;                // rows of the (batch) system (K.n_pad - n padding rows follow)
     int32_t maxit, stall;
 };
 
@@ -156,7 +169,7 @@ __device__ __forceinline__ df64 split_dbl(double x, int sc) {
 }
 
 // Inner products of the solve: double-float accumulators on the FP32 pipe.  FP64 vectors enter
-// through split_dbl with the solve's scale (a power of two near the root mean square of b, so
+// through split_dbl with the system's scale (a power of two near the root mean square of b, so
 // that every product stays in the float range); double-float vectors enter as they are.
 template <typename V> struct PkwIn;
 template <> struct PkwIn<double> {
@@ -166,95 +179,260 @@ template <> struct PkwIn<df64> {
     static __device__ __forceinline__ df64 get(df64 x, int) { return x; }
 };
 
-// Grid sums of NV (2 or 4) accumulators (DotAcc<df64>, or DotAcc<double> for the first sums of an
-// FP64 solve), the same in every block: the block's per-thread values go to shared memory, warp w
-// adds chunk w / NV of value w % NV, and warp k < NV adds the chunk sums of value k and stores the
-// block partial in part[k * G + block] (double-float pairs in the 8-byte slots, or doubles); after
-// the barrier warp k adds the G partials of value k (lanes over partials in one fixed order, then
-// the warp's tree).  Every block thus computes the same sums in the same order, on the FP32 pipe
-// for double-float values.  false when the barrier's wait ran out.
-template <typename A, int NV>
-__device__ __forceinline__ bool pkw_allreduce(PGrid *bar, double *part, const A (&acc)[NV], uint32_t &nbar,
-                                              double (&tot)[NV]) {
+// Block partials of NV (2 or 4) accumulators (DotAcc<df64>, or DotAcc<double> for the first sums
+// of an FP64 solve): the per-thread values go to shared memory (`stage`, PKW_STAGE_BYTES of the
+// window buffer, which no thread reads any more), warp w adds chunk w / NV of value
+// w % NV, and warp k < NV adds the chunk sums of value k and stores it in part[k * stride +
+// index] (double-float pairs in the 8-byte slots, or doubles).  One fixed order, on the FP32
+// pipe for double-float values.  Ends with the stores issued (the caller's barrier orders them).
+template <int BLOCK, typename A, int NV>
+__device__ __forceinline__ void pkw_block_partial(const A (&acc)[NV], double *part, int64_t stride, int64_t index,
+                                                  void *stage) {
     constexpr bool DF = std::is_same<A, DotAcc<df64>>::value;
     using T = typename std::conditional<DF, df64, double>::type;
-    constexpr int NW = PKW_BLOCK / 32, CH = NW / NV, PER = PKW_BLOCK / CH;
+    constexpr int NW = BLOCK / 32, CH = NW / NV, PER = BLOCK / CH;
     static_assert(NV == 2 || NV == 4, "two or four sums");
-    __shared__ __align__(16) T s_acc[NV * PKW_BLOCK];
+    static_assert(PER % 32 == 0, "whole warps per chunk");
+    static_assert(NV * BLOCK * sizeof(T) <= PKW_STAGE_BYTES, "staging fits the window buffer");
+    T *s_acc = reinterpret_cast<T *>(stage);
     __shared__ T s_ch[NV][CH];
-    __shared__ double s_tot[4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int G = int(gridDim.x);
-    auto add = [](T a, T b) -> T {
-        if constexpr (DF) return df_add(a, b);
-        else return a + b;
-    };
-    auto shfl = [](T a, int o) -> T {
-        if constexpr (DF) return shfl_xor_df(a, o);
-        else return __shfl_xor_sync(0xffffffffu, a, o);
-    };
+    __syncthreads();   // the window's readers (and the previous partial's readers of s_ch) are done
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        if constexpr (DF) s_acc[k * PKW_BLOCK + threadIdx.x] = df_two_sum(acc[k].hi, acc[k].lo);
-        else s_acc[k * PKW_BLOCK + threadIdx.x] = acc[k].value();
+        if constexpr (DF) s_acc[k * BLOCK + threadIdx.x] = df_two_sum(acc[k].hi, acc[k].lo);
+        else s_acc[k * BLOCK + threadIdx.x] = acc[k].value();
     }
     __syncthreads();
     {
         const int k = w % NV, c = w / NV;
-        T x = s_acc[k * PKW_BLOCK + c * PER + lane];
+        T x = s_acc[k * BLOCK + c * PER + lane];
 #pragma unroll
-        for (int q = lane + 32; q < PER; q += 32) x = add(x, s_acc[k * PKW_BLOCK + c * PER + q]);
+        for (int q = lane + 32; q < PER; q += 32) {
+            if constexpr (DF) x = df_add(x, s_acc[k * BLOCK + c * PER + q]);
+            else x = x + s_acc[k * BLOCK + c * PER + q];
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = add(x, shfl(x, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            if constexpr (DF) x = df_add(x, shfl_xor_df(x, o));
+            else x = x + __shfl_xor_sync(0xffffffffu, x, o);
+        }
         if (lane == 0) s_ch[k][c] = x;
     }
     __syncthreads();
     if (w < NV && lane == 0) {
         T x = s_ch[w][0];
 #pragma unroll
-        for (int c = 1; c < CH; ++c) x = add(x, s_ch[w][c]);
-        if constexpr (DF) reinterpret_cast<float2 *>(part)[int64_t(w) * G + blockIdx.x] = make_float2(x.hi, x.lo);
-        else part[int64_t(w) * G + blockIdx.x] = x;
+        for (int c = 1; c < CH; ++c) {
+            if constexpr (DF) x = df_add(x, s_ch[w][c]);
+            else x = x + s_ch[w][c];
+        }
+        if constexpr (DF) reinterpret_cast<float2 *>(part)[int64_t(w) * stride + index] = make_float2(x.hi, x.lo);
+        else part[int64_t(w) * stride + index] = x;
     }
-    if (!pk1_sync(bar, nbar)) return false;
-    if (w < NV) {
-        T x;
-        if constexpr (DF) x = df64{0.f, 0.f};
-        else x = 0.0;
-        for (int q = lane; q < G; q += 32) {
-            if constexpr (DF) {
-                const float2 t = __ldcg(reinterpret_cast<const float2 *>(part) + int64_t(w) * G + q);
-                x = df_add(x, df64{t.x, t.y});
-            } else {
-                x = x + __ldcg(part + int64_t(w) * G + q);
-            }
+}
+
+// One warp: the sum of the n partials part[k * stride + q0 .. q0 + n) in one fixed order (lanes
+// over partials, then the warp's tree), in double-float (DF) or FP64; every lane returns it.
+template <bool DF>
+__device__ __forceinline__ double pkw_warp_sum(const double *part, int64_t k, int64_t stride, int64_t q0, int64_t n) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (DF) {
+        df64 x = {0.f, 0.f};
+        for (int64_t q = lane; q < n; q += 32) {
+            const float2 t = __ldcg(reinterpret_cast<const float2 *>(part) + k * stride + q0 + q);
+            x = df_add(x, df64{t.x, t.y});
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = add(x, shfl(x, o));
-        if constexpr (DF) { if (lane == 0) s_tot[w] = df_to_double(x); }
-        else { if (lane == 0) s_tot[w] = x; }
+        for (int o = 16; o > 0; o >>= 1) x = df_add(x, shfl_xor_df(x, o));
+        return df_to_double(x);
+    } else {
+        double x = 0.0;
+        for (int64_t q = lane; q < n; q += 32) x += __ldcg(part + k * stride + q0 + q);
+        return warp_sum(x);
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = s_tot[k];
-    return true;
 }
 
 // x + (a p + w s): two FMAs in FP64, the sloppy double-float sums for double-float vectors
 __device__ __forceinline__ double pkw_xupd(double x, double a, double p, double w, double s) { return fma(w, s, fma(a, p, x)); }
 __device__ __forceinline__ df64 pkw_xupd(df64 x, df64 a, df64 p, df64 w, df64 s) { return dfs_add(x, dfs_add(a * p, w * s)); }
 
+// ---- the phases of one tile (all threads of the block; BLOCK threads, R rows each per trip)
+
+// A, window: r_k = s - w t and p_k = r_k + b (p_{k-1} - w v_{k-1}) on [lo, hi) into xw (k = 0:
+// r = p = b); on the tile [rb, re): x_k (k = 0: 0), r_k and p_k stored, (r_k, r_k) accumulated
+// (FP64 at k = 0 of an FP64 solve, else split double-float)
+template <typename V, int BLOCK>
+__device__ __forceinline__ void pkw_a_window(const KVecs<V> &K, V *xw, int64_t lo, int64_t hi, int64_t rb, int64_t re,
+                                             int32_t k, double a_, double w_, double b_, const V *p_old, const V *v_old,
+                                             V *p_new, int sc, DotAcc<df64> &acc, DotAcc<double> &acc0) {
+    using Op = PkOps<V>;
+    constexpr int R = VecT<V>::R;
+    constexpr bool F64 = std::is_same<V, double>::value;
+    const V al = cvt<V>(a_), om = cvt<V>(w_), be = cvt<V>(b_);
+#pragma unroll 1
+    for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(BLOCK) * R) {
+        Pack<V> rk, pk;
+        const bool own = j0 >= rb && j0 < re;
+        if (k == 0) {
+            rk = ldv(K.b + j0);
+            pk = rk;
+            if (own) {
+                Pack<V> z;
+#pragma unroll
+                for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
+                stv(K.x + j0, z);
+            }
+        } else {
+            const Pack<V> s = ldcv(K.s + j0), tv = ldcv(K.t + j0), po = ldcv(p_old + j0), vo = ldcv(v_old + j0);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                rk.v[j] = Op::sub(s.v[j], om * tv.v[j]);
+                pk.v[j] = Op::add(rk.v[j], be * Op::sub(po.v[j], om * vo.v[j]));
+            }
+            if (own) {
+                Pack<V> x = ldcv(K.x + j0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) x.v[j] = pkw_xupd(x.v[j], al, po.v[j], om, s.v[j]);
+                stv(K.x + j0, x);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) xw[j0 - lo + j] = pk.v[j];
+        if (own) {
+            stv(K.r + j0, rk);
+            stv(p_new + j0, pk);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (F64 && k == 0) acc0.add(to_d(rk.v[j]), to_d(rk.v[j]));
+                else { const df64 q = PkwIn<V>::get(rk.v[j], sc); acc.add(q, q); }
+            }
+        }
+    }
+}
+
+// A, operator: v_k = A p_k on the tile from the window; (rh, v_k) with rh = b
+template <typename V, int BLOCK>
+__device__ __forceinline__ void pkw_a_spmv(const KVecs<V> &K, const V *xw, int64_t lo, int64_t rb, int64_t re, int64_t n,
+                                           int32_t k, V *v_new, int sc, DotAcc<df64> &acc, DotAcc<double> &acc0) {
+    constexpr int R = VecT<V>::R;
+    constexpr bool F64 = std::is_same<V, double>::value;
+#pragma unroll 1
+    for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(BLOCK) * R) {
+        Pack<V> pi;
+#pragma unroll
+        for (int j = 0; j < R; ++j) pi.v[j] = xw[r0 - lo + j];
+        const Pack<V> y = pkw_spmv(K, r0, xw, lo, n, pi);
+        stv(v_new + r0, y);
+        const Pack<V> rh = ldv(K.b + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (F64 && k == 0) acc0.add(to_d(rh.v[j]), to_d(y.v[j]));
+            else acc.add(PkwIn<V>::get(rh.v[j], sc), PkwIn<V>::get(y.v[j], sc));
+        }
+    }
+}
+
+// B, window: s = r_k - alpha v_k on [lo, hi) into xw, stored on the tile
+template <typename V, int BLOCK>
+__device__ __forceinline__ void pkw_b_window(const KVecs<V> &K, V *xw, int64_t lo, int64_t hi, int64_t rb, int64_t re,
+                                             double a_, const V *v_new) {
+    using Op = PkOps<V>;
+    constexpr int R = VecT<V>::R;
+    const V al = cvt<V>(a_);
+#pragma unroll 1
+    for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(BLOCK) * R) {
+        const Pack<V> r = ldcv(K.r + j0), v = ldcv(v_new + j0);
+        Pack<V> s;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            s.v[j] = Op::sub(r.v[j], al * v.v[j]);
+            xw[j0 - lo + j] = s.v[j];
+        }
+        if (j0 >= rb && j0 < re) stv(K.s + j0, s);
+    }
+}
+
+// B, operator: t = A s on the tile from the window; (t, s), (t, t), (rh, s), (rh, t)
+template <typename V, int BLOCK>
+__device__ __forceinline__ void pkw_b_spmv(const KVecs<V> &K, const V *xw, int64_t lo, int64_t rb, int64_t re, int64_t n,
+                                           int sc, DotAcc<df64> (&acc)[4]) {
+    constexpr int R = VecT<V>::R;
+#pragma unroll 1
+    for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(BLOCK) * R) {
+        Pack<V> si;
+#pragma unroll
+        for (int j = 0; j < R; ++j) si.v[j] = xw[r0 - lo + j];
+        const Pack<V> y = pkw_spmv(K, r0, xw, lo, n, si);
+        stv(K.t + r0, y);
+        const Pack<V> rh = ldv(K.b + r0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const df64 qt = PkwIn<V>::get(y.v[j], sc), qs = PkwIn<V>::get(si.v[j], sc), qb = PkwIn<V>::get(rh.v[j], sc);
+            acc[0].add(qt, qs);
+            acc[1].add(qt, qt);
+            acc[2].add(qb, qs);
+            acc[3].add(qb, qt);
+        }
+    }
+}
+
+// ---- the scalar updates (one thread per system copy)
+
+// After G1 of step k: at k = 0 the setup of the state from (b, b) (and, for an FP64 solve, the
+// scale of the later inner products: 2^sc near ||b||, the same in every block that holds a part of
+// the system); then the tests of pk_after_c on r_k (beta was formed at G2 and is used only if
+// running) and alpha_k.
+__device__ __forceinline__ void pkw_after_g1(KState &S, int32_t k, double rr, double rv, double rho_next, double rt,
+                                             int32_t maxit, int32_t stall, bool f64, int &sc) {
+    if (k == 0) {
+        S.iter = 0; S.last_improve = 0; S.maxit = maxit; S.stall = stall; S.ticket = 0u;
+        S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+        S.rho = S.rr = S.rr0 = S.best_rr = rr;
+        S.tol2 = rt * rt * rr;
+        S.stall_rr = 4e-6 * rr;
+        S.done = (rr == 0.0) ? K_CONVERGED : (!isfinite(rr) ? K_NONFINITE : (maxit <= 0 ? K_MAXIT : K_RUNNING));
+        if (f64 && S.done == K_RUNNING) {
+            int ex = 0;
+            frexp(sqrt(rr), &ex);
+            sc = ex;
+        }
+    } else {
+        const double beta = S.beta;
+        pk_after_c(S, rho_next, rr, maxit, stall);
+        S.beta = beta;
+    }
+    if (S.done == K_RUNNING) {
+        if (rv == 0.0 || !isfinite(rv)) S.done = isfinite(rv) ? K_BREAKDOWN : K_NONFINITE;
+        else S.alpha = S.rho / rv;
+    }
+}
+
+// After G2: omega_k, rho_{k+1} = (rh, s) - omega_k (rh, t), beta_k (a zero omega or rho ends the
+// solve at the next tests, before beta is used)
+__device__ __forceinline__ void pkw_after_g2(KState &S, const double (&tot)[4], double &rho_next) {
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+        S.done = K_NONFINITE;
+        return;
+    }
+    S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
+    rho_next = tot[2] - S.omega * tot[3];
+    S.beta = (S.omega != 0.0 && S.rho != 0.0) ? (rho_next / S.rho) * (S.alpha / S.omega) : 0.0;
+}
+
+// ---------------------------------------------------------------------------------
+// One system: one tile per block
+// ---------------------------------------------------------------------------------
+
 template <typename V>
 __global__ void __launch_bounds__(PKW_BLOCK, PKW_MIN_BLOCKS) pkw_solve(PkwArgs<V> P) {
-    using Op = PkOps<V>;
-    using In = PkwIn<V>;
-    constexpr int R = VecT<V>::R;
     constexpr bool F64 = std::is_same<V, double>::value;
     extern __shared__ __align__(16) unsigned char pkw_dyn[];
     V *xw = reinterpret_cast<V *>(pkw_dyn);   // the window of the vector being multiplied
     __shared__ KState S;
     __shared__ double s_rho_next;
     __shared__ int s_sc;                       // scale of the split inner products (FP64 solve)
+    __shared__ double s_tot[4];
     __shared__ BTile T;
     __shared__ PkWin Wn;
     if (P.active && !P.active[0]) return;
@@ -262,155 +440,63 @@ __global__ void __launch_bounds__(PKW_BLOCK, PKW_MIN_BLOCKS) pkw_solve(PkwArgs<V
     if (threadIdx.x == 0) { T = P.tiles[blockIdx.x]; Wn = P.win[blockIdx.x]; s_sc = 0; }
     __syncthreads();
     const int64_t rb = T.r_begin, re = T.r_end, lo = Wn.lo, hi = Wn.hi;
+    const int64_t G = gridDim.x;
+    const int w = threadIdx.x >> 5;
     uint32_t nbar = 0;
     bool ok = true;
     for (int32_t k = 0;; ++k) {
         V *const p_old = (k & 1) ? K.p : P.p2, *const v_old = (k & 1) ? K.v : P.v2;
         V *const p_new = (k & 1) ? P.p2 : K.p, *const v_new = (k & 1) ? P.v2 : K.v;
         const int sc = s_sc;
-        // ---- A_k: r_k and p_k on the window, x_k on the tile; v_k = A p_k; (r_k, r_k), (rh, v_k)
+        // ---- A_k
         {
-            const V al = cvt<V>(k ? S.alpha : 0.0), om = cvt<V>(k ? S.omega : 0.0), be = cvt<V>(k ? S.beta : 0.0);
             DotAcc<df64> acc[2];
-            DotAcc<double> acc0[2];   // the first sums of an FP64 solve, which fix its scale
-#pragma unroll 1
-            for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(PKW_BLOCK) * R) {
-                Pack<V> rk, pk;
-                const bool own = j0 >= rb && j0 < re;
-                if (k == 0) {
-                    rk = ldv(K.b + j0);
-                    pk = rk;
-                    if (own) {
-                        Pack<V> z;
-#pragma unroll
-                        for (int j = 0; j < R; ++j) z.v[j] = cvt<V>(0.0);
-                        stv(K.x + j0, z);
-                    }
-                } else {
-                    const Pack<V> s = ldcv(K.s + j0), tv = ldcv(K.t + j0), po = ldcv(p_old + j0), vo = ldcv(v_old + j0);
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        rk.v[j] = Op::sub(s.v[j], om * tv.v[j]);
-                        pk.v[j] = Op::add(rk.v[j], be * Op::sub(po.v[j], om * vo.v[j]));
-                    }
-                    if (own) {
-                        Pack<V> x = ldcv(K.x + j0);
-#pragma unroll
-                        for (int j = 0; j < R; ++j) x.v[j] = pkw_xupd(x.v[j], al, po.v[j], om, s.v[j]);
-                        stv(K.x + j0, x);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < R; ++j) xw[j0 - lo + j] = pk.v[j];
-                if (own) {
-                    stv(K.r + j0, rk);
-                    stv(p_new + j0, pk);
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        if (F64 && k == 0) acc0[0].add(to_d(rk.v[j]), to_d(rk.v[j]));
-                        else { const df64 q = In::get(rk.v[j], sc); acc[0].add(q, q); }
-                    }
-                }
+            DotAcc<double> acc0[2];
+            pkw_a_window<V, PKW_BLOCK>(K, xw, lo, hi, rb, re, k, k ? S.alpha : 0.0, k ? S.omega : 0.0, k ? S.beta : 0.0,
+                                       p_old, v_old, p_new, sc, acc[0], acc0[0]);
+            __syncthreads();
+            pkw_a_spmv<V, PKW_BLOCK>(K, xw, lo, rb, re, P.n, k, v_new, sc, acc[1], acc0[1]);
+            const bool d64 = F64 && k == 0;
+            if (d64) pkw_block_partial<PKW_BLOCK, DotAcc<double>, 2>(acc0, P.part, G, blockIdx.x, xw);
+            else pkw_block_partial<PKW_BLOCK, DotAcc<df64>, 2>(acc, P.part, G, blockIdx.x, xw);
+            if (!(ok = pk1_sync(P.bar, nbar))) break;
+            if (w < 2) {
+                const double x = d64 ? pkw_warp_sum<false>(P.part, w, G, 0, G) : pkw_warp_sum<true>(P.part, w, G, 0, G);
+                if ((threadIdx.x & 31) == 0) s_tot[w] = x;
             }
             __syncthreads();
-#pragma unroll 1
-            for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(PKW_BLOCK) * R) {
-                Pack<V> pi;
-#pragma unroll
-                for (int j = 0; j < R; ++j) pi.v[j] = xw[r0 - lo + j];
-                const Pack<V> y = pkw_spmv(K, r0, xw, lo, P.n, pi);
-                stv(v_new + r0, y);
-                const Pack<V> rh = ldv(K.b + r0);
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if (F64 && k == 0) acc0[1].add(to_d(rh.v[j]), to_d(y.v[j]));
-                    else acc[1].add(In::get(rh.v[j], sc), In::get(y.v[j], sc));
-                }
-            }
-            double tot[2];
-            if (F64 && k == 0) ok = pkw_allreduce<DotAcc<double>, 2>(P.bar, P.part, acc0, nbar, tot);
-            else ok = pkw_allreduce<DotAcc<df64>, 2>(P.bar, P.part, acc, nbar, tot);
-            if (!ok) break;
             if (threadIdx.x == 0) {
                 const double f = F64 ? ldexp(1.0, sc) : 1.0;   // sums of split products carry 2^-2sc
-                const double rr = tot[0] * f * f, rv = tot[1] * f * f;
-                if (k == 0) {
-                    const double rt = P.rtol ? P.rtol[0] : P.rtol0;
-                    S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
-                    S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
-                    S.rho = S.rr = S.rr0 = S.best_rr = rr;
-                    S.tol2 = rt * rt * rr;
-                    S.stall_rr = 4e-6 * rr;
-                    S.done = (rr == 0.0) ? K_CONVERGED : (!isfinite(rr) ? K_NONFINITE : (P.maxit <= 0 ? K_MAXIT : K_RUNNING));
-                    // scale of the later inner products: 2^sc near the root mean square of b
-                    if (F64 && S.done == K_RUNNING) {
-                        int ex = 0;
-                        frexp(sqrt(rr / double(P.n > 0 ? P.n : 1)), &ex);
-                        s_sc = ex;
-                    }
-                } else {
-                    // the tests of pk_after_c on r_k; beta was formed at G2 and is used only if running
-                    const double rho1 = s_rho_next, beta = S.beta;
-                    pk_after_c(S, rho1, rr, P.maxit, P.stall);
-                    S.beta = beta;
-                }
-                if (S.done == K_RUNNING) {
-                    if (rv == 0.0 || !isfinite(rv)) S.done = isfinite(rv) ? K_BREAKDOWN : K_NONFINITE;
-                    else S.alpha = S.rho / rv;
-                }
+                int scn = s_sc;
+                pkw_after_g1(S, k, s_tot[0] * f * f, s_tot[1] * f * f, s_rho_next, P.rtol ? P.rtol[0] : P.rtol0, P.maxit,
+                             P.stall, F64, scn);
+                s_sc = scn;
             }
             __syncthreads();
             if (S.done != K_RUNNING) break;
         }
-        // ---- B_k: s on the window; t = A s; (t, s), (t, t), (rh, s), (rh, t)
+        // ---- B_k
         {
-            const V al = cvt<V>(S.alpha);
             const int scb = s_sc;
             DotAcc<df64> acc[4];
-#pragma unroll 1
-            for (int64_t j0 = lo + int64_t(threadIdx.x) * R; j0 < hi; j0 += int64_t(PKW_BLOCK) * R) {
-                const Pack<V> r = ldcv(K.r + j0), v = ldcv(v_new + j0);
-                Pack<V> s;
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    s.v[j] = Op::sub(r.v[j], al * v.v[j]);
-                    xw[j0 - lo + j] = s.v[j];
-                }
-                if (j0 >= rb && j0 < re) stv(K.s + j0, s);
+            pkw_b_window<V, PKW_BLOCK>(K, xw, lo, hi, rb, re, S.alpha, v_new);
+            __syncthreads();
+            pkw_b_spmv<V, PKW_BLOCK>(K, xw, lo, rb, re, P.n, scb, acc);
+            pkw_block_partial<PKW_BLOCK, DotAcc<df64>, 4>(acc, P.part, G, blockIdx.x, xw);
+            if (!(ok = pk1_sync(P.bar, nbar))) break;
+            if (w < 4) {
+                const double x = pkw_warp_sum<true>(P.part, w, G, 0, G);
+                if ((threadIdx.x & 31) == 0) s_tot[w] = x;
             }
             __syncthreads();
-#pragma unroll 1
-            for (int64_t r0 = rb + int64_t(threadIdx.x) * R; r0 < re; r0 += int64_t(PKW_BLOCK) * R) {
-                Pack<V> si;
-#pragma unroll
-                for (int j = 0; j < R; ++j) si.v[j] = xw[r0 - lo + j];
-                const Pack<V> y = pkw_spmv(K, r0, xw, lo, P.n, si);
-                stv(K.t + r0, y);
-                const Pack<V> rh = ldv(K.b + r0);
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const df64 qt = In::get(y.v[j], scb), qs = In::get(si.v[j], scb), qb = In::get(rh.v[j], scb);
-                    acc[0].add(qt, qs);
-                    acc[1].add(qt, qt);
-                    acc[2].add(qb, qs);
-                    acc[3].add(qb, qt);
-                }
-            }
-            double tot[4];
-            if (!(ok = pkw_allreduce<DotAcc<df64>, 4>(P.bar, P.part, acc, nbar, tot))) break;
             if (threadIdx.x == 0) {
                 const double f = F64 ? ldexp(1.0, scb) : 1.0;
+                double tot[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tot[q] = tot[q] * f * f;
-                if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-                    S.done = K_NONFINITE;
-                } else {
-                    S.omega = tot[1] == 0.0 ? 0.0 : tot[0] / tot[1];
-                    const double rho1 = tot[2] - S.omega * tot[3];
-                    s_rho_next = rho1;
-                    // a zero omega or rho ends the solve at the next tests, before beta is used
-                    S.beta = (S.omega != 0.0 && S.rho != 0.0) ? (rho1 / S.rho) * (S.alpha / S.omega) : 0.0;
-                }
+                for (int q = 0; q < 4; ++q) tot[q] = s_tot[q] * f * f;
+                double rn = 0.0;
+                pkw_after_g2(S, tot, rn);
+                s_rho_next = rn;
             }
             __syncthreads();
             if (S.done != K_RUNNING) break;
@@ -420,6 +506,126 @@ __global__ void __launch_bounds__(PKW_BLOCK, PKW_MIN_BLOCKS) pkw_solve(PkwArgs<V
         KState F = S;
         if (!ok) F.done = K_TIMEOUT;
         *P.st = F;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// A batch: tiles dealt to blocks, every block keeps the states of its tiles' systems
+// ---------------------------------------------------------------------------------
+
+constexpr int PKWB_MAXT = 48;   // tiles per block
+
+// After a barrier: for each owned tile whose system runs, warp (tile mod warps) adds the NV
+// partials of all tiles of that system (pkw_warp_sum) and lane 0 calls upd(tile, sums).
+template <int NV, typename U>
+__device__ __forceinline__ void pkwb_sums(const double *part, int64_t ntiles, int nt, const KState *st, const BTile *tl,
+                                          bool df, U &&upd) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = w; t < nt; t += PKWB_BLOCK / 32) {
+        if (st[t].done != K_RUNNING) continue;
+        double x[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            x[k] = df ? pkw_warp_sum<true>(part, k, ntiles, tl[t].tile0, tl[t].ntiles_inst)
+                      : pkw_warp_sum<false>(part, k, ntiles, tl[t].tile0, tl[t].ntiles_inst);
+        if (lane == 0) upd(t, x);
+    }
+    __syncthreads();
+}
+
+template <typename V>
+__global__ void __launch_bounds__(PKWB_BLOCK, PKWB_MIN_BLOCKS) pkwb_solve(PkwArgs<V> P) {
+    constexpr bool F64 = std::is_same<V, double>::value;
+    extern __shared__ __align__(16) unsigned char pkw_dyn[];
+    V *xw = reinterpret_cast<V *>(pkw_dyn);
+    __shared__ KState s_st[PKWB_MAXT];
+    __shared__ BTile s_tl[PKWB_MAXT];
+    __shared__ PkWin s_win[PKWB_MAXT];
+    __shared__ double s_rn[PKWB_MAXT];   // rho_{k+1} of each owned tile's system
+    __shared__ int s_sc[PKWB_MAXT];      // scale of its split inner products (FP64 solve)
+    const int64_t G = gridDim.x;
+    if (P.ntiles > G * PKWB_MAXT) {   // the host keeps to the limit; every block leaves at once
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.bar->err = 2;
+        return;
+    }
+    const int nt = int64_t(blockIdx.x) < P.ntiles ? int((P.ntiles - blockIdx.x + G - 1) / G) : 0;
+    const KVecs<V> &K = P.K;
+    for (int t = threadIdx.x; t < nt; t += PKWB_BLOCK) {
+        const int64_t tile = blockIdx.x + int64_t(t) * G;
+        const BTile Tt = P.tiles[tile];
+        s_tl[t] = Tt;
+        s_win[t] = P.win[tile];
+        KState &S = s_st[t];
+        S.done = (!P.active || P.active[Tt.inst]) ? K_RUNNING : K_CONVERGED;
+        S.iter = 0; S.last_improve = 0; S.maxit = P.maxit; S.stall = P.stall; S.ticket = 0u;
+        S.alpha = 1.0; S.omega = 1.0; S.beta = 0.0; S.scratch[0] = S.scratch[1] = 0.0;
+        S.rho = S.rr = S.rr0 = S.best_rr = S.tol2 = S.stall_rr = 0.0;
+        s_rn[t] = 0.0;
+        s_sc[t] = 0;
+    }
+    __syncthreads();
+    auto running = [&]() {
+        int a = 0;
+        for (int t = 0; t < nt; ++t) a |= (s_st[t].done == K_RUNNING);
+        return a;
+    };
+    uint32_t nbar = 0, live = 0;
+    bool ok = true;
+    for (int32_t k = 0;; ++k) {
+        V *const p_old = (k & 1) ? K.p : P.p2, *const v_old = (k & 1) ? K.v : P.v2;
+        V *const p_new = (k & 1) ? P.p2 : K.p, *const v_new = (k & 1) ? P.v2 : K.v;
+        const bool d64 = F64 && k == 0;
+        // ---- A_k, tile by tile
+        for (int t = 0; t < nt; ++t) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &Tt = s_tl[t];
+            const PkWin Wt = s_win[t];
+            const KState &S = s_st[t];
+            DotAcc<df64> acc[2];
+            DotAcc<double> acc0[2];
+            __syncthreads();   // the previous tile's readers of the window are done
+            pkw_a_window<V, PKWB_BLOCK>(K, xw, Wt.lo, Wt.hi, Tt.r_begin, Tt.r_end, k, k ? S.alpha : 0.0, k ? S.omega : 0.0,
+                                        k ? S.beta : 0.0, p_old, v_old, p_new, s_sc[t], acc[0], acc0[0]);
+            __syncthreads();
+            pkw_a_spmv<V, PKWB_BLOCK>(K, xw, Wt.lo, Tt.r_begin, Tt.r_end, P.n, k, v_new, s_sc[t], acc[1], acc0[1]);
+            const int64_t tile = blockIdx.x + int64_t(t) * G;
+            if (d64) pkw_block_partial<PKWB_BLOCK, DotAcc<double>, 2>(acc0, P.part, P.ntiles, tile, xw);
+            else pkw_block_partial<PKWB_BLOCK, DotAcc<df64>, 2>(acc, P.part, P.ntiles, tile, xw);
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+        pkwb_sums<2>(P.part, P.ntiles, nt, s_st, s_tl, !d64, [&](int t, const double *tot) {
+            const double f = F64 ? ldexp(1.0, s_sc[t]) : 1.0;
+            int scn = s_sc[t];
+            pkw_after_g1(s_st[t], k, tot[0] * f * f, tot[1] * f * f, s_rn[t], P.rtol ? P.rtol[s_tl[t].inst] : P.rtol0,
+                         P.maxit, P.stall, F64, scn);
+            s_sc[t] = scn;
+        });
+        // ---- B_k, tile by tile
+        for (int t = 0; t < nt; ++t) {
+            if (s_st[t].done != K_RUNNING) continue;
+            const BTile &Tt = s_tl[t];
+            const PkWin Wt = s_win[t];
+            DotAcc<df64> acc[4];
+            __syncthreads();
+            pkw_b_window<V, PKWB_BLOCK>(K, xw, Wt.lo, Wt.hi, Tt.r_begin, Tt.r_end, s_st[t].alpha, v_new);
+            __syncthreads();
+            pkw_b_spmv<V, PKWB_BLOCK>(K, xw, Wt.lo, Tt.r_begin, Tt.r_end, P.n, s_sc[t], acc);
+            pkw_block_partial<PKWB_BLOCK, DotAcc<df64>, 4>(acc, P.part, P.ntiles, blockIdx.x + int64_t(t) * G, xw);
+        }
+        if (!(ok = pkb_sync(P.bar, nbar, running(), live)) || !live) break;
+        pkwb_sums<4>(P.part, P.ntiles, nt, s_st, s_tl, true, [&](int t, const double *tot) {
+            const double f = F64 ? ldexp(1.0, s_sc[t]) : 1.0;
+            double tt[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tt[q] = tot[q] * f * f;
+            pkw_after_g2(s_st[t], tt, s_rn[t]);
+        });
+    }
+    for (int t = threadIdx.x; t < nt; t += PKWB_BLOCK) {
+        if (blockIdx.x + int64_t(t) * G != s_tl[t].tile0) continue;
+        KState F = s_st[t];
+        if (!ok) F.done = K_TIMEOUT;
+        P.st[s_tl[t].inst] = F;
     }
 }
 
