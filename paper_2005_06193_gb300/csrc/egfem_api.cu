@@ -238,7 +238,7 @@ egfem_status ensure_mixed_tensor(egfem_t *h, cudaStream_t s) {
 // mixed-precision tensor action (FP32 Jacobian) serves it.
 bool mixed_tensor_action(const egfem_t *h, const CsfArgs &A) {
     return h->opts.op == EGFEM_OP_CSF && h->mixed_ta_ready && A.a32 && A.r && A.q64 && !A.a64 && !A.jcsr && !A.jsell &&
-           !A.dinv && !A.q32 && !A.inst_mask;
+           !A.dinv && !A.q32;
 }
 
 // Pointwise nonlinearity + residual + Jacobian fill at A.u; returns the kernels launched.
@@ -2301,8 +2301,9 @@ egfem_status gn_build(egfem_t *h, KWork<V> &W, double *d_u, const double *d_d, i
     gn_mid<<<1, 256, 0, h->hs>>>(G);
     kb_update<V><<<gu, 256, 0, h->hs>>>(h->n, h->slice_inst, h->inst_mask, h->inst_lam, d_u, W.x);
     CsfArgs A = csf_args(h, d_u, d_d);
-    A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
-    if (mixed) A.a32 = h->k32.A;
+    A.r = h->r; A.q64 = h->k64.b;
+    if (mixed) A.a32 = h->k32.A;   // the FP64 redo, which needs the FP64 operator, is the host loop's
+    else A.a64 = h->k64.A;
     A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
     nodes += launch_csf(h, A, h->hs);
     if (mixed) { cast_kernel<double, df64><<<gu, 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b); ++nodes; }
@@ -2389,18 +2390,34 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
     std::vector<int32_t> st(nb, EGFEM_OK);
     int64_t launches = 0;
     // evaluate residual/operator for instances with mask m
+    // mixed path: the residual in FP64 and the FP32 operator (csf_mixed_kernel); the FP64 operator
+    // is formed only for the instances whose step is redone in FP64 (eval64 below)
+    if (mixed && h->opts.op == EGFEM_OP_CSF) EG_TRY(ensure_mixed_tensor(h, h->hs));
     auto eval = [&](const std::vector<int> &m) -> egfem_status {
         for (int b = 0; b < nb; ++b) h->h_mask[b] = uint8_t(m[b]);
         EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
         CsfArgs A = csf_args(h, d_u, d_d);
-        A.r = h->r; A.a64 = h->k64.A; A.q64 = h->k64.b;
+        A.r = h->r; A.q64 = h->k64.b;
         if (mixed) A.a32 = h->k32.A;
+        else A.a64 = h->k64.A;
         A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
         launches += launch_csf(h, A, h->hs) + 1 + (mixed ? 1 : 0);
         if (mixed) cast_kernel<double, df64><<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->k64.b, h->k32.b);
         EG_CUDA(cudaGetLastError());
         EG_TRY(batch_norms(h));
         for (int b = 0; b < nb; ++b) if (m[b]) rn[b] = std::sqrt(h->h_norm2[b]);
+        return EGFEM_OK;
+    };
+    // the FP64 operator (and D r) at the current u for instances with mask m: the FP64 redo of a
+    // mixed step
+    auto eval64 = [&](const std::vector<int> &m) -> egfem_status {
+        for (int b = 0; b < nb; ++b) h->h_mask[b] = uint8_t(m[b]);
+        EG_CUDA(cudaMemcpyAsync(h->inst_mask, h->h_mask, size_t(nb), cudaMemcpyHostToDevice, h->hs));
+        CsfArgs A = csf_args(h, d_u, d_d);
+        A.r = h->r; A.q64 = h->k64.b; A.a64 = h->k64.A;
+        A.slice_inst = h->slice_inst; A.inst_mask = h->inst_mask;
+        launches += launch_csf(h, A, h->hs);
+        EG_CUDA(cudaGetLastError());
         return EGFEM_OK;
     };
     // u -= lam_b x_b for instances with mask m, x from the FP32 (p32) or FP64 workspace
@@ -2477,6 +2494,12 @@ egfem_status batch_newton(egfem_t *h, double *d_u, const double *d_d, egfem_stat
                 todo = todo || pending[b];
             }
             if (!todo) continue;
+            if (mixed && !p32) {
+                // the FP64 operator of the instances redone in FP64 (the mixed evaluations skip it)
+                std::vector<int> redo(pending.begin(), pending.end());
+                EG_TRY(eval64(redo));
+                for (int b = 0; b < nb; ++b) h->h_mask[b] = uint8_t(pending[b]);
+            }
             if (p32) EG_TRY(run_batch_bicgstab(h, h->k32, h->bgraph32, kMixedStall, &launches));
             else EG_TRY(run_batch_bicgstab(h, h->k64, h->bgraph64, 0, &launches));
             std::vector<int> ok(nb, 0);
