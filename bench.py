@@ -297,11 +297,13 @@ def p3_batch(torch, P, dev, meshes, fs, **opts):
 
 
 def profile_batch(torch, P, dev, count=16):
-    """One batched Newton step (host loop, BiCGStab capped at 40 iterations) on the first
-    `count` P3 instances, twice; the second call, after the tile autotuning, runs inside the
-    NVTX range "capture" (ncu --nvtx --nvtx-include capture/ selects its batched solve)."""
+    """One batched Newton step (host loop, BiCGStab run for exactly 40 iterations: a fixed forcing
+    term of 1e-14) on the first `count` P3 instances, twice; the second call, after the tile
+    autotuning, runs inside the NVTX range "capture" (ncu --nvtx --nvtx-include capture/ selects
+    its batched solve)."""
     meshes, fs = p3_instances(count)
-    hb, d = p3_batch(torch, P, dev, meshes, fs, newton_graph=0, newton_maxit=1, newton_rtol=0.9, krylov_maxit=40)
+    hb, d = p3_batch(torch, P, dev, meshes, fs, newton_graph=0, newton_maxit=1, newton_rtol=0.9, krylov_maxit=40,
+                     fixed_eta=1, eta_max=1e-14)
     u = torch.zeros_like(d)
     hb.batch_newton_solve(u, d, check=False)
     torch.cuda.synchronize()

@@ -69,6 +69,8 @@ def test_converged_1024_solution_satisfies_oracle_residual(P):
     h.residual(u, d, r)
     torch.cuda.synchronize()
     assert st.status == 0 and st.res_final <= 1e-10 * st.res0
+    # at this size the one-system BiCGStab is the windowed two-reduction kernel
+    assert "kry_window" in {p["name"] for p in h.profile_kernels(u, d, reps=1)}
     rows = sample_rows(mesh, 300, 5, extra=[0, n + 2, mesh.n_nodes // 2, mesh.n_nodes - n - 3])
     orc = oracle.Problem(mesh, a=("pow", 2.0), a_deg=2, cells=cells_around(mesh, rows))
     b = orc.load_vector_cellwise(f_cell) * (1 - mesh.dirichlet)
