@@ -318,6 +318,24 @@ def profile_batch(torch, P, dev, count=16):
     return out
 
 
+def profile_p3batch(torch, P, dev, count):
+    """The batched mixed Newton solve of `count` P3 instances (the default 256) with the host
+    Newton loop, so that every kernel is a top-level launch (for an ncu launch list): a warm
+    solve, then one more."""
+    meshes, fs = p3_instances(count)
+    hb, d = p3_batch(torch, P, dev, meshes, fs, newton_graph=0)
+    u = torch.zeros_like(d)
+    hb.batch_newton_solve(u, d)
+    u.zero_()
+    t0 = time.perf_counter()
+    st = hb.batch_newton_solve(u, d)
+    torch.cuda.synchronize()
+    out = {"instances": count, "rows": int(hb.sizes.n_nodes), "seconds": time.perf_counter() - t0,
+           "krylov_iters_sum": int(sum(s.krylov_iters for s in st)), "newton_max": int(max(s.newton_iters for s in st))}
+    hb.close()
+    return out
+
+
 def batched_p3_extra(torch, P, dev, count, barrier):
     """Newton solves per second on the first `count` instances of the 256-instance batch
     (n ~ U{64..512}, w = u^3 in P3, 8-mode sine sources): plain sequential FP64 solves
@@ -615,7 +633,8 @@ def main():
     ap.add_argument("--p3-instances", type=int, default=256)
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=2935)
-    ap.add_argument("--profile-only", default=None, choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch"],
+    ap.add_argument("--profile-only", default=None,
+                    choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch"],
                     help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
                          "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
@@ -643,6 +662,9 @@ def main():
 
     if args.profile_only == "batch":
         print(json.dumps(profile_batch(torch, P, torch.device("cuda", local))), flush=True)
+        return
+    if args.profile_only == "p3batch":
+        print(json.dumps(profile_p3batch(torch, P, torch.device("cuda", local), args.p3_instances)), flush=True)
         return
     if args.profile_only in ("gradient", "quadrature", "supercond"):
         setup = {"gradient": gradient_setup, "quadrature": quadrature_setup,

@@ -274,11 +274,22 @@ int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
         }
         return launched;
     }
+    // the Newton steps' evaluations (residual and solver operator) accumulate the Jacobian in
+    // double-float; egfem_jacobian (CSR values) and the adjoint (jsell, dinv) in FP64
+    if (!A.jcsr && !A.jsell && !A.dinv) {
+        switch (h->maxc_tpl) {
+            case 8: csf_fused_kernel<8, true><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(B); break;
+            case 16: csf_fused_kernel<16, true><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(B); break;
+            case 32: csf_fused_kernel<32, true><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(B); break;
+            default: csf_fused_kernel<64, true><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(B); break;
+        }
+        return launched;
+    }
     switch (h->maxc_tpl) {
-        case 8: csf_fused_kernel<8><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(B); break;
-        case 16: csf_fused_kernel<16><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(B); break;
-        case 32: csf_fused_kernel<32><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(B); break;
-        default: csf_fused_kernel<64><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(B); break;
+        case 8: csf_fused_kernel<8, false><<<grid(csf_block<8>()), csf_block<8>(), 0, s>>>(B); break;
+        case 16: csf_fused_kernel<16, false><<<grid(csf_block<16>()), csf_block<16>(), 0, s>>>(B); break;
+        case 32: csf_fused_kernel<32, false><<<grid(csf_block<32>()), csf_block<32>(), 0, s>>>(B); break;
+        default: csf_fused_kernel<64, false><<<grid(csf_block<64>()), csf_block<64>(), 0, s>>>(B); break;
     }
     return launched;
 }
@@ -408,15 +419,16 @@ egfem_status pkw_plan(egfem_t *h, KWork<V> &W) {
     // outnumber a tile's own rows twice over (3D meshes in lexicographic order: a halo of one
     // grid plane on each side, 9 times the tile on the 64^3 Kuhn mesh), the five-barrier kernel
     // is faster (64^3, FP64: 98 against 70 Newton solves/s)
-    int64_t wmax = 0, halo_max = 0, tile_min = h->n_pad;
-    std::vector<BTile> tl(size_t(W.pk_ntiles));
+    // (against the nominal tile length: the last tile is shorter)
+    int64_t wmax = 0, halo_max = 0, tile_len = 0;
+    std::vector<BTile> tl(static_cast<size_t>(W.pk_ntiles));
     EG_CUDA(cudaMemcpy(tl.data(), W.pk_tiles, tl.size() * sizeof(BTile), cudaMemcpyDeviceToHost));
     for (size_t t = 0; t < win.size(); ++t) {
         wmax = std::max(wmax, win[t].hi - win[t].lo);
         halo_max = std::max(halo_max, (win[t].hi - win[t].lo) - (tl[t].r_end - tl[t].r_begin));
-        if (tl[t].r_end > tl[t].r_begin) tile_min = std::min(tile_min, tl[t].r_end - tl[t].r_begin);
+        tile_len = std::max(tile_len, tl[t].r_end - tl[t].r_begin);
     }
-    if (halo_max > 2 * tile_min && W.pk_ntiles > 1) return EGFEM_OK;
+    if (halo_max > 2 * tile_len && W.pk_ntiles > 1) return EGFEM_OK;
     const size_t smem = std::max(size_t(wmax) * sizeof(V), PKW_STAGE_BYTES);
     int optin = 0;
     EG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));

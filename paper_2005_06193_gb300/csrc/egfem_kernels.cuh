@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "egfem_df64.cuh"
 #include "egfem_internal.h"
 
 namespace egfem {
@@ -103,14 +104,48 @@ __device__ __forceinline__ void scatter_pi32(uint32_t info, float e, float *J, i
     if (kind == W_FACE) { const float h = e * (1.0f / 3.0f); J[c0 * stride] += h; J[c1 * stride] += h; J[c2 * stride] += h; }
 }
 
+// double-float variant of scatter_pi: J_{i, c_t} += e * w_t with the weights in double-float
+__device__ __forceinline__ void scatter_pi_df(uint32_t info, df64 e, df64 *J, int stride) {
+    const uint32_t kind = (info >> 24) & 0xF;
+    const uint32_t c0 = info & 0xFF, c1 = (info >> 8) & 0xFF, c2 = (info >> 16) & 0xFF;
+    if (kind == W_VERTEX) { J[c0 * stride] = df_acc(J[c0 * stride], e); return; }
+    if (kind == W_MID) {
+        const df64 h = {__fmul_rn(0.5f, e.hi), __fmul_rn(0.5f, e.lo)};   // exact
+        J[c0 * stride] = df_acc(J[c0 * stride], h);
+        J[c1 * stride] = df_acc(J[c1 * stride], h);
+        return;
+    }
+    // 1/3 as a float pair (0x3eaaaaab and the rounded remainder), accurate to about 2^-48
+    const df64 h = df_mul(e, df64{0.333333343f, -9.93410748e-09f});
+    if (kind == W_THIRD) {
+        J[c0 * stride] = df_acc(J[c0 * stride], df64{__fmul_rn(2.0f, h.hi), __fmul_rn(2.0f, h.lo)});
+        J[c1 * stride] = df_acc(J[c1 * stride], h);
+        return;
+    }
+    if (kind == W_FACE) {
+        J[c0 * stride] = df_acc(J[c0 * stride], h);
+        J[c1 * stride] = df_acc(J[c1 * stride], h);
+        J[c2 * stride] = df_acc(J[c2 * stride], h);
+    }
+}
+
 // Fused pointwise nonlinearity + residual + Jacobian fill (one thread per row).
 // MAXC bounds the local columns of a row; du and J live in shared memory, one column
 // of csf_block<MAXC>() entries per local column.
-template <int MAXC>
+//
+// JDF: the Jacobian is accumulated in double-float on the FP32 pipe (J1 = T .2 a per leaf, the
+// Pi scatter of D g' per fibre, T_ii a per fibre), from exact splits of the FP64 values
+// (split_dbl), and rounded to FP64 once per entry.  The residual, D = T .3 u and everything
+// written from them stay FP64.  GB300 retires about two FP64 operations per SM and clock, and
+// this kernel is bound by that pipe: the variant takes about a third of its FP64 operations off
+// it.  Its entries agree with the FP64 accumulation to about 1e-14 relative; it serves the
+// Newton steps' operator (the Jacobian only steers the Newton direction, the residual is exact
+// FP64), while egfem_jacobian and the adjoint use the FP64 accumulation.
+template <int MAXC, bool JDF>
 __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A) {
     constexpr int BLK = csf_block<MAXC>();
     __shared__ double s_du[MAXC * BLK];
-    __shared__ double s_J[MAXC * BLK];
+    __shared__ double s_J[MAXC * BLK];   // FP64 entries, or double-float pairs (JDF)
     const int tid = threadIdx.x;
     const int64_t row = int64_t(blockIdx.x) * BLK + tid;
     if (row >= A.n_rows) return;
@@ -136,13 +171,16 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         }
         return;
     }
+    df64 *Jd = reinterpret_cast<df64 *>(s_J) + tid;
     for (int c = 0; c < M.ncol; ++c) {
         const int32_t g = A.col_idx[M.col_base + int64_t(c) * SLICE + lane];
         du[c * BLK] = A.u[g] - ui;
-        J[c * BLK] = 0.0;
+        if constexpr (JDF) Jd[c * BLK] = df64{0.f, 0.f};
+        else J[c * BLK] = 0.0;
     }
     const Nonlin nl = A.nl;
     double r = 0.0, j1d = 0.0, D = 0.0, a = 0.0, gp = 0.0;
+    df64 a_df = {0.f, 0.f}, j1d_df = {0.f, 0.f};
     uint32_t info = 0;
     bool j2 = false;
     int f = -1;
@@ -156,7 +194,10 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 r += a * D;
-                if (j2) scatter_pi(info, D * gp, J, BLK);
+                if (j2) {
+                    if constexpr (JDF) scatter_pi_df(info, split_dbl(D * gp, 0), Jd, BLK);
+                    else scatter_pi(info, D * gp, J, BLK);
+                }
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
@@ -177,18 +218,27 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
                 g_eval(nl.a_kind, nl.a_pi, nl.a_scale, pu, w, gp);
                 a = (nl.kappa_field ? nl.kappa_field[A.fib_m[fq]] : nl.kappa) + w;
             }
-            j1d += td * a;
+            if constexpr (JDF) {
+                a_df = split_dbl(a, 0);
+                j1d_df = df_acc_prod(j1d_df, split_dbl(td, 0), a_df);
+            } else {
+                j1d += td * a;
+            }
             D = 0.0;
         }
         const int c = lc & LEAF_PAD;
         if (c != LEAF_PAD) {
             D += T * du[c * BLK];
-            J[c * BLK] += T * a;
+            if constexpr (JDF) Jd[c * BLK] = df_acc_prod(Jd[c * BLK], split_dbl(T, 0), a_df);
+            else J[c * BLK] += T * a;
         }
     }
     if (f >= 0) {
         r += a * D;
-        if (j2) scatter_pi(info, D * gp, J, BLK);
+        if (j2) {
+            if constexpr (JDF) scatter_pi_df(info, split_dbl(D * gp, 0), Jd, BLK);
+            else scatter_pi(info, D * gp, J, BLK);
+        }
     }
     // reaction gamma M^c c, c = c_scale g_c(Pi_c u)
     for (int j = 0; j < M.nrx; ++j) {
@@ -206,9 +256,14 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
             g_eval(nl.c_kind, nl.c_pi, nl.c_scale, pc, cv, cp);
         }
         r += nl.gamma * mv * cv;
-        if (!nl.picard) scatter_pi(xi, nl.gamma * mv * cp, J, BLK);
+        if (!nl.picard) {
+            if constexpr (JDF) scatter_pi_df(xi, split_dbl(nl.gamma * mv * cp, 0), Jd, BLK);
+            else scatter_pi(xi, nl.gamma * mv * cp, J, BLK);
+        }
     }
-    const double diag = j1d + J[0];
+    double diag;
+    if constexpr (JDF) diag = df_to_double_bits(df_acc(j1d_df, Jd[0]));
+    else diag = j1d + J[0];
     const double res = r - di;
     if (A.r) A.r[row] = res;
     double dinv = 0.0;
@@ -221,7 +276,9 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
     for (int c = 0; c < M.ncol; ++c) {
         const int64_t q = M.col_base + int64_t(c) * SLICE + lane;
         const int32_t slot = A.col_slot[q];
-        const double v = (c == 0) ? diag : J[c * BLK];
+        double v;
+        if constexpr (JDF) v = (c == 0) ? diag : df_to_double_bits(Jd[c * BLK]);
+        else v = (c == 0) ? diag : J[c * BLK];
         if (A.jcsr && slot >= 0) A.jcsr[slot] = v;
         if (A.jsell) A.jsell[q] = slot >= 0 ? v : 0.0;
         // the scaled diagonal is stored as exactly 1 (the persistent FP64 solve relies on it)

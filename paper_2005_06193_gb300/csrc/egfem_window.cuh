@@ -141,33 +141,6 @@ __device__ __forceinline__ Pack<V> pkw_spmv(const KVecs<V> &K, int64_t r0, const
     return y;
 }
 
-// x 2^-sc as a pair of floats (hi, lo) built from the bit pattern with integer operations (no
-// FP64 instruction): hi holds the leading 24 significand bits, lo the next 23 (lo = 0 below 2^-80
-// after scaling), so hi + lo equals x 2^-sc to a relative error below 2^-46.  Zero and values
-// below 2^-126 after scaling give (0, 0); infinities, NaN and values beyond the float range after
-// scaling give a non-finite hi, so a non-finite vector still makes the sums non-finite.
-__device__ __forceinline__ df64 split_dbl(double x, int sc) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned hi32 = unsigned(b >> 32), lo32 = unsigned(b);
-    const unsigned sign = hi32 & 0x80000000u;
-    const int eb = int((hi32 >> 20) & 0x7ffu);
-    const int e = eb - sc;
-    df64 r;
-    if (eb == 0x7ff || e > 1150) {
-        const bool nan = eb == 0x7ff && ((hi32 & 0xfffffu) | lo32) != 0u;
-        r.hi = __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
-        r.lo = 0.f;
-    } else if (e < 897) {
-        r.hi = 0.f;
-        r.lo = 0.f;
-    } else {
-        r.hi = __uint_as_float(sign | (unsigned(e - 896) << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
-        const float f = __fsub_rn(__uint_as_float(0x4B000000u | ((lo32 >> 6) & 0x7fffffu)), 8388608.0f);
-        r.lo = e >= 943 ? __fmul_rn(f, __uint_as_float(sign | (unsigned(e - 942) << 23))) : 0.f;
-    }
-    return r;
-}
-
 // Inner products of the solve: double-float accumulators on the FP32 pipe.  FP64 vectors enter
 // through split_dbl with the system's scale (a power of two near the root mean square of b, so
 // that every product stays in the float range); double-float vectors enter as they are.
