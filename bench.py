@@ -268,11 +268,13 @@ def batched_adjoint_extra(torch, P, dev, count, n, barrier):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     err = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(g_batch, g_plain))
+    tbytes, tshare = hb.tensor_storage()
     hs.close()
     hb.close()
     return {"workload": f"{count} x {n}x{n} P1/P2 u^2, 16x16 cellwise theta, j = 0.5||u-u_d||^2",
             "unit": "solves+gradients/s", "plain_fp64_sequential": count / t_plain, "batched_mixed": count / t_batch,
-            "speedup": t_plain / t_batch, "max_rel_gradient_difference": err}
+            "speedup": t_plain / t_batch, "max_rel_gradient_difference": err,
+            "tensor_bytes": tbytes, "tensor_shared_by": tshare}
 
 
 def p3_instances(count):

@@ -178,6 +178,12 @@ typedef struct {
                                 finished by the host loop (needs krylov_persistent).
                                 0: the host loop only; 2: the graph loop is required (the
                                 solve returns EGFEM_ERR_UNSUPPORTED where it is unavailable) */
+    int32_t batch_share;     /* egfem_batch_build: nonzero (default): when every instance has
+                                the same mesh (nodes, coordinates, cells and Dirichlet flags
+                                equal byte for byte) the tensor's leaves, fibres and reaction
+                                entries are stored once and read by every instance (their W
+                                indices offset per instance by the kernels); 0: one copy per
+                                instance.  The results are the same bit for bit         */
 } egfem_options;
 
 #define EGFEM_HIST 64
@@ -229,6 +235,11 @@ egfem_status egfem_set_options(egfem_handle h, const egfem_options *opts);
 /* Sizes: P1 nodes, W_a nodes, W_c nodes, rows and nonzeros of the Jacobian pattern. */
 egfem_status egfem_sizes(egfem_handle h, int64_t *n_nodes, int64_t *n_wa, int64_t *n_wc,
                          int64_t *jac_rows, int64_t *jac_nnz);
+
+/* Device bytes of the stored tensor T (Sec. 3.2: leaves, fibres) and of the reaction entries
+ * M^c, and the number of batch instances that read one copy of them (0: not shared; see
+ * egfem_options.batch_share).  Either output may be NULL. */
+egfem_status egfem_tensor_storage(egfem_handle h, int64_t *bytes, int32_t *share_count);
 
 /* Host copy of the W-space node coordinates ([n * dim]); which = 0: W_a, 1: W_c. */
 egfem_status egfem_w_coords(egfem_handle h, int32_t which, double *coords_host);

@@ -149,6 +149,7 @@ struct egfem_t {
     // batch (egfem_batch_build): instance b owns rows [inst_off[b], inst_off[b+1])
     int32_t nb = 0;
     std::vector<int64_t> inst_off;
+    WShare ws{};                        // one tensor for a batch of one mesh (ws.k > 0)
     int32_t *slice_inst = nullptr;
     uint8_t *inst_mask = nullptr, *h_mask = nullptr;
     double *inst_eta = nullptr, *h_eta = nullptr;
@@ -263,7 +264,10 @@ int launch_csf(egfem_t *h, const CsfArgs &A, cudaStream_t s) {
         B.wc_val = h->wc_val; B.wc_gp = h->wc_gp;
         ++launched;
     }
-    auto grid = [&](int blk) { return unsigned((h->n + blk - 1) / blk); };
+    // a shared tensor: ws.k blocks per range of local rows, one per instance (csf_row)
+    auto grid = [&](int blk) {
+        return h->ws.k > 0 ? unsigned((h->ws.rows + blk - 1) / blk * h->ws.k) : unsigned((h->n + blk - 1) / blk);
+    };
     if (mix) {
         B.leaf_val32 = h->leaf_val32;
         switch (h->maxc_tpl) {
@@ -315,6 +319,7 @@ CsfArgs csf_args(egfem_t *h, const double *u, const double *d) {
     A.nl.picard = h->opts.iteration == EGFEM_ITER_PICARD;
     A.u = u; A.d = d;
     A.status = h->status;
+    A.ws = h->ws;
     return A;
 }
 
@@ -789,7 +794,10 @@ egfem_status lagrange_local(int d, int p, MfLocal &L) {
     return EGFEM_OK;
 }
 
-egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
+// share_k > 1: the mesh is the disjoint union of share_k copies of one mesh of share_rows rows
+// (egfem_batch_build), whose tensor is then stored once when the copies' entries agree.
+egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out,
+                        int32_t share_k = 0, int64_t share_rows = 0) {
     if (!mesh || !prob || !out) { g_last_error = "null argument"; return EGFEM_ERR_INVALID_ARG; }
     *out = nullptr;
     std::string err;
@@ -921,6 +929,7 @@ egfem_status build_impl(const egfem_mesh *mesh, const egfem_problem *prob, const
                 }
         }
     }
+    if (share_k > 1 && h->opts.batch_share) share_tensor(H, share_k, share_rows, h->ws);   // else h->ws.k stays 0
     DeviceCSF &D = h->csf;
     D.n_rows = H.n_rows; D.n_slices = H.n_slices; D.max_cols = H.max_cols;
     D.n_colentries = int64_t(H.col_idx.size()); D.n_leaves = int64_t(H.leaf_val.size());
@@ -1199,6 +1208,7 @@ void egfem_default_options(egfem_options *o) {
     o->krylov_block_rows = 0;
     o->krylov_cluster = 0;
     o->newton_graph = 1;
+    o->batch_share = 1;
 }
 
 egfem_status egfem_build(const egfem_mesh *mesh, const egfem_problem *prob, const egfem_options *opts, egfem_handle *out) {
@@ -1276,6 +1286,17 @@ egfem_status egfem_sizes(egfem_handle h, int64_t *n_nodes, int64_t *n_wa, int64_
     if (n_wc) *n_wc = h->nwc;
     if (jac_rows) *jac_rows = h->n;
     if (jac_nnz) *jac_nnz = h->csf.nnz;
+    return EGFEM_OK;
+}
+
+egfem_status egfem_tensor_storage(egfem_handle h, int64_t *bytes, int32_t *share_count) {
+    if (!h) return EGFEM_ERR_INVALID_ARG;
+    const DeviceCSF &D = h->csf;
+    if (bytes)
+        *bytes = D.n_leaves * int64_t(sizeof(double) + sizeof(uint8_t)) +
+                 D.n_fibres * int64_t(sizeof(uint32_t) + sizeof(double) + sizeof(int32_t)) +
+                 D.n_rx * int64_t(sizeof(double) + sizeof(uint32_t) + sizeof(int32_t));
+    if (share_count) *share_count = h->ws.k;
     return EGFEM_OK;
 }
 
@@ -1601,9 +1622,10 @@ __global__ void add_into_kernel(int64_t n, const double *x, double *acc) {
 // grad_kappa_m -= lambda_i sum_k T_imk (u_k - u_i)   (sum_k T_imk = 0)
 __global__ void grad_kappa_kernel(int64_t n_rows, const SliceMeta *meta, const int32_t *col_idx, const double *leaf_val,
                                   const uint8_t *leaf_col, const uint32_t *fib_info, const int32_t *fib_m, const uint8_t *dir,
-                                  const double *u, const double *lam, double *grad) {
+                                  const double *u, const double *lam, double *grad, WShare ws) {
     const int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (row >= n_rows || dir[row]) return;
+    const int64_t inst = ws.k > 0 ? row / ws.rows : 0;   // a shared tensor's W indices are instance 0's
     const double li = lam[row];
     if (li == 0.0) return;
     const SliceMeta M = meta[row / SLICE];
@@ -1617,7 +1639,7 @@ __global__ void grad_kappa_kernel(int64_t n_rows, const SliceMeta *meta, const i
         if (lc & LEAF_FIBRE_START) {
             if (f >= 0) {
                 const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-                if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq]], -li * D);
+                if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq] + ws_stride(ws.a, fib_info[fq]) * inst], -li * D);
             }
             ++f;
             D = 0.0;
@@ -1627,7 +1649,7 @@ __global__ void grad_kappa_kernel(int64_t n_rows, const SliceMeta *meta, const i
     }
     if (f >= 0) {
         const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-        if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq]], -li * D);
+        if (((fib_info[fq] >> 24) & 0xF) != W_CONST) atomicAdd(&grad[fib_m[fq] + ws_stride(ws.a, fib_info[fq]) * inst], -li * D);
     }
 }
 
@@ -1838,7 +1860,10 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
     // FP64 operations: 2 per leaf (D and J1), per fibre the residual, diagonal and J2 scatter
     // (6; 12 when g is evaluated per fibre), 4 per reaction entry, 2 per local column, and
     // the nodal pass (interpolation and g, about 6 per node)
-    double csf_flops = L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10) + CE * 2 + (NWA + NWC) * 6;
+    // (a tensor shared by the ws.k instances of a batch is read once from DRAM but applied to
+    // every instance: its bytes count once, its operations ws.k times)
+    const double KS = h->ws.k > 0 ? double(h->ws.k) : 1.0;
+    double csf_flops = KS * (L * 4 + F * (NWA > 0 ? 6 : 12) + RX * (NWC > 0 ? 4 : 10)) + CE * 2 + (NWA + NWC) * 6;
     if (h->opts.op == EGFEM_OP_MATRIX_FREE) {
         // cell pass: S u in difference form (3 per off-diagonal pair), then per local W node
         // the interpolation, g and the c^K update (4 nv + 6; the gradient coefficient: 3 nv and
@@ -1868,7 +1893,7 @@ egfem_status profile_impl(egfem_t *h, KWork<V> &W, const double *d_u, const doub
         ta_name = "csf_mixed";
         csf_bytes = (NWA + NWC) * (1 + 12 + 2 * 16) + NWA * 8 + L * 13 + F * 8 + NWA * 16 + RX * 16 + NWC * 16 +
                     CE * (8 + 4) + N * (8 + 8 + 8 + 8 + 1) + SM;
-        csf_flops = L * 2 + F * 3 + RX * 4 + CE * 1 + (NWA + NWC) * 6;
+        csf_flops = KS * (L * 2 + F * 3 + RX * 4) + CE * 1 + (NWA + NWC) * 6;
     }
     EG_TRY(timeit(ta_name, csf_bytes, csf_flops, 1, [&] { launch_csf(h, A, h->hs); }));
     if (!std::is_same<V, double>::value)
@@ -1977,7 +2002,7 @@ egfem_status egfem_adjoint(egfem_handle h, const double *d_u, const double *d_dJ
         EG_CUDA(cudaMemsetAsync(d_grad_kappa, 0, size_t(h->nwa) * sizeof(double), h->hs));
         grad_kappa_kernel<<<unsigned((h->n + 255) / 256), 256, 0, h->hs>>>(h->n, h->csf.meta, h->csf.col_idx, h->csf.leaf_val,
                                                                           h->csf.leaf_col, h->csf.fib_info, h->csf.fib_m, h->csf.dir, d_u, d_lambda,
-                                                                          d_grad_kappa);
+                                                                          d_grad_kappa, h->ws);
         EG_CUDA(cudaGetLastError());
     }
     S.status = st;
@@ -2616,8 +2641,17 @@ egfem_status egfem_batch_build(int32_t count, const egfem_mesh *meshes, const eg
             for (int64_t v = 0; v < m.n_nodes; ++v) dir[size_t(off[b] + v)] = m.dirichlet ? (m.dirichlet[v] ? 1 : 0) : 0;
             for (int64_t c = 0; c < m.n_cells * (dim + 1); ++c) cells[size_t(coff[b] * (dim + 1) + c)] = int32_t(m.cells[c] + off[b]);
         }
+        // one mesh for every instance (byte for byte): the tensor can be stored once
+        bool same = count > 1;
+        for (int32_t b = 1; b < count && same; ++b) {
+            const egfem_mesh &m = meshes[b], &m0 = meshes[0];
+            same = m.n_nodes == m0.n_nodes && m.n_cells == m0.n_cells &&
+                   std::memcmp(&X[size_t(off[b]) * dim], &X[0], sizeof(double) * size_t(m.n_nodes) * dim) == 0 &&
+                   std::memcmp(&dir[size_t(off[b])], &dir[0], size_t(m.n_nodes)) == 0 &&
+                   std::memcmp(m.cells, m0.cells, sizeof(int32_t) * size_t(m.n_cells) * (dim + 1)) == 0;
+        }
         egfem_mesh U{dim, N, C, X.data(), cells.data(), dir.data()};
-        egfem_status st = build_impl(&U, prob, opts, out);
+        egfem_status st = build_impl(&U, prob, opts, out, same ? count : 0, same ? off[1] : 0);
         if (st != EGFEM_OK) return st;
         egfem_t *h = *out;
         h->nb = count;

@@ -575,6 +575,68 @@ egfem_status build_csf(const egfem_mesh &m, const egfem_problem &prob, const Hos
     return EGFEM_OK;
 }
 
+// A batch of k copies of one mesh (instance b owns the rows [b rows, (b + 1) rows), rows a
+// whole number of slices): when the slices of every instance hold instance 0's tensor entries,
+// with W indices that differ from instance 0's by b times one stride per node kind and space,
+// keep instance 0's leaves, fibres and reaction entries only, point every instance's slices at
+// them and return the strides in ws.  Otherwise return false and leave H as it was.  Local
+// columns, the Jacobian pattern and the per-row arrays stay per instance.
+bool share_tensor(HostCSF &H, int32_t k, int64_t rows, WShare &ws) {
+    if (k < 2 || rows <= 0 || rows % SLICE != 0 || H.n_rows != rows * k) return false;
+    const int64_t s0 = rows / SLICE;
+    int64_t sa[5] = {0, 0, 0, 0, 0}, sc[5] = {0, 0, 0, 0, 0};
+    bool ka[5] = {}, kc[5] = {};
+    // instance b's W index m against instance 0's m0 for a node of kind w: m - m0 = b stride[w]
+    auto stride_ok = [](int64_t *st, bool *known, uint32_t w, int64_t m, int64_t m0, int64_t b) {
+        if (w == W_CONST) return true;   // no W node (padding): its index is never read
+        const int64_t dm = m - m0;
+        if (!known[w]) {
+            if (dm % b != 0 || dm < 0) return false;
+            st[w] = dm / b;
+            known[w] = true;
+        }
+        return dm == b * st[w];
+    };
+    for (int64_t b = 1; b < k; ++b)
+        for (int64_t l = 0; l < s0; ++l) {
+            const SliceMeta &M = H.meta[size_t(b * s0 + l)], &M0 = H.meta[size_t(l)];
+            if (M.ncol != M0.ncol || M.nleaf != M0.nleaf || M.nfib != M0.nfib || M.nrx != M0.nrx) return false;
+            const size_t nl = size_t(M.nleaf) * SLICE, nf = size_t(M.nfib) * SLICE, nr = size_t(M.nrx) * SLICE;
+            if (std::memcmp(H.leaf_val.data() + M.leaf_base, H.leaf_val.data() + M0.leaf_base, nl * sizeof(double)) != 0 ||
+                std::memcmp(H.leaf_col.data() + M.leaf_base, H.leaf_col.data() + M0.leaf_base, nl) != 0 ||
+                std::memcmp(H.fib_info.data() + M.fib_base, H.fib_info.data() + M0.fib_base, nf * sizeof(uint32_t)) != 0 ||
+                std::memcmp(H.fib_tdiag.data() + M.fib_base, H.fib_tdiag.data() + M0.fib_base, nf * sizeof(double)) != 0 ||
+                std::memcmp(H.rx_val.data() + M.rx_base, H.rx_val.data() + M0.rx_base, nr * sizeof(double)) != 0 ||
+                std::memcmp(H.rx_info.data() + M.rx_base, H.rx_info.data() + M0.rx_base, nr * sizeof(uint32_t)) != 0)
+                return false;
+            for (size_t q = 0; q < nf; ++q)
+                if (!stride_ok(sa, ka, (H.fib_info[M.fib_base + q] >> 24) & 0xF, H.fib_m[M.fib_base + q],
+                               H.fib_m[M0.fib_base + q], b))
+                    return false;
+            for (size_t q = 0; q < nr; ++q)
+                if (!stride_ok(sc, kc, (H.rx_info[M.rx_base + q] >> 24) & 0xF, H.rx_m[M.rx_base + q], H.rx_m[M0.rx_base + q], b))
+                    return false;
+        }
+    // instance 0's entries come first (slices are stored in row order)
+    const SliceMeta E = H.meta[size_t(s0)];
+    H.leaf_val.resize(size_t(E.leaf_base)); H.leaf_col.resize(size_t(E.leaf_base));
+    H.fib_info.resize(size_t(E.fib_base)); H.fib_tdiag.resize(size_t(E.fib_base)); H.fib_m.resize(size_t(E.fib_base));
+    H.rx_val.resize(size_t(E.rx_base)); H.rx_info.resize(size_t(E.rx_base)); H.rx_m.resize(size_t(E.rx_base));
+    H.leaf_val.shrink_to_fit(); H.leaf_col.shrink_to_fit(); H.fib_info.shrink_to_fit(); H.fib_tdiag.shrink_to_fit();
+    H.fib_m.shrink_to_fit(); H.rx_val.shrink_to_fit(); H.rx_info.shrink_to_fit(); H.rx_m.shrink_to_fit();
+    for (size_t s = size_t(s0); s < H.meta.size(); ++s) {
+        const SliceMeta &M0 = H.meta[s % size_t(s0)];
+        H.meta[s].leaf_base = M0.leaf_base;
+        H.meta[s].fib_base = M0.fib_base;
+        H.meta[s].rx_base = M0.rx_base;
+    }
+    ws = WShare{};
+    ws.k = k;
+    ws.rows = rows;
+    for (int w = 0; w < 5; ++w) { ws.a[w] = sa[w]; ws.c[w] = sc[w]; }
+    return true;
+}
+
 }  // namespace egfem
 
 // Host-only reconstruction of the stored tensor (see egfem_inspect_tensor in egfem.h).

@@ -108,6 +108,16 @@ struct DeviceCSF {
     int64_t n_colentries = 0, n_leaves = 0, n_fibres = 0, n_rx = 0, nnz = 0;
 };
 
+// A batch whose instances all use one mesh, stored with one copy of the tensor (k > 0): instance
+// b owns rows [b rows, (b + 1) rows); every instance's slices point at instance 0's leaves,
+// fibres and reaction entries, whose W indices are instance 0's: instance b's W index of a
+// node of kind w (WKind) is that plus b a[w] (coefficient space) or b c[w] (reaction space).
+struct WShare {
+    int32_t k;
+    int64_t rows;
+    int64_t a[5], c[5];
+};
+
 // Problem constants passed by value to the kernels.
 struct Nonlin {
     int32_t a_kind; int32_t a_pi; double a_scale;
@@ -127,6 +137,7 @@ egfem_status build_csf(const egfem_mesh &mesh, const egfem_problem &prob, const 
                        const std::vector<int32_t> &cell2wa, int nloc_a, const HostWSpace &Wc,
                        const std::vector<int32_t> &cell2wc, int nloc_c, HostCSF &out, std::string &err);
 egfem_status validate_mesh(const egfem_mesh &mesh, std::string &err);
+bool share_tensor(HostCSF &H, int32_t k, int64_t rows, WShare &ws);
 double basis_integral(int dim, int degree, int kind);   // int_K eta_m / |K| by node kind
 void cell_stiffness(const egfem_mesh &mesh, std::vector<double> &vol, std::vector<double> *S);
 std::vector<double> cell_centroids(const egfem_mesh &mesh);

@@ -53,6 +53,7 @@ struct CsfArgs {
     const float *leaf_val32;           // FP32 copy of leaf_val (csf_mixed_kernel)
     const int32_t *slice_inst;   // batch: instance of each slice (nullable)
     const uint8_t *inst_mask;    // batch: rows of instances with mask 0 are skipped (nullable)
+    WShare ws;                   // one tensor for a batch of one mesh (ws.k > 0), else ws.k = 0
     int32_t *status;       // error word (singular diagonal)
 };
 
@@ -81,6 +82,37 @@ __device__ __forceinline__ double interp_du(uint32_t info, const double *du, int
     if (kind == W_THIRD) return (2.0 * d0 + d1) * (1.0 / 3.0);
     const double d2 = du[((info >> 16) & 0xFF) * stride];
     return (d0 + d1 + d2) * (1.0 / 3.0);
+}
+
+// The row of this thread, and its instance in a batch of one shared mesh (else 0): with a
+// shared tensor the blocks take the instances in turn for each range of local rows, so the
+// instances that read the same part of the tensor do so close together (from L2).  -1 past the
+// end.
+template <int BLK>
+__device__ __forceinline__ int64_t csf_row(const CsfArgs &A, int32_t &inst) {
+    if (A.ws.k > 0) {
+        const int32_t lb = int32_t(blockIdx.x) / A.ws.k, b = int32_t(blockIdx.x) % A.ws.k;
+        const int64_t lr = int64_t(lb) * BLK + threadIdx.x;
+        inst = b;
+        return lr < A.ws.rows ? int64_t(b) * A.ws.rows + lr : -1;
+    }
+    inst = 0;
+    return int64_t(blockIdx.x) * BLK + threadIdx.x;
+}
+
+// The stride of a node kind, chosen with selects (an indexed read of a kernel argument would
+// copy the argument to local memory)
+__device__ __forceinline__ int64_t ws_stride(const int64_t (&st)[5], uint32_t info) {
+    const uint32_t w = (info >> 24) & 0xF;
+    return w == W_VERTEX ? st[W_VERTEX] : w == W_MID ? st[W_MID] : w == W_THIRD ? st[W_THIRD] : w == W_FACE ? st[W_FACE] : 0;
+}
+
+// W index of a fibre's node (coefficient space) or a reaction entry's node, for the row's instance
+__device__ __forceinline__ int64_t wa_index(const CsfArgs &A, int32_t m, uint32_t info, int32_t inst) {
+    return A.ws.k > 0 ? int64_t(m) + ws_stride(A.ws.a, info) * int64_t(inst) : int64_t(m);
+}
+__device__ __forceinline__ int64_t wc_index(const CsfArgs &A, int32_t m, uint32_t info, int32_t inst) {
+    return A.ws.k > 0 ? int64_t(m) + ws_stride(A.ws.c, info) * int64_t(inst) : int64_t(m);
 }
 
 // J_{i, c_t} += e * w_t  (the Pi_ml factor of the eliminated Jacobian, Sec. 4)
@@ -147,8 +179,9 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
     __shared__ double s_du[MAXC * BLK];
     __shared__ double s_J[MAXC * BLK];   // FP64 entries, or double-float pairs (JDF)
     const int tid = threadIdx.x;
-    const int64_t row = int64_t(blockIdx.x) * BLK + tid;
-    if (row >= A.n_rows) return;
+    int32_t inst;
+    const int64_t row = csf_row<BLK>(A, inst);
+    if (row < 0 || row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     const int lane = int(row % SLICE);
     if (A.inst_mask && !A.inst_mask[A.slice_inst[sl]]) return;
@@ -209,14 +242,14 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
                 a = nl.kappa;
                 gp = 0.0;
             } else if (A.wa_val) {
-                const int32_t m = __ldg(A.fib_m + fq);
+                const int64_t m = wa_index(A, __ldg(A.fib_m + fq), info, inst);
                 a = A.wa_val[m];
                 gp = A.wa_gp[m];
             } else {
                 const double pu = ui + interp_du(info, du, BLK);
                 double w;
                 g_eval(nl.a_kind, nl.a_pi, nl.a_scale, pu, w, gp);
-                a = (nl.kappa_field ? nl.kappa_field[A.fib_m[fq]] : nl.kappa) + w;
+                a = (nl.kappa_field ? nl.kappa_field[wa_index(A, A.fib_m[fq], info, inst)] : nl.kappa) + w;
             }
             if constexpr (JDF) {
                 a_df = split_dbl(a, 0);
@@ -248,7 +281,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
         const uint32_t xi = A.rx_info[q];
         double cv, cp;
         if (A.wc_val) {
-            const int32_t m = A.rx_m[q];
+            const int64_t m = wc_index(A, A.rx_m[q], xi, inst);
             cv = A.wc_val[m];
             cp = A.wc_gp[m];
         } else {
@@ -308,8 +341,9 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A)
     __shared__ float s_du32[MAXC * BLK];
     __shared__ float s_J[MAXC * BLK];
     const int tid = threadIdx.x;
-    const int64_t row = int64_t(blockIdx.x) * BLK + tid;
-    if (row >= A.n_rows) return;
+    int32_t inst;
+    const int64_t row = csf_row<BLK>(A, inst);
+    if (row < 0 || row >= A.n_rows) return;
     const int64_t sl = row / SLICE;
     const int lane = int(row % SLICE);
     if (A.inst_mask && !A.inst_mask[A.slice_inst[sl]]) return;
@@ -367,7 +401,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A)
                 a32 = float(nl.kappa);
                 gp32 = 0.0f;
             } else {
-                const int32_t m = __ldg(A.fib_m + fq);
+                const int64_t m = wa_index(A, __ldg(A.fib_m + fq), info, inst);
                 a = A.wa_val[m];
                 a32 = A.wa_val32[m];
                 gp32 = A.wa_gp32[m];
@@ -398,7 +432,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A)
         const int64_t q = M.rx_base + int64_t(j) * SLICE + lane;
         const double mv = A.rx_val[q];
         if (mv == 0.0) continue;
-        const int32_t m = A.rx_m[q];
+        const int64_t m = wc_index(A, A.rx_m[q], A.rx_info[q], inst);
         r += nl.gamma * mv * A.wc_val[m];
         if (!nl.picard) {
             const float e = float(nl.gamma * mv * A.wc_gp[m]);

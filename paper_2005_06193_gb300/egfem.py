@@ -54,7 +54,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("op", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
                 ("fixed_eta", ctypes.c_int32), ("krylov_persistent", ctypes.c_int32), ("iteration", ctypes.c_int32),
                 ("krylov_block_rows", ctypes.c_int32), ("krylov_cluster", ctypes.c_int32),
-                ("newton_graph", ctypes.c_int32)]
+                ("newton_graph", ctypes.c_int32), ("batch_share", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         "egfem_set_options": (S, [_P, ctypes.POINTER(Options)]),
         "egfem_sizes": (S, [_P] + [ctypes.POINTER(ctypes.c_int64)] * 5),
         "egfem_w_coords": (S, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+        "egfem_tensor_storage": (S, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
         "egfem_jacobian_pattern": (S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
         "egfem_set_kappa": (S, [_P, _DP, _P]),
         "egfem_pointwise": (S, [_P, _DP, _DP, _DP, _P]),
@@ -271,6 +272,12 @@ class Handle:
             pass
 
     # --- inspection ---
+    def tensor_storage(self):
+        """(device bytes of the stored tensor and reaction entries, instances sharing them or 0)"""
+        b, k = ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(lib().egfem_tensor_storage(self._h, ctypes.byref(b), ctypes.byref(k)), "egfem_tensor_storage")
+        return b.value, k.value
+
     def w_coords(self, which=0) -> np.ndarray:
         n = self.sizes.n_wa if which == 0 else self.sizes.n_wc
         out = np.empty((n, self.dim))
