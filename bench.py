@@ -320,6 +320,29 @@ def profile_batch(torch, P, dev, count=16):
     return out
 
 
+def profile_adjbatch(torch, P, dev, count=16, n=512):
+    """One batched Newton step (host loop, exactly 40 BiCGStab iterations: a fixed forcing term of
+    1e-14) on `count` instances of the n x n P1/P2 u^2 problem on ONE mesh (the adjoint workload's
+    layout: the tensor stored once for all instances), with seeded random loads, twice; the second
+    call's batched solve is the one to capture (ncu -s 1 -c 1 on pkwb_solve)."""
+    import workloads as wl
+    mesh = wl.unit_square_mesh(n)
+    prob = P.make_problem(a=("pow", 2), a_degree=2)
+    hb = P.BatchHandle([mesh] * count, prob, P.default_options(
+        precision=P.PREC_MIXED, newton_graph=0, newton_maxit=1, newton_rtol=0.9, krylov_maxit=40, fixed_eta=1,
+        eta_max=1e-14))
+    free = 1 - mesh.dirichlet
+    d = hb.scatter([wl.random_vector(mesh.n_nodes, 3 + b, 1.0) * free for b in range(count)])
+    for _ in range(2):
+        u = torch.zeros_like(d)
+        st = hb.batch_newton_solve(u, d, check=False)
+        torch.cuda.synchronize()
+    out = {"instances": count, "rows": int(hb.sizes.n_nodes), "tensor_storage": hb.tensor_storage(),
+           "krylov_iters": [int(s.krylov_iters) for s in st][:4]}
+    hb.close()
+    return out
+
+
 def profile_p3batch(torch, P, dev, count):
     """The batched mixed Newton solve of `count` P3 instances (the default 256) with the host
     Newton loop, so that every kernel is a top-level launch (for an ncu launch list): a warm
@@ -636,7 +659,7 @@ def main():
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=2935)
     ap.add_argument("--profile-only", default=None,
-                    choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch"],
+                    choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch", "adjbatch"],
                     help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
                          "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
@@ -664,6 +687,9 @@ def main():
 
     if args.profile_only == "batch":
         print(json.dumps(profile_batch(torch, P, torch.device("cuda", local))), flush=True)
+        return
+    if args.profile_only == "adjbatch":
+        print(json.dumps(profile_adjbatch(torch, P, torch.device("cuda", local))), flush=True)
         return
     if args.profile_only == "p3batch":
         print(json.dumps(profile_p3batch(torch, P, torch.device("cuda", local), args.p3_instances)), flush=True)

@@ -20,6 +20,13 @@ constexpr int CSF_BLOCK = 128;
 // Threads per block of the row kernels for MAXC local columns: their per-thread shared arrays
 // (up to 16 B per column) keep to 32 KB, below the 48 KB static limit.
 template <int MAXC> __host__ __device__ constexpr int csf_block() { return MAXC <= 16 ? CSF_BLOCK : 2048 / MAXC; }
+// Resident blocks per SM that the tensor-action kernels are compiled for.  Their per-row fibre
+// chains wait on dependent gathers (fibre index, then the W node's nodal values), so more
+// resident warps hide more of that latency: for up to 8 local columns (2D P1 rows, 16 KB of
+// shared memory per block) twelve blocks, which caps the registers at 40 and measured about 5 %
+// faster than the compiler's choice of 56-63 registers (nine blocks) at 1024^2 in FP64 and
+// mixed precision; ten or fourteen blocks were slower.  Wider rows keep the compiler's choice.
+template <int MAXC> __host__ __device__ constexpr int csf_min_blocks() { return MAXC <= 8 ? 12 : 1; }
 
 struct CsfArgs {
     int64_t n_rows;
@@ -174,7 +181,7 @@ __device__ __forceinline__ void scatter_pi_df(uint32_t info, df64 e, df64 *J, in
 // Newton steps' operator (the Jacobian only steers the Newton direction, the residual is exact
 // FP64), while egfem_jacobian and the adjoint use the FP64 accumulation.
 template <int MAXC, bool JDF>
-__global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A) {
+__global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf_fused_kernel(CsfArgs A) {
     constexpr int BLK = csf_block<MAXC>();
     __shared__ double s_du[MAXC * BLK];
     __shared__ double s_J[MAXC * BLK];   // FP64 entries, or double-float pairs (JDF)
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(csf_block<MAXC>()) csf_fused_kernel(CsfArgs A)
 // per leaf and one per fibre.  Needs wa_val/wa_val32 (or a constant coefficient), wc_val for
 // a reaction, leaf_val32, r, q64 and a32.
 template <int MAXC>
-__global__ void __launch_bounds__(csf_block<MAXC>()) csf_mixed_kernel(CsfArgs A) {
+__global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf_mixed_kernel(CsfArgs A) {
     constexpr int BLK = csf_block<MAXC>();
     __shared__ double s_du[MAXC * BLK];
     __shared__ float s_du32[MAXC * BLK];
