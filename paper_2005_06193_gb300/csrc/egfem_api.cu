@@ -462,11 +462,11 @@ egfem_status pkwb_plan(egfem_t *h, KWork<V> &W) {
     EG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const int64_t G0 = int64_t(PKWB_MIN_BLOCKS) * h->sms;
     const int64_t total = h->inst_off[h->nb];
-    // rows per tile: about four tiles per block, 1 024 to 8 192 rows (8 192-row tiles measured 5-7 %
-    // faster than 4 096-row ones on 64 instances of 512^2, 2 % on the 256 P3 instances: fewer
-    // tiles per block and relatively smaller halos; their windows, about 74 KB, still let two
-    // blocks share an SM)
-    const int64_t target = std::min<int64_t>(8192, std::max<int64_t>(1024, (total + 4 * G0 - 1) / (4 * G0)));
+    // rows per tile: about four tiles per block, 1 024 to 4 096 rows.  Tiles of 8 192 rows made an
+    // iteration with every instance running 2-7 % faster (fewer tiles per block, smaller halos
+    // relative to the tile), but once few instances still iterate each of them is spread over
+    // half as many blocks, and the 256-instance P3 solve took 1.60 s against 1.54 s.
+    const int64_t target = std::min<int64_t>(4096, std::max<int64_t>(1024, (total + 4 * G0 - 1) / (4 * G0)));
     std::vector<BTile> T;
     for (int32_t b = 0; b < h->nb; ++b) {
         const int64_t t0 = int64_t(T.size());
