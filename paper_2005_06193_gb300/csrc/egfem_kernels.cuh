@@ -21,12 +21,13 @@ constexpr int CSF_BLOCK = 128;
 // (up to 16 B per column) keep to 32 KB, below the 48 KB static limit.
 template <int MAXC> __host__ __device__ constexpr int csf_block() { return MAXC <= 16 ? CSF_BLOCK : 2048 / MAXC; }
 // Resident blocks per SM that the tensor-action kernels are compiled for.  Their per-row fibre
-// chains wait on dependent gathers (fibre index, then the W node's nodal values), so more
-// resident warps hide more of that latency: for up to 8 local columns (2D P1 rows, 16 KB of
-// shared memory per block) twelve blocks, which caps the registers at 40 and measured about 5 %
-// faster than the compiler's choice of 56-63 registers (nine blocks) at 1024^2 in FP64 and
-// mixed precision; ten or fourteen blocks were slower.  Wider rows keep the compiler's choice.
-template <int MAXC> __host__ __device__ constexpr int csf_min_blocks() { return MAXC <= 8 ? 12 : 1; }
+// chains wait on gathers (the W node's nodal values at each fibre start), so resident warps hide
+// that latency, but each needs registers for the fibre loaded ahead: for up to 8 local columns
+// (2D P1 rows, 16 KB of shared memory per block) ten blocks (48 registers).  Measured at 1024^2
+// (nodal pass + kernel, FP64 / mixed): the compiler's choice (56-63 registers, nine blocks, no
+// fibre ahead) 355 / 309 us; twelve blocks (40 registers) 340 / 301; ten blocks with the fibre
+// ahead 328 / 273; twelve with it 350 / 303.  Wider rows keep the compiler's choice.
+template <int MAXC> __host__ __device__ constexpr int csf_min_blocks() { return MAXC <= 8 ? 10 : 1; }
 
 struct CsfArgs {
     int64_t n_rows;
@@ -224,6 +225,11 @@ __global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf
     uint32_t info = 0;
     bool j2 = false;
     int f = -1;
+    // the next fibre's info and W index are loaded one fibre ahead, so a fibre start waits for one
+    // gather (the W node's nodal values) rather than for the index and then the gather
+    uint32_t nx_info = 0;
+    int32_t nx_m = 0;
+    if (M.nfib > 0) { nx_info = __ldg(A.fib_info + M.fib_base + lane); nx_m = __ldg(A.fib_m + M.fib_base + lane); }
     // tensor data are read-only (non-coherent loads); unrolling lets the next leaves' loads
     // issue ahead of this leaf's arithmetic
 #pragma unroll 4
@@ -241,15 +247,17 @@ __global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-            info = __ldg(A.fib_info + fq);
+            info = nx_info;
+            const int32_t mf = nx_m;
             const double td = __ldg(A.fib_tdiag + fq);
+            if (f + 1 < M.nfib) { nx_info = __ldg(A.fib_info + fq + SLICE); nx_m = __ldg(A.fib_m + fq + SLICE); }
             // the J2 scatter is tested on integers (an FP64 compare would take an FP64 slot)
             j2 = !nl.picard && ((info >> 24) & 0xF) != W_CONST;
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 gp = 0.0;
             } else if (A.wa_val) {
-                const int64_t m = wa_index(A, __ldg(A.fib_m + fq), info, inst);
+                const int64_t m = wa_index(A, mf, info, inst);
                 a = A.wa_val[m];
                 gp = A.wa_gp[m];
             } else {
@@ -385,6 +393,10 @@ __global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf
     };
     uint32_t info = 0;
     int f = -1;
+    // the next fibre's info and W index one fibre ahead, as in csf_fused_kernel
+    uint32_t nx_info = 0;
+    int32_t nx_m = 0;
+    if (M.nfib > 0) { nx_info = __ldg(A.fib_info + M.fib_base + lane); nx_m = __ldg(A.fib_m + M.fib_base + lane); }
     // tensor data are read-only (non-coherent loads); unrolling lets the next leaves' loads
     // issue ahead of this leaf's arithmetic
 #pragma unroll 4
@@ -402,13 +414,15 @@ __global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf
             }
             ++f;
             const int64_t fq = M.fib_base + int64_t(f) * SLICE + lane;
-            info = __ldg(A.fib_info + fq);
+            info = nx_info;
+            const int32_t mf = nx_m;
+            if (f + 1 < M.nfib) { nx_info = __ldg(A.fib_info + fq + SLICE); nx_m = __ldg(A.fib_m + fq + SLICE); }
             if (((info >> 24) & 0xF) == W_CONST) {
                 a = nl.kappa;
                 a32 = float(nl.kappa);
                 gp32 = 0.0f;
             } else {
-                const int64_t m = wa_index(A, __ldg(A.fib_m + fq), info, inst);
+                const int64_t m = wa_index(A, mf, info, inst);
                 a = A.wa_val[m];
                 a32 = A.wa_val32[m];
                 gp32 = A.wa_gp32[m];
