@@ -12,6 +12,8 @@
 #include <stdint.h>
 
 #include "egfem_df64.cuh"
+#include <climits>
+
 #include "egfem_internal.h"
 
 namespace egfem {
@@ -481,12 +483,35 @@ __global__ void __launch_bounds__(csf_block<MAXC>(), csf_min_blocks<MAXC>()) csf
     A.a32[M.col_base + lane] = dinv * (rs_hi + rs_lo);
 }
 
+// The exponent e when x = 2^e exactly (a positive normal number with an empty significand), else
+// INT_MIN
+__device__ __forceinline__ int pow2_exponent(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = int((b >> 52) & 0x7ffu);
+    return ((b & 0x000fffffffffffffull) == 0ull && ex != 0 && ex != 0x7ff && (b >> 63) == 0ull) ? ex - 1023 : INT_MIN;
+}
+
+// f x for f = 2^e (e = pow2_exponent(f), INT_MIN when f is no power of two): an exponent shift on
+// the integer pipe when x is a normal number and the product stays normal, else one FP64
+// multiplication.  Both give the same bits (the product by a power of two is exact there).
+__device__ __forceinline__ double mul_pow2(double x, double f, int e) {
+    if (e != INT_MIN) {
+        const long long b = __double_as_longlong(x);
+        const int ex = int((b >> 52) & 0x7ff);
+        if (ex != 0 && ex != 0x7ff && ex + e >= 1 && ex + e <= 0x7fe)
+            return __longlong_as_double(b + (static_cast<long long>(e) << 52));
+    }
+    return f * x;
+}
+
 // Nodal values of one nonlinearity on its W space (Sec. 3.1 eq. (5), Sec. 3.2), one thread
 // per W node, each node evaluated once: val_m = base_m + g((Pi u)_m), gp_m = g'((Pi u)_m),
 // with base = kappa (constant, or the field when base_field is set) for the coefficient
 // space and 0 for the reaction space.  Every FP64 operation costs a slot of GB300's narrow
 // FP64 pipe, so the integer power is written with few: t = s^(p-1), gp = (scale p) t with
-// scale p from the host, val = base + (scale t) s.
+// scale p from the host, val = base + (scale t) s; products by powers of two (the midpoint's
+// 1/2, and scale or scale p when they are such, e.g. 1 and 2 for w = u^2) are exponent shifts
+// on the integer pipe with the same bits (mul_pow2).
 __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *kind, const int32_t *sup, const double *u,
                                                     int32_t g_kind, int32_t g_p, double g_scale, double g_scale_p,
                                                     double base, const double *base_field, double *val, double *gp,
@@ -497,7 +522,7 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
     const double u0 = u[sup[3 * m]];
     double pu;
     if (k == W_VERTEX) pu = u0;
-    else if (k == W_MID) pu = 0.5 * (u0 + u[sup[3 * m + 1]]);
+    else if (k == W_MID) pu = mul_pow2(u0 + u[sup[3 * m + 1]], 0.5, -1);
     else if (k == W_THIRD) pu = fma(2.0, u0, u[sup[3 * m + 1]]) * (1.0 / 3.0);
     else pu = (u0 + u[sup[3 * m + 1]] + u[sup[3 * m + 2]]) * (1.0 / 3.0);
     const double b0 = base_field ? base_field[m] : base;
@@ -506,8 +531,9 @@ __global__ void __launch_bounds__(256) wnode_kernel(int64_t n_w, const uint8_t *
         double t = 1.0;                       // pu^(p-1)
         if (g_p >= 2) t = pu;
         for (int32_t k = 2; k < g_p; ++k) t *= pu;
-        d = g_p == 1 ? g_scale : g_scale_p * t;
-        v = b0 + (g_scale * t) * pu;   // this rounding order: the Krylov iteration counts follow a's last bit
+        d = g_p == 1 ? g_scale : mul_pow2(t, g_scale_p, pow2_exponent(g_scale_p));
+        const double st = mul_pow2(t, g_scale, pow2_exponent(g_scale));
+        v = b0 + st * pu;   // this rounding order: the Krylov iteration counts follow a's last bit
     } else {
         double g;
         g_eval(g_kind, g_p, g_scale, pu, g, d);
