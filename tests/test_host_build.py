@@ -241,3 +241,48 @@ def test_default_options_leave_the_choices_to_the_library(egf):
     # keyword overrides reach the structure
     o2 = egf.default_options(eta_max=0.3, iteration=egf.ITER_PICARD)
     assert o2.eta_max == 0.3 and o2.iteration == egf.ITER_PICARD
+
+
+def _union(mesh, k):
+    """k copies of one mesh laid out as a batch lays out its instances: each copy's nodes padded to
+    whole 32-row slices with isolated Dirichlet nodes (no cells)."""
+    rows = -(-mesh.n_nodes // 32) * 32
+    X = np.zeros((k * rows, mesh.dim))
+    cells = np.concatenate([mesh.cells + b * rows for b in range(k)]).astype(np.int32)
+    dirichlet = np.ones(k * rows, dtype=np.uint8)
+    for b in range(k):
+        X[b * rows:b * rows + mesh.n_nodes] = mesh.coords
+        dirichlet[b * rows:b * rows + mesh.n_nodes] = mesh.dirichlet
+    return wl.Mesh(mesh.dim, X, cells, dirichlet), rows
+
+
+@pytest.mark.parametrize("dim,n,deg", [(2, 7, 2), (2, 6, 3), (3, 2, 2)])
+def test_union_of_one_mesh_is_instance_affine(egf, dim, n, deg):
+    """The premise of the shared-tensor batch: in the disjoint union of k copies of one mesh, copy
+    b's stored tensor is copy 0's, entry by entry in stored order, with rows and columns shifted by
+    b x (padded rows) and every W index shifted by b times one stride per node kind (the W nodes
+    are numbered kind by kind, copy after copy inside each kind)."""
+    mesh = wl.unit_square_mesh(n) if dim == 2 else wl.unit_cube_mesh(n)
+    k = 3
+    U, rows = _union(mesh, k)
+    I, M, K, V, W = egf.inspect_tensor(U, egf.make_problem(a=("pow", 2), a_degree=deg))
+    grp = [np.flatnonzero((I >= b * rows) & (I < (b + 1) * rows)) for b in range(k)]
+    assert len(grp[0]) > 0 and all(len(g) == len(grp[0]) for g in grp)
+    i0, m0, k0, v0 = I[grp[0]], M[grp[0]], K[grp[0]], V[grp[0]]
+    strides = set()
+    for b in range(1, k):
+        g = grp[b]
+        assert np.array_equal(I[g] - b * rows, i0)
+        assert np.array_equal(K[g] - b * rows, k0)
+        assert np.array_equal(V[g], v0)   # the same tensor values, bit for bit
+        assert np.array_equal(M[g] < 0, m0 < 0)
+        w = m0 >= 0
+        dm = M[g][w] - m0[w]
+        assert np.all(dm % b == 0)
+        assert np.array_equal(W[M[g][w]], W[m0[w]])   # the same W node of the copy
+        strides.add(tuple(sorted(set((dm // b).tolist()))))
+    # one stride per node kind that the tensor holds, the same for every copy: on triangles the P2
+    # vertex functions integrate to zero, so T holds edge nodes only (one stride); P3 on triangles
+    # and P2 on tetrahedra hold vertices too (and P3 face nodes)
+    assert len(strides) == 1
+    assert len(next(iter(strides))) == {(2, 2): 1, (2, 3): 3, (3, 2): 2}[(dim, deg)]
