@@ -187,3 +187,32 @@ def test_shared_tensor_profile_counts_bytes_once(P):
     assert pu["csf_fused"]["bytes"] - ps["csf_fused"]["bytes"] == pytest.approx((K - 1) * bs, rel=1e-12)
     hs.close()
     hu.close()
+
+
+@pytest.mark.parametrize("n,k", [(4, 3), (4, 40), (9, 17)])
+def test_shared_tensor_small_instances_many_copies(P, n, k):
+    """Instances of one slice (a 4 x 4 grid: 25 nodes in 32 rows) and many copies: the tensor
+    action's blocks then cover fewer rows than a block holds and take the instances in turn; the
+    residual and Jacobian still equal those of the per-instance copies bit for bit and the oracle's
+    per instance."""
+    mesh = wl.unit_square_mesh(n)
+    prob = P.make_problem(a=("pow", 3), a_degree=3)
+    hs = P.BatchHandle([mesh] * k, prob, P.default_options())
+    hu = P.BatchHandle([mesh] * k, prob, P.default_options(batch_share=0))
+    assert hs.tensor_storage()[1] == k and hu.tensor_storage()[1] == 0
+    free = 1 - mesh.dirichlet
+    us = [wl.random_vector(mesh.n_nodes, 100 + b, 0.6) * free for b in range(k)]
+    ds = [wl.random_vector(mesh.n_nodes, 300 + b, 1.0) * free for b in range(k)]
+    u, d = hs.scatter(us), hs.scatter(ds)
+    r_s, r_u = torch.empty_like(u), torch.empty_like(u)
+    hs.residual(u, d, r_s)
+    hu.residual(u, d, r_u)
+    torch.cuda.synchronize()
+    assert torch.equal(r_s, r_u)
+    assert torch.equal(_jacobian(hs, u), _jacobian(hu, u))
+    orc = oracle.Problem(mesh, a=("pow", 3.0), a_deg=3)
+    rs = hs.gather(r_s, [mesh.n_nodes] * k)
+    for b in (0, k // 2, k - 1):
+        assert rel(rs[b], orc.residual(us[b], ds[b])) <= 1e-12, b
+    hs.close()
+    hu.close()
