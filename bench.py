@@ -343,6 +343,34 @@ def profile_adjbatch(torch, P, dev, count=16, n=512):
     return out
 
 
+def profile_adjoint64(torch, P, dev, count, n):
+    """The batched half of the adjoint workload (count instances of the n x n P1/P2 u^2 problem on
+    one mesh, 16 x 16 cellwise theta, j = 0.5 ||u - u_d||^2): the batched mixed Newton solve and the
+    block-diagonal adjoint through autograd, a warm pass and one more (for an ncu launch list)."""
+    import workloads as wl
+    from paper_2005_06193_gb300 import autograd as ag
+    mesh = wl.unit_square_mesh(n)
+    pc = torch.tensor(wl.param_cell_of_cells(mesh, 16), device=dev, dtype=torch.int64)
+    ud = torch.tensor(wl.adjoint_target()(mesh.coords[:, 0], mesh.coords[:, 1]), device=dev)
+    free = torch.tensor(1.0 - mesh.dirichlet, device=dev)
+    thetas = [torch.tensor(wl.adjoint_theta(b), device=dev) for b in range(count)]
+    hb = P.BatchHandle([mesh] * count, P.make_problem(a=("pow", 2), a_degree=2),
+                       P.default_options(precision=P.PREC_MIXED, newton_graph=0))
+    off = hb.offsets
+    for _ in range(2):
+        ts = [th.clone().requires_grad_(True) for th in thetas]
+        d = ag.load_cellwise(torch.cat([t.reshape(-1)[pc] for t in ts]), hb)
+        u = ag.newton_solve(d, None, hb)
+        J = sum(0.5 * torch.sum(((u[off[b]:off[b] + mesh.n_nodes] - ud) * free) ** 2) for b in range(count))
+        t0 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+    out = {"instances": count, "rows": int(hb.sizes.n_nodes), "tensor_storage": hb.tensor_storage(),
+           "backward_s": time.perf_counter() - t0}
+    hb.close()
+    return out
+
+
 def profile_p3batch(torch, P, dev, count):
     """The batched mixed Newton solve of `count` P3 instances (the default 256) with the host
     Newton loop, so that every kernel is a top-level launch (for an ncu launch list): a warm
@@ -659,7 +687,8 @@ def main():
     ap.add_argument("--ref-newton-steps", type=int, default=7)
     ap.add_argument("--ref-krylov-iters", type=int, default=2935)
     ap.add_argument("--profile-only", default=None,
-                    choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch", "adjbatch"],
+                    choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch", "adjbatch",
+                             "adjoint64"],
                     help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
                          "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
@@ -690,6 +719,10 @@ def main():
         return
     if args.profile_only == "adjbatch":
         print(json.dumps(profile_adjbatch(torch, P, torch.device("cuda", local))), flush=True)
+        return
+    if args.profile_only == "adjoint64":
+        print(json.dumps(profile_adjoint64(torch, P, torch.device("cuda", local), args.batch_instances, args.batch_n)),
+              flush=True)
         return
     if args.profile_only == "p3batch":
         print(json.dumps(profile_p3batch(torch, P, torch.device("cuda", local), args.p3_instances)), flush=True)
