@@ -320,17 +320,17 @@ def profile_batch(torch, P, dev, count=16):
     return out
 
 
-def profile_adjbatch(torch, P, dev, count=16, n=512):
+def profile_adjbatch(torch, P, dev, count=16, n=512, fp64=False):
     """One batched Newton step (host loop, exactly 40 BiCGStab iterations: a fixed forcing term of
-    1e-14) on `count` instances of the n x n P1/P2 u^2 problem on ONE mesh (the adjoint workload's
+    1e-14; mixed precision, or FP64 with fp64) on `count` instances of the n x n P1/P2 u^2 problem on ONE mesh (the adjoint workload's
     layout: the tensor stored once for all instances), with seeded random loads, twice; the second
     call's batched solve is the one to capture (ncu -s 1 -c 1 on pkwb_solve)."""
     import workloads as wl
     mesh = wl.unit_square_mesh(n)
     prob = P.make_problem(a=("pow", 2), a_degree=2)
     hb = P.BatchHandle([mesh] * count, prob, P.default_options(
-        precision=P.PREC_MIXED, newton_graph=0, newton_maxit=1, newton_rtol=0.9, krylov_maxit=40, fixed_eta=1,
-        eta_max=1e-14))
+        precision=P.PREC_FP64 if fp64 else P.PREC_MIXED, newton_graph=0, newton_maxit=1, newton_rtol=0.9,
+        krylov_maxit=40, fixed_eta=1, eta_max=1e-14))
     free = 1 - mesh.dirichlet
     d = hb.scatter([wl.random_vector(mesh.n_nodes, 3 + b, 1.0) * free for b in range(count)])
     for _ in range(2):
@@ -688,7 +688,7 @@ def main():
     ap.add_argument("--ref-krylov-iters", type=int, default=2935)
     ap.add_argument("--profile-only", default=None,
                     choices=["fp64", "mixed", "gradient", "quadrature", "supercond", "batch", "p3batch", "adjbatch",
-                             "adjoint64"],
+                             "adjbatch64", "adjoint64"],
                     help="build the workload (gradient: minimal surface; quadrature: quadratic example with I_3), "
                          "run the per-kernel profile once and print it (for ncu captures)")
     args = ap.parse_args()
@@ -717,8 +717,9 @@ def main():
     if args.profile_only == "batch":
         print(json.dumps(profile_batch(torch, P, torch.device("cuda", local))), flush=True)
         return
-    if args.profile_only == "adjbatch":
-        print(json.dumps(profile_adjbatch(torch, P, torch.device("cuda", local))), flush=True)
+    if args.profile_only in ("adjbatch", "adjbatch64"):
+        print(json.dumps(profile_adjbatch(torch, P, torch.device("cuda", local), fp64=args.profile_only == "adjbatch64")),
+              flush=True)
         return
     if args.profile_only == "adjoint64":
         print(json.dumps(profile_adjoint64(torch, P, torch.device("cuda", local), args.batch_instances, args.batch_n)),
